@@ -1,0 +1,186 @@
+"""CPU oracle -- test infrastructure only.
+
+ctypes binding of oracle.c (plain C, built with gcc).  Only the tests,
+the smoke check and the benchmark's CPU-baseline leg may import this
+package; the routing library never does.  It shares no code with the
+CUDA path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "liboracle.so")
+
+INF = 2**31 - 1
+MAX_K = 12
+LEG_MAX = 10324440
+OK, UNREACHABLE, BADORDER, RANGE = 0, 1, 2, 3
+SSSP = {"rounds": 0, "fifo": 1, "dijkstra": 2}
+TOUR = {"brute": 0, "heldkarp": 1}
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    src = os.path.join(HERE, "oracle.c")
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(HERE, "oracle.h"))):
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-o", tmp, src,
+                               "-lpthread"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def _configure(L):
+    P = ctypes.c_void_p
+    i32, i64, I = ctypes.c_int32, ctypes.c_int64, ctypes.c_int
+    L.or_bf_rounds.argtypes = [i32, P, P, P, i32, P, P]
+    L.or_bf_fifo.argtypes = [i32, P, P, P, i32, P]
+    L.or_dijkstra.argtypes = [i32, P, P, P, i32, P]
+    L.or_floyd_warshall.argtypes = [i32, P, P, P, P]
+    L.or_sssp_rows.argtypes = [i32, P, P, P, i32, P, I, I, P]
+    L.or_tour_brute.argtypes = [i32, P, P, P]
+    L.or_tour_held_karp.argtypes = [i32, P, P, P]
+    L.or_route_orders.argtypes = [i32, P, P, P, i32, i32, P, P, I, I, I, P, P, P]
+    L.or_route_with_rows.argtypes = [i32, i32, i32, P, P, i32, P, P, I, I, P, P, P]
+    L.or_factorial.argtypes = [i32]
+    L.or_factorial.restype = i64
+    L.or_patched_route_count.argtypes = [i32, P]
+    L.or_patched_route_count.restype = i64
+    return L
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = _configure(ctypes.CDLL(LIB))
+    return _lib
+
+
+class using:
+    """Context manager that points this module at another build of oracle.c
+    (the mutation tests compile deliberately broken copies)."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _lib
+        _lib = _configure(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _csr(g):
+    return (np.ascontiguousarray(g.row_ptr, dtype=np.int64), np.ascontiguousarray(g.col, dtype=np.int32),
+            np.ascontiguousarray(g.w, dtype=np.int32))
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with {rc}")
+
+
+def bf_rounds(g, src: int):
+    rp, c, w = _csr(g)
+    d = np.empty(g.V, dtype=np.int32)
+    r = np.zeros(1, dtype=np.int32)
+    _check(lib().or_bf_rounds(g.V, _p(rp), _p(c), _p(w), int(src), _p(d), _p(r)), "bf_rounds")
+    return d, int(r[0])
+
+
+def bf_fifo(g, src: int):
+    rp, c, w = _csr(g)
+    d = np.empty(g.V, dtype=np.int32)
+    _check(lib().or_bf_fifo(g.V, _p(rp), _p(c), _p(w), int(src), _p(d)), "bf_fifo")
+    return d
+
+
+def dijkstra(g, src: int):
+    rp, c, w = _csr(g)
+    d = np.empty(g.V, dtype=np.int32)
+    _check(lib().or_dijkstra(g.V, _p(rp), _p(c), _p(w), int(src), _p(d)), "dijkstra")
+    return d
+
+
+def floyd_warshall(g):
+    rp, c, w = _csr(g)
+    d = np.empty((g.V, g.V), dtype=np.int32)
+    _check(lib().or_floyd_warshall(g.V, _p(rp), _p(c), _p(w), _p(d)), "floyd_warshall")
+    return d
+
+
+def sssp_rows(g, src, kind: str = "dijkstra", n_threads: int = 1):
+    rp, c, w = _csr(g)
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    rows = np.empty((src.shape[0], g.V), dtype=np.int32)
+    _check(lib().or_sssp_rows(g.V, _p(rp), _p(c), _p(w), src.shape[0], _p(src), SSSP[kind],
+                              int(n_threads), _p(rows)), "sssp_rows")
+    return rows
+
+
+def tour(D, kind: str = "brute"):
+    """(status, cost, perm) of the best closed tour over the (k+1)x(k+1) matrix D."""
+    D = np.ascontiguousarray(D, dtype=np.int32)
+    k = D.shape[0] - 1
+    cost = np.zeros(1, dtype=np.int32)
+    perm = np.zeros(max(k, 1), dtype=np.int32)
+    f = lib().or_tour_brute if kind == "brute" else lib().or_tour_held_karp
+    st = f(k, _p(D), _p(cost), _p(perm))
+    if st < 0:
+        raise RuntimeError(f"oracle tour failed with {st}")
+    return int(st), int(cost[0]), perm[:k].copy()
+
+
+def route_orders(g, orders, sssp: str = "dijkstra", tour_kind: str = "brute", n_threads: int = 1):
+    rp, c, w = _csr(g)
+    offs = np.ascontiguousarray(orders.offs, dtype=np.int64)
+    picks = np.ascontiguousarray(orders.picks, dtype=np.int32)
+    n = offs.shape[0] - 1
+    cost = np.zeros(n, dtype=np.int32)
+    perm = np.zeros(max(int(offs[-1]), 1), dtype=np.int32)
+    status = np.zeros(n, dtype=np.int32)
+    _check(lib().or_route_orders(g.V, _p(rp), _p(c), _p(w), int(g.depot), n, _p(offs), _p(picks),
+                                 SSSP[sssp], TOUR[tour_kind], int(n_threads), _p(cost), _p(perm),
+                                 _p(status)), "route_orders")
+    return cost, perm[:int(offs[-1])], status
+
+
+def route_with_rows(V, depot, src_nodes, rows, orders, tour_kind: str = "brute", n_threads: int = 1):
+    src_nodes = np.ascontiguousarray(src_nodes, dtype=np.int32)
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    offs = np.ascontiguousarray(orders.offs, dtype=np.int64)
+    picks = np.ascontiguousarray(orders.picks, dtype=np.int32)
+    n = offs.shape[0] - 1
+    cost = np.zeros(n, dtype=np.int32)
+    perm = np.zeros(max(int(offs[-1]), 1), dtype=np.int32)
+    status = np.zeros(n, dtype=np.int32)
+    _check(lib().or_route_with_rows(int(V), int(depot), src_nodes.shape[0], _p(src_nodes), _p(rows), n,
+                                    _p(offs), _p(picks), TOUR[tour_kind], int(n_threads), _p(cost),
+                                    _p(perm), _p(status)), "route_with_rows")
+    return cost, perm[:int(offs[-1])], status
+
+
+def factorial(n: int) -> int:
+    return int(lib().or_factorial(int(n)))
+
+
+def patched_route_count(n_j) -> int:
+    a = np.ascontiguousarray(n_j, dtype=np.int32)
+    return int(lib().or_patched_route_count(a.shape[0], _p(a)))

@@ -1,0 +1,455 @@
+/*
+ * CPU oracle for exact warehouse pick routing -- TEST INFRASTRUCTURE ONLY.
+ * See oracle.h for what is computed and the conventions taken.  Nothing in
+ * the product path calls this file; it shares no code with the CUDA path.
+ */
+#include "oracle.h"
+
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef int64_t i64;
+#define BIG ((i64)1 << 62)
+
+/* ------------------------------------------------------------------ */
+/* Single-source shortest paths                                        */
+/* ------------------------------------------------------------------ */
+
+/* Sec. 4.7: Bellman-Ford relaxes every arc of the arc list per round and
+ * needs at most V-1 rounds.  Each round here reads the previous round's
+ * distances (a Jacobi round); the loop stops at the first round that
+ * changes nothing, which leaves the same fixpoint. */
+int or_bf_rounds(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                 int32_t src, int32_t* dist, int32_t* rounds_out) {
+    if (V <= 0 || src < 0 || src >= V) return -1;
+    i64* cur = (i64*)malloc(sizeof(i64) * (size_t)V);
+    i64* nxt = (i64*)malloc(sizeof(i64) * (size_t)V);
+    if (!cur || !nxt) { free(cur); free(nxt); return -2; }
+    for (int32_t v = 0; v < V; ++v) cur[v] = BIG;
+    cur[src] = 0;
+    int32_t rounds = 0;
+    for (int32_t r = 0; r < V - 1; ++r) {
+        int changed = 0;
+        memcpy(nxt, cur, sizeof(i64) * (size_t)V);
+        for (int32_t u = 0; u < V; ++u) {
+            if (cur[u] >= BIG) continue;
+            for (int64_t a = row_ptr[u]; a < row_ptr[u + 1]; ++a) {
+                i64 cand = cur[u] + (i64)w[a];
+                if (cand < nxt[col[a]]) { nxt[col[a]] = cand; changed = 1; }
+            }
+        }
+        i64* t = cur; cur = nxt; nxt = t;
+        if (!changed) break;
+        ++rounds;
+    }
+    for (int32_t v = 0; v < V; ++v) dist[v] = cur[v] >= BIG ? OR_INF : (int32_t)cur[v];
+    if (rounds_out) *rounds_out = rounds;
+    free(cur); free(nxt);
+    return 0;
+}
+
+/* Bellman-Ford-Moore: a FIFO queue of vertices whose distance dropped. */
+int or_bf_fifo(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+               int32_t src, int32_t* dist) {
+    if (V <= 0 || src < 0 || src >= V) return -1;
+    i64* d = (i64*)malloc(sizeof(i64) * (size_t)V);
+    int32_t* q = (int32_t*)malloc(sizeof(int32_t) * (size_t)V);
+    char* inq = (char*)calloc((size_t)V, 1);
+    if (!d || !q || !inq) { free(d); free(q); free(inq); return -2; }
+    for (int32_t v = 0; v < V; ++v) d[v] = BIG;
+    d[src] = 0;
+    int64_t head = 0, count = 1;
+    q[0] = src; inq[src] = 1;
+    while (count > 0) {
+        int32_t u = q[head]; head = (head + 1) % V; --count; inq[u] = 0;
+        for (int64_t a = row_ptr[u]; a < row_ptr[u + 1]; ++a) {
+            int32_t v = col[a];
+            i64 cand = d[u] + (i64)w[a];
+            if (cand < d[v]) {
+                d[v] = cand;
+                if (!inq[v]) { q[(head + count) % V] = v; ++count; inq[v] = 1; }
+            }
+        }
+    }
+    for (int32_t v = 0; v < V; ++v) dist[v] = d[v] >= BIG ? OR_INF : (int32_t)d[v];
+    free(d); free(q); free(inq);
+    return 0;
+}
+
+/* Dijkstra with a binary heap of (key, vertex) and lazy deletion. */
+typedef struct { i64 key; int32_t v; } hitem;
+
+static void heap_push(hitem* h, int64_t* n, hitem x) {
+    int64_t i = (*n)++;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (h[p].key <= x.key) break;
+        h[i] = h[p]; i = p;
+    }
+    h[i] = x;
+}
+
+static hitem heap_pop(hitem* h, int64_t* n) {
+    hitem top = h[0];
+    hitem last = h[--(*n)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t c = 2 * i + 1;
+        if (c >= *n) break;
+        if (c + 1 < *n && h[c + 1].key < h[c].key) ++c;
+        if (last.key <= h[c].key) break;
+        h[i] = h[c]; i = c;
+    }
+    if (*n > 0) h[i] = last;
+    return top;
+}
+
+int or_dijkstra(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                int32_t src, int32_t* dist) {
+    if (V <= 0 || src < 0 || src >= V) return -1;
+    int64_t E = row_ptr[V];
+    i64* d = (i64*)malloc(sizeof(i64) * (size_t)V);
+    char* done = (char*)calloc((size_t)V, 1);
+    hitem* h = (hitem*)malloc(sizeof(hitem) * (size_t)(E + 1));
+    if (!d || !done || !h) { free(d); free(done); free(h); return -2; }
+    for (int32_t v = 0; v < V; ++v) d[v] = BIG;
+    d[src] = 0;
+    int64_t n = 0;
+    hitem s0 = {0, src};
+    heap_push(h, &n, s0);
+    while (n > 0) {
+        hitem it = heap_pop(h, &n);
+        int32_t u = it.v;
+        if (done[u]) continue;
+        done[u] = 1;
+        for (int64_t a = row_ptr[u]; a < row_ptr[u + 1]; ++a) {
+            int32_t v = col[a];
+            i64 cand = d[u] + (i64)w[a];
+            if (cand < d[v]) { d[v] = cand; hitem x = {cand, v}; heap_push(h, &n, x); }
+        }
+    }
+    for (int32_t v = 0; v < V; ++v) dist[v] = d[v] >= BIG ? OR_INF : (int32_t)d[v];
+    free(d); free(done); free(h);
+    return 0;
+}
+
+int or_floyd_warshall(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                      int32_t* dist) {
+    if (V <= 0 || V > 4096) return -1;
+    size_t n = (size_t)V;
+    i64* d = (i64*)malloc(sizeof(i64) * n * n);
+    if (!d) return -2;
+    for (size_t i = 0; i < n * n; ++i) d[i] = BIG;
+    for (size_t i = 0; i < n; ++i) d[i * n + i] = 0;
+    for (int32_t u = 0; u < V; ++u)
+        for (int64_t a = row_ptr[u]; a < row_ptr[u + 1]; ++a)
+            if ((i64)w[a] < d[(size_t)u * n + (size_t)col[a]]) d[(size_t)u * n + (size_t)col[a]] = w[a];
+    for (size_t m = 0; m < n; ++m)
+        for (size_t i = 0; i < n; ++i) {
+            if (d[i * n + m] >= BIG) continue;
+            for (size_t j = 0; j < n; ++j) {
+                if (d[m * n + j] >= BIG) continue;
+                i64 c = d[i * n + m] + d[m * n + j];
+                if (c < d[i * n + j]) d[i * n + j] = c;
+            }
+        }
+    for (size_t i = 0; i < n * n; ++i) dist[i] = d[i] >= BIG ? OR_INF : (int32_t)d[i];
+    free(d);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Threaded drivers (static split of independent work items)           */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t V; const int64_t* row_ptr; const int32_t* col; const int32_t* w;
+    int32_t n_src; const int32_t* src; int kind; int32_t* rows;
+    int tid, nthr; int rc;
+} rows_job;
+
+static void* rows_worker(void* p) {
+    rows_job* j = (rows_job*)p;
+    j->rc = 0;
+    for (int32_t i = j->tid; i < j->n_src; i += j->nthr) {
+        int32_t* out = j->rows + (size_t)i * (size_t)j->V;
+        int rc;
+        if (j->kind == OR_SSSP_ROUNDS) rc = or_bf_rounds(j->V, j->row_ptr, j->col, j->w, j->src[i], out, 0);
+        else if (j->kind == OR_SSSP_FIFO) rc = or_bf_fifo(j->V, j->row_ptr, j->col, j->w, j->src[i], out);
+        else rc = or_dijkstra(j->V, j->row_ptr, j->col, j->w, j->src[i], out);
+        if (rc) { j->rc = rc; return 0; }
+    }
+    return 0;
+}
+
+int or_sssp_rows(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                 int32_t n_src, const int32_t* src, int kind, int n_threads, int32_t* rows) {
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    rows_job jobs[256];
+    pthread_t th[256];
+    for (int t = 0; t < n_threads; ++t) {
+        rows_job j = {V, row_ptr, col, w, n_src, src, kind, rows, t, n_threads, 0};
+        jobs[t] = j;
+    }
+    for (int t = 1; t < n_threads; ++t) pthread_create(&th[t], 0, rows_worker, &jobs[t]);
+    rows_worker(&jobs[0]);
+    int rc = jobs[0].rc;
+    for (int t = 1; t < n_threads; ++t) { pthread_join(th[t], 0); if (jobs[t].rc) rc = jobs[t].rc; }
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Tours                                                               */
+/* ------------------------------------------------------------------ */
+
+/* Cost of the closed tour 0 -> p[0] -> ... -> p[k-1] -> 0 over D, where p
+ * holds pick indices 1..k; BIG if a leg is unreachable. */
+static i64 tour_cost(int32_t k, const int32_t* D, const int32_t* p) {
+    int32_t n = k + 1;
+    i64 c = 0;
+    int32_t prev = 0;
+    for (int32_t i = 0; i <= k; ++i) {
+        int32_t nx = (i < k) ? p[i] : 0;
+        int32_t leg = D[prev * n + nx];
+        if (leg == OR_INF) return BIG;
+        c += leg;
+        prev = nx;
+    }
+    return c;
+}
+
+/* Next permutation in lexicographic order; 0 when p was the last one. */
+static int next_perm(int32_t* p, int32_t k) {
+    int32_t i = k - 2;
+    while (i >= 0 && p[i] >= p[i + 1]) --i;
+    if (i < 0) return 0;
+    int32_t j = k - 1;
+    while (p[j] <= p[i]) --j;
+    int32_t t = p[i]; p[i] = p[j]; p[j] = t;
+    for (int32_t a = i + 1, b = k - 1; a < b; ++a, --b) { t = p[a]; p[a] = p[b]; p[b] = t; }
+    return 1;
+}
+
+static int range_check(int32_t k, const int32_t* D) {
+    int32_t n = k + 1;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = 0; j < n; ++j)
+            if (i != j && D[i * n + j] != OR_INF && (D[i * n + j] < 0 || D[i * n + j] > OR_LEG_MAX))
+                return 0;
+    return 1;
+}
+
+static void identity(int32_t k, int32_t* perm) {
+    for (int32_t i = 0; i < k; ++i) perm[i] = i;
+}
+
+/* Sec. 4.6: every one of the k! sequences is evaluated, in lexicographic
+ * order; a strict '<' keeps the first (lowest-rank) minimiser. */
+int or_tour_brute(int32_t k, const int32_t* D, int32_t* cost, int32_t* perm) {
+    if (k < 1 || k > OR_MAX_K) return OR_BADORDER;
+    if (!range_check(k, D)) { *cost = OR_INF; identity(k, perm); return OR_RANGE; }
+    int32_t p[OR_MAX_K], best_p[OR_MAX_K];
+    for (int32_t i = 0; i < k; ++i) p[i] = i + 1;
+    i64 best = BIG;
+    do {
+        i64 c = tour_cost(k, D, p);
+        if (c < best) { best = c; memcpy(best_p, p, sizeof(int32_t) * (size_t)k); }
+    } while (next_perm(p, k));
+    if (best >= BIG) { *cost = OR_INF; identity(k, perm); return OR_UNREACHABLE; }
+    *cost = (int32_t)best;
+    for (int32_t i = 0; i < k; ++i) perm[i] = best_p[i] - 1;
+    return OR_OK;
+}
+
+/* Held-Karp (Sec. 3 reference point): h(S, c) = cheapest way to start at
+ * pick c having visited the pick set S (c in S), visit the rest and return
+ * to the depot.  Reconstruction takes the smallest pick index attaining
+ * the optimum at every step, which gives the lexicographically first
+ * optimal sequence. */
+int or_tour_held_karp(int32_t k, const int32_t* D, int32_t* cost, int32_t* perm) {
+    if (k < 1 || k > OR_MAX_K) return OR_BADORDER;
+    if (!range_check(k, D)) { *cost = OR_INF; identity(k, perm); return OR_RANGE; }
+    int32_t n = k + 1;
+    uint32_t full = (1u << k) - 1u;
+    size_t ns = (size_t)1 << k;
+    i64* h = (i64*)malloc(sizeof(i64) * ns * (size_t)k);
+    if (!h) return -2;
+#define H(S, c) h[(size_t)(S) * (size_t)k + (size_t)(c)]
+#define LEG(a, b) (D[(a) * n + (b)] == OR_INF ? BIG : (i64)D[(a) * n + (b)])
+    for (uint32_t S = full + 1; S-- > 0;) {
+        for (int32_t c = 0; c < k; ++c) {
+            if (!(S & (1u << c))) continue;
+            if (S == full) { H(S, c) = LEG(c + 1, 0); continue; }
+            i64 best = BIG;
+            for (int32_t j = 0; j < k; ++j) {
+                if (S & (1u << j)) continue;
+                i64 l = LEG(c + 1, j + 1);
+                i64 r = H(S | (1u << j), j);
+                if (l >= BIG || r >= BIG) continue;
+                if (l + r < best) best = l + r;
+            }
+            H(S, c) = best;
+        }
+    }
+    i64 best = BIG;
+    for (int32_t j = 0; j < k; ++j) {
+        i64 l = LEG(0, j + 1), r = H(1u << j, j);
+        if (l < BIG && r < BIG && l + r < best) best = l + r;
+    }
+    if (best >= BIG) { free(h); *cost = OR_INF; identity(k, perm); return OR_UNREACHABLE; }
+    /* reconstruct */
+    uint32_t S = 0;
+    int32_t cur = 0; /* matrix index of the current stop (0 = depot) */
+    i64 remaining = best;
+    for (int32_t pos = 0; pos < k; ++pos) {
+        for (int32_t j = 0; j < k; ++j) {
+            if (S & (1u << j)) continue;
+            i64 l = LEG(cur, j + 1), r = H(S | (1u << j), j);
+            if (l < BIG && r < BIG && l + r == remaining) {
+                perm[pos] = j;
+                S |= 1u << j;
+                remaining = r;
+                cur = j + 1;
+                break;
+            }
+        }
+    }
+#undef H
+#undef LEG
+    free(h);
+    *cost = (int32_t)best;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Whole path                                                          */
+/* ------------------------------------------------------------------ */
+
+static int32_t find_row(int32_t n_rows, const int32_t* src_nodes, int32_t node) {
+    int32_t lo = 0, hi = n_rows - 1;
+    while (lo <= hi) {
+        int32_t mid = lo + (hi - lo) / 2;
+        if (src_nodes[mid] == node) return mid;
+        if (src_nodes[mid] < node) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+typedef struct {
+    int32_t V, depot, n_rows; const int32_t* src_nodes; const int32_t* rows;
+    int32_t n_orders; const int64_t* offs; const int32_t* picks; int tour_kind;
+    int32_t* cost; int32_t* perm; int32_t* status; int tid, nthr; int rc;
+} tour_job;
+
+static void* tour_worker(void* p) {
+    tour_job* j = (tour_job*)p;
+    int32_t D[(OR_MAX_K + 1) * (OR_MAX_K + 1)];
+    int32_t pts[OR_MAX_K + 1];
+    j->rc = 0;
+    for (int32_t o = j->tid; o < j->n_orders; o += j->nthr) {
+        int64_t b = j->offs[o], e = j->offs[o + 1];
+        int64_t k64 = e - b;
+        int32_t* perm = j->perm + b;
+        if (k64 < 1 || k64 > OR_MAX_K) {
+            j->cost[o] = OR_INF; j->status[o] = OR_BADORDER;
+            for (int64_t i = 0; i < k64; ++i) perm[i] = (int32_t)i;
+            continue;
+        }
+        int32_t k = (int32_t)k64, bad = 0;
+        pts[0] = j->depot;
+        for (int32_t i = 0; i < k; ++i) {
+            pts[i + 1] = j->picks[b + i];
+            if (pts[i + 1] < 0 || pts[i + 1] >= j->V) bad = 1;
+        }
+        if (bad) { j->cost[o] = OR_INF; j->status[o] = OR_BADORDER; identity(k, perm); continue; }
+        int32_t n = k + 1;
+        for (int32_t a = 0; a < n; ++a) {
+            int32_t r = find_row(j->n_rows, j->src_nodes, pts[a]);
+            if (r < 0) { j->rc = -3; return 0; }
+            for (int32_t c = 0; c < n; ++c)
+                D[a * n + c] = j->rows[(size_t)r * (size_t)j->V + (size_t)pts[c]];
+        }
+        int st = (j->tour_kind == OR_TOUR_HELDKARP) ? or_tour_held_karp(k, D, &j->cost[o], perm)
+                                                    : or_tour_brute(k, D, &j->cost[o], perm);
+        if (st < 0) { j->rc = st; return 0; }
+        j->status[o] = st;
+    }
+    return 0;
+}
+
+int or_route_with_rows(int32_t V, int32_t depot, int32_t n_rows, const int32_t* src_nodes,
+                       const int32_t* rows, int32_t n_orders, const int64_t* offs,
+                       const int32_t* picks, int tour_kind, int n_threads,
+                       int32_t* cost, int32_t* perm, int32_t* status) {
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    tour_job jobs[256];
+    pthread_t th[256];
+    for (int t = 0; t < n_threads; ++t) {
+        tour_job j = {V, depot, n_rows, src_nodes, rows, n_orders, offs, picks, tour_kind,
+                      cost, perm, status, t, n_threads, 0};
+        jobs[t] = j;
+    }
+    for (int t = 1; t < n_threads; ++t) pthread_create(&th[t], 0, tour_worker, &jobs[t]);
+    tour_worker(&jobs[0]);
+    int rc = jobs[0].rc;
+    for (int t = 1; t < n_threads; ++t) { pthread_join(th[t], 0); if (jobs[t].rc) rc = jobs[t].rc; }
+    return rc;
+}
+
+static int cmp_i32(const void* a, const void* b) {
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+int or_route_orders(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                    int32_t depot, int32_t n_orders, const int64_t* offs, const int32_t* picks,
+                    int sssp_kind, int tour_kind, int n_threads,
+                    int32_t* cost, int32_t* perm, int32_t* status) {
+    if (V <= 0 || depot < 0 || depot >= V || n_orders < 0) return -1;
+    int64_t np = offs[n_orders];
+    int32_t* nodes = (int32_t*)malloc(sizeof(int32_t) * (size_t)(np + 1));
+    if (!nodes) return -2;
+    int32_t cnt = 0;
+    nodes[cnt++] = depot;
+    for (int32_t o = 0; o < n_orders; ++o) {
+        int64_t k = offs[o + 1] - offs[o];
+        if (k < 1 || k > OR_MAX_K) continue;
+        int bad = 0;
+        for (int64_t i = offs[o]; i < offs[o + 1]; ++i) if (picks[i] < 0 || picks[i] >= V) bad = 1;
+        if (bad) continue;
+        for (int64_t i = offs[o]; i < offs[o + 1]; ++i) nodes[cnt++] = picks[i];
+    }
+    qsort(nodes, (size_t)cnt, sizeof(int32_t), cmp_i32);
+    int32_t u = 0;
+    for (int32_t i = 0; i < cnt; ++i) if (i == 0 || nodes[i] != nodes[i - 1]) nodes[u++] = nodes[i];
+    int32_t* rows = (int32_t*)malloc(sizeof(int32_t) * (size_t)u * (size_t)V);
+    if (!rows) { free(nodes); return -2; }
+    int rc = or_sssp_rows(V, row_ptr, col, w, u, nodes, sssp_kind, n_threads, rows);
+    if (rc == 0)
+        rc = or_route_with_rows(V, depot, u, nodes, rows, n_orders, offs, picks, tour_kind, n_threads,
+                                cost, perm, status);
+    free(rows); free(nodes);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Counting                                                            */
+/* ------------------------------------------------------------------ */
+
+int64_t or_factorial(int32_t n) {
+    int64_t f = 1;
+    for (int32_t i = 2; i <= n; ++i) f *= i;
+    return f;
+}
+
+/* Theorem of Sec. 3: m! 2^(m-1) orderings of m cluster routes with their
+ * boundary-node choices, plus (n_1! + ... + n_m!)/2 undirected routes
+ * inside the clusters. */
+int64_t or_patched_route_count(int32_t m, const int32_t* n_j) {
+    int64_t s = 0;
+    for (int32_t j = 0; j < m; ++j) s += or_factorial(n_j[j]);
+    return or_factorial(m) * ((int64_t)1 << (m - 1)) + s / 2;
+}

@@ -1,0 +1,94 @@
+/*
+ * CPU oracle for exact warehouse pick routing -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, obviously correct C.  It shares no code with the CUDA
+ * path.  Only the test suite, the smoke check and the benchmark's CPU
+ * baseline may load it; the product path never calls it.
+ *
+ * What it computes (arXiv 2504.20655):
+ *   - single-source shortest path distances by round-based Bellman-Ford
+ *     over the arc list (Sec. 4.7, GPU Implementation: every round relaxes
+ *     every arc u->v with weight w, at most V-1 rounds), cross-checked by
+ *     Dijkstra as in the Remark of Sec. 4.7, by a FIFO Bellman-Ford-Moore
+ *     queue, and by Floyd-Warshall on small graphs;
+ *   - for one order (depot P_0, picks P_1..P_k): D[i][j] = dist(P_i, P_j)
+ *     and the minimum over all k! pick sequences pi of
+ *         cost(pi) = D[0][pi_1] + sum_{i<k} D[pi_i][pi_{i+1}] + D[pi_k][0]
+ *     (Sec. 4.6: n! routes, each evaluated over its transitions; routes are
+ *     orderings of the stops, Sec. 2.4), keeping the lexicographically
+ *     first minimiser, by brute force in lexicographic order and by
+ *     Held-Karp (Sec. 3 reference point) with lexicographic reconstruction.
+ *
+ * Conventions (readings of points the paper leaves open):
+ *   - distances are int32, unreachable = OR_INF (INT32_MAX); weights >= 0;
+ *   - a tour with an unreachable leg is not a candidate; if every tour has
+ *     one the order is OR_UNREACHABLE (cost OR_INF, perm = identity);
+ *   - any finite off-diagonal D entry above OR_LEG_MAX makes the order
+ *     OR_RANGE (cost OR_INF, perm = identity): 13 legs of at most
+ *     OR_LEG_MAX stay below 2^27, so exact sums fit int32;
+ *   - k < 1, k > OR_MAX_K or a node id outside [0, V) is OR_BADORDER;
+ *   - perm[j] is the 0-based index into the order's own pick list.
+ */
+#ifndef WROUTE_ORACLE_H
+#define WROUTE_ORACLE_H
+#include <stdint.h>
+
+#define OR_INF INT32_MAX
+#define OR_MAX_K 12
+#define OR_LEG_MAX 10324440
+#define OR_OK 0
+#define OR_UNREACHABLE 1
+#define OR_BADORDER 2
+#define OR_RANGE 3
+
+#define OR_SSSP_ROUNDS 0
+#define OR_SSSP_FIFO 1
+#define OR_SSSP_DIJKSTRA 2
+#define OR_TOUR_BRUTE 0
+#define OR_TOUR_HELDKARP 1
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Out-arc CSR: arcs of u are [row_ptr[u], row_ptr[u+1]) with head col[] and weight w[]. */
+int or_bf_rounds(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                 int32_t src, int32_t* dist, int32_t* rounds_out);
+int or_bf_fifo(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+               int32_t src, int32_t* dist);
+int or_dijkstra(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                int32_t src, int32_t* dist);
+/* dist is V*V, row-major dist[s*V + t]. */
+int or_floyd_warshall(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                      int32_t* dist);
+
+/* Rows for n_src sources: rows[i*V + v] = dist(src[i], v).  kind = OR_SSSP_*. */
+int or_sssp_rows(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                 int32_t n_src, const int32_t* src, int kind, int n_threads, int32_t* rows);
+
+/* Tours over a (k+1)x(k+1) matrix D (row-major, index 0 = depot). */
+int or_tour_brute(int32_t k, const int32_t* D, int32_t* cost, int32_t* perm);
+int or_tour_held_karp(int32_t k, const int32_t* D, int32_t* cost, int32_t* perm);
+
+/* Whole path for a batch of orders; picks of order i are picks[offs[i]..offs[i+1]). */
+int or_route_orders(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                    int32_t depot, int32_t n_orders, const int64_t* offs, const int32_t* picks,
+                    int sssp_kind, int tour_kind, int n_threads,
+                    int32_t* cost, int32_t* perm, int32_t* status);
+
+/* Routing of orders whose distance rows are given: rows[r*V + v] for the
+ * source node src_nodes[r] (sorted ascending, must contain every node used). */
+int or_route_with_rows(int32_t V, int32_t depot, int32_t n_rows, const int32_t* src_nodes,
+                       const int32_t* rows, int32_t n_orders, const int64_t* offs,
+                       const int32_t* picks, int tour_kind, int n_threads,
+                       int32_t* cost, int32_t* perm, int32_t* status);
+
+/* Counting helpers used by the pins: n!, and the Theorem of Sec. 3:
+ * m! * 2^(m-1) + (n_1! + ... + n_m!)/2. */
+int64_t or_factorial(int32_t n);
+int64_t or_patched_route_count(int32_t m, const int32_t* n_j);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

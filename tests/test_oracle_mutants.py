@@ -1,0 +1,106 @@
+"""The pins catch plausible oracle mistakes.
+
+Each case plants one mistake in a copy of oracle.c (on the CPU, in a
+temporary directory), builds it, and checks that at least one pin from
+the oracle test files fails against the broken build.
+"""
+import json
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_20655_gb300 import synth
+from tests.graphs import path_graph, random_graph
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "tours_by_hand.json")))
+
+MUTANTS = [
+    ("bf dropped weight", "i64 cand = cur[u] + (i64)w[a];", "i64 cand = cur[u];"),
+    ("bf extra term", "i64 cand = cur[u] + (i64)w[a];", "i64 cand = cur[u] + (i64)w[a] + 1;"),
+    ("bf too few rounds", "for (int32_t r = 0; r < V - 1; ++r) {", "for (int32_t r = 0; r < V / 3; ++r) {"),
+    ("bf reversed arcs", "if (cand < nxt[col[a]]) { nxt[col[a]] = cand; changed = 1; }",
+     "if (cur[col[a]] < BIG && cur[col[a]] + (i64)w[a] < nxt[u]) { nxt[u] = cur[col[a]] + (i64)w[a]; changed = 1; }"),
+    ("tour no return leg", "for (int32_t i = 0; i <= k; ++i) {", "for (int32_t i = 0; i < k; ++i) {"),
+    ("tour transposed leg", "int32_t leg = D[prev * n + nx];", "int32_t leg = D[nx * n + prev];"),
+    ("tour last minimiser", "if (c < best) { best = c; memcpy(best_p",
+     "if (c <= best) { best = c; memcpy(best_p"),
+    ("tour off-by-one perm", "for (int32_t i = 0; i < k; ++i) perm[i] = best_p[i] - 1;",
+     "for (int32_t i = 0; i < k; ++i) perm[i] = best_p[i];"),
+    ("heldkarp largest index", "for (int32_t j = 0; j < k; ++j) {\n            if (S & (1u << j)) continue;\n            i64 l = LEG(cur, j + 1)",
+     "for (int32_t j = k - 1; j >= 0; --j) {\n            if (S & (1u << j)) continue;\n            i64 l = LEG(cur, j + 1)"),
+    ("heldkarp no return", "if (S == full) { H(S, c) = LEG(c + 1, 0); continue; }",
+     "if (S == full) { H(S, c) = 0; continue; }"),
+    ("dijkstra no decrease", "if (cand < d[v]) { d[v] = cand; hitem x",
+     "if (cand < d[v] && d[v] == BIG) { d[v] = cand; hitem x"),
+    ("range limit off", "D[i * n + j] > OR_LEG_MAX", "D[i * n + j] > OR_LEG_MAX + 1"),
+]
+
+
+def pins_pass() -> bool:
+    """A compact run of the pins in test_oracle_sssp.py / test_oracle_tour.py."""
+    try:
+        A, S, a, c = 5, 6, 13, 41
+        lay = synth.Layout(A=A, S=S, F=1, C=2, step_lo=a, step_hi=a, cross_w=c)
+        g = lay.build()
+        rows = oracle.sssp_rows(g, np.arange(lay.n_slots), "rounds")
+        for p in range(lay.n_slots):
+            a1, s1 = divmod(p, S)
+            for q in range(lay.n_slots):
+                a2, s2 = divmod(q, S)
+                exp = abs(s1 - s2) * a if a1 == a2 else \
+                    min(s1 + s2 + 2, 2 * S - s1 - s2) * a + abs(a1 - a2) * c
+                if rows[p, q] != exp:
+                    return False
+        pg = path_graph(40, 2)
+        d, r = oracle.bf_rounds(pg, 0)
+        if r != 39 or (d != 2 * np.arange(40)).any():
+            return False
+        for seed in range(3):
+            rg = random_graph(60, 200, seed + 50, w_lo=1)
+            for s in range(0, 60, 11):
+                if (oracle.bf_rounds(rg, s)[0] != oracle.dijkstra(rg, s)).any():
+                    return False
+        for case in GOLD["cases"]:
+            D = np.array(case["D"], dtype=np.int32)
+            for kind in ("brute", "heldkarp"):
+                st, cost, perm = oracle.tour(D, kind)
+                if st != case["status"] or cost != case["cost"] or perm.tolist() != case["perm"]:
+                    return False
+        for k in range(1, 8):
+            for seed in range(4):
+                n = k + 1
+                D = synth.uniform_int(seed + 17 * k, n * n, 0, 9).reshape(n, n).astype(np.int32)
+                np.fill_diagonal(D, 0)
+                b, h = oracle.tour(D, "brute"), oracle.tour(D, "heldkarp")
+                if b[:2] != h[:2] or (b[2] != h[2]).any():
+                    return False
+        D = np.full((5, 5), 7, dtype=np.int32)
+        np.fill_diagonal(D, 0)
+        D[1, 2] = oracle.LEG_MAX + 1
+        if oracle.tour(D, "brute")[0] != oracle.RANGE:
+            return False
+        return True
+    except Exception:
+        return False
+
+
+def test_pins_pass_on_the_real_oracle():
+    assert pins_pass()
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, name, old, new):
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site not unique: {name}"
+    src = tmp_path / "oracle.c"
+    src.write_text(text.replace(old, new))
+    (tmp_path / "oracle.h").write_text(open(os.path.join(os.path.dirname(SRC), "oracle.h")).read())
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-w", "-o", str(so), str(src),
+                           "-lpthread"])
+    with oracle.using(str(so)):
+        assert not pins_pass(), f"mutant survived: {name}"

@@ -1,0 +1,131 @@
+"""Pins of the oracle's tour search (CPU only).
+
+Brute force over all k! sequences in lexicographic order (Sec. 4.6) is
+checked against: hand-worked cases (tests/golden/tours_by_hand.json),
+Held-Karp with lexicographic reconstruction (Sec. 3 reference point),
+an independent itertools enumeration written here, the reversal symmetry
+of undirected instances, and the status rules.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2504_20655_gb300 import synth
+
+INF = 2**31 - 1
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "tours_by_hand.json")
+
+
+def py_tour(D):
+    """Independent enumeration: itertools yields permutations in lexicographic order."""
+    k = D.shape[0] - 1
+    best, arg = None, None
+    for p in itertools.permutations(range(1, k + 1)):
+        seq = (0,) + p + (0,)
+        legs = [int(D[a, b]) for a, b in zip(seq[:-1], seq[1:])]
+        if any(x == INF for x in legs):
+            continue
+        c = sum(legs)
+        if best is None or c < best:
+            best, arg = c, [x - 1 for x in p]
+    return best, arg
+
+
+def rand_D(k, seed, lo=0, hi=30, p_inf=0.0, sym=False):
+    n = k + 1
+    D = synth.uniform_int(seed, n * n, lo, hi).reshape(n, n)
+    if p_inf > 0:
+        D = np.where(synth.uniform01(seed ^ 99, n * n).reshape(n, n) < p_inf, INF, D)
+    if sym:
+        D = np.minimum(D, D.T)
+    np.fill_diagonal(D, 0)
+    return D.astype(np.int32)
+
+
+def rank_of(perm):
+    """Lexicographic rank of a permutation of 0..k-1 (factorial number system)."""
+    k = len(perm)
+    rest = sorted(perm)
+    r = 0
+    for i, x in enumerate(perm):
+        j = rest.index(x)
+        r = r * (k - i) + j
+        rest.pop(j)
+    return r
+
+
+@pytest.mark.parametrize("case", json.load(open(GOLD))["cases"], ids=lambda c: c["name"])
+def test_hand_worked(orc, case):
+    D = np.array(case["D"], dtype=np.int32)
+    for kind in ("brute", "heldkarp"):
+        st, cost, perm = orc.tour(D, kind)
+        assert st == case["status"] and cost == case["cost"] and perm.tolist() == case["perm"], kind
+
+
+@pytest.mark.parametrize("k", range(1, 8))
+def test_brute_equals_itertools(orc, k):
+    for seed in range(5):
+        for p_inf, hi in ((0.0, 3), (0.0, 1000), (0.3, 50)):
+            D = rand_D(k, seed * 31 + k, hi=hi, p_inf=p_inf)
+            st, cost, perm = orc.tour(D, "brute")
+            best, arg = py_tour(D)
+            if best is None:
+                assert st == 1 and cost == INF and perm.tolist() == list(range(k))
+            else:
+                assert st == 0 and cost == best and perm.tolist() == arg
+
+
+@pytest.mark.parametrize("k", range(1, 11))
+def test_brute_equals_held_karp(orc, k):
+    n_cases = 12 if k <= 8 else 3
+    for seed in range(n_cases):
+        hi = (2, 9, 500)[seed % 3]
+        D = rand_D(k, seed * 7 + 1000 * k, hi=hi, p_inf=0.1 if seed % 4 == 0 else 0.0)
+        assert orc.tour(D, "brute")[:2] == orc.tour(D, "heldkarp")[:2]
+        b, h = orc.tour(D, "brute"), orc.tour(D, "heldkarp")
+        assert (b[2] == h[2]).all()
+
+
+def test_reversal_symmetry(orc):
+    for k in range(2, 8):
+        D = rand_D(k, 4242 + k, hi=20, sym=True)
+        st, cost, perm = orc.tour(D, "brute")
+        rev = perm[::-1]
+        Dl = D.astype(np.int64)
+        seq = [0] + [p + 1 for p in rev] + [0]
+        assert sum(Dl[a, b] for a, b in zip(seq[:-1], seq[1:])) == cost
+        assert rank_of(perm.tolist()) <= rank_of(rev.tolist())
+
+
+def test_duplicate_picks_give_zero_legs(orc):
+    x = np.array([0, 4, 4, 10, 4])
+    D = np.abs(np.subtract.outer(x, x)).astype(np.int32)
+    st, cost, perm = orc.tour(D, "brute")
+    assert st == 0 and cost == 20
+    assert py_tour(D) == (cost, perm.tolist())
+
+
+def test_range_and_bad_orders(orc):
+    D = rand_D(4, 5, hi=50)
+    D[1, 2] = 10324441
+    st, cost, perm = orc.tour(D, "brute")
+    assert st == 3 and cost == INF and perm.tolist() == [0, 1, 2, 3]
+    D[1, 2] = 10324440
+    assert orc.tour(D, "brute")[0] == 0
+    assert orc.tour(np.zeros((14, 14), dtype=np.int32), "brute")[0] == 2  # k = 13 > 12
+
+
+def test_route_orders_statuses(orc):
+    g = synth.tiny_layout().build()
+    offs = np.array([0, 2, 2, 4, 17, 19], dtype=np.int64)
+    picks = np.array([1, 2, 3, g.V, *range(13), 5, 5], dtype=np.int32)
+    o = synth.Orders(offs, picks)
+    cost, perm, status = orc.route_orders(g, o)
+    assert status.tolist() == [0, 2, 2, 2, 0]
+    assert cost[1] == INF and cost[2] == INF and cost[3] == INF
+    assert perm[2:4].tolist() == [0, 1]
+    assert perm[4:17].tolist() == list(range(13))
+    assert cost[4] == 2 * orc.dijkstra(g, g.depot)[5]

@@ -1,0 +1,77 @@
+"""The seeded input generators: sizes follow the layout formulas, draws are reproducible."""
+import numpy as np
+import pytest
+
+from paper_2504_20655_gb300 import synth
+
+
+def und_edges(A, S, F, C):
+    return A * F * (S + C - 1) + A * S * (F - 1) + C * (A - 1) + 1
+
+
+@pytest.mark.parametrize("name,V,E_und", [
+    ("tiny", 421, 639), ("medium", 20401, 30997), ("serve", 80801, 121997), ("scale", 1002001, 1503999)])
+def test_layout_sizes(name, V, E_und):
+    lay = getattr(synth, f"{name}_layout")()
+    assert lay.V == V == lay.A * lay.F * lay.S + lay.A * lay.C + 1
+    assert und_edges(lay.A, lay.S, lay.F, lay.C) == E_und
+    if name == "scale":
+        return  # built in the slow GPU tests; the formula is what is pinned here
+    g = lay.build()
+    assert g.meta["undirected_edges"] == E_und
+    n_oneway_arcs = g.meta["oneway_aisles"] * lay.F * (lay.S + lay.C - 1)
+    assert g.E == 2 * E_und - n_oneway_arcs
+    assert g.row_ptr[-1] == g.E and (np.diff(g.row_ptr) >= 0).all()
+    assert g.w.min() >= 0 and g.col.min() >= 0 and g.col.max() < g.V
+
+
+def test_chain_boundaries():
+    assert synth.medium_layout().boundaries() == [0, 33, 67, 100]
+    assert synth.tiny_layout().boundaries() == [0, 20]
+
+
+def test_weights_in_range_and_deterministic():
+    a = synth.medium_layout().build()
+    b = synth.medium_layout().build()
+    assert (a.w == b.w).all() and (a.col == b.col).all()
+    assert set(np.unique(a.w[a.w != 300])) <= set(range(80, 121))
+    c = synth.Layout(A=100, S=100, F=2, C=4, oneway_frac=0.1, seed=7).build()
+    assert not (c.w == a.w).all()
+
+
+def test_splitmix64_reference_values():
+    # splitmix64 with state 0: the first outputs of the published generator
+    z = synth.splitmix64(0, 3)
+    assert [int(x) for x in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_orders_medium():
+    g, o = synth.medium_workload()
+    k = o.k()
+    assert o.n == 1024 and k.min() >= 4 and k.max() <= 10
+    assert set(np.unique(k)) == set(range(4, 11))
+    assert o.picks.min() >= 0 and o.picks.max() < g.n_slots
+
+
+def test_orders_batching_k_distribution():
+    _, o = synth.batching_workload()
+    k = o.k()
+    assert k.min() == 2 and k.max() == 12
+    frac = np.array([(k == j).mean() for j in range(2, 13)])
+    p = 0.3 * 0.7 ** np.arange(11)
+    p /= p.sum()
+    assert np.abs(frac - p).max() < 0.01
+
+
+def test_zipf_head():
+    smap = np.arange(50_000, dtype=np.int32)
+    k = np.full(20_000, 1)
+    o = synth.zipf_orders(20_000, k, smap, 1.1, 3)
+    h = np.bincount(o.picks, minlength=50_000) / 20_000
+    cdf = synth.zipf_cdf(50_000, 1.1)
+    assert abs(h[0] - cdf[0]) < 0.01 and abs(h[1] - (cdf[1] - cdf[0])) < 0.01
+
+
+def test_distinct_sources():
+    s = synth.distinct_sources(4096, 1_000_000, 1)
+    assert len(np.unique(s)) == 4096 and s.max() < 1_000_000
