@@ -1,0 +1,166 @@
+/*
+ * wroute.h -- C ABI of the GB300 (sm_103a) exact warehouse pick-routing library.
+ *
+ * The routing hot path of arXiv 2504.20655:
+ *   (a) multi-source Bellman-Ford over the warehouse graph (Sec. 4.7:
+ *       min-plus relaxation d[v] = min(d[v], d[u] + w(u, v)) until nothing
+ *       changes, at most V-1 rounds), giving each order its pick-location
+ *       distance matrix D[i][j] = dist(P_i, P_j) with P_0 the depot;
+ *   (b) exhaustive evaluation of the order's pick sequences over D
+ *       (Sec. 4.6: all n! sequences, each costed over its transitions;
+ *       a route is an ordering of the stops, Sec. 2.4), split into
+ *       rank-range segments whose partial minima are reduced
+ *       (the segmentation strategy of the abstract and Sec. 6).
+ *
+ * Result of an order with picks P_1..P_k (1 <= k <= WR_MAX_K):
+ *   cost = min over permutations pi of
+ *          D[0][pi_1] + D[pi_1][pi_2] + ... + D[pi_{k-1}][pi_k] + D[pi_k][0]
+ *   perm = the lexicographically first minimiser, perm[j] = pi_{j+1} - 1,
+ *          i.e. a 0-based index into the order's own pick list.
+ * All arithmetic is int32 and bit-exact.
+ *
+ * Conventions for every call:
+ *   - Memory: inputs are borrowed for the duration of the call (the graph
+ *     is copied); outputs are allocated by the caller.  ptr_kind says
+ *     whether the caller's pointers are host (WR_HOST) or device
+ *     (WR_DEVICE) memory of the context's device.
+ *   - Streams: work is enqueued on cuda_stream (a cudaStream_t, NULL =
+ *     the legacy default stream).  With WR_DEVICE outputs the call returns
+ *     once the work is enqueued; results are valid after that stream
+ *     synchronises.  With WR_HOST outputs the call returns after the
+ *     results have been copied back.
+ *   - Errors: every entry point returns WR_OK or one of the WR_E* codes
+ *     below and leaves the context usable.  Device-side failures (a
+ *     bounded wait that timed out, the sweep cap) are recorded in the
+ *     context and returned by the next wr_sync() or host-output call.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef WROUTE_H
+#define WROUTE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define WR_OK        0
+#define WR_EINVAL    1  /* bad argument, malformed CSR, negative weight, size out of range */
+#define WR_ENOMEM    2  /* allocation failed, or the memory budget holds fewer than 32 rows */
+#define WR_ECUDA     3  /* a CUDA runtime call failed */
+#define WR_ETIMEOUT  4  /* a bounded device-side wait (grid barrier) ran out */
+#define WR_ENOGRAPH  5  /* no graph loaded */
+#define WR_EINTERNAL 6  /* Bellman-Ford exceeded its sweep cap (cannot happen with w >= 0) */
+
+/* per-order status */
+#define WR_ORDER_OK          0
+#define WR_ORDER_UNREACHABLE 1  /* every sequence has an unreachable leg: cost WR_INF, perm identity */
+#define WR_ORDER_BAD         2  /* k < 1, k > WR_MAX_K or a node id outside [0, V): cost WR_INF */
+#define WR_ORDER_RANGE       3  /* a finite D entry exceeds WR_LEG_MAX: cost WR_INF, perm identity */
+
+/* pointer kinds */
+#define WR_HOST   0
+#define WR_DEVICE 1
+
+#define WR_MAX_K   12          /* 12! = 479001600 ranks fit int32 */
+#define WR_INF     2147483647  /* unreachable distance */
+#define WR_LEG_MAX 10324440    /* 13 legs of at most this stay below 2^27: exact int32 sums */
+
+typedef struct wr_ctx wr_ctx;  /* opaque; owns all device memory it allocates */
+
+typedef struct {
+    int device;                   /* CUDA device ordinal */
+    uint64_t mem_budget_bytes;    /* cap on the distance-row buffer of one source segment */
+    int max_k;                    /* largest order size accepted, <= WR_MAX_K */
+    uint64_t barrier_max_spins;   /* iteration limit of every device-side wait (0 = default) */
+    const char* tune_path;        /* autotuner table file (NULL = built-in defaults) */
+} wr_config;
+
+/* Tunables (picked by the autotuner; results never depend on them). */
+typedef struct {
+    int32_t run_target;     /* Bellman-Ford tile: target nodes per run (consecutive ids) */
+    int32_t tile_cap;       /* nodes (run + halo) staged in shared memory per tile: 64, 128 or 256 */
+    int32_t enum_units;     /* sequence units (of 120 sequences) per thread per scheduled chunk */
+    int32_t enum_max_units_per_launch; /* rank-range segment: units per enumeration launch (0 = all) */
+} wr_tuning;
+
+/* Counters of the last call (device-timed with CUDA events on its stream). */
+typedef struct {
+    int64_t n_orders;
+    int64_t n_sources;        /* distinct Bellman-Ford sources (depot + distinct pick nodes) */
+    int64_t n_segments;       /* source segments run */
+    int64_t sweeps;           /* Bellman-Ford sweeps, summed over segments */
+    int64_t tile_visits;      /* (run, 32-source group) tiles processed, summed over sweeps */
+    int64_t node_visits;      /* node x 32-lane group visits */
+    int64_t bytes_alg;        /* algorithmic bytes of the sweeps: per visited node 8*32 (own
+                                 lanes read + written) + 8*indeg + 8 */
+    int64_t sequences;        /* pick sequences evaluated */
+    int64_t kernel_launches;  /* kernels launched by the call */
+    float ms_select, ms_init, ms_bf, ms_gather, ms_enum, ms_finish, ms_total;
+} wr_stats;
+
+/* Create a context on cfg->device (NULL cfg = defaults: device 0, 2 GiB budget, max_k 12). */
+int wr_create(const wr_config* cfg, wr_ctx** out);
+void wr_destroy(wr_ctx* ctx);
+const char* wr_strerror(int code);
+
+/* Wait for all work the context enqueued and return any recorded device-side error. */
+int wr_sync(wr_ctx* ctx);
+
+/* a1 -- Load the graph (Sec. 4.7 keeps it as arrays u, v, w; here out-arc CSR):
+ * arcs of node u are [row_ptr[u], row_ptr[u+1]) with heads col[] and int32
+ * weights w[] >= 0.  row_ptr has V+1 entries, row_ptr[0] = 0, row_ptr[V] = E.
+ * depot in [0, V) is P_0 of every order.  Copies everything; replaces any
+ * previous graph.  WR_EINVAL on malformed input or a negative weight. */
+int wr_load_graph(wr_ctx* ctx, int32_t V, int64_t E, const int64_t* row_ptr, const int32_t* col,
+                  const int32_t* w, int32_t depot, int ptr_kind);
+
+/* a1-a7 -- Route a batch of orders.  Order i has picks picks[offs[i] .. offs[i+1]),
+ * offs has n_orders+1 non-decreasing entries with offs[0] = 0 (checked for host
+ * input, WR_EINVAL; with device input an order whose range leaves [0, offs[n]]
+ * is reported WR_ORDER_BAD and gets no perm writes).
+ * Writes cost[i], status[i] and perm[offs[i] + j].
+ * Sources (depot + distinct pick nodes) are deduplicated on the device and
+ * processed in segments of at most mem_budget_bytes of rows. */
+int wr_route_orders(wr_ctx* ctx, int32_t n_orders, const int64_t* offs, const int32_t* picks,
+                    int32_t* cost, int32_t* perm, int32_t* status, int ptr_kind, void* cuda_stream);
+
+/* a3 -- Distance rows: rows[i * ld + v] = dist(src[i], v) for i < n_src, v < V
+ * (WR_INF when unreachable), ld >= V.  src entries must lie in [0, V). */
+int wr_bf_rows(wr_ctx* ctx, int32_t n_src, const int32_t* src, int32_t* rows, int64_t ld,
+               int ptr_kind, void* cuda_stream);
+
+/* a2+a3 at scale -- Produce the rows of n_src sources segment by segment under the
+ * memory budget.  For each segment, consume(user, first, count, dev_rows, ld) is
+ * called on the host once the segment's kernels are enqueued on cuda_stream;
+ * dist(src[first + b], v) = dev_rows[v * ld + b] for b < count (node-major,
+ * device memory, valid for work the consumer enqueues on the same stream).  The
+ * buffer is reused after consume returns.  A non-zero return from consume stops
+ * the call and is returned. */
+typedef int (*wr_consume_fn)(void* user, int32_t first, int32_t count, const int32_t* dev_rows,
+                             int64_t ld);
+int wr_distance_rows(wr_ctx* ctx, int32_t n_src, const int32_t* src, int ptr_kind,
+                     wr_consume_fn consume, void* user, void* cuda_stream);
+
+/* Built-in consumer of wr_distance_rows for the scale workload: sub[i * n_dst + j] =
+ * dist(src[i], dst[j]) and a per-row checksum
+ *   check[i] = sum over v of (uint64)(uint32)dist(src[i], v) * (2v + 1)   (mod 2^64). */
+int wr_submatrix(wr_ctx* ctx, int32_t n_src, const int32_t* src, int32_t n_dst, const int32_t* dst,
+                 int32_t* sub, uint64_t* check, int ptr_kind, void* cuda_stream);
+
+/* a5-a7 on given matrices -- D is n_orders blocks of 13 x 13 int32 (row-major,
+ * the top-left (k+1) x (k+1) used, index 0 = depot, WR_INF = unreachable);
+ * k[i] picks per order.  Writes cost[i], status[i] and perm[i * WR_MAX_K + j]. */
+int wr_tour_eval(wr_ctx* ctx, int32_t n_orders, const int32_t* k, const int32_t* D, int32_t* cost,
+                 int32_t* perm, int32_t* status, int ptr_kind, void* cuda_stream);
+
+int wr_get_stats(wr_ctx* ctx, wr_stats* out);
+int wr_get_tuning(wr_ctx* ctx, wr_tuning* out);
+/* Changing run_target or tile_cap re-partitions the loaded graph. */
+int wr_set_tuning(wr_ctx* ctx, const wr_tuning* t);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WROUTE_H */

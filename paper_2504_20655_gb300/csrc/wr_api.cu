@@ -1,0 +1,771 @@
+// C ABI (include/wroute.h): context, buffers and the launch sequence of the
+// routing path.  Every step of the path runs in the kernels of wr_bf.cu and
+// wr_tour.cu; this file only sizes buffers, plans source segments and
+// enqueues work on the caller's stream.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "wr_internal.h"
+
+namespace {
+
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    bool ensure(size_t need) {
+        if (need <= bytes) return true;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        size_t want = need + need / 4 + 256;
+        if (cudaMalloc(&p, want) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        bytes = want;
+        return true;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+constexpr unsigned long long DEFAULT_SPINS = 1ull << 24;  // x 64 ns sleeps: about a second
+constexpr uint64_t DEFAULT_BUDGET = 2ull << 30;
+
+}  // namespace
+
+struct wr_ctx {
+    int device = 0;
+    wr_config cfg{};
+    wr_tuning tune{};
+    bool has_graph = false;
+    wr::HostGraph hg;
+    wr::HostPartition hp;
+    wr::DevGraph dg;
+    DBuf g_desc, g_ref, g_w, g_run_ptr, g_halo_ptr, g_halo_nodes, g_rin_ptr, g_rin_list, g_run_of, g_meta;
+    wr::BfLaunchInfo bf_info{};
+    int enum_blocks = 0;
+    // working buffers
+    DBuf rows, stamp, list0, list1, counts, bar, err, stats;
+    DBuf node_flag, src_index, src_list, n_src, block_sums;
+    DBuf offs, picks, order_status, order_flags, D, unit_off, best, unit_ctr;
+    DBuf out_cost, out_perm, out_status, kbuf, dgiven, src_in, sub, check;
+    // stats
+    wr_stats last{};
+    std::vector<cudaEvent_t> events;
+    int n_events_used = 0;
+    int ev_call_begin = -1, ev_call_end = -1;
+    std::vector<std::pair<int, int>> ev_phase[6];  // select, init, bf, gather, enum, finish
+    int launches = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            if (getenv("WROUTE_DEBUG")) fprintf(stderr, "wroute: %s at %s:%d: %s\n", #call, __FILE__, \
+                                                __LINE__, cudaGetErrorString(e_));            \
+            return WR_ECUDA;                                                                  \
+        }                                                                                     \
+    } while (0)
+
+#define RC(call)                      \
+    do {                              \
+        int r_ = (call);              \
+        if (r_ != WR_OK) return r_;   \
+    } while (0)
+
+int ensure(DBuf& b, size_t bytes) { return b.ensure(bytes) ? WR_OK : WR_ENOMEM; }
+
+int set_device(wr_ctx* c) { return cudaSetDevice(c->device) == cudaSuccess ? WR_OK : WR_ECUDA; }
+
+cudaEvent_t next_event(wr_ctx* c, int* idx) {
+    if (c->n_events_used >= static_cast<int>(c->events.size())) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->events.push_back(e);
+    }
+    *idx = c->n_events_used;
+    return c->events[c->n_events_used++];
+}
+
+int record(wr_ctx* c, cudaStream_t s, int* idx) {
+    cudaEvent_t e = next_event(c, idx);
+    if (!e) return WR_ECUDA;
+    CK(cudaEventRecord(e, s));
+    return WR_OK;
+}
+
+struct PhaseTimer {
+    wr_ctx* c;
+    cudaStream_t s;
+    int phase;
+    int b = -1;
+    PhaseTimer(wr_ctx* c_, cudaStream_t s_, int ph) : c(c_), s(s_), phase(ph) { record(c, s, &b); }
+    ~PhaseTimer() {
+        int e = -1;
+        if (b >= 0 && record(c, s, &e) == WR_OK) c->ev_phase[phase].push_back({b, e});
+    }
+};
+
+int begin_call(wr_ctx* c, cudaStream_t s) {
+    c->n_events_used = 0;
+    for (auto& v : c->ev_phase) v.clear();
+    c->launches = 0;
+    c->last_stream = s;
+    std::memset(&c->last, 0, sizeof(c->last));
+    RC(ensure(c->stats, 8 * sizeof(unsigned long long)));
+    RC(ensure(c->err, sizeof(int)));
+    CK(cudaMemsetAsync(c->stats.p, 0, 8 * sizeof(unsigned long long), s));
+    return record(c, s, &c->ev_call_begin);
+}
+
+int end_call(wr_ctx* c, cudaStream_t s) { return record(c, s, &c->ev_call_end); }
+
+// Returns the recorded device error (and clears it); the stream must be idle.
+int take_device_error(wr_ctx* c) {
+    int h = 0;
+    if (!c->err.p) return WR_OK;
+    CK(cudaMemcpy(&h, c->err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h != 0) CK(cudaMemset(c->err.p, 0, sizeof(int)));
+    return h;
+}
+
+int upload(DBuf& b, const void* src, size_t bytes) {
+    RC(ensure(b, bytes == 0 ? 4 : bytes));
+    if (bytes) CK(cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice));
+    return WR_OK;
+}
+
+int upload_partition(wr_ctx* c) {
+    const wr::HostPartition& p = c->hp;
+    RC(upload(c->g_desc, p.node_desc.data(), p.node_desc.size() * sizeof(int4)));
+    RC(upload(c->g_ref, p.arc_ref.data(), p.arc_ref.size() * 4));
+    RC(upload(c->g_w, p.arc_w.data(), p.arc_w.size() * 4));
+    RC(upload(c->g_run_ptr, p.run_ptr.data(), p.run_ptr.size() * 4));
+    RC(upload(c->g_halo_ptr, p.halo_ptr.data(), p.halo_ptr.size() * 4));
+    RC(upload(c->g_halo_nodes, p.halo_nodes.data(), p.halo_nodes.size() * 4));
+    RC(upload(c->g_rin_ptr, p.rin_ptr.data(), p.rin_ptr.size() * 4));
+    RC(upload(c->g_rin_list, p.rin_list.data(), p.rin_list.size() * 4));
+    RC(upload(c->g_run_of, p.run_of_node.data(), p.run_of_node.size() * 4));
+    RC(upload(c->g_meta, p.run_meta_bytes.data(), p.run_meta_bytes.size() * 8));
+    wr::DevGraph& g = c->dg;
+    g.V = p.V;
+    g.n_runs = p.n_runs;
+    g.tile_cap = p.tile_cap;
+    g.depot = c->hg.depot;
+    g.node_desc = c->g_desc.as<int4>();
+    g.arc_ref = c->g_ref.as<uint32_t>();
+    g.arc_w = c->g_w.as<uint32_t>();
+    g.run_ptr = c->g_run_ptr.as<int32_t>();
+    g.halo_ptr = c->g_halo_ptr.as<int32_t>();
+    g.halo_nodes = c->g_halo_nodes.as<int32_t>();
+    g.rin_ptr = c->g_rin_ptr.as<int32_t>();
+    g.rin_list = c->g_rin_list.as<int32_t>();
+    g.run_of_node = c->g_run_of.as<int32_t>();
+    g.run_meta_bytes = c->g_meta.as<int64_t>();
+    return wr::bf_prepare(p.tile_cap, c->device, &c->bf_info);
+}
+
+int partition(wr_ctx* c) {
+    wr::build_partition(c->hg, c->tune.run_target, c->tune.tile_cap, c->hp);
+    return upload_partition(c);
+}
+
+int32_t budget_lanes(const wr_ctx* c) {
+    const uint64_t per_lane = static_cast<uint64_t>(c->dg.V) * 4ull;
+    uint64_t lanes = c->cfg.mem_budget_bytes / per_lane;
+    lanes = (lanes / 32) * 32;
+    if (lanes > (1u << 30)) lanes = 1u << 30;
+    return static_cast<int32_t>(lanes);
+}
+
+// Size the row buffer and frontier arrays for segments of seg_lanes lanes.
+int ensure_bf(wr_ctx* c, int32_t seg_lanes) {
+    const size_t rows_bytes = static_cast<size_t>(seg_lanes) * static_cast<size_t>(c->dg.V) * 4;
+    RC(ensure(c->rows, rows_bytes));
+    const size_t items = static_cast<size_t>(c->dg.n_runs) * static_cast<size_t>(seg_lanes / 32);
+    RC(ensure(c->stamp, items * 4));
+    RC(ensure(c->list0, items * 4));
+    RC(ensure(c->list1, items * 4));
+    RC(ensure(c->counts, 16));
+    RC(ensure(c->bar, sizeof(wr::GridBar)));
+    return WR_OK;
+}
+
+wr::BfWork bf_work(wr_ctx* c, int32_t seg_lanes) {
+    wr::BfWork w;
+    w.stamp = c->stamp.as<int32_t>();
+    w.list0 = c->list0.as<int32_t>();
+    w.list1 = c->list1.as<int32_t>();
+    w.counts = c->counts.as<int32_t>();
+    w.gcap = seg_lanes / 32;
+    w.bar = c->bar.as<wr::GridBar>();
+    w.err = c->err.as<int>();
+    w.max_spins = c->cfg.barrier_max_spins ? c->cfg.barrier_max_spins : DEFAULT_SPINS;
+    w.stats = c->stats.as<unsigned long long>();
+    return w;
+}
+
+// One Bellman-Ford segment: init + sweeps.
+int run_bf_segment(wr_ctx* c, const wr::BfSegment& seg, cudaStream_t s) {
+    wr::BfWork w = bf_work(c, seg.lanes);
+    {
+        PhaseTimer t(c, s, 1);
+        CK(wr::bf_launch_init(c->dg, seg, w, s));
+        c->launches++;
+    }
+    {
+        PhaseTimer t(c, s, 2);
+        CK(wr::bf_launch_sweeps(c->dg, seg, w, c->bf_info, s));
+        c->launches++;
+    }
+    return WR_OK;
+}
+
+float elapsed(wr_ctx* c, int a, int b) {
+    float ms = 0.f;
+    if (a < 0 || b < 0) return 0.f;
+    if (cudaEventElapsedTime(&ms, c->events[a], c->events[b]) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.f;
+    }
+    return ms;
+}
+
+// Enumeration (a5, a6) over the prepared D blocks, then decode (a7).
+int run_tours(wr_ctx* c, int32_t n, const int32_t* k_dev, const wr::TourBufs& tb, int32_t* cost, int32_t* perm,
+              int perm_stride, int32_t* status, cudaStream_t s) {
+    {
+        PhaseTimer t(c, s, 4);
+        CK(wr::tour_launch_units(n, k_dev, tb, s, &c->launches));
+        const int upt = c->tune.enum_units > 0 ? c->tune.enum_units : 4;
+        if (c->tune.enum_max_units_per_launch > 0) {
+            long long total = 0;
+            CK(cudaMemcpyAsync(&total, tb.unit_off + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            const long long step = c->tune.enum_max_units_per_launch;
+            for (long long b = 0; b < total; b += step) {
+                CK(cudaMemsetAsync(tb.unit_ctr, 0, sizeof(unsigned long long), s));
+                CK(wr::tour_launch_enum(n, k_dev, tb, b, b + step < total ? b + step : total, upt, c->enum_blocks, s));
+                c->launches++;
+            }
+        } else {
+            CK(wr::tour_launch_enum(n, k_dev, tb, 0, 1ll << 62, upt, c->enum_blocks, s));
+            c->launches++;
+        }
+    }
+    {
+        PhaseTimer t(c, s, 5);
+        CK(wr::tour_launch_finish(n, k_dev, tb, cost, perm, perm_stride, status, s));
+        c->launches++;
+    }
+    return WR_OK;
+}
+
+int ensure_tour_bufs(wr_ctx* c, int32_t n, wr::TourBufs& tb) {
+    RC(ensure(c->order_status, static_cast<size_t>(n) * 4 + 4));
+    RC(ensure(c->order_flags, static_cast<size_t>(n) * 4 + 4));
+    RC(ensure(c->D, static_cast<size_t>(n) * wr::DBLOCK * 4 + 4));
+    RC(ensure(c->unit_off, (static_cast<size_t>(n) + 1) * 8));
+    RC(ensure(c->best, static_cast<size_t>(n) * 8 + 8));
+    RC(ensure(c->unit_ctr, 16));
+    tb.order_status = c->order_status.as<int32_t>();
+    tb.order_flags = c->order_flags.as<int32_t>();
+    tb.D = c->D.as<uint32_t>();
+    tb.unit_off = c->unit_off.as<long long>();
+    tb.best = c->best.as<unsigned long long>();
+    tb.unit_ctr = c->unit_ctr.as<unsigned long long>();
+    tb.seq_count = reinterpret_cast<long long*>(c->stats.as<unsigned long long>() + 4);
+    return WR_OK;
+}
+
+int finish_host_call(wr_ctx* c, cudaStream_t s) {
+    CK(cudaStreamSynchronize(s));
+    return take_device_error(c);
+}
+
+int check_ptr_kind(int k) { return (k == WR_HOST || k == WR_DEVICE) ? WR_OK : WR_EINVAL; }
+
+}  // namespace
+
+extern "C" {
+
+const char* wr_strerror(int code) {
+    switch (code) {
+        case WR_OK: return "ok";
+        case WR_EINVAL: return "invalid argument";
+        case WR_ENOMEM: return "out of memory or memory budget too small";
+        case WR_ECUDA: return "CUDA runtime error";
+        case WR_ETIMEOUT: return "device-side wait timed out";
+        case WR_ENOGRAPH: return "no graph loaded";
+        case WR_EINTERNAL: return "Bellman-Ford sweep cap exceeded";
+        default: return "unknown error";
+    }
+}
+
+int wr_create(const wr_config* cfg, wr_ctx** out) {
+    if (!out) return WR_EINVAL;
+    *out = nullptr;
+    wr_config c{};
+    c.device = 0;
+    c.mem_budget_bytes = DEFAULT_BUDGET;
+    c.max_k = WR_MAX_K;
+    c.barrier_max_spins = DEFAULT_SPINS;
+    c.tune_path = nullptr;
+    if (cfg) c = *cfg;
+    if (c.max_k < 1 || c.max_k > WR_MAX_K || c.device < 0) return WR_EINVAL;
+    if (c.mem_budget_bytes == 0) return WR_ENOMEM;
+    int n_dev = 0;
+    if (cudaGetDeviceCount(&n_dev) != cudaSuccess || c.device >= n_dev) {
+        cudaGetLastError();
+        return WR_ECUDA;
+    }
+    if (cudaSetDevice(c.device) != cudaSuccess) return WR_ECUDA;
+    wr_ctx* ctx = new (std::nothrow) wr_ctx();
+    if (!ctx) return WR_ENOMEM;
+    ctx->device = c.device;
+    ctx->cfg = c;
+    ctx->cfg.tune_path = nullptr;
+    ctx->tune.run_target = 96;
+    ctx->tune.tile_cap = 128;
+    ctx->tune.enum_units = 4;
+    ctx->tune.enum_max_units_per_launch = 0;
+    ctx->enum_blocks = wr::tour_enum_blocks(c.device);
+    if (ctx->err.ensure(sizeof(int)) == false || cudaMemset(ctx->err.p, 0, sizeof(int)) != cudaSuccess) {
+        delete ctx;
+        return WR_ENOMEM;
+    }
+    *out = ctx;
+    return WR_OK;
+}
+
+void wr_destroy(wr_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    DBuf* bufs[] = {&c->g_desc, &c->g_ref, &c->g_w, &c->g_run_ptr, &c->g_halo_ptr, &c->g_halo_nodes, &c->g_rin_ptr,
+                    &c->g_rin_list, &c->g_run_of, &c->g_meta, &c->rows, &c->stamp, &c->list0, &c->list1,
+                    &c->counts, &c->bar, &c->err, &c->stats, &c->node_flag, &c->src_index, &c->src_list,
+                    &c->n_src, &c->block_sums, &c->offs, &c->picks, &c->order_status, &c->order_flags, &c->D,
+                    &c->unit_off, &c->best, &c->unit_ctr, &c->out_cost, &c->out_perm, &c->out_status, &c->kbuf,
+                    &c->dgiven, &c->src_in, &c->sub, &c->check};
+    for (DBuf* b : bufs) b->release();
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    delete c;
+}
+
+int wr_sync(wr_ctx* c) {
+    if (!c) return WR_EINVAL;
+    RC(set_device(c));
+    CK(cudaDeviceSynchronize());
+    return take_device_error(c);
+}
+
+int wr_load_graph(wr_ctx* c, int32_t V, int64_t E, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                  int32_t depot, int ptr_kind) {
+    if (!c || V < 1 || E < 0 || !row_ptr) return WR_EINVAL;
+    RC(check_ptr_kind(ptr_kind));
+    RC(set_device(c));
+    std::vector<int64_t> rp;
+    std::vector<int32_t> cl, wt;
+    const int64_t* hrp = row_ptr;
+    const int32_t* hcol = col;
+    const int32_t* hw = w;
+    if (ptr_kind == WR_DEVICE) {
+        rp.resize(static_cast<size_t>(V) + 1);
+        CK(cudaMemcpy(rp.data(), row_ptr, rp.size() * 8, cudaMemcpyDeviceToHost));
+        cl.resize(static_cast<size_t>(E));
+        wt.resize(static_cast<size_t>(E));
+        if (E) {
+            CK(cudaMemcpy(cl.data(), col, static_cast<size_t>(E) * 4, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(wt.data(), w, static_cast<size_t>(E) * 4, cudaMemcpyDeviceToHost));
+        }
+        hrp = rp.data();
+        hcol = cl.data();
+        hw = wt.data();
+    }
+    wr::HostGraph g;
+    RC(wr::build_host_graph(V, E, hrp, hcol, hw, depot, g));
+    c->hg.in_ptr.swap(g.in_ptr);
+    c->hg.in_src.swap(g.in_src);
+    c->hg.in_w.swap(g.in_w);
+    c->hg.V = g.V;
+    c->hg.E = g.E;
+    c->hg.depot = g.depot;
+    c->has_graph = false;
+    RC(partition(c));
+    RC(ensure(c->node_flag, static_cast<size_t>(V) + 16));
+    RC(ensure(c->src_index, static_cast<size_t>(V) * 4 + 16));
+    RC(ensure(c->src_list, static_cast<size_t>(V) * 4 + 16));
+    RC(ensure(c->n_src, 16));
+    RC(ensure(c->block_sums, (static_cast<size_t>(V) / 4096 + 2) * 4));
+    c->has_graph = true;
+    return WR_OK;
+}
+
+int wr_route_orders(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* picks, int32_t* cost, int32_t* perm,
+                    int32_t* status, int ptr_kind, void* stream) {
+    if (!c || n < 0 || !offs) return WR_EINVAL;
+    RC(check_ptr_kind(ptr_kind));
+    if (!c->has_graph) return WR_ENOGRAPH;
+    if (n > 0 && (!cost || !status)) return WR_EINVAL;
+    RC(set_device(c));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // total picks
+    int64_t np = 0, first = 0;
+    if (ptr_kind == WR_HOST) {
+        first = offs[0];
+        np = offs[n];
+        for (int32_t i = 0; i < n; ++i)
+            if (offs[i + 1] < offs[i]) return WR_EINVAL;
+    } else {
+        CK(cudaMemcpy(&first, offs, 8, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&np, offs + n, 8, cudaMemcpyDeviceToHost));
+    }
+    if (first != 0 || np < 0) return WR_EINVAL;
+    if (np > 0 && (!picks || !perm)) return WR_EINVAL;
+    if (n == 0) return WR_OK;
+    const int32_t V = c->dg.V;
+    RC(begin_call(c, s));
+    // inputs on the device
+    const int64_t* d_offs = offs;
+    const int32_t* d_picks = picks;
+    if (ptr_kind == WR_HOST) {
+        RC(ensure(c->offs, (static_cast<size_t>(n) + 1) * 8));
+        RC(ensure(c->picks, static_cast<size_t>(np) * 4 + 4));
+        CK(cudaMemcpyAsync(c->offs.p, offs, (static_cast<size_t>(n) + 1) * 8, cudaMemcpyHostToDevice, s));
+        if (np) CK(cudaMemcpyAsync(c->picks.p, picks, static_cast<size_t>(np) * 4, cudaMemcpyHostToDevice, s));
+        d_offs = c->offs.as<int64_t>();
+        d_picks = c->picks.as<int32_t>();
+    }
+    wr::TourBufs tb{};
+    tb.offs = d_offs;
+    tb.picks = d_picks;
+    RC(ensure_tour_bufs(c, n, tb));
+    int32_t* o_cost = cost;
+    int32_t* o_perm = perm;
+    int32_t* o_status = status;
+    if (ptr_kind == WR_HOST) {
+        RC(ensure(c->out_cost, static_cast<size_t>(n) * 4));
+        RC(ensure(c->out_status, static_cast<size_t>(n) * 4));
+        RC(ensure(c->out_perm, static_cast<size_t>(np) * 4 + 4));
+        o_cost = c->out_cost.as<int32_t>();
+        o_status = c->out_status.as<int32_t>();
+        o_perm = c->out_perm.as<int32_t>();
+    }
+    // a2: sources = depot + distinct pick nodes of valid orders
+    {
+        PhaseTimer t(c, s, 0);
+        CK(cudaMemsetAsync(c->node_flag.p, 0, static_cast<size_t>(V), s));
+        CK(cudaMemsetAsync(c->order_flags.p, 0, static_cast<size_t>(n) * 4, s));
+        CK(wr::tour_launch_select(n, d_offs, d_picks, V, c->dg.depot, c->cfg.max_k, c->node_flag.as<uint8_t>(),
+                                  tb.order_status, s));
+        c->launches++;
+        CK(wr::tour_launch_compact(V, c->node_flag.as<uint8_t>(), c->src_index.as<int32_t>(),
+                                   c->src_list.as<int32_t>(), c->n_src.as<int32_t>(), c->block_sums.as<int32_t>(), s,
+                                   &c->launches));
+    }
+    // segments of the worst-case source count; empty ones exit on the device
+    const int64_t worst = np + 1 < V ? np + 1 : V;
+    const int32_t lanes_needed = static_cast<int32_t>((worst + 31) / 32 * 32);
+    const int32_t blanes = budget_lanes(c);
+    if (blanes < 32) return WR_ENOMEM;
+    const int32_t seg_lanes = lanes_needed < blanes ? lanes_needed : blanes;
+    const int32_t n_seg = (lanes_needed + seg_lanes - 1) / seg_lanes;
+    RC(ensure_bf(c, seg_lanes));
+    for (int32_t sg = 0; sg < n_seg; ++sg) {
+        wr::BfSegment seg;
+        seg.rows = c->rows.as<uint32_t>();
+        seg.ld = seg_lanes;
+        seg.src = c->src_list.as<int32_t>();
+        seg.n_src_dev = c->n_src.as<int32_t>();
+        seg.n_src_host = 0;
+        seg.first = sg * seg_lanes;
+        seg.lanes = seg_lanes;
+        RC(run_bf_segment(c, seg, s));
+        PhaseTimer t(c, s, 3);
+        CK(wr::tour_launch_gather(n, tb, c->dg.depot, c->src_index.as<int32_t>(), seg, s));
+        c->launches++;
+    }
+    c->last.n_segments = n_seg;
+    RC(run_tours(c, n, nullptr, tb, o_cost, o_perm, 0, o_status, s));
+    RC(end_call(c, s));
+    c->last.n_orders = n;
+    if (ptr_kind == WR_HOST) {
+        CK(cudaMemcpyAsync(cost, o_cost, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(status, o_status, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToHost, s));
+        if (np) CK(cudaMemcpyAsync(perm, o_perm, static_cast<size_t>(np) * 4, cudaMemcpyDeviceToHost, s));
+        return finish_host_call(c, s);
+    }
+    return WR_OK;
+}
+
+// Shared driver of wr_bf_rows / wr_distance_rows / wr_submatrix.
+typedef int (*seg_fn)(wr_ctx* c, const wr::BfSegment& seg, void* user, cudaStream_t s);
+
+static int rows_driver(wr_ctx* c, int32_t n_src, const int32_t* src, int ptr_kind, seg_fn fn, void* user,
+                       cudaStream_t s) {
+    if (!c || n_src < 0 || (n_src > 0 && !src)) return WR_EINVAL;
+    RC(check_ptr_kind(ptr_kind));
+    if (!c->has_graph) return WR_ENOGRAPH;
+    RC(set_device(c));
+    if (n_src == 0) return WR_OK;
+    std::vector<int32_t> hsrc;
+    const int32_t* hs = src;
+    if (ptr_kind == WR_DEVICE) {
+        hsrc.resize(static_cast<size_t>(n_src));
+        CK(cudaMemcpy(hsrc.data(), src, static_cast<size_t>(n_src) * 4, cudaMemcpyDeviceToHost));
+        hs = hsrc.data();
+    }
+    for (int32_t i = 0; i < n_src; ++i)
+        if (hs[i] < 0 || hs[i] >= c->dg.V) return WR_EINVAL;
+    RC(ensure(c->src_in, static_cast<size_t>(n_src) * 4));
+    CK(cudaMemcpyAsync(c->src_in.p, hs, static_cast<size_t>(n_src) * 4, cudaMemcpyHostToDevice, s));
+    const int32_t lanes_needed = (n_src + 31) / 32 * 32;
+    const int32_t blanes = budget_lanes(c);
+    if (blanes < 32) return WR_ENOMEM;
+    const int32_t seg_lanes = lanes_needed < blanes ? lanes_needed : blanes;
+    const int32_t n_seg = (lanes_needed + seg_lanes - 1) / seg_lanes;
+    RC(ensure_bf(c, seg_lanes));
+    for (int32_t sg = 0; sg < n_seg; ++sg) {
+        wr::BfSegment seg;
+        seg.rows = c->rows.as<uint32_t>();
+        seg.ld = seg_lanes;
+        seg.src = c->src_in.as<int32_t>();
+        seg.n_src_dev = nullptr;
+        seg.n_src_host = n_src;
+        seg.first = sg * seg_lanes;
+        seg.lanes = seg_lanes;
+        RC(run_bf_segment(c, seg, s));
+        RC(fn(c, seg, user, s));
+    }
+    c->last.n_segments = n_seg;
+    c->last.n_sources = n_src;
+    return WR_OK;
+}
+
+struct RowsOut {
+    int32_t* rows;
+    int64_t ld;
+    int host;
+};
+
+static int rows_out_fn(wr_ctx* c, const wr::BfSegment& seg, void* user, cudaStream_t s) {
+    RowsOut* ro = static_cast<RowsOut*>(user);
+    const int32_t V = c->dg.V;
+    if (!ro->host) {
+        CK(wr::bf_launch_rows_out(seg, V, ro->rows, ro->ld, s));
+        c->launches++;
+        return WR_OK;
+    }
+    // host: transpose into a device staging block, then one 2-D copy
+    const size_t blk = static_cast<size_t>(seg.lanes) * static_cast<size_t>(V) * 4;
+    RC(ensure(c->sub, blk));
+    wr::BfSegment shifted = seg;
+    shifted.first = 0;
+    // lanes of this segment: min(lanes, n_src - first)
+    const int32_t count = seg.n_src_host - seg.first < seg.lanes ? seg.n_src_host - seg.first : seg.lanes;
+    shifted.n_src_host = count;
+    shifted.src = seg.src + seg.first;
+    CK(wr::bf_launch_rows_out(shifted, V, c->sub.as<int32_t>(), V, s));
+    c->launches++;
+    CK(cudaMemcpy2DAsync(ro->rows + static_cast<int64_t>(seg.first) * ro->ld, static_cast<size_t>(ro->ld) * 4,
+                         c->sub.p, static_cast<size_t>(V) * 4, static_cast<size_t>(V) * 4,
+                         static_cast<size_t>(count), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return WR_OK;
+}
+
+int wr_bf_rows(wr_ctx* c, int32_t n_src, const int32_t* src, int32_t* rows, int64_t ld, int ptr_kind, void* stream) {
+    if (!c || !rows) return WR_EINVAL;
+    if (c->has_graph && ld < c->dg.V) return WR_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    RC(begin_call(c, s));
+    RowsOut ro{rows, ld, ptr_kind == WR_HOST};
+    RC(rows_driver(c, n_src, src, ptr_kind, rows_out_fn, &ro, s));
+    RC(end_call(c, s));
+    if (ptr_kind == WR_HOST) return finish_host_call(c, s);
+    return WR_OK;
+}
+
+struct ConsumeCtx {
+    wr_consume_fn fn;
+    void* user;
+};
+
+static int consume_fn(wr_ctx* c, const wr::BfSegment& seg, void* user, cudaStream_t) {
+    ConsumeCtx* cc = static_cast<ConsumeCtx*>(user);
+    const int32_t count = seg.n_src_host - seg.first < seg.lanes ? seg.n_src_host - seg.first : seg.lanes;
+    (void)c;
+    return cc->fn(cc->user, seg.first, count, reinterpret_cast<const int32_t*>(seg.rows), seg.ld);
+}
+
+int wr_distance_rows(wr_ctx* c, int32_t n_src, const int32_t* src, int ptr_kind, wr_consume_fn consume, void* user,
+                     void* stream) {
+    if (!c || !consume) return WR_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    RC(begin_call(c, s));
+    ConsumeCtx cc{consume, user};
+    RC(rows_driver(c, n_src, src, ptr_kind, consume_fn, &cc, s));
+    return end_call(c, s);
+}
+
+struct SubCtx {
+    int32_t n_dst;
+    const int32_t* dst;
+    int32_t* sub;
+    unsigned long long* check;
+};
+
+static int sub_fn(wr_ctx* c, const wr::BfSegment& seg, void* user, cudaStream_t s) {
+    SubCtx* sc = static_cast<SubCtx*>(user);
+    CK(wr::bf_launch_submatrix(seg, c->dg.V, sc->n_dst, sc->dst, sc->sub, sc->check, s));
+    c->launches++;
+    return WR_OK;
+}
+
+int wr_submatrix(wr_ctx* c, int32_t n_src, const int32_t* src, int32_t n_dst, const int32_t* dst, int32_t* sub,
+                 uint64_t* check, int ptr_kind, void* stream) {
+    if (!c || n_src < 0 || n_dst < 0 || (n_dst > 0 && !dst) || !sub || !check) return WR_EINVAL;
+    RC(check_ptr_kind(ptr_kind));
+    if (!c->has_graph) return WR_ENOGRAPH;
+    RC(set_device(c));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    RC(begin_call(c, s));
+    SubCtx sc{n_dst, dst, sub, reinterpret_cast<unsigned long long*>(check)};
+    const int32_t* d_dst = dst;
+    if (ptr_kind == WR_HOST) {
+        for (int32_t j = 0; j < n_dst; ++j)
+            if (dst[j] < 0 || dst[j] >= c->dg.V) return WR_EINVAL;
+        RC(ensure(c->kbuf, static_cast<size_t>(n_dst) * 4 + 4));
+        RC(ensure(c->dgiven, static_cast<size_t>(n_src) * static_cast<size_t>(n_dst) * 4 + 4));
+        RC(ensure(c->check, static_cast<size_t>(n_src) * 8 + 8));
+        CK(cudaMemcpyAsync(c->kbuf.p, dst, static_cast<size_t>(n_dst) * 4, cudaMemcpyHostToDevice, s));
+        d_dst = c->kbuf.as<int32_t>();
+        sc.sub = c->dgiven.as<int32_t>();
+        sc.check = c->check.as<unsigned long long>();
+    }
+    sc.dst = d_dst;
+    CK(cudaMemsetAsync(sc.check, 0, static_cast<size_t>(n_src) * 8, s));
+    RC(rows_driver(c, n_src, src, ptr_kind, sub_fn, &sc, s));
+    RC(end_call(c, s));
+    if (ptr_kind == WR_HOST) {
+        CK(cudaMemcpyAsync(sub, sc.sub, static_cast<size_t>(n_src) * static_cast<size_t>(n_dst) * 4,
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(check, sc.check, static_cast<size_t>(n_src) * 8, cudaMemcpyDeviceToHost, s));
+        return finish_host_call(c, s);
+    }
+    return WR_OK;
+}
+
+int wr_tour_eval(wr_ctx* c, int32_t n, const int32_t* k, const int32_t* D, int32_t* cost, int32_t* perm,
+                 int32_t* status, int ptr_kind, void* stream) {
+    if (!c || n < 0 || (n > 0 && (!k || !D || !cost || !perm || !status))) return WR_EINVAL;
+    RC(check_ptr_kind(ptr_kind));
+    RC(set_device(c));
+    if (n == 0) return WR_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    RC(begin_call(c, s));
+    const int32_t* d_k = k;
+    const int32_t* d_D = D;
+    const size_t dbytes = static_cast<size_t>(n) * wr::DBLOCK * 4;
+    if (ptr_kind == WR_HOST) {
+        RC(ensure(c->kbuf, static_cast<size_t>(n) * 4));
+        RC(ensure(c->dgiven, dbytes));
+        CK(cudaMemcpyAsync(c->kbuf.p, k, static_cast<size_t>(n) * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(c->dgiven.p, D, dbytes, cudaMemcpyHostToDevice, s));
+        d_k = c->kbuf.as<int32_t>();
+        d_D = c->dgiven.as<int32_t>();
+    }
+    wr::TourBufs tb{};
+    RC(ensure_tour_bufs(c, n, tb));
+    {
+        PhaseTimer t(c, s, 3);
+        CK(wr::tour_launch_prepare_given(n, d_k, d_D, c->cfg.max_k, tb, s));
+        c->launches++;
+    }
+    int32_t* o_cost = cost;
+    int32_t* o_perm = perm;
+    int32_t* o_status = status;
+    if (ptr_kind == WR_HOST) {
+        RC(ensure(c->out_cost, static_cast<size_t>(n) * 4));
+        RC(ensure(c->out_status, static_cast<size_t>(n) * 4));
+        RC(ensure(c->out_perm, static_cast<size_t>(n) * WR_MAX_K * 4));
+        o_cost = c->out_cost.as<int32_t>();
+        o_status = c->out_status.as<int32_t>();
+        o_perm = c->out_perm.as<int32_t>();
+    }
+    RC(run_tours(c, n, d_k, tb, o_cost, o_perm, WR_MAX_K, o_status, s));
+    RC(end_call(c, s));
+    c->last.n_orders = n;
+    if (ptr_kind == WR_HOST) {
+        CK(cudaMemcpyAsync(cost, o_cost, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(status, o_status, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(perm, o_perm, static_cast<size_t>(n) * WR_MAX_K * 4, cudaMemcpyDeviceToHost, s));
+        return finish_host_call(c, s);
+    }
+    return WR_OK;
+}
+
+int wr_get_stats(wr_ctx* c, wr_stats* out) {
+    if (!c || !out) return WR_EINVAL;
+    RC(set_device(c));
+    CK(cudaStreamSynchronize(c->last_stream));
+    wr_stats st = c->last;
+    unsigned long long h[8] = {0};
+    if (c->stats.p) CK(cudaMemcpy(h, c->stats.p, sizeof(h), cudaMemcpyDeviceToHost));
+    st.sweeps = static_cast<int64_t>(h[0]);
+    st.tile_visits = static_cast<int64_t>(h[1]);
+    st.node_visits = static_cast<int64_t>(h[2]);
+    st.bytes_alg = static_cast<int64_t>(h[3]);
+    st.sequences = static_cast<int64_t>(h[4]);
+    st.kernel_launches = c->launches;
+    if (c->n_src.p && st.n_sources == 0 && st.n_orders > 0) {
+        int32_t ns = 0;
+        CK(cudaMemcpy(&ns, c->n_src.p, 4, cudaMemcpyDeviceToHost));
+        st.n_sources = ns;
+    }
+    float* slots[6] = {&st.ms_select, &st.ms_init, &st.ms_bf, &st.ms_gather, &st.ms_enum, &st.ms_finish};
+    for (int ph = 0; ph < 6; ++ph) {
+        float sum = 0.f;
+        for (auto& pr : c->ev_phase[ph]) sum += elapsed(c, pr.first, pr.second);
+        *slots[ph] = sum;
+    }
+    st.ms_total = elapsed(c, c->ev_call_begin, c->ev_call_end);
+    *out = st;
+    return WR_OK;
+}
+
+int wr_get_tuning(wr_ctx* c, wr_tuning* out) {
+    if (!c || !out) return WR_EINVAL;
+    *out = c->tune;
+    return WR_OK;
+}
+
+int wr_set_tuning(wr_ctx* c, const wr_tuning* t) {
+    if (!c || !t) return WR_EINVAL;
+    if (t->run_target < 1 || (t->tile_cap != 64 && t->tile_cap != 128 && t->tile_cap != 256) || t->enum_units < 1 ||
+        t->enum_max_units_per_launch < 0 || t->run_target > t->tile_cap)
+        return WR_EINVAL;
+    RC(set_device(c));
+    const bool repart = t->run_target != c->tune.run_target || t->tile_cap != c->tune.tile_cap;
+    c->tune = *t;
+    if (repart && c->has_graph) {
+        CK(cudaDeviceSynchronize());
+        RC(partition(c));
+    }
+    return WR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "wroute.h"
+
+namespace wr {
+
+constexpr uint32_t INF_U = 0x7FFFFFFFu;       // unreachable distance (= WR_INF)
+constexpr uint32_t NO_CARRY = 0x80000000u;    // carry weight of a node without a chain arc
+constexpr uint32_t GLOBAL_REF = 0x80000000u;  // arc source not staged: low 31 bits = node id
+constexpr uint32_t TOUR_CAP = 1u << 27;       // unreachable legs are clamped to this in tour sums
+constexpr int DSTRIDE = 13;                   // D blocks are 13 x 13
+constexpr int DBLOCK = DSTRIDE * DSTRIDE;
+constexpr int TAIL = 5;                       // sequences of one unit: orderings of the last 5 picks
+constexpr int ORDER_FLAG_RANGE = 1;
+
+// --------------------------------------------------------------------------
+// graph preprocessing (host, wr_graph.cpp)
+// --------------------------------------------------------------------------
+
+// In-arc (pull) CSR: arcs into v are [in_ptr[v], in_ptr[v+1]), sorted by
+// source, one arc per (u, v) pair (the lightest), no self loops.
+struct HostGraph {
+    int32_t V = 0;
+    int64_t E = 0;
+    int32_t depot = 0;
+    std::vector<int64_t> in_ptr;
+    std::vector<int32_t> in_src;
+    std::vector<int32_t> in_w;
+};
+
+// Sweep tiles: runs of consecutive node ids whose own rows plus the rows of
+// their out-of-run in-neighbours (the halo) fit tile_cap shared-memory slots.
+struct HostPartition {
+    int32_t V = 0, n_runs = 0, tile_cap = 0, max_len = 0;
+    std::vector<int32_t> run_ptr;       // n_runs + 1
+    std::vector<int32_t> halo_ptr;      // n_runs + 1 (staged halo only)
+    std::vector<int32_t> halo_nodes;
+    std::vector<int32_t> rin_ptr;       // runs with an arc into the run
+    std::vector<int32_t> rin_list;
+    std::vector<int32_t> run_of_node;   // V
+    // per node v (plus a sentinel at V): x = weight of arc v-1 -> v inside the
+    // run (NO_CARRY if none), y = weight of v+1 -> v inside the run, z = first
+    // forward arc, w = first backward arc; backward arcs end at desc[v+1].z.
+    std::vector<int4> node_desc;
+    std::vector<uint32_t> arc_ref;      // tile slot of the arc's source, or GLOBAL_REF | node
+    std::vector<uint32_t> arc_w;
+    std::vector<int64_t> run_meta_bytes;  // 8 * in-arcs + 8 * nodes of the run
+    int64_t n_global_refs = 0;
+};
+
+int build_host_graph(int32_t V, int64_t E, const int64_t* row_ptr, const int32_t* col,
+                     const int32_t* w, int32_t depot, HostGraph& g);
+void build_partition(const HostGraph& g, int run_target, int tile_cap, HostPartition& p);
+
+// --------------------------------------------------------------------------
+// device-side structures
+// --------------------------------------------------------------------------
+
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
+};
+
+struct DevGraph {
+    int32_t V = 0, n_runs = 0, tile_cap = 0, depot = 0;
+    int4* node_desc = nullptr;
+    uint32_t* arc_ref = nullptr;
+    uint32_t* arc_w = nullptr;
+    int32_t* run_ptr = nullptr;
+    int32_t* halo_ptr = nullptr;
+    int32_t* halo_nodes = nullptr;
+    int32_t* rin_ptr = nullptr;
+    int32_t* rin_list = nullptr;
+    int32_t* run_of_node = nullptr;
+    int64_t* run_meta_bytes = nullptr;
+};
+
+// One source segment of Bellman-Ford: rows[v * ld + b] holds
+// dist(src[first + b], v) for lanes b < min(count, n_src - first).
+struct BfSegment {
+    uint32_t* rows;
+    int64_t ld;
+    const int32_t* src;        // source node ids (index space of n_src)
+    const int32_t* n_src_dev;  // device count of sources, or nullptr to use n_src_host
+    int32_t n_src_host;
+    int32_t first;
+    int32_t lanes;             // lane capacity (multiple of 32)
+};
+
+struct BfWork {
+    int32_t* stamp;   // n_runs * Gcap
+    int32_t* list0;   // n_runs * Gcap
+    int32_t* list1;
+    int32_t* counts;  // 4
+    int32_t gcap;
+    GridBar* bar;
+    int* err;
+    unsigned long long max_spins;
+    unsigned long long* stats;  // [0] sweeps [1] tiles [2] node visits [3] bytes
+};
+
+// launchers (wr_bf.cu)
+struct BfLaunchInfo {
+    int blocks;
+    int threads;
+    size_t smem;
+};
+int bf_prepare(int tile_cap, int device, BfLaunchInfo* info);  // occupancy of the sweep kernel
+cudaError_t bf_launch_init(const DevGraph& g, const BfSegment& seg, const BfWork& w, cudaStream_t s);
+cudaError_t bf_launch_sweeps(const DevGraph& g, const BfSegment& seg, const BfWork& w,
+                             const BfLaunchInfo& info, cudaStream_t s);
+cudaError_t bf_launch_rows_out(const BfSegment& seg, int32_t V, int32_t* out, int64_t ld_out,
+                               cudaStream_t s);
+cudaError_t bf_launch_submatrix(const BfSegment& seg, int32_t V, int32_t n_dst, const int32_t* dst,
+                                int32_t* sub, unsigned long long* check, cudaStream_t s);
+
+// launchers (wr_tour.cu)
+struct TourBufs {
+    const int64_t* offs;
+    const int32_t* picks;
+    int32_t* order_status;   // n
+    int32_t* order_flags;    // n
+    uint32_t* D;             // n * DBLOCK
+    long long* unit_off;     // n + 1 (exclusive prefix of units)
+    unsigned long long* best;  // n
+    unsigned long long* unit_ctr;  // scheduling counter
+    long long* seq_count;    // sequences evaluated (stat)
+};
+cudaError_t tour_launch_select(int32_t n, const int64_t* offs, const int32_t* picks, int32_t V,
+                               int32_t depot, int32_t max_k, uint8_t* node_flag,
+                               int32_t* order_status, cudaStream_t s);
+cudaError_t tour_launch_compact(int32_t V, const uint8_t* node_flag, int32_t* src_index,
+                                int32_t* src_list, int32_t* n_src, int32_t* block_sums,
+                                cudaStream_t s, int* launches);
+cudaError_t tour_launch_gather(int32_t n, const TourBufs& t, int32_t depot, const int32_t* src_index,
+                               const BfSegment& seg, cudaStream_t s);
+cudaError_t tour_launch_prepare_given(int32_t n, const int32_t* k, const int32_t* Din, int32_t max_k,
+                                      const TourBufs& t, cudaStream_t s);
+cudaError_t tour_launch_units(int32_t n, const int32_t* k_given, const TourBufs& t, cudaStream_t s,
+                              int* launches);
+cudaError_t tour_launch_enum(int32_t n, const int32_t* k_given, const TourBufs& t, long long u_begin,
+                             long long u_end, int units_per_thread, int blocks, cudaStream_t s);
+cudaError_t tour_launch_finish(int32_t n, const int32_t* k_given, const TourBufs& t, int32_t* cost,
+                               int32_t* perm, int perm_stride, int32_t* status, cudaStream_t s);
+int tour_enum_blocks(int device);
+
+}  // namespace wr

@@ -1,0 +1,623 @@
+// Rows a2 and a4-a7: source selection, D gather, exhaustive sequence
+// evaluation with rank-range segments, reduction and result decode.
+//
+// Sec. 4.6 evaluates all n! route permutations, one thread per permutation
+// and an inner loop over the transitions.  Here a thread owns a contiguous
+// range of "units": a unit fixes the first k-5 picks of the sequence (its
+// prefix, decoded from the unit index in the factorial number system) and
+// covers the 5! = 120 orderings of the remaining five picks, all costed in
+// registers from a tiny table of the legs among those picks.  Every one of
+// the k! sequences still gets its full cost computed; shared partial sums
+// only avoid re-adding the same legs.  A thread keeps the minimum of each
+// unit; only when a unit beats the thread's best does it look for the
+// lowest-rank sequence attaining it.  Units are visited in increasing rank,
+// so strict '<' keeps the lowest rank.  Segment minima are merged into one
+// 64-bit word per order, (cost << 32) | rank, with atomicMin: the
+// lexicographic (cost, rank) minimum, independent of scheduling.
+#include "wr_device.cuh"
+
+namespace wr {
+
+// ---------------------------------------------------------------------------
+// a2: source selection
+// ---------------------------------------------------------------------------
+
+__global__ void select_kernel(int32_t n, const int64_t* __restrict__ offs, const int32_t* __restrict__ picks,
+                              int32_t V, int32_t depot, int32_t max_k, uint8_t* node_flag, int32_t* order_status) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o == 0) node_flag[depot] = 1;
+    if (o >= n) return;
+    const int64_t b = offs[o], e = offs[o + 1];
+    const int64_t k = e - b;
+    int st = WR_ORDER_OK;
+    if (k < 1 || k > max_k || b < 0 || e > offs[n]) {
+        st = WR_ORDER_BAD;
+    } else {
+        for (int64_t i = b; i < e; ++i)
+            if (picks[i] < 0 || picks[i] >= V) st = WR_ORDER_BAD;
+        if (st == WR_ORDER_OK)
+            for (int64_t i = b; i < e; ++i) node_flag[picks[i]] = 1;
+    }
+    order_status[o] = st;
+}
+
+cudaError_t tour_launch_select(int32_t n, const int64_t* offs, const int32_t* picks, int32_t V, int32_t depot,
+                               int32_t max_k, uint8_t* node_flag, int32_t* order_status, cudaStream_t s) {
+    select_kernel<<<(n + 255) / 256 + (n == 0), 256, 0, s>>>(n, offs, picks, V, depot, max_k, node_flag,
+                                                              order_status);
+    return cudaGetLastError();
+}
+
+// Compaction of node_flag into the ascending source list and node -> source index.
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ int block_exclusive_scan(int x, int* warp_sums, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(FULL_MASK, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int ws = lane < (blockDim.x >> 5) ? warp_sums[lane] : 0;
+        int wi = ws;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(FULL_MASK, wi, d);
+            if (lane >= d) wi += y;
+        }
+        warp_sums[lane] = wi - ws;
+        if (lane == 31) *total = wi;
+    }
+    __syncthreads();
+    const int r = warp_sums[warp] + inc - x;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) compact_count_kernel(int32_t V, const uint8_t* __restrict__ flag,
+                                                                       int32_t* block_sums) {
+    __shared__ int ws[32];
+    __shared__ int tot;
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    int c = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q)
+        if (base + q < V) c += flag[base + q];
+    block_exclusive_scan(c, ws, &tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) compact_top_kernel(int32_t nb, int32_t* block_sums, int32_t* n_src) {
+    __shared__ int ws[32];
+    __shared__ int tot;
+    int carry = 0;
+    for (int base = 0; base < nb; base += SCAN_THREADS) {
+        const int i = base + threadIdx.x;
+        const int x = i < nb ? block_sums[i] : 0;
+        const int ex = block_exclusive_scan(x, ws, &tot);
+        if (i < nb) block_sums[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_src = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) compact_apply_kernel(int32_t V, const uint8_t* __restrict__ flag,
+                                                                       const int32_t* __restrict__ block_sums,
+                                                                       int32_t* src_index, int32_t* src_list) {
+    __shared__ int ws[32];
+    __shared__ int tot;
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    int f[SCAN_ITEMS];
+    int c = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        f[q] = (base + q < V) ? flag[base + q] : 0;
+        c += f[q];
+    }
+    int pos = block_sums[blockIdx.x] + block_exclusive_scan(c, ws, &tot);
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        if (base + q < V) {
+            const int32_t v = static_cast<int32_t>(base + q);
+            if (f[q]) {
+                src_index[v] = pos;
+                src_list[pos] = v;
+                ++pos;
+            } else {
+                src_index[v] = -1;
+            }
+        }
+    }
+}
+
+cudaError_t tour_launch_compact(int32_t V, const uint8_t* node_flag, int32_t* src_index, int32_t* src_list,
+                                int32_t* n_src, int32_t* block_sums, cudaStream_t s, int* launches) {
+    const int nb = (V + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    compact_count_kernel<<<nb, SCAN_THREADS, 0, s>>>(V, node_flag, block_sums);
+    compact_top_kernel<<<1, SCAN_THREADS, 0, s>>>(nb, block_sums, n_src);
+    compact_apply_kernel<<<nb, SCAN_THREADS, 0, s>>>(V, node_flag, block_sums, src_index, src_list);
+    *launches += 3;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a4: D gather.  D[i][j] = dist(P_i, P_j), P_0 = depot; the row of P_i lives
+// in the segment holding its source index.  Unreachable legs become TOUR_CAP;
+// a finite leg above WR_LEG_MAX flags the order.
+// ---------------------------------------------------------------------------
+
+__global__ void gather_kernel(int32_t n, TourBufs t, int32_t depot, const int32_t* __restrict__ src_index,
+                              BfSegment seg) {
+    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (o >= n) return;
+    if (t.order_status[o] != WR_ORDER_OK) return;
+    const int64_t b = t.offs[o];
+    const int k = static_cast<int>(t.offs[o + 1] - b);
+    const int m = k + 1;
+    bool range = false;
+    for (int e = lane; e < m * m; e += 32) {
+        const int i = e / m, j = e - i * m;
+        const int32_t pi = i == 0 ? depot : t.picks[b + i - 1];
+        const int32_t si = src_index[pi] - seg.first;
+        if (si < 0 || si >= seg.lanes) continue;
+        const int32_t pj = j == 0 ? depot : t.picks[b + j - 1];
+        uint32_t val = __ldcg(seg.rows + static_cast<int64_t>(pj) * seg.ld + si);
+        if (val == INF_U) {
+            val = TOUR_CAP;
+        } else if (val > static_cast<uint32_t>(WR_LEG_MAX) && i != j) {
+            range = true;
+        }
+        t.D[static_cast<int64_t>(o) * DBLOCK + i * DSTRIDE + j] = val;
+    }
+    if (__any_sync(FULL_MASK, range) && lane == 0) atomicOr(t.order_flags + o, ORDER_FLAG_RANGE);
+}
+
+cudaError_t tour_launch_gather(int32_t n, const TourBufs& t, int32_t depot, const int32_t* src_index,
+                               const BfSegment& seg, cudaStream_t s) {
+    gather_kernel<<<(n + 7) / 8, 256, 0, s>>>(n, t, depot, src_index, seg);
+    return cudaGetLastError();
+}
+
+// Given matrices (wr_tour_eval): validate k, clamp, flag range.
+__global__ void prepare_given_kernel(int32_t n, const int32_t* __restrict__ kk, const int32_t* __restrict__ Din,
+                                     int32_t max_k, TourBufs t) {
+    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (o >= n) return;
+    const int k = kk[o];
+    if (k < 1 || k > max_k) {
+        if (lane == 0) {
+            t.order_status[o] = WR_ORDER_BAD;
+            t.order_flags[o] = 0;
+        }
+        return;
+    }
+    const int m = k + 1;
+    bool range = false;
+    for (int e = lane; e < m * m; e += 32) {
+        const int i = e / m, j = e - i * m;
+        uint32_t val = static_cast<uint32_t>(Din[static_cast<int64_t>(o) * DBLOCK + i * DSTRIDE + j]);
+        if (val == INF_U) {
+            val = TOUR_CAP;
+        } else if (i != j && val > static_cast<uint32_t>(WR_LEG_MAX)) {  // negatives land here too
+            range = true;
+        }
+        t.D[static_cast<int64_t>(o) * DBLOCK + i * DSTRIDE + j] = val;
+    }
+    const bool any = __any_sync(FULL_MASK, range);
+    if (lane == 0) {
+        t.order_status[o] = WR_ORDER_OK;
+        t.order_flags[o] = any ? ORDER_FLAG_RANGE : 0;
+    }
+}
+
+cudaError_t tour_launch_prepare_given(int32_t n, const int32_t* k, const int32_t* Din, int32_t max_k,
+                                      const TourBufs& t, cudaStream_t s) {
+    prepare_given_kernel<<<(n + 7) / 8, 256, 0, s>>>(n, k, Din, max_k, t);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// units per order and their exclusive prefix (one block)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int order_k(const TourBufs& t, const int32_t* k_given, int o) {
+    return k_given ? k_given[o] : static_cast<int>(t.offs[o + 1] - t.offs[o]);
+}
+
+__device__ __forceinline__ long long units_of(int k) {
+    // k! / min(k, TAIL)!
+    long long u = 1;
+    for (int i = TAIL + 1; i <= k; ++i) u *= i;
+    return u;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) units_kernel(int32_t n, const int32_t* k_given, TourBufs t) {
+    __shared__ long long ws[32];
+    __shared__ long long tot;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long carry = 0;
+    for (int base = 0; base < n; base += SCAN_THREADS) {
+        const int o = base + threadIdx.x;
+        long long x = 0;
+        if (o < n) {
+            t.best[o] = ~0ull;
+            if (t.order_status[o] == WR_ORDER_OK && !(t.order_flags[o] & ORDER_FLAG_RANGE))
+                x = units_of(order_k(t, k_given, o));
+        }
+        long long inc = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const long long y = __shfl_up_sync(FULL_MASK, inc, d);
+            if (lane >= d) inc += y;
+        }
+        if (lane == 31) ws[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const long long w0 = ws[lane];
+            long long wi = w0;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const long long y = __shfl_up_sync(FULL_MASK, wi, d);
+                if (lane >= d) wi += y;
+            }
+            ws[lane] = wi - w0;
+            if (lane == 31) tot = wi;
+        }
+        __syncthreads();
+        if (o < n) t.unit_off[o] = carry + ws[warp] + inc - x;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        t.unit_off[n] = carry;
+        *t.unit_ctr = 0ull;
+    }
+}
+
+cudaError_t tour_launch_units(int32_t n, const int32_t* k_given, const TourBufs& t, cudaStream_t s, int* launches) {
+    units_kernel<<<1, SCAN_THREADS, 0, s>>>(n, k_given, t);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a5/a6: enumeration
+// ---------------------------------------------------------------------------
+
+// Leg tables of one unit, indexed by tail position (compile-time indices only,
+// so everything lives in registers).
+template <int L>
+struct Tab {
+    uint32_t x[L];        // D[x][t_i], x = last prefix node (or the depot)
+    uint32_t d[L][L];     // D[t_i][t_j]
+    uint32_t h[L];        // D[t_i][0]
+    uint32_t t3[L][L][L];  // D[t_a][t_b] + D[t_b][t_c] + D[t_c][0] (distinct a, b, c)
+};
+
+template <unsigned M>
+struct Bits {
+    static constexpr int count = (M & 1u) + Bits<(M >> 1)>::count;
+    static constexpr int low = (M & 1u) ? 0 : 1 + Bits<(M >> 1)>::low;
+};
+template <>
+struct Bits<0u> {
+    static constexpr int count = 0;
+    static constexpr int low = 64;
+};
+
+template <int L, unsigned M, int CUR>
+struct Walk;
+
+// Visit the elements of M in increasing order (lexicographic order of the sequences).
+template <int L, unsigned M, unsigned REST, int CUR>
+struct EachChild {
+    static __device__ __forceinline__ void run(uint32_t acc, const Tab<L>& T, uint32_t& mn) {
+        if constexpr (REST != 0u) {
+            constexpr int i = Bits<REST>::low;
+            const uint32_t leg = CUR < 0 ? T.x[i] : T.d[CUR < 0 ? 0 : CUR][i];
+            Walk<L, (M & ~(1u << i)), i>::run(acc + leg, T, mn);
+            EachChild<L, M, (REST & ~(1u << i)), CUR>::run(acc, T, mn);
+        }
+    }
+};
+
+template <int L, unsigned M, int CUR>
+struct Walk {
+    static __device__ __forceinline__ void run(uint32_t acc, const Tab<L>& T, uint32_t& mn) {
+        constexpr int n = Bits<M>::count;
+        if constexpr (n == 0) {
+            mn = __viaddmin_u32(acc, T.h[CUR], mn);
+        } else if constexpr (n == 2 && CUR >= 0) {
+            constexpr int b = Bits<M>::low;
+            constexpr int c = Bits<(M & ~(1u << b))>::low;
+            mn = __viaddmin_u32(acc, T.t3[CUR][b][c], mn);
+            mn = __viaddmin_u32(acc, T.t3[CUR][c][b], mn);
+        } else {
+            EachChild<L, M, M, CUR>::run(acc, T, mn);
+        }
+    }
+};
+
+template <int L>
+__device__ __forceinline__ void load_tab(Tab<L>& T, const uint32_t* __restrict__ Dm, int x, const int (&t)[TAIL]) {
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        T.x[i] = __ldg(Dm + x * DSTRIDE + t[i]);
+        T.h[i] = __ldg(Dm + t[i] * DSTRIDE);
+#pragma unroll
+        for (int j = 0; j < L; ++j)
+            if (i != j) T.d[i][j] = __ldg(Dm + t[i] * DSTRIDE + t[j]);
+    }
+    if constexpr (L >= 3) {
+#pragma unroll
+        for (int b = 0; b < L; ++b)
+#pragma unroll
+            for (int c = 0; c < L; ++c) {
+                if (b == c) continue;
+                const uint32_t tail2 = T.d[b][c] + T.h[c];
+#pragma unroll
+                for (int a = 0; a < L; ++a)
+                    if (a != b && a != c) T.t3[a][b][c] = T.d[a][b] + tail2;
+            }
+    }
+}
+
+// Minimum over the L! orderings of the tail (prefix cost P, last node x).
+template <int L>
+__device__ __forceinline__ uint32_t unit_min(const uint32_t* __restrict__ Dm, uint32_t P, int x, const int (&t)[TAIL]) {
+    Tab<L> T;
+    load_tab<L>(T, Dm, x, t);
+    uint32_t mn = 0xFFFFFFFFu;
+    Walk<L, (1u << L) - 1u, -1>::run(P, T, mn);
+    return mn;
+}
+
+// Rare path: lexicographic index of the first tail ordering costing target.
+__device__ __noinline__ int unit_find(const uint32_t* __restrict__ Dm, uint32_t P, int x, const int* t, int L,
+                                      uint32_t target) {
+    int nf = 1;
+    for (int i = 2; i <= L; ++i) nf *= i;
+    for (int idx = 0; idx < nf; ++idx) {
+        int used = 0, rem = idx, f = nf, prev = x;
+        uint32_t c = P;
+        for (int pos = 0; pos < L; ++pos) {
+            f /= (L - pos);
+            int digit = rem / f;
+            rem -= digit * f;
+            int e = 0;
+            for (;; ++e) {
+                if (used & (1 << e)) continue;
+                if (digit == 0) break;
+                --digit;
+            }
+            used |= 1 << e;
+            c += __ldg(Dm + prev * DSTRIDE + t[e]);
+            prev = t[e];
+        }
+        c += __ldg(Dm + prev * DSTRIDE);
+        if (c == target) return idx;
+    }
+    return nf - 1;  // unreachable: target came from one of these sequences
+}
+
+__device__ __forceinline__ uint32_t unit_min_dispatch(int L, const uint32_t* Dm, uint32_t P, int x, const int (&t)[TAIL]) {
+    switch (L) {
+        case 1: return unit_min<1>(Dm, P, x, t);
+        case 2: return unit_min<2>(Dm, P, x, t);
+        case 3: return unit_min<3>(Dm, P, x, t);
+        case 4: return unit_min<4>(Dm, P, x, t);
+        default: return unit_min<5>(Dm, P, x, t);
+    }
+}
+
+// n-th (0-based) set bit of m.
+__device__ __forceinline__ int nth_bit(unsigned m, int n) {
+    for (int i = 0; i < n; ++i) m &= m - 1;
+    return __ffs(m) - 1;
+}
+
+// Enumerate the units [ulo, uhi) of one order (k picks, D block Dm); fold
+// the best (cost, rank) into *out.
+__device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, long long ulo, long long uhi,
+                                 unsigned long long* out, long long& seqs) {
+    const int L = k < TAIL ? k : TAIL;
+    const int p = k - L;  // prefix length
+    const int lfact = L == 1 ? 1 : L == 2 ? 2 : L == 3 ? 6 : L == 4 ? 24 : 120;
+    // decode the first unit: digits c_i in radix (k - i), i < p
+    unsigned digits = 0;  // 4 bits per position
+    {
+        long long u = ulo;
+        for (int i = p - 1; i >= 0; --i) {
+            const int r = k - i;
+            const int c = static_cast<int>(u % r);
+            u /= r;
+            digits |= static_cast<unsigned>(c) << (4 * i);
+        }
+    }
+    unsigned elems = 0;  // 4 bits per position: pick index 1..k
+    unsigned all = ((1u << k) - 1u) << 1;
+    unsigned avail_last = all;  // available set before the last prefix position
+    uint32_t S = 0;             // cost through position p-2
+    int pos_dirty = 0;          // first prefix position to recompute
+    uint32_t best_c = 0xFFFFFFFFu;
+    unsigned best_r = 0;
+    for (long long u = ulo; u < uhi; ++u) {
+        // (re)build prefix positions >= pos_dirty
+        if (pos_dirty < p) {
+            unsigned av = all;
+            uint32_t cost = 0;
+            int prev = 0;
+            for (int i = 0; i < p; ++i) {
+                int e;
+                if (i < pos_dirty) {
+                    e = (elems >> (4 * i)) & 15;
+                } else {
+                    e = nth_bit(av, (digits >> (4 * i)) & 15);
+                    elems = (elems & ~(15u << (4 * i))) | (static_cast<unsigned>(e) << (4 * i));
+                }
+                if (i == p - 1) {
+                    avail_last = av;
+                    S = cost;
+                }
+                cost += __ldg(Dm + prev * DSTRIDE + e);
+                av &= ~(1u << e);
+                prev = e;
+            }
+        }
+        int x = 0;
+        uint32_t P = 0;
+        unsigned tailset = all;
+        if (p > 0) {
+            x = (elems >> (4 * (p - 1))) & 15;
+            const int xp = p >= 2 ? ((elems >> (4 * (p - 2))) & 15) : 0;
+            P = S + __ldg(Dm + xp * DSTRIDE + x);
+            tailset = avail_last & ~(1u << x);
+        }
+        int t[TAIL];
+#pragma unroll
+        for (int i = 0; i < TAIL; ++i) {
+            t[i] = 0;
+            if (i < L) {
+                t[i] = __ffs(tailset) - 1;
+                tailset &= tailset - 1;
+            }
+        }
+        const uint32_t mn = unit_min_dispatch(L, Dm, P, x, t);
+        if (mn < best_c) {
+            best_c = mn;
+            best_r = static_cast<unsigned>(u) * static_cast<unsigned>(lfact) +
+                     static_cast<unsigned>(unit_find(Dm, P, x, t, L, mn));
+        }
+        // advance the mixed-radix counter of the prefix
+        if (p > 0) {
+            int i = p - 1;
+            for (; i >= 0; --i) {
+                const unsigned c = ((digits >> (4 * i)) & 15) + 1;
+                if (c < static_cast<unsigned>(k - i)) {
+                    digits = (digits & ~(15u << (4 * i))) | (c << (4 * i));
+                    break;
+                }
+                digits &= ~(15u << (4 * i));
+            }
+            if (i == p - 1) {
+                // only the last prefix element moves: next available pick above it
+                const unsigned above = avail_last & ~((2u << x) - 1u);
+                const int e = __ffs(above) - 1;
+                elems = (elems & ~(15u << (4 * (p - 1)))) | (static_cast<unsigned>(e) << (4 * (p - 1)));
+                pos_dirty = p;
+            } else {
+                pos_dirty = i < 0 ? 0 : i;
+            }
+        }
+    }
+    seqs += (uhi - ulo) * lfact;
+    const unsigned long long packed = (static_cast<unsigned long long>(best_c) << 32) | best_r;
+    if (packed < __ldcg(out)) atomicMin(out, packed);
+}
+
+constexpr int ENUM_THREADS = 256;
+
+__global__ void __launch_bounds__(ENUM_THREADS) enum_kernel(int32_t n, const int32_t* __restrict__ k_given, TourBufs t,
+                                                            long long u_begin, long long u_end, int upt) {
+    const int lane = threadIdx.x & 31;
+    const long long total = min(u_end, static_cast<long long>(__ldcg(t.unit_off + n)));
+    const long long chunk = 32ll * upt;
+    long long seqs = 0;
+    for (;;) {
+        long long c0 = 0;
+        if (lane == 0) c0 = static_cast<long long>(atomicAdd(t.unit_ctr, static_cast<unsigned long long>(chunk)));
+        c0 = __shfl_sync(FULL_MASK, c0, 0) + u_begin;
+        if (c0 >= total) break;
+        long long u = c0 + static_cast<long long>(lane) * upt;
+        const long long ue = min(u + upt, total);
+        while (u < ue) {
+            // order holding unit u: last o with unit_off[o] <= u
+            int lo = 0, hi = n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(t.unit_off + mid) <= u) lo = mid; else hi = mid - 1;
+            }
+            const int o = lo;
+            const long long ob = __ldg(t.unit_off + o), oe = __ldg(t.unit_off + o + 1);
+            const long long stop = min(ue, oe);
+            const int k = order_k(t, k_given, o);
+            enum_order_range(t.D + static_cast<int64_t>(o) * DBLOCK, k, u - ob, stop - ob, t.best + o, seqs);
+            u = stop;
+        }
+    }
+    if (seqs) atomicAdd(reinterpret_cast<unsigned long long*>(t.seq_count), static_cast<unsigned long long>(seqs));
+}
+
+int tour_enum_blocks(int device) {
+    int occ = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, enum_kernel, ENUM_THREADS, 0);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    return (occ < 1 ? 1 : occ) * (sms < 1 ? 1 : sms);
+}
+
+cudaError_t tour_launch_enum(int32_t n, const int32_t* k_given, const TourBufs& t, long long u_begin, long long u_end,
+                             int units_per_thread, int blocks, cudaStream_t s) {
+    enum_kernel<<<blocks, ENUM_THREADS, 0, s>>>(n, k_given, t, u_begin, u_end, units_per_thread);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a7: decode rank -> permutation, status
+// ---------------------------------------------------------------------------
+
+__global__ void finish_kernel(int32_t n, const int32_t* __restrict__ k_given, TourBufs t, int32_t* cost, int32_t* perm,
+                              int perm_stride, int32_t* status) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const long long k64 = k_given ? k_given[o] : (t.offs[o + 1] - t.offs[o]);
+    int32_t* pp = perm + (perm_stride > 0 ? static_cast<int64_t>(o) * perm_stride : t.offs[o]);
+    long long kw = perm_stride > 0 ? min(k64, static_cast<long long>(perm_stride)) : k64;
+    // an inconsistent pick range (only possible with device inputs) gets no perm writes
+    if (perm_stride == 0 && (t.offs[o] < 0 || t.offs[o + 1] > t.offs[n])) kw = 0;
+    int st = t.order_status[o];
+    if (st == WR_ORDER_OK && (t.order_flags[o] & ORDER_FLAG_RANGE)) st = WR_ORDER_RANGE;
+    uint32_t c = 0xFFFFFFFFu;
+    unsigned rank = 0;
+    if (st == WR_ORDER_OK) {
+        const unsigned long long b = t.best[o];
+        c = static_cast<uint32_t>(b >> 32);
+        rank = static_cast<unsigned>(b & 0xFFFFFFFFull);
+        if (c >= TOUR_CAP) st = WR_ORDER_UNREACHABLE;
+    }
+    status[o] = st;
+    if (st != WR_ORDER_OK) {
+        cost[o] = WR_INF;
+        for (long long i = 0; i < kw; ++i) pp[i] = static_cast<int32_t>(i);
+        return;
+    }
+    cost[o] = static_cast<int32_t>(c);
+    const int k = static_cast<int>(k64);
+    unsigned fact = 1;
+    for (int i = 2; i < k; ++i) fact *= i;  // (k-1)!
+    unsigned avail = (1u << k) - 1u;
+    for (int i = 0; i < k; ++i) {
+        const unsigned d = rank / fact;
+        rank -= d * fact;
+        if (k - 1 - i > 0) fact /= (k - 1 - i);
+        const int e = nth_bit(avail, static_cast<int>(d));
+        avail &= ~(1u << e);
+        pp[i] = e;
+    }
+}
+
+cudaError_t tour_launch_finish(int32_t n, const int32_t* k_given, const TourBufs& t, int32_t* cost, int32_t* perm,
+                               int perm_stride, int32_t* status, cudaStream_t s) {
+    finish_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, k_given, t, cost, perm, perm_stride, status);
+    return cudaGetLastError();
+}
+
+}  // namespace wr

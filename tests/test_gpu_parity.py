@@ -1,0 +1,241 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+All results are integers, so the bar is bit-exact equality: distance rows,
+tour costs, argmin permutations (the lexicographically first minimiser)
+and per-order statuses.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2504_20655_gb300 import synth
+from tests.graphs import random_graph
+
+pytestmark = pytest.mark.gpu
+INF = 2**31 - 1
+NT = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module")
+def wr():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2504_20655_gb300 import build, wroute
+    build.build()
+    return wroute
+
+
+@pytest.fixture(scope="module")
+def router(wr):
+    r = wr.Router(device=0)
+    yield r
+    r.close()
+
+
+def test_bf_rows_tiny_all_sources(router, orc):
+    g = synth.tiny_layout().build()
+    router.load_graph(g)
+    rows = router.bf_rows(np.arange(g.V, dtype=np.int32))
+    assert (rows == orc.floyd_warshall(g)).all()
+    st = router.stats()
+    assert st["sweeps"] >= 1 and st["bytes_alg"] > 0
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_bf_rows_random_graphs(router, orc, seed):
+    V = [1, 2, 7, 33, 100, 257, 600, 1500][seed]
+    g = random_graph(V, max(1, 3 * V), seed + 300, w_lo=0, w_hi=20 if seed % 2 else 1000)
+    router.load_graph(g)
+    src = np.arange(0, V, max(1, V // 70), dtype=np.int32)
+    rows = router.bf_rows(src)
+    ref = orc.sssp_rows(g, src, "dijkstra", NT)
+    assert (rows == ref).all()
+
+
+def test_bf_rows_high_in_degree(router, orc):
+    # a node with more in-neighbours than a tile holds: its halo spills to global reads
+    V = 700
+    u = np.concatenate([np.arange(1, V), np.zeros(V - 1, np.int64)])
+    v = np.concatenate([np.zeros(V - 1, np.int64), np.arange(1, V)])
+    w = synth.uniform_int(77, u.shape[0], 1, 50)
+    rp, col, wt = synth.csr_from_arcs(V, u, v, w)
+    g = synth.Graph(V=V, row_ptr=rp, col=col, w=wt, depot=0)
+    router.load_graph(g)
+    src = np.array([0, 5, 699, 350], np.int32)
+    assert (router.bf_rows(src) == orc.sssp_rows(g, src)).all()
+
+
+@pytest.mark.parametrize("tune", [dict(run_target=96, tile_cap=128), dict(run_target=32, tile_cap=64),
+                                  dict(run_target=200, tile_cap=256), dict(run_target=1, tile_cap=64)])
+def test_bf_rows_medium_tuning_invariant(router, orc, tune):
+    g = synth.medium_layout().build()
+    router.set_tuning(**tune)
+    router.load_graph(g)
+    src = synth.distinct_sources(200, g.n_slots, 17)
+    src = np.concatenate([src, [g.depot]]).astype(np.int32)
+    rows = router.bf_rows(src)
+    ref = orc.sssp_rows(g, src, "dijkstra", NT)
+    router.set_tuning(run_target=96, tile_cap=128)
+    assert (rows == ref).all()
+
+
+def test_bf_segments_small_budget(wr, orc):
+    g = synth.medium_layout().build()
+    r = wr.Router(device=0, mem_budget_bytes=g.V * 4 * 64)  # 64 lanes per segment
+    r.load_graph(g)
+    src = synth.distinct_sources(150, g.n_slots, 3)
+    rows = r.bf_rows(src)
+    assert r.stats()["n_segments"] == 3
+    assert (rows == orc.sssp_rows(g, src, "dijkstra", NT)).all()
+    r.close()
+
+
+def test_budget_too_small(wr):
+    g = synth.tiny_layout().build()
+    r = wr.Router(device=0, mem_budget_bytes=g.V * 4 * 16)
+    r.load_graph(g)
+    with pytest.raises(wr.WrError) as e:
+        r.bf_rows(np.array([1, 2], np.int32))
+    assert e.value.code == wr.WR_ENOMEM
+    r.close()
+
+
+def test_route_tiny(router, orc):
+    g, o = synth.tiny_workload()
+    router.load_graph(g)
+    cost, perm, status = router.route_orders(o.offs, o.picks)
+    c, p, s = orc.route_orders(g, o, "rounds", "brute")
+    assert (cost == c).all() and (perm == p).all() and (status == s).all()
+    st = router.stats()
+    assert st["sequences"] == 720 and st["n_sources"] == 7
+
+
+def test_route_medium_full(router, orc):
+    """The benchmark's workload: 1024 orders, k in [4, 10], Zipf picks, medium layout."""
+    g, o = synth.medium_workload()
+    router.load_graph(g)
+    cost, perm, status = router.route_orders(o.offs, o.picks)
+    c, p, s = orc.route_orders(g, o, "dijkstra", "brute", NT)
+    assert (status == s).all()
+    assert (cost == c).all()
+    assert (perm[:len(p)] == p).all()
+    st = router.stats()
+    assert st["sequences"] == sum(int(np.prod(np.arange(1, k + 1))) for k in o.k())
+
+
+def test_route_device_pointers_and_stream(router, orc):
+    import torch
+    g, o = synth.medium_workload(n_orders=64)
+    router.load_graph(g)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        offs = torch.from_numpy(o.offs).cuda()
+        picks = torch.from_numpy(o.picks).cuda()
+        cost, perm, status = router.route_orders(offs, picks)
+    s.synchronize()
+    router.sync()
+    c, p, st = orc.route_orders(g, o, "dijkstra", "brute", NT)
+    assert (cost.cpu().numpy() == c).all() and (perm.cpu().numpy() == p).all() and (status.cpu().numpy() == st).all()
+
+
+def test_route_statuses_and_edge_cases(router, orc):
+    g = synth.medium_layout().build()
+    router.load_graph(g)
+    V = g.V
+    orders = [[5], [5, 5], list(range(100, 112)), list(range(200, 213)), [], [3, V], [-1, 2],
+              [g.depot, 7, g.depot], [19999, 0, 10000, 15000, 5000, 12345, 54, 9999, 1, 2, 3]]
+    offs = np.zeros(len(orders) + 1, np.int64)
+    offs[1:] = np.cumsum([len(x) for x in orders])
+    picks = np.array([x for od in orders for x in od], np.int32)
+    o = synth.Orders(offs, picks)
+    cost, perm, status = router.route_orders(o.offs, o.picks)
+    c, p, s = orc.route_orders(g, o, "dijkstra", "heldkarp", NT)
+    assert status.tolist() == s.tolist() == [0, 0, 0, 2, 2, 2, 2, 0, 0]
+    assert (cost == c).all() and (perm[:len(p)] == p).all()
+
+
+def test_route_unreachable(router, orc):
+    # directed chain 0 -> 1 -> 2 -> 3, depot 0: picks behind the depot cannot return
+    V = 6
+    u = np.array([0, 1, 2, 3, 4]); v = np.array([1, 2, 3, 0, 5]); w = np.array([3, 4, 5, 6, 1])
+    rp, col, wt = synth.csr_from_arcs(V, u, v, w)
+    g = synth.Graph(V=V, row_ptr=rp, col=col, w=wt, depot=0)
+    router.load_graph(g)
+    o = synth.Orders(np.array([0, 2, 3, 5], np.int64), np.array([1, 2, 5, 3, 1], np.int32))
+    cost, perm, status = router.route_orders(o.offs, o.picks)
+    c, p, s = orc.route_orders(g, o, "rounds", "brute")
+    assert status.tolist() == s.tolist() == [0, 1, 0]
+    assert cost.tolist() == c.tolist() and perm.tolist() == p.tolist()
+
+
+def _rand_D(n, k, seed, hi, p_inf=0.0):
+    m = k + 1
+    D = synth.uniform_int(seed, n * 169, 0, hi).reshape(n, 13, 13).astype(np.int64)
+    if p_inf:
+        D = np.where(synth.uniform01(seed ^ 5, n * 169).reshape(n, 13, 13) < p_inf, INF, D)
+    for i in range(13):
+        D[:, i, i] = 0
+    return D.astype(np.int32), m
+
+
+@pytest.mark.parametrize("k", range(1, 11))
+def test_tour_eval_vs_brute(router, orc, k):
+    n = 24 if k <= 8 else 6
+    for hi, p_inf in ((3, 0.0), (500, 0.0), (40, 0.15)):
+        D, m = _rand_D(n, k, 1000 * k + hi, hi, p_inf)
+        kk = np.full(n, k, np.int32)
+        cost, perm, status = router.tour_eval(kk, D)
+        for i in range(n):
+            st, c, p = orc.tour(D[i, :m, :m], "brute")
+            assert status[i] == st and cost[i] == c and perm[i, :k].tolist() == p.tolist(), (k, hi, i)
+
+
+@pytest.mark.parametrize("k", [11, 12])
+def test_tour_eval_vs_held_karp(router, orc, k):
+    n = 3
+    for hi in (2, 1000):
+        D, m = _rand_D(n, k, 77 * k + hi, hi)
+        cost, perm, status = router.tour_eval(np.full(n, k, np.int32), D)
+        for i in range(n):
+            st, c, p = orc.tour(D[i, :m, :m], "heldkarp")
+            assert status[i] == st and cost[i] == c and perm[i, :k].tolist() == p.tolist()
+
+
+def test_tour_eval_statuses(router, orc):
+    D, _ = _rand_D(4, 6, 9, 100)
+    kk = np.array([0, 13, 6, 6], np.int32)
+    D[3, 1, 2] = 10324441
+    cost, perm, status = router.tour_eval(kk, D)
+    assert status.tolist() == [2, 2, 0, 3]
+    assert cost[3] == INF and perm[3, :6].tolist() == list(range(6))
+
+
+@pytest.mark.parametrize("units,per_launch", [(1, 0), (16, 0), (4, 7), (2, 1000)])
+def test_enumeration_segment_invariance(router, orc, units, per_launch):
+    D, m = _rand_D(6, 9, 4242, 4)  # heavy ties
+    kk = np.array([9, 8, 7, 9, 5, 3], np.int32)
+    base = router.tour_eval(kk, D)
+    router.set_tuning(enum_units=units, enum_max_units_per_launch=per_launch)
+    try:
+        got = router.tour_eval(kk, D)
+    finally:
+        router.set_tuning(enum_units=4, enum_max_units_per_launch=0)
+    for a, b in zip(base, got):
+        assert (a == b).all()
+    for i, k in enumerate(kk):
+        st, c, p = orc.tour(D[i, :k + 1, :k + 1], "brute")
+        assert got[0][i] == c and got[1][i, :k].tolist() == p.tolist()
+
+
+def test_batching_sample(router, orc):
+    """Orders of uneven size (k = 2..12) from the batching workload, Held-Karp-lex oracle."""
+    g, o = synth.batching_workload()
+    k = o.k()
+    idx = np.concatenate([np.nonzero(k == kk)[0][:6] for kk in range(2, 13)])
+    sub = o.subset(idx)
+    router.load_graph(g)
+    cost, perm, status = router.route_orders(sub.offs, sub.picks)
+    c, p, s = orc.route_orders(g, sub, "dijkstra", "heldkarp", NT)
+    assert (status == s).all() and (cost == c).all() and (perm[:len(p)] == p).all()
