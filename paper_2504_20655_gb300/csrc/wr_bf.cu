@@ -203,13 +203,14 @@ __global__ void __launch_bounds__(NW * 32) bf_sweeps_kernel(BfParams p) {
     const int gwarp = blockIdx.x * NW + warp;
     const int nwarps = gridDim.x * NW;
 
-    // seeds: the tile holding each source, stamp 1
+    // seeds: writing d[s][s] = 0 is the change of "sweep 0": the tile holding
+    // each source gets stamp 1, and sweep 1 visits it and the tiles it feeds
     for (int b = gtid; b < n_lanes; b += nthreads) {
         const int r = __ldg(p.g.run_of_node + p.seg.src[p.seg.first + b]);
         p.w.stamp[static_cast<int64_t>(r) * G + (b >> 5)] = 1;
     }
     if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) return;
-    build_list(p, G, 1, false, p.w.list0, p.w.counts + 0);
+    build_list(p, G, 1, true, p.w.list0, p.w.counts + 0);
     if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) return;
 
     unsigned long long tiles = 0, nodes = 0, bytes = 0;

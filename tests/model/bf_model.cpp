@@ -1,0 +1,151 @@
+// Sequential CPU model of the Bellman-Ford sweep kernel, for the CPU tests.
+// It runs the library's own graph preprocessing (wr_graph.cpp) and replays
+// the kernel's per-tile forward/backward passes and frontier rules one tile
+// at a time, so the algorithm (not the GPU) can be checked against the
+// oracle without a device.  It also checks the partition's invariants.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "wr_internal.h"
+
+using namespace wr;
+
+extern "C" int bfm_rows(int V, long long E, const long long* rp, const int* col, const int* w, int n_src,
+                        const int* src, int run_target, int tile_cap, int* out, int* sweeps_out) {
+    HostGraph g;
+    int rc = build_host_graph(V, E, reinterpret_cast<const int64_t*>(rp), col, w, 0, g);
+    if (rc) return rc;
+    HostPartition p;
+    build_partition(g, run_target, tile_cap, p);
+    const int G = (n_src + 31) / 32;
+    const size_t ld = static_cast<size_t>(G) * 32;
+    std::vector<uint32_t> rows(static_cast<size_t>(V) * ld, INF_U);
+    for (int b = 0; b < n_src; ++b) rows[static_cast<size_t>(src[b]) * ld + b] = 0;
+    std::vector<int> stamp(static_cast<size_t>(p.n_runs) * G, 0);
+    for (int b = 0; b < n_src; ++b) stamp[static_cast<size_t>(p.run_of_node[src[b]]) * G + b / 32] = 1;
+    auto build = [&](int match) {
+        std::vector<int> l;
+        for (int it = 0; it < p.n_runs * G; ++it) {
+            const int r = it / G, gg = it % G;
+            bool act = stamp[it] == match;
+            for (int q = p.rin_ptr[r]; !act && q < p.rin_ptr[r + 1]; ++q)
+                act = stamp[static_cast<size_t>(p.rin_list[q]) * G + gg] == match;
+            if (act) l.push_back(it);
+        }
+        return l;
+    };
+    std::vector<int> list = build(1);
+    int sweep = 1;
+    std::vector<uint32_t> tile(static_cast<size_t>(tile_cap));
+    for (;; ++sweep) {
+        if (list.empty()) break;
+        if (sweep > V + 1) return 99;
+        for (int item : list) {
+            const int r = item / G, gg = item % G;
+            const int r0 = p.run_ptr[r], len = p.run_ptr[r + 1] - r0;
+            const int h0 = p.halo_ptr[r], hn = p.halo_ptr[r + 1] - h0;
+            if (len + hn > tile_cap) return 98;
+            bool changed = false;
+            for (int lane = 0; lane < 32; ++lane) {
+                const size_t c = static_cast<size_t>(gg) * 32 + lane;
+                for (int i = 0; i < len; ++i) tile[i] = rows[static_cast<size_t>(r0 + i) * ld + c];
+                for (int h = 0; h < hn; ++h) tile[len + h] = rows[static_cast<size_t>(p.halo_nodes[h0 + h]) * ld + c];
+                std::vector<char> dirty(static_cast<size_t>(len), 0);
+                uint32_t carry = INF_U;
+                for (int i = 0; i < len; ++i) {
+                    const int4 d = p.node_desc[r0 + i];
+                    const uint32_t cur = tile[i];
+                    uint32_t best = std::min(carry + static_cast<uint32_t>(d.x), cur);
+                    for (int a = d.z; a < d.w; ++a) {
+                        const uint32_t ref = p.arc_ref[a];
+                        const uint32_t x = (ref & GLOBAL_REF) ? rows[static_cast<size_t>(ref & ~GLOBAL_REF) * ld + c] : tile[ref];
+                        best = std::min(x + p.arc_w[a], best);
+                    }
+                    if (best < cur) { tile[i] = best; dirty[i] = 1; changed = true; }
+                    carry = best;
+                }
+                carry = INF_U;
+                int nb = p.node_desc[r0 + len].z;
+                for (int i = len - 1; i >= 0; --i) {
+                    const int4 d = p.node_desc[r0 + i];
+                    const uint32_t cur = tile[i];
+                    uint32_t best = std::min(carry + static_cast<uint32_t>(d.y), cur);
+                    for (int a = d.w; a < nb; ++a) best = std::min(tile[p.arc_ref[a]] + p.arc_w[a], best);
+                    nb = d.z;
+                    if (best < cur) { tile[i] = best; dirty[i] = 1; changed = true; }
+                    carry = best;
+                }
+                for (int i = 0; i < len; ++i)
+                    if (dirty[i]) rows[static_cast<size_t>(r0 + i) * ld + c] = tile[i];
+            }
+            if (changed) stamp[item] = sweep + 1;
+        }
+        list = build(sweep + 1);
+    }
+    *sweeps_out = sweep - 1;
+    for (int b = 0; b < n_src; ++b)
+        for (int v = 0; v < V; ++v) out[static_cast<size_t>(b) * V + v] = static_cast<int>(rows[static_cast<size_t>(v) * ld + b]);
+    return 0;
+}
+
+// Partition invariants; returns 0 or a non-zero code naming the broken rule.
+extern "C" int bfm_check_partition(int V, long long E, const long long* rp, const int* col, const int* w,
+                                   int run_target, int tile_cap, int* n_runs_out) {
+    HostGraph g;
+    if (build_host_graph(V, E, reinterpret_cast<const int64_t*>(rp), col, w, 0, g)) return 1;
+    HostPartition p;
+    build_partition(g, run_target, tile_cap, p);
+    *n_runs_out = p.n_runs;
+    if (p.run_ptr.front() != 0 || p.run_ptr.back() != V) return 2;
+    for (int r = 0; r < p.n_runs; ++r) {
+        const int s = p.run_ptr[r], e = p.run_ptr[r + 1], len = e - s;
+        if (len < 1 || len > run_target) return 3;
+        const int hn = p.halo_ptr[r + 1] - p.halo_ptr[r];
+        if (len + hn > tile_cap) return 4;
+        for (int v = s; v < e; ++v)
+            if (p.run_of_node[v] != r) return 5;
+        // every in-arc of the run's nodes appears exactly once, with its weight
+        std::vector<int> halo(p.halo_nodes.begin() + p.halo_ptr[r], p.halo_nodes.begin() + p.halo_ptr[r + 1]);
+        std::vector<int> runs_in;
+        for (int v = s; v < e; ++v) {
+            const int4 d = p.node_desc[v];
+            std::vector<std::pair<int, uint32_t>> got;
+            if (static_cast<uint32_t>(d.x) != NO_CARRY) got.emplace_back(v - 1, static_cast<uint32_t>(d.x));
+            if (static_cast<uint32_t>(d.y) != NO_CARRY) got.emplace_back(v + 1, static_cast<uint32_t>(d.y));
+            const int end = p.node_desc[v + 1].z;
+            for (int a = d.z; a < end; ++a) {
+                const uint32_t ref = p.arc_ref[a];
+                int u;
+                if (ref & GLOBAL_REF) u = static_cast<int>(ref & ~GLOBAL_REF);
+                else if (static_cast<int>(ref) < len) u = s + static_cast<int>(ref);
+                else {
+                    if (static_cast<int>(ref) - len >= hn) return 6;
+                    u = halo[ref - len];
+                }
+                const bool fw = a < d.w;
+                if (u >= s && u < e) {
+                    if (fw && !(u < v)) return 7;   // forward arcs come from lower ids
+                    if (!fw && !(u > v)) return 8;  // backward arcs from higher ids
+                } else if (!fw) {
+                    return 9;  // out-of-run sources are read in the forward pass
+                }
+                got.emplace_back(u, p.arc_w[a]);
+            }
+            std::vector<std::pair<int, uint32_t>> want;
+            for (int64_t a = g.in_ptr[v]; a < g.in_ptr[v + 1]; ++a)
+                want.emplace_back(g.in_src[a], static_cast<uint32_t>(g.in_w[a]));
+            std::sort(got.begin(), got.end());
+            if (got != want) return 10;
+            for (auto& pr : want)
+                if (pr.first < s || pr.first >= e) runs_in.push_back(p.run_of_node[pr.first]);
+        }
+        std::sort(runs_in.begin(), runs_in.end());
+        runs_in.erase(std::unique(runs_in.begin(), runs_in.end()), runs_in.end());
+        std::vector<int> rin(p.rin_list.begin() + p.rin_ptr[r], p.rin_list.begin() + p.rin_ptr[r + 1]);
+        std::sort(rin.begin(), rin.end());
+        if (rin != runs_in) return 11;
+    }
+    return 0;
+}

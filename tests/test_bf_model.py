@@ -1,0 +1,106 @@
+"""Host logic of the Bellman-Ford path, on the CPU.
+
+tests/model/bf_model.cpp runs the library's graph preprocessing
+(wr_graph.cpp) and replays the sweep kernel's tile passes and frontier
+rules sequentially.  The tests check the partition's invariants and that
+the replayed sweeps reach the oracle's distances for several tilings.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2504_20655_gb300 import synth
+from tests.graphs import random_graph
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CUDA_INC = "/usr/local/cuda/include"
+
+
+@pytest.fixture(scope="module")
+def model(tmp_path_factory):
+    so = str(tmp_path_factory.mktemp("bfm") / "libbfm.so")
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I", os.path.join(ROOT, "include"),
+                           "-I", os.path.join(ROOT, "paper_2504_20655_gb300", "csrc"), "-I", CUDA_INC,
+                           os.path.join(HERE, "model", "bf_model.cpp"),
+                           os.path.join(ROOT, "paper_2504_20655_gb300", "csrc", "wr_graph.cpp"), "-o", so])
+    return ctypes.CDLL(so)
+
+
+def _arrs(g):
+    return (np.ascontiguousarray(g.row_ptr, np.int64), np.ascontiguousarray(g.col, np.int32),
+            np.ascontiguousarray(g.w, np.int32))
+
+
+def model_rows(model, g, src, run_target, tile_cap):
+    P = ctypes.c_void_p
+    rp, c, w = _arrs(g)
+    src = np.ascontiguousarray(src, np.int32)
+    out = np.empty((len(src), g.V), np.int32)
+    sw = np.zeros(1, np.int32)
+    rc = model.bfm_rows(g.V, ctypes.c_longlong(g.E), rp.ctypes.data_as(P), c.ctypes.data_as(P), w.ctypes.data_as(P),
+                        len(src), src.ctypes.data_as(P), run_target, tile_cap, out.ctypes.data_as(P),
+                        sw.ctypes.data_as(P))
+    assert rc == 0, rc
+    return out, int(sw[0])
+
+
+def check_partition(model, g, run_target, tile_cap):
+    P = ctypes.c_void_p
+    rp, c, w = _arrs(g)
+    nr = np.zeros(1, np.int32)
+    rc = model.bfm_check_partition(g.V, ctypes.c_longlong(g.E), rp.ctypes.data_as(P), c.ctypes.data_as(P),
+                                   w.ctypes.data_as(P), run_target, tile_cap, nr.ctypes.data_as(P))
+    return rc, int(nr[0])
+
+
+TILINGS = [(96, 128), (32, 64), (200, 256), (1, 64), (64, 64)]
+
+
+@pytest.mark.parametrize("rt,tc", TILINGS)
+def test_partition_invariants(model, rt, tc):
+    graphs = [random_graph(V, 3 * V, V + 5, w_lo=0, w_hi=100) for V in (1, 5, 100, 700)]
+    graphs += [synth.tiny_layout().build(), synth.medium_layout().build()]
+    for g in graphs:
+        rc, n_runs = check_partition(model, g, rt, tc)
+        assert rc == 0, (g.V, rc)
+        assert n_runs >= (g.V + rt - 1) // rt
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_model_sweeps_random(model, orc, seed):
+    V = [1, 2, 7, 33, 100, 257, 600, 1500][seed]
+    g = random_graph(V, max(1, 3 * V), seed + 300, w_lo=0, w_hi=20 if seed % 2 else 1000)
+    src = np.arange(0, V, max(1, V // 70), dtype=np.int32)
+    ref = orc.sssp_rows(g, src, "dijkstra", 4)
+    for rt, tc in TILINGS:
+        out, sweeps = model_rows(model, g, src, rt, tc)
+        assert (out == ref).all(), (rt, tc)
+        assert sweeps <= V + 1
+
+
+def test_model_sweeps_medium_layout(model, orc):
+    g = synth.medium_layout().build()
+    src = synth.distinct_sources(64, g.n_slots, 17)
+    ref = orc.sssp_rows(g, src, "dijkstra", 4)
+    for rt, tc in ((96, 128), (200, 256)):
+        out, sweeps = model_rows(model, g, src, rt, tc)
+        assert (out == ref).all()
+        # far fewer sweeps than the hop diameter a Jacobi round count needs
+        _, rounds = orc.bf_rounds(g, int(src[0]))
+        assert sweeps < rounds
+
+
+def test_high_in_degree_spills_to_global(model, orc):
+    V = 700
+    u = np.concatenate([np.arange(1, V), np.zeros(V - 1, np.int64)])
+    v = np.concatenate([np.zeros(V - 1, np.int64), np.arange(1, V)])
+    w = synth.uniform_int(77, u.shape[0], 1, 50)
+    rp, col, wt = synth.csr_from_arcs(V, u, v, w)
+    g = synth.Graph(V=V, row_ptr=rp, col=col, w=wt, depot=0)
+    src = np.array([0, 5, 699, 350], np.int32)
+    out, _ = model_rows(model, g, src, 96, 128)
+    assert (out == orc.sssp_rows(g, src)).all()
