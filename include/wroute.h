@@ -155,6 +155,25 @@ int wr_submatrix(wr_ctx* ctx, int32_t n_src, const int32_t* src, int32_t n_dst, 
 int wr_tour_eval(wr_ctx* ctx, int32_t n_orders, const int32_t* k, const int32_t* D, int32_t* cost,
                  int32_t* perm, int32_t* status, int ptr_kind, void* cuda_stream);
 
+/* Tour evaluation that allocates no device memory (the paper has no counterpart).
+ * For callers that cannot call cudaMalloc: a process whose device memory is owned
+ * by another allocator (a framework's caching allocator, a fixed arena) that must
+ * not be grown or fragmented behind its back, or a latency-critical loop that
+ * cannot take the device-wide synchronisation cudaMalloc/cudaFree may imply.
+ * Same results as wr_tour_eval (same arguments, no context), computed on the
+ * current device.  All pointers must be device-accessible (device memory, or
+ * managed/mapped memory); the work is enqueued on cuda_stream.
+ * Scratch: a file-scope device array sized for WR_STATIC_MAX_ORDERS orders
+ * (about 2.9 MB), held by every device that loads the library until the
+ * process exits.  n_orders > WR_STATIC_MAX_ORDERS returns WR_EINVAL.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call shares
+ * the one array, so calls that overlap on the GPU (other streams, other host
+ * threads) race: order them on one stream or synchronise between them. */
+#define WR_STATIC_MAX_ORDERS 4096
+int wr_tour_eval_static(int32_t n_orders, const int32_t* k, const int32_t* D, int32_t* cost,
+                        int32_t* perm, int32_t* status, void* cuda_stream);
+
 int wr_get_stats(wr_ctx* ctx, wr_stats* out);
 int wr_get_tuning(wr_ctx* ctx, wr_tuning* out);
 /* Changing run_target or tile_cap re-partitions the loaded graph. */

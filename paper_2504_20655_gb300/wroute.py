@@ -27,7 +27,9 @@ WR_LEG_MAX = 10324440
 DSTRIDE = 13
 
 EXPORTS = ["wr_create", "wr_destroy", "wr_strerror", "wr_sync", "wr_load_graph", "wr_route_orders", "wr_bf_rows",
-           "wr_distance_rows", "wr_submatrix", "wr_tour_eval", "wr_get_stats", "wr_get_tuning", "wr_set_tuning"]
+           "wr_distance_rows", "wr_submatrix", "wr_tour_eval", "wr_tour_eval_static", "wr_get_stats",
+           "wr_get_tuning", "wr_set_tuning"]
+WR_STATIC_MAX_ORDERS = 4096
 
 
 class wr_config(ctypes.Structure):
@@ -86,6 +88,7 @@ def load_library(path: str = LIB_PATH):
     L.wr_distance_rows.argtypes = [P, i32, P, I, CONSUME_FN, P, P]
     L.wr_submatrix.argtypes = [P, i32, P, i32, P, P, P, I, P]
     L.wr_tour_eval.argtypes = [P, i32, P, P, P, P, P, I, P]
+    L.wr_tour_eval_static.argtypes = [i32, P, P, P, P, P, P]
     L.wr_get_stats.argtypes = [P, ctypes.POINTER(wr_stats)]
     L.wr_get_tuning.argtypes = [P, ctypes.POINTER(wr_tuning)]
     L.wr_set_tuning.argtypes = [P, ctypes.POINTER(wr_tuning)]
@@ -241,6 +244,22 @@ def wr_tour_eval(ctx, k, D, cost, perm, status, stream=None):
     p_s, k5, a5 = _ptr(status, np.int32)
     _check(load_library().wr_tour_eval(ctx, n, p_k, p_D, p_c, p_p, p_s, _kind(k1, k2, k3, k4, k5),
                                        _stream(stream)), "wr_tour_eval")
+
+
+def wr_tour_eval_static(k, D, cost, perm, status, stream=None):
+    """wr_tour_eval without a context and without allocating device memory
+    (for callers whose device memory belongs to another allocator, or that
+    cannot take cudaMalloc's synchronisation).  Device tensors only; uses
+    the static scratch of the current device (at most WR_STATIC_MAX_ORDERS
+    orders; calls that overlap on the GPU race on that scratch)."""
+    n = int(len(k))
+    ptrs = []
+    for x, dt in ((k, np.int32), (D, np.int32), (cost, np.int32), (perm, np.int32), (status, np.int32)):
+        p, kind, _ = _ptr(x, dt)
+        if kind != WR_DEVICE:
+            raise ValueError("wr_tour_eval_static takes device tensors only")
+        ptrs.append(p)
+    _check(load_library().wr_tour_eval_static(n, *ptrs, _stream(stream)), "wr_tour_eval_static")
 
 
 def wr_get_stats(ctx) -> dict:
