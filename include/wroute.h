@@ -80,7 +80,7 @@ typedef struct {
 /* Tunables (picked by the autotuner; results never depend on them). */
 typedef struct {
     int32_t run_target;     /* Bellman-Ford tile: target nodes per run (consecutive ids) */
-    int32_t tile_cap;       /* nodes (run + halo) staged in shared memory per tile: 64, 128 or 256 */
+    int32_t tile_cap;       /* nodes (run + halo) staged in shared memory per tile: 64, 128, 256 or 512 */
     int32_t enum_units;     /* sequence units (of 120 sequences) per thread per scheduled chunk */
     int32_t enum_max_units_per_launch; /* rank-range segment: units per enumeration launch (0 = all) */
 } wr_tuning;

@@ -49,7 +49,7 @@ struct wr_ctx {
     wr::HostGraph hg;
     wr::HostPartition hp;
     wr::DevGraph dg;
-    DBuf g_desc, g_ref, g_w, g_run_ptr, g_halo_ptr, g_halo_nodes, g_rin_ptr, g_rin_list, g_run_of, g_meta;
+    DBuf g_desc, g_ref, g_w, g_arc2, g_run_ptr, g_halo_ptr, g_halo_nodes, g_rin_ptr, g_rin_list, g_run_of, g_meta, g_flags, g_ix, g_xarc;
     wr::BfLaunchInfo bf_info{};
     int enum_blocks = 0;
     // working buffers
@@ -152,6 +152,11 @@ int upload_partition(wr_ctx* c) {
     RC(upload(c->g_desc, p.node_desc.data(), p.node_desc.size() * sizeof(int4)));
     RC(upload(c->g_ref, p.arc_ref.data(), p.arc_ref.size() * 4));
     RC(upload(c->g_w, p.arc_w.data(), p.arc_w.size() * 4));
+    {
+        std::vector<uint2> a2(p.arc_ref.size());
+        for (size_t i = 0; i < a2.size(); ++i) a2[i] = make_uint2(p.arc_ref[i], p.arc_w[i]);
+        RC(upload(c->g_arc2, a2.data(), a2.size() * sizeof(uint2)));
+    }
     RC(upload(c->g_run_ptr, p.run_ptr.data(), p.run_ptr.size() * 4));
     RC(upload(c->g_halo_ptr, p.halo_ptr.data(), p.halo_ptr.size() * 4));
     RC(upload(c->g_halo_nodes, p.halo_nodes.data(), p.halo_nodes.size() * 4));
@@ -159,6 +164,9 @@ int upload_partition(wr_ctx* c) {
     RC(upload(c->g_rin_list, p.rin_list.data(), p.rin_list.size() * 4));
     RC(upload(c->g_run_of, p.run_of_node.data(), p.run_of_node.size() * 4));
     RC(upload(c->g_meta, p.run_meta_bytes.data(), p.run_meta_bytes.size() * 8));
+    RC(upload(c->g_flags, p.run_flags.data(), p.run_flags.size() * 4));
+    RC(upload(c->g_ix, p.node_ix.data(), p.node_ix.size() * sizeof(uint4)));
+    RC(upload(c->g_xarc, p.xarc2.data(), p.xarc2.size() * sizeof(uint2)));
     wr::DevGraph& g = c->dg;
     g.V = p.V;
     g.n_runs = p.n_runs;
@@ -167,6 +175,7 @@ int upload_partition(wr_ctx* c) {
     g.node_desc = c->g_desc.as<int4>();
     g.arc_ref = c->g_ref.as<uint32_t>();
     g.arc_w = c->g_w.as<uint32_t>();
+    g.arc2 = c->g_arc2.as<uint2>();
     g.run_ptr = c->g_run_ptr.as<int32_t>();
     g.halo_ptr = c->g_halo_ptr.as<int32_t>();
     g.halo_nodes = c->g_halo_nodes.as<int32_t>();
@@ -174,6 +183,9 @@ int upload_partition(wr_ctx* c) {
     g.rin_list = c->g_rin_list.as<int32_t>();
     g.run_of_node = c->g_run_of.as<int32_t>();
     g.run_meta_bytes = c->g_meta.as<int64_t>();
+    g.run_flags = c->g_flags.as<int32_t>();
+    g.node_ix = c->g_ix.as<uint4>();
+    g.xarc2 = c->g_xarc.as<uint2>();
     return wr::bf_prepare(p.tile_cap, c->device, &c->bf_info);
 }
 
@@ -337,8 +349,8 @@ int wr_create(const wr_config* cfg, wr_ctx** out) {
     ctx->device = c.device;
     ctx->cfg = c;
     ctx->cfg.tune_path = nullptr;
-    ctx->tune.run_target = 96;
-    ctx->tune.tile_cap = 128;
+    ctx->tune.run_target = 200;
+    ctx->tune.tile_cap = 256;
     ctx->tune.enum_units = 4;
     ctx->tune.enum_max_units_per_launch = 0;
     ctx->enum_blocks = wr::tour_enum_blocks(c.device);
@@ -354,8 +366,8 @@ void wr_destroy(wr_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    DBuf* bufs[] = {&c->g_desc, &c->g_ref, &c->g_w, &c->g_run_ptr, &c->g_halo_ptr, &c->g_halo_nodes, &c->g_rin_ptr,
-                    &c->g_rin_list, &c->g_run_of, &c->g_meta, &c->rows, &c->stamp, &c->list0, &c->list1,
+    DBuf* bufs[] = {&c->g_desc, &c->g_ref, &c->g_w, &c->g_arc2, &c->g_run_ptr, &c->g_halo_ptr, &c->g_halo_nodes, &c->g_rin_ptr,
+                    &c->g_rin_list, &c->g_run_of, &c->g_meta, &c->g_flags, &c->g_ix, &c->g_xarc, &c->rows, &c->stamp, &c->list0, &c->list1,
                     &c->counts, &c->bar, &c->err, &c->stats, &c->node_flag, &c->src_index, &c->src_list,
                     &c->n_src, &c->block_sums, &c->offs, &c->picks, &c->order_status, &c->order_flags, &c->D,
                     &c->unit_off, &c->best, &c->unit_ctr, &c->out_cost, &c->out_perm, &c->out_status, &c->kbuf,
@@ -755,7 +767,7 @@ int wr_get_tuning(wr_ctx* c, wr_tuning* out) {
 
 int wr_set_tuning(wr_ctx* c, const wr_tuning* t) {
     if (!c || !t) return WR_EINVAL;
-    if (t->run_target < 1 || (t->tile_cap != 64 && t->tile_cap != 128 && t->tile_cap != 256) || t->enum_units < 1 ||
+    if (t->run_target < 1 || (t->tile_cap != 64 && t->tile_cap != 128 && t->tile_cap != 256 && t->tile_cap != 512) || t->enum_units < 1 ||
         t->enum_max_units_per_launch < 0 || t->run_target > t->tile_cap)
         return WR_EINVAL;
     RC(set_device(c));

@@ -98,89 +98,304 @@ __device__ __forceinline__ void build_list(const BfParams& p, int G, int match, 
     }
 }
 
-// One tile: stage, forward pass, backward pass, write back dropped rows.
-// Returns true (warp-uniform) if any row of the tile dropped.
+// Shared memory of one warp: the tile's rows (own nodes then halo), the
+// run's inline node descriptors and extra arcs, and a dirty bit per own node.
 template <int TILE>
-__device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, uint32_t* tile, uint32_t* dirty,
-                                           int lane, unsigned long long& node_visits) {
+struct TileSmem {
+    uint32_t rows[TILE * 32];
+    uint4 ix[2 * (TILE + 1)];
+    uint2 xarcs[TILE];
+    uint32_t dirty[TILE / 32];
+};
+
+// cp.async.wait_group takes an immediate: dispatch on the pending count.
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+    switch (n) {
+        case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
+        case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
+        case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
+        case 3: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
+        case 4: asm volatile("cp.async.wait_group 4;\n" ::: "memory"); break;
+        case 5: asm volatile("cp.async.wait_group 5;\n" ::: "memory"); break;
+        case 6: asm volatile("cp.async.wait_group 6;\n" ::: "memory"); break;
+        case 7: asm volatile("cp.async.wait_group 7;\n" ::: "memory"); break;
+        case 8: asm volatile("cp.async.wait_group 8;\n" ::: "memory"); break;
+        case 9: asm volatile("cp.async.wait_group 9;\n" ::: "memory"); break;
+        case 10: asm volatile("cp.async.wait_group 10;\n" ::: "memory"); break;
+        case 11: asm volatile("cp.async.wait_group 11;\n" ::: "memory"); break;
+        case 12: asm volatile("cp.async.wait_group 12;\n" ::: "memory"); break;
+        case 13: asm volatile("cp.async.wait_group 13;\n" ::: "memory"); break;
+        case 14: asm volatile("cp.async.wait_group 14;\n" ::: "memory"); break;
+        case 15: asm volatile("cp.async.wait_group 15;\n" ::: "memory"); break;
+        default: asm volatile("cp.async.wait_group 16;\n" ::: "memory"); break;
+    }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async8_ca(void* smem, const void* gmem) {
+    unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// Tile rows are swizzled: the 16-byte chunk q (sources 4q..4q+3) of node i
+// sits at chunk q ^ (i & 7) of the node's 128-byte row, so 8 consecutive
+// nodes reading the same chunk hit 8 distinct bank groups.
+__device__ __forceinline__ int swz(int i, int q) { return i * 32 + ((q ^ (i & 7)) << 2); }
+__device__ __forceinline__ int swz_lane(int i, int lane) { return swz(i, lane >> 2) + (lane & 3); }
+
+__device__ __forceinline__ uint4 ld4(const uint32_t* rs, int i, int q) {
+    return *reinterpret_cast<const uint4*>(rs + swz(i, q));
+}
+__device__ __forceinline__ uint4 addmin4(uint4 x, uint32_t w, uint4 m) {
+    return make_uint4(__viaddmin_u32(x.x, w, m.x), __viaddmin_u32(x.y, w, m.y), __viaddmin_u32(x.z, w, m.z),
+                      __viaddmin_u32(x.w, w, m.w));
+}
+__device__ __forceinline__ uint4 min4(uint4 a, uint4 b) {
+    return make_uint4(min(a.x, b.x), min(a.y, b.y), min(a.z, b.z), min(a.w, b.w));
+}
+__device__ __forceinline__ uint4 shfl_up4(uint4 v, int d) {
+    return make_uint4(__shfl_up_sync(FULL_MASK, v.x, d), __shfl_up_sync(FULL_MASK, v.y, d),
+                      __shfl_up_sync(FULL_MASK, v.z, d), __shfl_up_sync(FULL_MASK, v.w, d));
+}
+
+// Fast passes (every arc source a staged tile slot).  A pass walks the run in
+// chunks of 32 nodes, one node per lane, 4 sources per lane at a time.  For a
+// chunk, each node first takes c = min(d[v], min over its non-carry arcs of
+// d[u] + w) -- sources in earlier chunks (or the halo) are already final for
+// this pass, sources in the same chunk are taken as they were at the chunk's
+// start -- and then the carry chain x_v = min(c_v, x_{v-1} + w(v-1, v)) is
+// solved for all 32 nodes at once as a (min, +) prefix scan over the warp
+// (Hillis-Steele, 5 shuffle steps; the weight prefixes are shared by all
+// sources).  The forward pass takes arcs from lower ids, the backward pass
+// from higher ids, so every arc is relaxed once per sweep.
+template <int TILE, bool FWD>
+__device__ __forceinline__ bool scan_pass(TileSmem<TILE>& sm, int len, uint32_t x0, int lane) {
+    constexpr int NCH = TILE / 32;
+    uint32_t* rs = sm.rows;
+    const uint2* xa = sm.xarcs;
+    bool changed = false;
+    const int nchunks = (len + 31) >> 5;
+    for (int cc = 0; cc < nchunks; ++cc) {
+        const int c = FWD ? cc : nchunks - 1 - cc;
+        if (FWD) {
+            cp_async_wait_pending(NCH - 1 - c);  // own-row chunk c has landed
+            __syncwarp();
+        }
+        // node of this lane: ascending ids forward, descending backward
+        const int i = FWD ? (c << 5) + lane : (len - 1) - ((cc << 5) + lane);
+        const bool valid = FWD ? i < len : i >= 0;
+        const int ii = valid ? i : 0;
+        const uint4 a = sm.ix[2 * ii];
+        const uint4 b = sm.ix[2 * ii + 1];
+        uint32_t wc = valid ? min(FWD ? a.x : a.y, INF_U) : INF_U;  // carry arc into this node
+        // inline non-carry arcs of this direction; absent ones read slot 0 and never win
+        const int s0 = FWD ? static_cast<int>(b.y & 0xFFFFu) : static_cast<int>(b.z & 0xFFFFu);
+        const int s1 = static_cast<int>(b.y >> 16);
+        const uint32_t w0 = FWD ? a.z : b.x;
+        const uint32_t w1 = a.w;
+        uint32_t xb = 0, xe = 0;  // extra arcs
+        if (valid && (b.z & IX_EXTRA)) {
+            const uint32_t nfx = (b.z >> 16) & 0xFFu;
+            if (FWD) {
+                xb = b.w;
+                xe = b.w + nfx;
+            } else {
+                xb = b.w + nfx;
+                xe = sm.ix[2 * ii + 3].w;
+            }
+        }
+        // weight prefixes of the carry chain: W[k] = sum of the carry weights of
+        // lanes (lane - 2^k, lane], saturated at INF_U
+        uint32_t W[5];
+        {
+            uint32_t w = wc;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                W[k] = w;
+                const uint32_t o = __shfl_up_sync(FULL_MASK, w, 1 << k);
+                if (lane >= (1 << k)) w = min(w + o, INF_U);
+            }
+        }
+        // carry into lane 0 from the last node of the previous chunk (already stored)
+        const int prev = FWD ? (c << 5) - 1 : i + 1;
+        const bool has_prev = lane == 0 && (FWD ? prev >= 0 : prev < len);
+        unsigned any_drop = 0u;
+#pragma unroll 2
+        for (int q = 0; q < 8; ++q) {
+            const uint4 cur = ld4(rs, ii, q);
+            uint4 cv = addmin4(ld4(rs, s0, q), w0, cur);
+            if constexpr (FWD) cv = addmin4(ld4(rs, s1, q), w1, cv);
+            for (uint32_t e = xb; e < xe; ++e) cv = addmin4(ld4(rs, xa[e - x0].x, q), xa[e - x0].y, cv);
+            if (has_prev) cv = addmin4(ld4(rs, prev, q), wc, cv);
+            if (!valid) cv = make_uint4(INF_U, INF_U, INF_U, INF_U);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const uint4 o = shfl_up4(cv, 1 << k);
+                if (lane >= (1 << k)) cv = addmin4(o, W[k], cv);
+            }
+            const bool dropped = valid && (cv.x < cur.x || cv.y < cur.y || cv.z < cur.z || cv.w < cur.w);
+            if (dropped) *reinterpret_cast<uint4*>(rs + swz(ii, q)) = min4(cv, cur);
+            any_drop |= dropped ? 1u : 0u;
+        }
+        const unsigned m = __ballot_sync(FULL_MASK, any_drop != 0u);
+        if (m) {
+            changed = true;
+            // dirty bits by node id; a backward chunk maps lane l to node top - l
+            if (lane == 0) {
+                if (FWD) {
+                    sm.dirty[c] |= m;
+                } else {
+                    const int top = (len - 1) - (cc << 5);
+                    unsigned mm = m;
+                    while (mm) {
+                        const int l = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                        const int node = top - l;
+                        sm.dirty[node >> 5] |= 1u << (node & 31);
+                    }
+                }
+            }
+        }
+        __syncwarp();  // stores of this chunk visible before the next chunk reads them
+    }
+    return changed;
+}
+
+template <int TILE>
+__device__ __forceinline__ bool passes_fast(TileSmem<TILE>& sm, int len, uint32_t x0, int lane) {
+    const bool f = scan_pass<TILE, true>(sm, len, x0, lane);
+    cp_async_wait_pending(0);
+    __syncwarp();
+    const bool b = scan_pass<TILE, false>(sm, len, x0, lane);
+    return f || b;
+}
+
+// Generic passes for runs the fast path cannot take (a single node with more
+// in-neighbours than the tile holds): descriptors and arcs from global memory,
+// sources from the tile or, past its capacity, from the rows in L2.
+template <int TILE>
+__device__ __noinline__ bool passes_generic(const BfParams& p, TileSmem<TILE>& sm, int r0, int len, int lane,
+                                            int64_t lane_off) {
+    const uint32_t* rs = sm.rows;
+    const uint32_t* rows = p.seg.rows;
+    const int64_t ld = p.seg.ld;
+    bool changed = false;
+    cp_async_wait_pending(0);
+    __syncwarp();
+    uint32_t carry = INF_U;
+    for (int i = 0; i < len; ++i) {
+        const int4 d = __ldg(p.g.node_desc + r0 + i);
+        const uint32_t cur = rs[swz_lane(i, lane)];
+        uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.x), cur);
+        for (int q = d.z; q < d.w; ++q) {
+            const uint2 e = __ldg(p.g.arc2 + q);
+            const uint32_t x = (e.x & GLOBAL_REF) ? ld_l2(rows + static_cast<int64_t>(e.x & ~GLOBAL_REF) * ld + lane_off + lane)
+                                                  : rs[swz_lane(static_cast<int>(e.x), lane)];
+            best = __viaddmin_u32(x, e.y, best);
+        }
+        const bool dropped = best < cur;
+        if (dropped) sm.rows[swz_lane(i, lane)] = best;
+        const unsigned m = __ballot_sync(FULL_MASK, dropped);
+        if (m) {
+            changed = true;
+            if (lane == 0) sm.dirty[i >> 5] |= 1u << (i & 31);
+        }
+        carry = best;
+    }
+    carry = INF_U;
+    for (int i = len - 1; i >= 0; --i) {
+        const int4 d = __ldg(p.g.node_desc + r0 + i);
+        const int end = __ldg(&p.g.node_desc[r0 + i + 1].z);
+        const uint32_t cur = rs[swz_lane(i, lane)];
+        uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.y), cur);
+        for (int q = d.w; q < end; ++q) {
+            const uint2 e = __ldg(p.g.arc2 + q);
+            best = __viaddmin_u32(rs[swz_lane(static_cast<int>(e.x), lane)], e.y, best);
+        }
+        const bool dropped = best < cur;
+        if (dropped) sm.rows[swz_lane(i, lane)] = best;
+        const unsigned m = __ballot_sync(FULL_MASK, dropped);
+        if (m) {
+            changed = true;
+            if (lane == 0) sm.dirty[i >> 5] |= 1u << (i & 31);
+        }
+        carry = best;
+    }
+    return changed;
+}
+
+// One tile: stage (own rows in 32-node chunks so the forward pass can start
+// on the first chunk while the rest is in flight), forward pass, backward
+// pass, write back the rows that dropped.  Returns true (warp-uniform) if
+// any row dropped.  Each pass relaxes every arc of its direction once.
+template <int TILE>
+__device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, TileSmem<TILE>& sm, int lane,
+                                           unsigned long long& node_visits) {
+    constexpr int NCH = TILE / 32;
     const int r0 = __ldg(p.g.run_ptr + r);
     const int len = __ldg(p.g.run_ptr + r + 1) - r0;
     const int h0 = __ldg(p.g.halo_ptr + r);
     const int hn = __ldg(p.g.halo_ptr + r + 1) - h0;
+    const bool simple = (__ldg(p.g.run_flags + r) & RUN_SIMPLE) != 0;
     const int64_t ld = p.seg.ld;
     const int64_t lane_off = static_cast<int64_t>(g) * 32;
     uint32_t* rows = p.seg.rows;
+    const uint32_t x0 = __ldg(&p.g.node_ix[2 * static_cast<int64_t>(r0) + 1].w);
+    const uint32_t x1 = __ldg(&p.g.node_ix[2 * static_cast<int64_t>(r0 + len) + 1].w);
 
-    // stage: 8 threads x 16 bytes per node row of the group
-    const int total = len + hn;
-    for (int i0 = 0; i0 < total; i0 += 4) {
+    // group 0: descriptors, extra arcs, halo rows
+    if (simple) {
+        for (int i = lane; i < 2 * (len + 1); i += 32) cp_async16(&sm.ix[i], &p.g.node_ix[2 * static_cast<int64_t>(r0) + i]);
+        for (uint32_t q = x0 + lane; q < x1; q += 32) cp_async8_ca(&sm.xarcs[q - x0], &p.g.xarc2[q]);
+    }
+    for (int i0 = 0; i0 < hn; i0 += 4) {
         const int i = i0 + (lane >> 3);
-        if (i < total) {
-            const int node = i < len ? r0 + i : __ldg(p.g.halo_nodes + h0 + (i - len));
-            cp_async16(tile + i * 32 + (lane & 7) * 4, rows + static_cast<int64_t>(node) * ld + lane_off + (lane & 7) * 4);
+        if (i < hn) {
+            const int node = __ldg(p.g.halo_nodes + h0 + i);
+            cp_async16(sm.rows + swz(len + i, lane & 7),
+                       rows + static_cast<int64_t>(node) * ld + lane_off + (lane & 7) * 4);
         }
     }
-    if (lane < TILE / 32) dirty[lane] = 0u;
-    cp_async_wait_all();
+    cp_async_commit();
+    // groups 1..NCH: own rows, 32 nodes each (empty groups complete at once)
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        const int base = c * 32;
+        if (base < len) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = base + q * 4 + (lane >> 3);
+                if (i < len)
+                    cp_async16(sm.rows + swz(i, lane & 7),
+                               rows + static_cast<int64_t>(r0 + i) * ld + lane_off + (lane & 7) * 4);
+            }
+        }
+        cp_async_commit();
+    }
+    if (lane < NCH) sm.dirty[lane] = 0u;
+    cp_async_wait_pending(NCH - 1);  // group 0 and the first row chunk landed
     __syncwarp();
 
-    bool changed = false;
-    // forward: arcs from lower ids (and the halo); carry = arc v-1 -> v
-    uint32_t carry = INF_U;
-#pragma unroll 2
-    for (int i = 0; i < len; ++i) {
-        const int4 d = __ldg(p.g.node_desc + r0 + i);
-        const uint32_t cur = tile[i * 32 + lane];
-        uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.x), cur);
-        for (int a = d.z; a < d.w; ++a) {
-            const uint32_t ref = __ldg(p.g.arc_ref + a);
-            const uint32_t wt = __ldg(p.g.arc_w + a);
-            const uint32_t x = (ref & GLOBAL_REF)
-                                   ? ld_l2(rows + static_cast<int64_t>(ref & ~GLOBAL_REF) * ld + lane_off + lane)
-                                   : tile[ref * 32 + lane];
-            best = __viaddmin_u32(x, wt, best);
-        }
-        const bool dropped = best < cur;
-        if (dropped) tile[i * 32 + lane] = best;
-        const unsigned m = __ballot_sync(FULL_MASK, dropped);
-        if (m) {
-            changed = true;
-            if (lane == 0) dirty[i >> 5] |= 1u << (i & 31);
-        }
-        carry = best;
-    }
-    // backward: arcs from higher ids; carry = arc v+1 -> v
-    carry = INF_U;
-    int next_begin = __ldg(&p.g.node_desc[r0 + len].z);
-#pragma unroll 2
-    for (int i = len - 1; i >= 0; --i) {
-        const int4 d = __ldg(p.g.node_desc + r0 + i);
-        const uint32_t cur = tile[i * 32 + lane];
-        uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.y), cur);
-        for (int a = d.w; a < next_begin; ++a) {
-            const uint32_t ref = __ldg(p.g.arc_ref + a);
-            const uint32_t wt = __ldg(p.g.arc_w + a);
-            best = __viaddmin_u32(tile[ref * 32 + lane], wt, best);
-        }
-        next_begin = d.z;
-        const bool dropped = best < cur;
-        if (dropped) tile[i * 32 + lane] = best;
-        const unsigned m = __ballot_sync(FULL_MASK, dropped);
-        if (m) {
-            changed = true;
-            if (lane == 0) dirty[i >> 5] |= 1u << (i & 31);
-        }
-        carry = best;
-    }
+    const bool changed = simple ? passes_fast<TILE>(sm, len, x0, lane) : passes_generic<TILE>(p, sm, r0, len, lane, lane_off);
     node_visits += static_cast<unsigned long long>(len);
     __syncwarp();
     if (changed) {
+        // 4 dirty nodes per step, 8 lanes x 16 bytes per node row
+        const int sub = lane >> 3, q = lane & 7;
         for (int wd = 0; wd < (len + 31) / 32; ++wd) {
-            uint32_t bits = dirty[wd];
+            uint32_t bits = sm.dirty[wd];
             while (bits) {
-                const int i = wd * 32 + __ffs(bits) - 1;
-                bits &= bits - 1;
-                __stcg(rows + static_cast<int64_t>(r0 + i) * ld + lane_off + lane, tile[i * 32 + lane]);
+                int pick = -1;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int bit = bits ? __ffs(bits) - 1 : -1;
+                    if (bit >= 0) bits &= bits - 1;
+                    if (t == sub) pick = bit;
+                }
+                if (pick >= 0) {
+                    const int i = wd * 32 + pick;
+                    __stcg(reinterpret_cast<uint4*>(rows + static_cast<int64_t>(r0 + i) * ld + lane_off + q * 4),
+                           *reinterpret_cast<const uint4*>(sm.rows + swz(i, q)));
+                }
             }
         }
     }
@@ -188,20 +403,17 @@ __device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, uint
     return changed;
 }
 
-template <int TILE, int NW>
-__global__ void __launch_bounds__(NW * 32) bf_sweeps_kernel(BfParams p) {
-    extern __shared__ uint32_t smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t* tile = smem + warp * TILE * 32;
-    uint32_t* dirty = smem + NW * TILE * 32 + warp * (TILE / 32);
+template <int TILE>
+__global__ void __launch_bounds__(32) bf_sweeps_kernel(BfParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileSmem<TILE>& sm = *reinterpret_cast<TileSmem<TILE>*>(smem_raw);
+    const int lane = threadIdx.x & 31;
 
     const int n_lanes = segment_lanes(p.seg);
     const int G = (n_lanes + 31) >> 5;
     if (G == 0) return;  // same decision in every block
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthreads = gridDim.x * blockDim.x;
-    const int gwarp = blockIdx.x * NW + warp;
-    const int nwarps = gridDim.x * NW;
 
     // seeds: writing d[s][s] = 0 is the change of "sweep 0": the tile holding
     // each source gets stamp 1, and sweep 1 visits it and the tiles it feeds
@@ -223,13 +435,20 @@ __global__ void __launch_bounds__(NW * 32) bf_sweeps_kernel(BfParams p) {
             if (gtid == 0) atomicCAS(p.w.err, 0, WR_EINTERNAL);
             break;
         }
-        if (gtid == 0) p.w.counts[cur ^ 1] = 0;
+        if (gtid == 0) {
+            p.w.counts[cur ^ 1] = 0;
+            p.w.counts[2 + (cur ^ 1)] = 0;
+        }
         const int32_t* list = cur ? p.w.list1 : p.w.list0;
-        for (int it = gwarp; it < cnt; it += nwarps) {
+        for (;;) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(p.w.counts + 2 + cur, 1);  // dynamic tile scheduling
+            it = __shfl_sync(FULL_MASK, it, 0);
+            if (it >= cnt) break;
             const int item = __ldcg(list + it);
             const int r = item / G;
             const int g = item - r * G;
-            const bool ch = sweep_tile<TILE>(p, r, g, tile, dirty, lane, nodes);
+            const bool ch = sweep_tile<TILE>(p, r, g, sm, lane, nodes);
             if (ch && lane == 0) p.w.stamp[item] = sweep + 1;
             ++tiles;
             bytes += static_cast<unsigned long long>(__ldg(p.g.run_meta_bytes + r)) +
@@ -250,37 +469,29 @@ __global__ void __launch_bounds__(NW * 32) bf_sweeps_kernel(BfParams p) {
 
 // ---------------------------------------------------------------------------
 
-template <int TILE, int NW>
-static size_t sweep_smem() {
-    return static_cast<size_t>(NW) * (TILE * 32 * sizeof(uint32_t) + (TILE / 32) * sizeof(uint32_t));
-}
-
-template <int TILE, int NW>
+template <int TILE>
 static int prepare_one(int device, BfLaunchInfo* info) {
-    const size_t smem = sweep_smem<TILE, NW>();
-    if (cudaFuncSetAttribute(bf_sweeps_kernel<TILE, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = sizeof(TileSmem<TILE>);
+    if (cudaFuncSetAttribute(bf_sweeps_kernel<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem)) != cudaSuccess)
         return WR_ECUDA;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bf_sweeps_kernel<TILE, NW>, NW * 32, smem) !=
-            cudaSuccess ||
-        occ < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bf_sweeps_kernel<TILE>, 32, smem) != cudaSuccess || occ < 1)
         return WR_ECUDA;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return WR_ECUDA;
     info->blocks = occ * sms;
-    info->threads = NW * 32;
+    info->threads = 32;
     info->smem = smem;
     return WR_OK;
 }
 
-constexpr int BF_NW = 4;
-
 int bf_prepare(int tile_cap, int device, BfLaunchInfo* info) {
     switch (tile_cap) {
-        case 64: return prepare_one<64, BF_NW>(device, info);
-        case 128: return prepare_one<128, BF_NW>(device, info);
-        case 256: return prepare_one<256, BF_NW>(device, info);
+        case 64: return prepare_one<64>(device, info);
+        case 128: return prepare_one<128>(device, info);
+        case 256: return prepare_one<256>(device, info);
+        case 512: return prepare_one<512>(device, info);
         default: return WR_EINVAL;
     }
 }
@@ -297,9 +508,10 @@ cudaError_t bf_launch_sweeps(const DevGraph& g, const BfSegment& seg, const BfWo
     void* args[] = {&p};
     const void* fn = nullptr;
     switch (g.tile_cap) {
-        case 64: fn = reinterpret_cast<const void*>(bf_sweeps_kernel<64, BF_NW>); break;
-        case 128: fn = reinterpret_cast<const void*>(bf_sweeps_kernel<128, BF_NW>); break;
-        case 256: fn = reinterpret_cast<const void*>(bf_sweeps_kernel<256, BF_NW>); break;
+        case 64: fn = reinterpret_cast<const void*>(bf_sweeps_kernel<64>); break;
+        case 128: fn = reinterpret_cast<const void*>(bf_sweeps_kernel<128>); break;
+        case 256: fn = reinterpret_cast<const void*>(bf_sweeps_kernel<256>); break;
+        case 512: fn = reinterpret_cast<const void*>(bf_sweeps_kernel<512>); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaLaunchCooperativeKernel(fn, dim3(info.blocks), dim3(info.threads), args, info.smem, s);

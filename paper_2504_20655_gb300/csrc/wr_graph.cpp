@@ -76,6 +76,7 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
     p.halo_ptr.push_back(0);
     p.rin_ptr.push_back(0);
     p.node_desc.resize(static_cast<size_t>(V) + 1);
+    p.node_ix.resize(2 * (static_cast<size_t>(V) + 1));
 
     std::vector<int32_t> halo_mark(static_cast<size_t>(V), -1);  // run id whose halo holds the node
     std::vector<int32_t> slot(static_cast<size_t>(V), 0);        // tile slot within the current run
@@ -84,17 +85,24 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
     int32_t s = 0;
     while (s < V) {
         int32_t len = 0, halo_cnt = 0;
+        int64_t n_arcs = 0;  // arcs kept in the run's arc list (all in-arcs but the two carries)
         halo_tmp.clear();
         while (s + len < V && len < run_target) {
             const int32_t v = s + len;
             const bool v_in_halo = halo_mark[v] == run;
             int32_t add = 0;
+            int64_t listed = 0;
             for (int64_t a = g.in_ptr[v]; a < g.in_ptr[v + 1]; ++a) {
                 int32_t u = g.in_src[a];
                 if ((u < s || u > v) && halo_mark[u] != run) ++add;
+                if (!(u == v - 1 && u >= s)) ++listed;  // may count the backward carry: conservative
             }
             const int32_t new_cnt = halo_cnt - (v_in_halo ? 1 : 0) + add;
+            // extra arcs beyond the inline ones (at most 3 inline), counted conservatively
+            const int64_t extra = listed > 3 ? listed - 2 : 0;
             if (len > 0 && len + 1 + new_cnt > tile_cap) break;
+            if (len > 0 && n_arcs + extra > static_cast<int64_t>(tile_cap)) break;
+            n_arcs += extra;
             if (v_in_halo) {
                 halo_mark[v] = -1;
                 --halo_cnt;
@@ -124,6 +132,8 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
             slot[halo_all[i]] = -1;  // read from global memory
         // node descriptors and arcs
         int64_t arcs_in_run = 0;
+        bool any_not_inline = false;
+        const uint32_t x_first = static_cast<uint32_t>(p.xarc2.size());
         for (int32_t v = s; v < e; ++v) {
             p.run_of_node[v] = run;
             uint32_t fw_cw = NO_CARRY, bw_cw = NO_CARRY;
@@ -164,8 +174,35 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
                 p.arc_w.push_back(pr.second);
             }
             p.node_desc[v] = d;
+            // inline form: up to two forward and one backward non-carry arcs
+            uint4 a, b;
+            a.x = fw_cw;
+            a.y = bw_cw;
+            a.z = fw.size() > 0 ? fw[0].second : NO_CARRY;
+            a.w = fw.size() > 1 ? fw[1].second : NO_CARRY;
+            const uint32_t s0 = fw.size() > 0 ? fw[0].first : 0u, s1 = fw.size() > 1 ? fw[1].first : 0u;
+            const uint32_t sb = bw.size() > 0 ? bw[0].first : 0u;
+            b.x = bw.size() > 0 ? bw[0].second : NO_CARRY;
+            b.y = (s0 & 0xFFFFu) | (s1 << 16);
+            const uint32_t nfx = fw.size() > 2 ? static_cast<uint32_t>(fw.size() - 2) : 0u;
+            const uint32_t nbx = bw.size() > 1 ? static_cast<uint32_t>(bw.size() - 1) : 0u;
+            const bool inline_ok = s0 < 0x10000u && s1 < 0x10000u && sb < 0x10000u && nfx < 256u &&
+                                   !((s0 | s1) & GLOBAL_REF);
+            b.z = (sb & 0xFFFFu) | (nfx << 16) | ((nfx + nbx) ? IX_EXTRA : 0u);
+            b.w = static_cast<uint32_t>(p.xarc2.size());
+            for (size_t q = 2; q < fw.size(); ++q) p.xarc2.push_back(make_uint2(fw[q].first, fw[q].second));
+            for (size_t q = 1; q < bw.size(); ++q) p.xarc2.push_back(make_uint2(bw[q].first, bw[q].second));
+            if (!inline_ok) any_not_inline = true;
+            p.node_ix[2 * static_cast<size_t>(v)] = a;
+            p.node_ix[2 * static_cast<size_t>(v) + 1] = b;
         }
         p.run_meta_bytes.push_back(8 * arcs_in_run + 8 * static_cast<int64_t>(len));
+        {
+            const int64_t extras = static_cast<int64_t>(p.xarc2.size()) - x_first;
+            const bool simple = extras <= static_cast<int64_t>(tile_cap) &&
+                                staged == static_cast<int32_t>(halo_all.size()) && !any_not_inline;
+            p.run_flags.push_back(simple ? RUN_SIMPLE : 0);
+        }
         p.run_ptr.push_back(e);
         p.halo_ptr.push_back(static_cast<int32_t>(p.halo_nodes.size()));
         p.max_len = std::max(p.max_len, len);
@@ -184,6 +221,8 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
     sentinel.z = static_cast<int>(p.arc_ref.size());
     sentinel.w = sentinel.z;
     p.node_desc[V] = sentinel;
+    p.node_ix[2 * static_cast<size_t>(V)] = make_uint4(NO_CARRY, NO_CARRY, NO_CARRY, NO_CARRY);
+    p.node_ix[2 * static_cast<size_t>(V) + 1] = make_uint4(NO_CARRY, 0u, 0u, static_cast<uint32_t>(p.xarc2.size()));
     // turn halo node ids into distinct run ids
     std::vector<int32_t> out_ptr(1, 0), out_list;
     for (int32_t r = 0; r < p.n_runs; ++r) {

@@ -18,6 +18,8 @@ constexpr int DSTRIDE = 13;                   // D blocks are 13 x 13
 constexpr int DBLOCK = DSTRIDE * DSTRIDE;
 constexpr int TAIL = 5;                       // sequences of one unit: orderings of the last 5 picks
 constexpr int ORDER_FLAG_RANGE = 1;
+constexpr int32_t RUN_SIMPLE = 1;             // run's extra arcs fit the tile buffer, halo fully staged
+constexpr uint32_t IX_EXTRA = 1u << 24;       // node has arcs beyond the inline ones
 
 // --------------------------------------------------------------------------
 // graph preprocessing (host, wr_graph.cpp)
@@ -50,7 +52,16 @@ struct HostPartition {
     std::vector<int4> node_desc;
     std::vector<uint32_t> arc_ref;      // tile slot of the arc's source, or GLOBAL_REF | node
     std::vector<uint32_t> arc_w;
+    // Inline form of the same arcs for the sweep kernel's fast path, two
+    // uint4 per node (plus a sentinel): a = {fw carry w, bw carry w, fw0 w,
+    // fw1 w}, b = {bw0 w, fw0 slot | fw1 slot << 16, bw0 slot | n_fw_extra <<
+    // 16 | IX_EXTRA, first extra}.  Absent inline arcs use slot 0 and weight
+    // NO_CARRY.  Arcs beyond the inline ones are in xarc2: forward extras then
+    // backward extras, ending at the next node's first extra.
+    std::vector<uint4> node_ix;
+    std::vector<uint2> xarc2;
     std::vector<int64_t> run_meta_bytes;  // 8 * in-arcs + 8 * nodes of the run
+    std::vector<int32_t> run_flags;       // RUN_SIMPLE
     int64_t n_global_refs = 0;
 };
 
@@ -72,6 +83,9 @@ struct DevGraph {
     int4* node_desc = nullptr;
     uint32_t* arc_ref = nullptr;
     uint32_t* arc_w = nullptr;
+    uint2* arc2 = nullptr;  // (arc_ref, arc_w) interleaved
+    uint4* node_ix = nullptr;  // inline descriptors, 2 per node
+    uint2* xarc2 = nullptr;    // extra arcs
     int32_t* run_ptr = nullptr;
     int32_t* halo_ptr = nullptr;
     int32_t* halo_nodes = nullptr;
@@ -79,6 +93,7 @@ struct DevGraph {
     int32_t* rin_list = nullptr;
     int32_t* run_of_node = nullptr;
     int64_t* run_meta_bytes = nullptr;
+    int32_t* run_flags = nullptr;
 };
 
 // One source segment of Bellman-Ford: rows[v * ld + b] holds

@@ -314,35 +314,54 @@ struct Bits<0u> {
     static constexpr int low = 64;
 };
 
-template <int L, unsigned M, int CUR>
+__host__ __device__ constexpr int cfact(int n) { return n <= 1 ? 1 : n * cfact(n - 1); }
+
+// Walk of the prefix tree below a node: M = tail positions still to visit,
+// CUR = tail position just visited (-1: the prefix end x), IDX = lexicographic
+// index of the subtree's first sequence within the unit.  Children are visited
+// in increasing position, i.e. lexicographic order of the sequences.
+// FIND = false: mn = min(mn, cost) over the leaves (fused add-min).
+// FIND = true:  idx = index of the first leaf whose cost equals target.
+template <int L, unsigned M, int CUR, int IDX, bool FIND>
 struct Walk;
 
-// Visit the elements of M in increasing order (lexicographic order of the sequences).
-template <int L, unsigned M, unsigned REST, int CUR>
+template <int L, unsigned M, unsigned REST, int CUR, int IDX, bool FIND>
 struct EachChild {
-    static __device__ __forceinline__ void run(uint32_t acc, const Tab<L>& T, uint32_t& mn) {
+    static __device__ __forceinline__ void run(uint32_t acc, const Tab<L>& T, uint32_t& mn, int& idx) {
         if constexpr (REST != 0u) {
             constexpr int i = Bits<REST>::low;
-            const uint32_t leg = CUR < 0 ? T.x[i] : T.d[CUR < 0 ? 0 : CUR][i];
-            Walk<L, (M & ~(1u << i)), i>::run(acc + leg, T, mn);
-            EachChild<L, M, (REST & ~(1u << i)), CUR>::run(acc, T, mn);
+            uint32_t leg;
+            if constexpr (CUR < 0) leg = T.x[i];
+            else leg = T.d[CUR][i];
+            Walk<L, (M & ~(1u << i)), i, IDX, FIND>::run(acc + leg, T, mn, idx);
+            constexpr int sub = cfact(Bits<M>::count - 1);
+            EachChild<L, M, (REST & ~(1u << i)), CUR, IDX + sub, FIND>::run(acc, T, mn, idx);
         }
     }
 };
 
-template <int L, unsigned M, int CUR>
+template <int L, unsigned M, int CUR, int IDX, bool FIND>
 struct Walk {
-    static __device__ __forceinline__ void run(uint32_t acc, const Tab<L>& T, uint32_t& mn) {
+    static __device__ __forceinline__ void run(uint32_t acc, const Tab<L>& T, uint32_t& mn, int& idx) {
         constexpr int n = Bits<M>::count;
         if constexpr (n == 0) {
-            mn = __viaddmin_u32(acc, T.h[CUR], mn);
+            if constexpr (FIND) {
+                if (idx < 0 && acc + T.h[CUR] == mn) idx = IDX;
+            } else {
+                mn = __viaddmin_u32(acc, T.h[CUR], mn);
+            }
         } else if constexpr (n == 2 && CUR >= 0) {
             constexpr int b = Bits<M>::low;
             constexpr int c = Bits<(M & ~(1u << b))>::low;
-            mn = __viaddmin_u32(acc, T.t3[CUR][b][c], mn);
-            mn = __viaddmin_u32(acc, T.t3[CUR][c][b], mn);
+            if constexpr (FIND) {
+                if (idx < 0 && acc + T.t3[CUR][b][c] == mn) idx = IDX;
+                if (idx < 0 && acc + T.t3[CUR][c][b] == mn) idx = IDX + 1;
+            } else {
+                mn = __viaddmin_u32(acc, T.t3[CUR][b][c], mn);
+                mn = __viaddmin_u32(acc, T.t3[CUR][c][b], mn);
+            }
         } else {
-            EachChild<L, M, M, CUR>::run(acc, T, mn);
+            EachChild<L, M, M, CUR, IDX, FIND>::run(acc, T, mn, idx);
         }
     }
 };
@@ -371,51 +390,52 @@ __device__ __forceinline__ void load_tab(Tab<L>& T, const uint32_t* __restrict__
     }
 }
 
-// Minimum over the L! orderings of the tail (prefix cost P, last node x).
+template <int L, int I>
+struct TopLevel {
+    static __device__ __forceinline__ void run(uint32_t P, const Tab<L>& T, uint32_t (&mins)[L], int& idx) {
+        if constexpr (I < L) {
+            Walk<L, (((1u << L) - 1u) & ~(1u << I)), I, I * cfact(L - 1), false>::run(P + T.x[I], T, mins[I], idx);
+            TopLevel<L, I + 1>::run(P, T, mins, idx);
+        }
+    }
+};
+
+// One unit: the L! orderings of the tail after a prefix of cost P ending at x.
+// Folds (cost, rank) into (best_c, best_r) when the unit holds a sequence that
+// is lexicographically smaller in (cost, rank); rank0 = rank of the unit's first
+// sequence.
 template <int L>
-__device__ __forceinline__ uint32_t unit_min(const uint32_t* __restrict__ Dm, uint32_t P, int x, const int (&t)[TAIL]) {
+__device__ __forceinline__ void unit_eval(const uint32_t* __restrict__ Dm, uint32_t P, int x, const int (&t)[TAIL],
+                                          unsigned rank0, uint32_t& best_c, unsigned& best_r) {
     Tab<L> T;
     load_tab<L>(T, Dm, x, t);
-    uint32_t mn = 0xFFFFFFFFu;
-    Walk<L, (1u << L) - 1u, -1>::run(P, T, mn);
-    return mn;
-}
-
-// Rare path: lexicographic index of the first tail ordering costing target.
-__device__ __noinline__ int unit_find(const uint32_t* __restrict__ Dm, uint32_t P, int x, const int* t, int L,
-                                      uint32_t target) {
-    int nf = 1;
-    for (int i = 2; i <= L; ++i) nf *= i;
-    for (int idx = 0; idx < nf; ++idx) {
-        int used = 0, rem = idx, f = nf, prev = x;
-        uint32_t c = P;
-        for (int pos = 0; pos < L; ++pos) {
-            f /= (L - pos);
-            int digit = rem / f;
-            rem -= digit * f;
-            int e = 0;
-            for (;; ++e) {
-                if (used & (1 << e)) continue;
-                if (digit == 0) break;
-                --digit;
-            }
-            used |= 1 << e;
-            c += __ldg(Dm + prev * DSTRIDE + t[e]);
-            prev = t[e];
+    uint32_t mins[L];
+    int idx = -1;
+    // one accumulator per first tail element: L independent add-min chains
+#pragma unroll
+    for (int i = 0; i < L; ++i) mins[i] = 0xFFFFFFFFu;
+    TopLevel<L, 0>::run(P, T, mins, idx);
+    uint32_t mn = mins[0];
+#pragma unroll
+    for (int i = 1; i < L; ++i) mn = min(mn, mins[i]);
+    if (mn < best_c || (mn == best_c && rank0 < best_r)) {
+        Walk<L, (1u << L) - 1u, -1, 0, true>::run(P, T, mn, idx);
+        const unsigned r = rank0 + static_cast<unsigned>(idx);
+        if (mn < best_c || r < best_r) {
+            best_c = mn;
+            best_r = r;
         }
-        c += __ldg(Dm + prev * DSTRIDE);
-        if (c == target) return idx;
     }
-    return nf - 1;  // unreachable: target came from one of these sequences
 }
 
-__device__ __forceinline__ uint32_t unit_min_dispatch(int L, const uint32_t* Dm, uint32_t P, int x, const int (&t)[TAIL]) {
+__device__ __forceinline__ void unit_eval_dispatch(int L, const uint32_t* Dm, uint32_t P, int x, const int (&t)[TAIL],
+                                                   unsigned rank0, uint32_t& best_c, unsigned& best_r) {
     switch (L) {
-        case 1: return unit_min<1>(Dm, P, x, t);
-        case 2: return unit_min<2>(Dm, P, x, t);
-        case 3: return unit_min<3>(Dm, P, x, t);
-        case 4: return unit_min<4>(Dm, P, x, t);
-        default: return unit_min<5>(Dm, P, x, t);
+        case 1: unit_eval<1>(Dm, P, x, t, rank0, best_c, best_r); break;
+        case 2: unit_eval<2>(Dm, P, x, t, rank0, best_c, best_r); break;
+        case 3: unit_eval<3>(Dm, P, x, t, rank0, best_c, best_r); break;
+        case 4: unit_eval<4>(Dm, P, x, t, rank0, best_c, best_r); break;
+        default: unit_eval<5>(Dm, P, x, t, rank0, best_c, best_r); break;
     }
 }
 
@@ -448,8 +468,10 @@ __device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, long lo
     unsigned avail_last = all;  // available set before the last prefix position
     uint32_t S = 0;             // cost through position p-2
     int pos_dirty = 0;          // first prefix position to recompute
-    uint32_t best_c = 0xFFFFFFFFu;
-    unsigned best_r = 0;
+    // start from the order's current best (a stale read is only larger, so safe)
+    const unsigned long long g0 = __ldcg(out);
+    uint32_t best_c = static_cast<uint32_t>(g0 >> 32);
+    unsigned best_r = static_cast<unsigned>(g0 & 0xFFFFFFFFull);
     for (long long u = ulo; u < uhi; ++u) {
         // (re)build prefix positions >= pos_dirty
         if (pos_dirty < p) {
@@ -491,12 +513,7 @@ __device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, long lo
                 tailset &= tailset - 1;
             }
         }
-        const uint32_t mn = unit_min_dispatch(L, Dm, P, x, t);
-        if (mn < best_c) {
-            best_c = mn;
-            best_r = static_cast<unsigned>(u) * static_cast<unsigned>(lfact) +
-                     static_cast<unsigned>(unit_find(Dm, P, x, t, L, mn));
-        }
+        unit_eval_dispatch(L, Dm, P, x, t, static_cast<unsigned>(u) * static_cast<unsigned>(lfact), best_c, best_r);
         // advance the mixed-radix counter of the prefix
         if (p > 0) {
             int i = p - 1;
@@ -521,10 +538,10 @@ __device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, long lo
     }
     seqs += (uhi - ulo) * lfact;
     const unsigned long long packed = (static_cast<unsigned long long>(best_c) << 32) | best_r;
-    if (packed < __ldcg(out)) atomicMin(out, packed);
+    if (packed < g0) atomicMin(out, packed);
 }
 
-constexpr int ENUM_THREADS = 256;
+constexpr int ENUM_THREADS = 128;
 
 __global__ void __launch_bounds__(ENUM_THREADS) enum_kernel(int32_t n, const int32_t* __restrict__ k_given, TourBufs t,
                                                             long long u_begin, long long u_end, int upt) {

@@ -105,10 +105,11 @@ class Layout:
     A aisles, S slot positions per aisle, F faces per position (two sides
     of an aisle, or two levels), C cross-aisles.  Slot node id(a, f, s) =
     (a*F + f)*S + s keeps consecutive slots of one aisle face at
-    consecutive ids.  Cross-aisle node X(a, j) = A*F*S + a*C + j sits at
+    consecutive ids.  Cross-aisle node X(a, j) = A*F*S + j*A + a sits at
     boundary b_j = round(j*S/(C-1)) of aisle a (b_0 = 0 before the first
-    slot, b_{C-1} = S after the last).  The depot is the last node and
-    links to X(0, 0).
+    slot, b_{C-1} = S after the last); numbering each cross-aisle along
+    the aisles keeps it a run of consecutive ids too.  The depot is the
+    last node and links to X(0, 0).
 
     Undirected edges:
       * chain of each (a, f): its slots in s order with X(a, j) inserted
@@ -145,7 +146,7 @@ class Layout:
         return (np.asarray(a) * self.F + np.asarray(f)) * self.S + np.asarray(s)
 
     def xnode(self, a, j):
-        return self.A * self.F * self.S + np.asarray(a) * self.C + np.asarray(j)
+        return self.A * self.F * self.S + np.asarray(j) * self.A + np.asarray(a)
 
     @property
     def depot(self) -> int:
@@ -187,7 +188,7 @@ class Layout:
         f = np.arange(F, dtype=np.int64)[None, :, None]
         kind = seq[:, 0][None, None, :]
         idx = seq[:, 1][None, None, :]
-        nodes = np.where(kind == 0, (a * F + f) * S + idx, A * F * S + a * C + idx)  # [A,F,L]
+        nodes = np.where(kind == 0, (a * F + f) * S + idx, A * F * S + idx * A + a)  # [A,F,L]
         cu = nodes[:, :, :-1].reshape(-1)
         cv = nodes[:, :, 1:].reshape(-1)
         n_chain = cu.shape[0]
@@ -204,8 +205,8 @@ class Layout:
 
         xa = np.arange(A - 1, dtype=np.int64)[:, None]
         xj = np.arange(C, dtype=np.int64)[None, :]
-        xu = (A * F * S + xa * C + xj).reshape(-1)
-        xv = (A * F * S + (xa + 1) * C + xj).reshape(-1)
+        xu = (A * F * S + xj * A + xa).reshape(-1)
+        xv = (A * F * S + xj * A + xa + 1).reshape(-1)
 
         depot = self.V - 1
         ws = self.seed ^ STREAM_WEIGHTS

@@ -53,29 +53,42 @@ extern "C" int bfm_rows(int V, long long E, const long long* rp, const int* col,
                 for (int i = 0; i < len; ++i) tile[i] = rows[static_cast<size_t>(r0 + i) * ld + c];
                 for (int h = 0; h < hn; ++h) tile[len + h] = rows[static_cast<size_t>(p.halo_nodes[h0 + h]) * ld + c];
                 std::vector<char> dirty(static_cast<size_t>(len), 0);
-                uint32_t carry = INF_U;
-                for (int i = 0; i < len; ++i) {
-                    const int4 d = p.node_desc[r0 + i];
-                    const uint32_t cur = tile[i];
-                    uint32_t best = std::min(carry + static_cast<uint32_t>(d.x), cur);
-                    for (int a = d.z; a < d.w; ++a) {
-                        const uint32_t ref = p.arc_ref[a];
-                        const uint32_t x = (ref & GLOBAL_REF) ? rows[static_cast<size_t>(ref & ~GLOBAL_REF) * ld + c] : tile[ref];
-                        best = std::min(x + p.arc_w[a], best);
+                // The kernel walks each pass in chunks of 32 nodes: a node's
+                // non-carry arcs read the tile as it was when its chunk started,
+                // then the carry chain is solved in node order.
+                std::vector<uint32_t> oth(static_cast<size_t>(len));
+                auto src = [&](uint32_t ref) {
+                    return (ref & GLOBAL_REF) ? rows[static_cast<size_t>(ref & ~GLOBAL_REF) * ld + c] : tile[ref];
+                };
+                for (int c0 = 0; c0 < len; c0 += 32) {
+                    const int c1 = std::min(len, c0 + 32);
+                    for (int i = c0; i < c1; ++i) {
+                        const int4 d = p.node_desc[r0 + i];
+                        uint32_t o = 0xFFFFFFFFu;
+                        for (int a = d.z; a < d.w; ++a) o = std::min(src(p.arc_ref[a]) + p.arc_w[a], o);
+                        oth[i] = o;
                     }
-                    if (best < cur) { tile[i] = best; dirty[i] = 1; changed = true; }
-                    carry = best;
+                    for (int i = c0; i < c1; ++i) {
+                        const uint32_t cw = std::min(static_cast<uint32_t>(p.node_desc[r0 + i].x), INF_U);
+                        uint32_t best = std::min(tile[i], oth[i]);
+                        if (i > 0) best = std::min(tile[i - 1] + cw, best);
+                        if (best < tile[i]) { tile[i] = best; dirty[i] = 1; changed = true; }
+                    }
                 }
-                carry = INF_U;
-                int nb = p.node_desc[r0 + len].z;
-                for (int i = len - 1; i >= 0; --i) {
-                    const int4 d = p.node_desc[r0 + i];
-                    const uint32_t cur = tile[i];
-                    uint32_t best = std::min(carry + static_cast<uint32_t>(d.y), cur);
-                    for (int a = d.w; a < nb; ++a) best = std::min(tile[p.arc_ref[a]] + p.arc_w[a], best);
-                    nb = d.z;
-                    if (best < cur) { tile[i] = best; dirty[i] = 1; changed = true; }
-                    carry = best;
+                for (int top = len - 1; top >= 0; top -= 32) {
+                    const int bot = std::max(-1, top - 32);
+                    for (int i = top; i > bot; --i) {
+                        const int4 d = p.node_desc[r0 + i];
+                        uint32_t o = 0xFFFFFFFFu;
+                        for (int a = d.w; a < p.node_desc[r0 + i + 1].z; ++a) o = std::min(tile[p.arc_ref[a]] + p.arc_w[a], o);
+                        oth[i] = o;
+                    }
+                    for (int i = top; i > bot; --i) {
+                        const uint32_t cw = std::min(static_cast<uint32_t>(p.node_desc[r0 + i].y), INF_U);
+                        uint32_t best = std::min(tile[i], oth[i]);
+                        if (i + 1 < len) best = std::min(tile[i + 1] + cw, best);
+                        if (best < tile[i]) { tile[i] = best; dirty[i] = 1; changed = true; }
+                    }
                 }
                 for (int i = 0; i < len; ++i)
                     if (dirty[i]) rows[static_cast<size_t>(r0 + i) * ld + c] = tile[i];
@@ -141,6 +154,35 @@ extern "C" int bfm_check_partition(int V, long long E, const long long* rp, cons
             for (auto& pr : want)
                 if (pr.first < s || pr.first >= e) runs_in.push_back(p.run_of_node[pr.first]);
         }
+        // the inline descriptors of a fast-path run hold the same arcs
+        if (p.run_flags[r] & RUN_SIMPLE) {
+            const uint32_t x0 = p.node_ix[2 * static_cast<size_t>(s) + 1].w;
+            const uint32_t x1 = p.node_ix[2 * static_cast<size_t>(e) + 1].w;
+            if (x1 - x0 > static_cast<uint32_t>(tile_cap)) return 12;
+            for (int v = s; v < e; ++v) {
+                const uint4 a = p.node_ix[2 * static_cast<size_t>(v)], b = p.node_ix[2 * static_cast<size_t>(v) + 1];
+                const uint4 bn = p.node_ix[2 * static_cast<size_t>(v) + 3];
+                const int4 d = p.node_desc[v];
+                if (a.x != static_cast<uint32_t>(d.x) || a.y != static_cast<uint32_t>(d.y)) return 13;
+                std::vector<std::pair<uint32_t, uint32_t>> fw_ix, bw_ix, fw_l, bw_l;
+                if (a.z != NO_CARRY) fw_ix.emplace_back(b.y & 0xFFFFu, a.z);
+                if (a.w != NO_CARRY) fw_ix.emplace_back(b.y >> 16, a.w);
+                if (b.x != NO_CARRY) bw_ix.emplace_back(b.z & 0xFFFFu, b.x);
+                const uint32_t nfx = (b.z >> 16) & 0xFFu;
+                if (!(b.z & IX_EXTRA) && bn.w != b.w) return 14;
+                for (uint32_t q = b.w; q < b.w + nfx; ++q) fw_ix.emplace_back(p.xarc2[q].x, p.xarc2[q].y);
+                for (uint32_t q = b.w + nfx; q < bn.w; ++q) bw_ix.emplace_back(p.xarc2[q].x, p.xarc2[q].y);
+                for (int q = d.z; q < d.w; ++q) fw_l.emplace_back(p.arc_ref[q], p.arc_w[q]);
+                for (int q = d.w; q < p.node_desc[v + 1].z; ++q) bw_l.emplace_back(p.arc_ref[q], p.arc_w[q]);
+                std::sort(fw_ix.begin(), fw_ix.end());
+                std::sort(bw_ix.begin(), bw_ix.end());
+                std::sort(fw_l.begin(), fw_l.end());
+                std::sort(bw_l.begin(), bw_l.end());
+                if (fw_ix != fw_l || bw_ix != bw_l) return 15;
+                for (auto& pr : fw_ix)
+                    if (pr.first >= static_cast<uint32_t>(tile_cap)) return 16;
+            }
+        }
         std::sort(runs_in.begin(), runs_in.end());
         runs_in.erase(std::unique(runs_in.begin(), runs_in.end()), runs_in.end());
         std::vector<int> rin(p.rin_list.begin() + p.rin_ptr[r], p.rin_list.begin() + p.rin_ptr[r + 1]);
@@ -148,4 +190,16 @@ extern "C" int bfm_check_partition(int V, long long E, const long long* rp, cons
         if (rin != runs_in) return 11;
     }
     return 0;
+}
+
+// Share of runs that take the kernel's fast path.
+extern "C" double bfm_fast_fraction(int V, long long E, const long long* rp, const int* col, const int* w,
+                                    int run_target, int tile_cap) {
+    HostGraph g;
+    if (build_host_graph(V, E, reinterpret_cast<const int64_t*>(rp), col, w, 0, g)) return -1.0;
+    HostPartition p;
+    build_partition(g, run_target, tile_cap, p);
+    int simple = 0;
+    for (int r = 0; r < p.n_runs; ++r) simple += (p.run_flags[r] & RUN_SIMPLE) ? 1 : 0;
+    return static_cast<double>(simple) / p.n_runs;
 }

@@ -27,7 +27,9 @@ def model(tmp_path_factory):
                            "-I", os.path.join(ROOT, "paper_2504_20655_gb300", "csrc"), "-I", CUDA_INC,
                            os.path.join(HERE, "model", "bf_model.cpp"),
                            os.path.join(ROOT, "paper_2504_20655_gb300", "csrc", "wr_graph.cpp"), "-o", so])
-    return ctypes.CDLL(so)
+    lib = ctypes.CDLL(so)
+    lib.bfm_fast_fraction.restype = ctypes.c_double
+    return lib
 
 
 def _arrs(g):
@@ -57,7 +59,14 @@ def check_partition(model, g, run_target, tile_cap):
     return rc, int(nr[0])
 
 
-TILINGS = [(96, 128), (32, 64), (200, 256), (1, 64), (64, 64)]
+def fast_path_fraction(model, g, run_target, tile_cap):
+    P = ctypes.c_void_p
+    rp, c, w = _arrs(g)
+    return float(model.bfm_fast_fraction(g.V, ctypes.c_longlong(g.E), rp.ctypes.data_as(P), c.ctypes.data_as(P),
+                                         w.ctypes.data_as(P), run_target, tile_cap))
+
+
+TILINGS = [(96, 128), (32, 64), (200, 256), (1, 64), (64, 64), (400, 512)]
 
 
 @pytest.mark.parametrize("rt,tc", TILINGS)
@@ -68,6 +77,9 @@ def test_partition_invariants(model, rt, tc):
         rc, n_runs = check_partition(model, g, rt, tc)
         assert rc == 0, (g.V, rc)
         assert n_runs >= (g.V + rt - 1) // rt
+    # the layouts run entirely on the fast path
+    for g in graphs[-2:]:
+        assert fast_path_fraction(model, g, rt, tc) == 1.0
 
 
 @pytest.mark.parametrize("seed", range(8))

@@ -68,16 +68,20 @@ def test_bf_rows_high_in_degree(router, orc):
 
 
 @pytest.mark.parametrize("tune", [dict(run_target=96, tile_cap=128), dict(run_target=32, tile_cap=64),
-                                  dict(run_target=200, tile_cap=256), dict(run_target=1, tile_cap=64)])
+                                  dict(run_target=200, tile_cap=256), dict(run_target=1, tile_cap=64),
+                                  dict(run_target=400, tile_cap=512), dict(run_target=256, tile_cap=256)])
 def test_bf_rows_medium_tuning_invariant(router, orc, tune):
     g = synth.medium_layout().build()
+    saved = router.tuning()
     router.set_tuning(**tune)
-    router.load_graph(g)
-    src = synth.distinct_sources(200, g.n_slots, 17)
-    src = np.concatenate([src, [g.depot]]).astype(np.int32)
-    rows = router.bf_rows(src)
+    try:
+        router.load_graph(g)
+        src = synth.distinct_sources(200, g.n_slots, 17)
+        src = np.concatenate([src, [g.depot]]).astype(np.int32)
+        rows = router.bf_rows(src)
+    finally:
+        router.set_tuning(**saved)
     ref = orc.sssp_rows(g, src, "dijkstra", NT)
-    router.set_tuning(run_target=96, tile_cap=128)
     assert (rows == ref).all()
 
 
