@@ -396,6 +396,7 @@ int wr_load_graph(wr_ctx* c, int32_t V, int64_t E, const int64_t* row_ptr, const
     const int32_t* hw = w;
     if (ptr_kind == WR_DEVICE) {
         rp.resize(static_cast<size_t>(V) + 1);
+        CK(cudaDeviceSynchronize());  // no stream argument: wait for all work writing the inputs
         CK(cudaMemcpy(rp.data(), row_ptr, rp.size() * 8, cudaMemcpyDeviceToHost));
         cl.resize(static_cast<size_t>(E));
         wt.resize(static_cast<size_t>(E));
@@ -442,8 +443,10 @@ int wr_route_orders(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pi
         for (int32_t i = 0; i < n; ++i)
             if (offs[i + 1] < offs[i]) return WR_EINVAL;
     } else {
-        CK(cudaMemcpy(&first, offs, 8, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(&np, offs + n, 8, cudaMemcpyDeviceToHost));
+        // ordered after the caller's work on its stream (which may not sync with the legacy stream)
+        CK(cudaMemcpyAsync(&first, offs, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&np, offs + n, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
     }
     if (first != 0 || np < 0) return WR_EINVAL;
     if (np > 0 && (!picks || !perm)) return WR_EINVAL;
@@ -537,7 +540,8 @@ static int rows_driver(wr_ctx* c, int32_t n_src, const int32_t* src, int ptr_kin
     const int32_t* hs = src;
     if (ptr_kind == WR_DEVICE) {
         hsrc.resize(static_cast<size_t>(n_src));
-        CK(cudaMemcpy(hsrc.data(), src, static_cast<size_t>(n_src) * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpyAsync(hsrc.data(), src, static_cast<size_t>(n_src) * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
         hs = hsrc.data();
     }
     for (int32_t i = 0; i < n_src; ++i)

@@ -102,10 +102,10 @@ __device__ __forceinline__ void build_list(const BfParams& p, int G, int match, 
 // run's inline node descriptors and extra arcs, and a dirty bit per own node.
 template <int TILE>
 struct TileSmem {
-    uint32_t rows[TILE * 32];
+    uint4 rows[8][TILE];  // quad-major: rows[q][pos(i)] = sources 4q..4q+3 of tile slot i
     uint4 ix[2 * (TILE + 1)];
     uint2 xarcs[TILE];
-    uint32_t dirty[TILE / 32];
+    uint8_t dirtyb[TILE];
 };
 
 // cp.async.wait_group takes an immediate: dispatch on the pending count.
@@ -136,124 +136,133 @@ __device__ __forceinline__ void cp_async8_ca(void* smem, const void* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
-// Tile rows are swizzled: the 16-byte chunk q (sources 4q..4q+3) of node i
-// sits at chunk q ^ (i & 7) of the node's 128-byte row, so 8 consecutive
-// nodes reading the same chunk hit 8 distinct bank groups.
-__device__ __forceinline__ int swz(int i, int q) { return i * 32 + ((q ^ (i & 7)) << 2); }
-__device__ __forceinline__ int swz_lane(int i, int lane) { return swz(i, lane >> 2) + (lane & 3); }
+// Scan chunks cover 64 consecutive node ids, aligned to multiples of 64, in
+// both passes; a lane owns 2 consecutive nodes of a chunk.  Within each
+// 64-slot block, slot o = 2l + j sits at position 32 j + l, so the 32 lanes
+// reading "their" j-th node touch 32 consecutive 16-byte positions: no bank
+// conflicts and a constant offset per quad.
+constexpr int SPAN = 64;
+__device__ __forceinline__ int pos_of(int i) { return (i & ~63) | ((i & 1) << 5) | ((i >> 1) & 31); }
 
-__device__ __forceinline__ uint4 ld4(const uint32_t* rs, int i, int q) {
-    return *reinterpret_cast<const uint4*>(rs + swz(i, q));
-}
 __device__ __forceinline__ uint4 addmin4(uint4 x, uint32_t w, uint4 m) {
     return make_uint4(__viaddmin_u32(x.x, w, m.x), __viaddmin_u32(x.y, w, m.y), __viaddmin_u32(x.z, w, m.z),
                       __viaddmin_u32(x.w, w, m.w));
-}
-__device__ __forceinline__ uint4 min4(uint4 a, uint4 b) {
-    return make_uint4(min(a.x, b.x), min(a.y, b.y), min(a.z, b.z), min(a.w, b.w));
 }
 __device__ __forceinline__ uint4 shfl_up4(uint4 v, int d) {
     return make_uint4(__shfl_up_sync(FULL_MASK, v.x, d), __shfl_up_sync(FULL_MASK, v.y, d),
                       __shfl_up_sync(FULL_MASK, v.z, d), __shfl_up_sync(FULL_MASK, v.w, d));
 }
+__device__ __forceinline__ uint32_t diff4(uint4 a, uint4 b) {
+    return (a.x ^ b.x) | (a.y ^ b.y) | (a.z ^ b.z) | (a.w ^ b.w);
+}
 
-// Fast passes (every arc source a staged tile slot).  A pass walks the run in
-// chunks of 32 nodes, one node per lane, 4 sources per lane at a time.  For a
-// chunk, each node first takes c = min(d[v], min over its non-carry arcs of
-// d[u] + w) -- sources in earlier chunks (or the halo) are already final for
-// this pass, sources in the same chunk are taken as they were at the chunk's
-// start -- and then the carry chain x_v = min(c_v, x_{v-1} + w(v-1, v)) is
-// solved for all 32 nodes at once as a (min, +) prefix scan over the warp
-// (Hillis-Steele, 5 shuffle steps; the weight prefixes are shared by all
-// sources).  The forward pass takes arcs from lower ids, the backward pass
-// from higher ids, so every arc is relaxed once per sweep.
+// Fast pass (every arc source a staged tile slot).  The run is walked in
+// 64-node chunks (ascending forward, descending backward); lane l owns two
+// consecutive nodes of the chunk in pass order and handles 4 sources at a
+// time.  Per node,
+//   c_v = min(d[v], min over non-carry arcs u -> v of d[u] + w)
+// with sources in earlier chunks (or the halo) already final for this pass
+// and sources in the same chunk as they were at the chunk's start.  Then the
+// carry chain x_v = min(c_v, x_prev + w(prev, v)) is solved exactly: each
+// lane runs it over its own nodes (x = min(L, x_in + S) with L the chain
+// from infinity and S the summed carry weights), a (min, +) warp scan over
+// the lanes' (L_last, S_last) pairs gives every lane its x_in, and a fix-up
+// writes min(L, x_in + S).  The forward pass takes arcs from lower ids, the
+// backward pass from higher ids, so every arc is relaxed once per sweep.
 template <int TILE, bool FWD>
 __device__ __forceinline__ bool scan_pass(TileSmem<TILE>& sm, int len, uint32_t x0, int lane) {
     constexpr int NCH = TILE / 32;
-    uint32_t* rs = sm.rows;
     const uint2* xa = sm.xarcs;
     bool changed = false;
-    const int nchunks = (len + 31) >> 5;
+    const int nchunks = (len + SPAN - 1) / SPAN;
     for (int cc = 0; cc < nchunks; ++cc) {
-        const int c = FWD ? cc : nchunks - 1 - cc;
+        const int c = FWD ? cc : nchunks - 1 - cc;  // chunk covers ids [64c, 64c + 64)
         if (FWD) {
-            cp_async_wait_pending(NCH - 1 - c);  // own-row chunk c has landed
+            const int last_grp = min(NCH - 1, (min(len, (c + 1) * SPAN) - 1) >> 5);
+            cp_async_wait_pending(NCH - 1 - last_grp);  // own rows of the chunk have landed
             __syncwarp();
         }
-        // node of this lane: ascending ids forward, descending backward
-        const int i = FWD ? (c << 5) + lane : (len - 1) - ((cc << 5) + lane);
-        const bool valid = FWD ? i < len : i >= 0;
-        const int ii = valid ? i : 0;
-        const uint4 a = sm.ix[2 * ii];
-        const uint4 b = sm.ix[2 * ii + 1];
-        uint32_t wc = valid ? min(FWD ? a.x : a.y, INF_U) : INF_U;  // carry arc into this node
-        // inline non-carry arcs of this direction; absent ones read slot 0 and never win
-        const int s0 = FWD ? static_cast<int>(b.y & 0xFFFFu) : static_cast<int>(b.z & 0xFFFFu);
-        const int s1 = static_cast<int>(b.y >> 16);
-        const uint32_t w0 = FWD ? a.z : b.x;
-        const uint32_t w1 = a.w;
-        uint32_t xb = 0, xe = 0;  // extra arcs
-        if (valid && (b.z & IX_EXTRA)) {
-            const uint32_t nfx = (b.z >> 16) & 0xFFu;
-            if (FWD) {
-                xb = b.w;
-                xe = b.w + nfx;
-            } else {
-                xb = b.w + nfx;
-                xe = sm.ix[2 * ii + 3].w;
+        int p_own[2], p0[2], p1[2];
+        bool valid[2];
+        uint32_t w[2], S[2], w0[2], w1[2], xb[2], xe[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            // pass order: forward node 64c + 2l + j, backward node 64c + 63 - 2l - j
+            const int node = FWD ? c * SPAN + 2 * lane + j : c * SPAN + 63 - 2 * lane - j;
+            valid[j] = node < len;
+            const int ii = valid[j] ? node : 0;
+            p_own[j] = FWD ? c * SPAN + j * 32 + lane : c * SPAN + (1 - j) * 32 + 31 - lane;
+            const uint4 a = sm.ix[2 * ii];
+            const uint4 b = sm.ix[2 * ii + 1];
+            w[j] = valid[j] ? min(FWD ? a.x : a.y, INF_U) : INF_U;
+            S[j] = j == 0 ? w[0] : min(S[0] + w[1], INF_U);
+            p0[j] = pos_of(FWD ? static_cast<int>(b.y & 0xFFFFu) : static_cast<int>(b.z & 0xFFFFu));
+            p1[j] = pos_of(static_cast<int>(b.y >> 16));
+            w0[j] = valid[j] ? (FWD ? a.z : b.x) : NO_CARRY;
+            w1[j] = valid[j] ? a.w : NO_CARRY;
+            xb[j] = 0u;
+            xe[j] = 0u;
+            if (valid[j] && (b.z & IX_EXTRA)) {
+                const uint32_t nfx = (b.z >> 16) & 0xFFu;
+                xb[j] = FWD ? b.w : b.w + nfx;
+                xe[j] = FWD ? b.w + nfx : sm.ix[2 * ii + 3].w;
             }
         }
-        // weight prefixes of the carry chain: W[k] = sum of the carry weights of
-        // lanes (lane - 2^k, lane], saturated at INF_U
+        // carry-weight prefixes over the lanes: W[k] = summed S over lanes
+        // (lane - 2^k, lane]; lanes below 2^k get INF_U, which never wins
         uint32_t W[5];
         {
-            uint32_t w = wc;
+            uint32_t acc = S[1];
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
-                W[k] = w;
-                const uint32_t o = __shfl_up_sync(FULL_MASK, w, 1 << k);
-                if (lane >= (1 << k)) w = min(w + o, INF_U);
+                W[k] = lane >= (1 << k) ? acc : INF_U;
+                const uint32_t o = __shfl_up_sync(FULL_MASK, acc, 1 << k);
+                if (lane >= (1 << k)) acc = min(acc + o, INF_U);
             }
         }
-        // carry into lane 0 from the last node of the previous chunk (already stored)
-        const int prev = FWD ? (c << 5) - 1 : i + 1;
+        // the node before the chunk in pass order feeds lane 0 (already final)
+        const int prev = FWD ? c * SPAN - 1 : (c + 1) * SPAN;
         const bool has_prev = lane == 0 && (FWD ? prev >= 0 : prev < len);
-        unsigned any_drop = 0u;
-#pragma unroll 2
-        for (int q = 0; q < 8; ++q) {
-            const uint4 cur = ld4(rs, ii, q);
-            uint4 cv = addmin4(ld4(rs, s0, q), w0, cur);
-            if constexpr (FWD) cv = addmin4(ld4(rs, s1, q), w1, cv);
-            for (uint32_t e = xb; e < xe; ++e) cv = addmin4(ld4(rs, xa[e - x0].x, q), xa[e - x0].y, cv);
-            if (has_prev) cv = addmin4(ld4(rs, prev, q), wc, cv);
-            if (!valid) cv = make_uint4(INF_U, INF_U, INF_U, INF_U);
+        const int p_prev = pos_of(has_prev ? prev : 0);
+        uint32_t drop0 = 0u, drop1 = 0u;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                const uint4 o = shfl_up4(cv, 1 << k);
-                if (lane >= (1 << k)) cv = addmin4(o, W[k], cv);
+        for (int q = 0; q < 8; ++q) {
+            const uint4* rq = sm.rows[q];
+            const uint4 cur0 = rq[p_own[0]];
+            const uint4 cur1 = rq[p_own[1]];
+            uint4 L0 = addmin4(rq[p0[0]], w0[0], cur0);
+            uint4 c1 = addmin4(rq[p0[1]], w0[1], cur1);
+            if constexpr (FWD) {
+                L0 = addmin4(rq[p1[0]], w1[0], L0);
+                c1 = addmin4(rq[p1[1]], w1[1], c1);
             }
-            const bool dropped = valid && (cv.x < cur.x || cv.y < cur.y || cv.z < cur.z || cv.w < cur.w);
-            if (dropped) *reinterpret_cast<uint4*>(rs + swz(ii, q)) = min4(cv, cur);
-            any_drop |= dropped ? 1u : 0u;
+            for (uint32_t e = xb[0]; e < xe[0]; ++e) L0 = addmin4(rq[pos_of(xa[e - x0].x)], xa[e - x0].y, L0);
+            for (uint32_t e = xb[1]; e < xe[1]; ++e) c1 = addmin4(rq[pos_of(xa[e - x0].x)], xa[e - x0].y, c1);
+            const uint4 L1 = addmin4(L0, w[1], c1);
+            uint4 cin = make_uint4(INF_U, INF_U, INF_U, INF_U);
+            uint4 A = L1;
+            if (has_prev) {
+                cin = rq[p_prev];
+                A = addmin4(cin, S[1], A);
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) A = addmin4(shfl_up4(A, 1 << k), W[k], A);
+            uint4 xin = shfl_up4(A, 1);
+            if (lane == 0) xin = cin;
+            const uint4 x0v = addmin4(xin, S[0], L0);
+            const uint4 x1v = addmin4(xin, S[1], L1);
+            // x <= cur always; store where valid, note any change
+            if (valid[0]) sm.rows[q][p_own[0]] = x0v;
+            if (valid[1]) sm.rows[q][p_own[1]] = x1v;
+            drop0 |= diff4(x0v, cur0);
+            drop1 |= diff4(x1v, cur1);
         }
-        const unsigned m = __ballot_sync(FULL_MASK, any_drop != 0u);
-        if (m) {
+        const bool d0 = valid[0] && drop0 != 0u, d1 = valid[1] && drop1 != 0u;
+        if (__any_sync(FULL_MASK, d0 || d1)) {
             changed = true;
-            // dirty bits by node id; a backward chunk maps lane l to node top - l
-            if (lane == 0) {
-                if (FWD) {
-                    sm.dirty[c] |= m;
-                } else {
-                    const int top = (len - 1) - (cc << 5);
-                    unsigned mm = m;
-                    while (mm) {
-                        const int l = __ffs(mm) - 1;
-                        mm &= mm - 1;
-                        const int node = top - l;
-                        sm.dirty[node >> 5] |= 1u << (node & 31);
-                    }
-                }
-            }
+            const int n0 = FWD ? c * SPAN + 2 * lane : c * SPAN + 63 - 2 * lane;
+            if (d0) sm.dirtyb[n0] = 1;
+            if (d1) sm.dirtyb[FWD ? n0 + 1 : n0 - 1] = 1;
         }
         __syncwarp();  // stores of this chunk visible before the next chunk reads them
     }
@@ -275,7 +284,9 @@ __device__ __forceinline__ bool passes_fast(TileSmem<TILE>& sm, int len, uint32_
 template <int TILE>
 __device__ __noinline__ bool passes_generic(const BfParams& p, TileSmem<TILE>& sm, int r0, int len, int lane,
                                             int64_t lane_off) {
-    const uint32_t* rs = sm.rows;
+    uint32_t* rs = reinterpret_cast<uint32_t*>(&sm.rows[0][0]);
+    // word of source lane `lane` of tile slot i in the quad-major layout
+    auto at = [&](int i) -> uint32_t& { return rs[((lane >> 2) * TILE + pos_of(i)) * 4 + (lane & 3)]; };
     const uint32_t* rows = p.seg.rows;
     const int64_t ld = p.seg.ld;
     bool changed = false;
@@ -284,20 +295,20 @@ __device__ __noinline__ bool passes_generic(const BfParams& p, TileSmem<TILE>& s
     uint32_t carry = INF_U;
     for (int i = 0; i < len; ++i) {
         const int4 d = __ldg(p.g.node_desc + r0 + i);
-        const uint32_t cur = rs[swz_lane(i, lane)];
+        const uint32_t cur = at(i);
         uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.x), cur);
         for (int q = d.z; q < d.w; ++q) {
             const uint2 e = __ldg(p.g.arc2 + q);
             const uint32_t x = (e.x & GLOBAL_REF) ? ld_l2(rows + static_cast<int64_t>(e.x & ~GLOBAL_REF) * ld + lane_off + lane)
-                                                  : rs[swz_lane(static_cast<int>(e.x), lane)];
+                                                  : at(static_cast<int>(e.x));
             best = __viaddmin_u32(x, e.y, best);
         }
         const bool dropped = best < cur;
-        if (dropped) sm.rows[swz_lane(i, lane)] = best;
+        if (dropped) at(i) = best;
         const unsigned m = __ballot_sync(FULL_MASK, dropped);
         if (m) {
             changed = true;
-            if (lane == 0) sm.dirty[i >> 5] |= 1u << (i & 31);
+            if (lane == 0) sm.dirtyb[i] = 1;
         }
         carry = best;
     }
@@ -305,18 +316,18 @@ __device__ __noinline__ bool passes_generic(const BfParams& p, TileSmem<TILE>& s
     for (int i = len - 1; i >= 0; --i) {
         const int4 d = __ldg(p.g.node_desc + r0 + i);
         const int end = __ldg(&p.g.node_desc[r0 + i + 1].z);
-        const uint32_t cur = rs[swz_lane(i, lane)];
+        const uint32_t cur = at(i);
         uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.y), cur);
         for (int q = d.w; q < end; ++q) {
             const uint2 e = __ldg(p.g.arc2 + q);
-            best = __viaddmin_u32(rs[swz_lane(static_cast<int>(e.x), lane)], e.y, best);
+            best = __viaddmin_u32(at(static_cast<int>(e.x)), e.y, best);
         }
         const bool dropped = best < cur;
-        if (dropped) sm.rows[swz_lane(i, lane)] = best;
+        if (dropped) at(i) = best;
         const unsigned m = __ballot_sync(FULL_MASK, dropped);
         if (m) {
             changed = true;
-            if (lane == 0) sm.dirty[i >> 5] |= 1u << (i & 31);
+            if (lane == 0) sm.dirtyb[i] = 1;
         }
         carry = best;
     }
@@ -351,7 +362,7 @@ __device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, Tile
         const int i = i0 + (lane >> 3);
         if (i < hn) {
             const int node = __ldg(p.g.halo_nodes + h0 + i);
-            cp_async16(sm.rows + swz(len + i, lane & 7),
+            cp_async16(&sm.rows[lane & 7][pos_of(len + i)],
                        rows + static_cast<int64_t>(node) * ld + lane_off + (lane & 7) * 4);
         }
     }
@@ -365,13 +376,22 @@ __device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, Tile
             for (int q = 0; q < 8; ++q) {
                 const int i = base + q * 4 + (lane >> 3);
                 if (i < len)
-                    cp_async16(sm.rows + swz(i, lane & 7),
+                    cp_async16(&sm.rows[lane & 7][pos_of(i)],
                                rows + static_cast<int64_t>(r0 + i) * ld + lane_off + (lane & 7) * 4);
             }
         }
         cp_async_commit();
     }
-    if (lane < NCH) sm.dirty[lane] = 0u;
+    for (int i = lane; i < len; i += 32) sm.dirtyb[i] = 0;
+    // Slots of the last 64-block past the staged rows are read (as nodes that
+    // do not exist) by the chunk scans; they must hold INF, not whatever the
+    // shared memory held before: a value above 2^31 plus a blocking INF
+    // weight would wrap to a small number.
+    {
+        const int top = ((len + SPAN - 1) / SPAN) * SPAN;
+        for (int t = len + hn + (lane >> 3); t < top; t += 4)
+            sm.rows[lane & 7][pos_of(t)] = make_uint4(INF_U, INF_U, INF_U, INF_U);
+    }
     cp_async_wait_pending(NCH - 1);  // group 0 and the first row chunk landed
     __syncwarp();
 
@@ -379,24 +399,13 @@ __device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, Tile
     node_visits += static_cast<unsigned long long>(len);
     __syncwarp();
     if (changed) {
-        // 4 dirty nodes per step, 8 lanes x 16 bytes per node row
+        // 4 nodes per step, 8 lanes x 16 bytes per node row
         const int sub = lane >> 3, q = lane & 7;
-        for (int wd = 0; wd < (len + 31) / 32; ++wd) {
-            uint32_t bits = sm.dirty[wd];
-            while (bits) {
-                int pick = -1;
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int bit = bits ? __ffs(bits) - 1 : -1;
-                    if (bit >= 0) bits &= bits - 1;
-                    if (t == sub) pick = bit;
-                }
-                if (pick >= 0) {
-                    const int i = wd * 32 + pick;
-                    __stcg(reinterpret_cast<uint4*>(rows + static_cast<int64_t>(r0 + i) * ld + lane_off + q * 4),
-                           *reinterpret_cast<const uint4*>(sm.rows + swz(i, q)));
-                }
-            }
+        for (int i0 = 0; i0 < len; i0 += 4) {
+            const int i = i0 + sub;
+            if (i < len && sm.dirtyb[i])
+                __stcg(reinterpret_cast<uint4*>(rows + static_cast<int64_t>(r0 + i) * ld + lane_off + q * 4),
+                       sm.rows[q][pos_of(i)]);
         }
     }
     __syncwarp();

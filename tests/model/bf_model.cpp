@@ -53,15 +53,17 @@ extern "C" int bfm_rows(int V, long long E, const long long* rp, const int* col,
                 for (int i = 0; i < len; ++i) tile[i] = rows[static_cast<size_t>(r0 + i) * ld + c];
                 for (int h = 0; h < hn; ++h) tile[len + h] = rows[static_cast<size_t>(p.halo_nodes[h0 + h]) * ld + c];
                 std::vector<char> dirty(static_cast<size_t>(len), 0);
-                // The kernel walks each pass in chunks of 32 nodes: a node's
-                // non-carry arcs read the tile as it was when its chunk started,
-                // then the carry chain is solved in node order.
+                // The kernel walks each pass in chunks of SPAN node ids aligned to
+                // multiples of SPAN (ascending forward, descending backward): a node's non-carry
+                // arcs read the tile as it was when its chunk started, then
+                // the carry chain is solved in pass order.
+                constexpr int SPAN = 64;
                 std::vector<uint32_t> oth(static_cast<size_t>(len));
                 auto src = [&](uint32_t ref) {
                     return (ref & GLOBAL_REF) ? rows[static_cast<size_t>(ref & ~GLOBAL_REF) * ld + c] : tile[ref];
                 };
-                for (int c0 = 0; c0 < len; c0 += 32) {
-                    const int c1 = std::min(len, c0 + 32);
+                for (int c0 = 0; c0 < len; c0 += SPAN) {
+                    const int c1 = std::min(len, c0 + SPAN);
                     for (int i = c0; i < c1; ++i) {
                         const int4 d = p.node_desc[r0 + i];
                         uint32_t o = 0xFFFFFFFFu;
@@ -75,8 +77,8 @@ extern "C" int bfm_rows(int V, long long E, const long long* rp, const int* col,
                         if (best < tile[i]) { tile[i] = best; dirty[i] = 1; changed = true; }
                     }
                 }
-                for (int top = len - 1; top >= 0; top -= 32) {
-                    const int bot = std::max(-1, top - 32);
+                for (int cb = ((len - 1) / SPAN) * SPAN; cb >= 0; cb -= SPAN) {
+                    const int top = std::min(len - 1, cb + SPAN - 1), bot = cb - 1;
                     for (int i = top; i > bot; --i) {
                         const int4 d = p.node_desc[r0 + i];
                         uint32_t o = 0xFFFFFFFFu;

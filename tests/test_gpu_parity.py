@@ -141,7 +141,31 @@ def test_route_device_pointers_and_stream(router, orc):
     s.synchronize()
     router.sync()
     c, p, st = orc.route_orders(g, o, "dijkstra", "brute", NT)
-    assert (cost.cpu().numpy() == c).all() and (perm.cpu().numpy() == p).all() and (status.cpu().numpy() == st).all()
+    _assert_same(o, (cost.cpu().numpy(), perm.cpu().numpy(), status.cpu().numpy()), (c, p, st))
+
+
+def test_route_device_pointers_default_stream(router, orc):
+    import torch
+    g, o = synth.medium_workload(n_orders=64)
+    router.load_graph(g)
+    offs = torch.from_numpy(o.offs).cuda()
+    picks = torch.from_numpy(o.picks).cuda()
+    cost, perm, status = router.route_orders(offs, picks)
+    torch.cuda.synchronize()
+    router.sync()
+    c, p, st = orc.route_orders(g, o, "dijkstra", "brute", NT)
+    _assert_same(o, (cost.cpu().numpy(), perm.cpu().numpy(), status.cpu().numpy()), (c, p, st))
+
+
+def _assert_same(o, got, want):
+    cost, perm, status = got
+    c, p, st = want
+    bad_st = np.nonzero(status != st)[0]
+    bad_c = np.nonzero(cost != c)[0]
+    bad_p = sorted({int(np.searchsorted(o.offs, i, side="right") - 1) for i in np.nonzero(perm[:len(p)] != p)[0]})
+    msg = (f"status differs at {bad_st[:10].tolist()}, cost differs at {bad_c[:10].tolist()} "
+           f"(got {cost[bad_c[:5]].tolist()} want {c[bad_c[:5]].tolist()}), perm differs in orders {bad_p[:10]}")
+    assert len(bad_st) == 0 and len(bad_c) == 0 and len(bad_p) == 0, msg
 
 
 def test_route_statuses_and_edge_cases(router, orc):
