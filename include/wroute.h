@@ -80,9 +80,10 @@ typedef struct {
 /* Tunables (picked by the autotuner; results never depend on them). */
 typedef struct {
     int32_t run_target;     /* Bellman-Ford tile: target nodes per run (consecutive ids) */
-    int32_t tile_cap;       /* nodes (run + halo) staged in shared memory per tile: 64, 128, 256 or 512 */
+    int32_t tile_cap;       /* nodes (run + halo) staged in shared memory per tile: 128, 256 or 512 */
     int32_t enum_units;     /* sequence units (of 120 sequences) per thread per scheduled chunk */
     int32_t enum_max_units_per_launch; /* rank-range segment: units per enumeration launch (0 = all) */
+    int32_t bf_warps;       /* warps sharing one sweep tile: 4 or 8 (0 = 8 for 512-node tiles, else 4) */
 } wr_tuning;
 
 /* Counters of the last call (device-timed with CUDA events on its stream). */

@@ -186,7 +186,7 @@ int upload_partition(wr_ctx* c) {
     g.run_flags = c->g_flags.as<int32_t>();
     g.node_ix = c->g_ix.as<uint4>();
     g.xarc2 = c->g_xarc.as<uint2>();
-    return wr::bf_prepare(p.tile_cap, c->device, &c->bf_info);
+    return wr::bf_prepare(p.tile_cap, c->tune.bf_warps, c->device, &c->bf_info);
 }
 
 int partition(wr_ctx* c) {
@@ -353,6 +353,7 @@ int wr_create(const wr_config* cfg, wr_ctx** out) {
     ctx->tune.tile_cap = 256;
     ctx->tune.enum_units = 4;
     ctx->tune.enum_max_units_per_launch = 0;
+    ctx->tune.bf_warps = 0;
     ctx->enum_blocks = wr::tour_enum_blocks(c.device);
     if (ctx->err.ensure(sizeof(int)) == false || cudaMemset(ctx->err.p, 0, sizeof(int)) != cudaSuccess) {
         delete ctx;
@@ -771,15 +772,20 @@ int wr_get_tuning(wr_ctx* c, wr_tuning* out) {
 
 int wr_set_tuning(wr_ctx* c, const wr_tuning* t) {
     if (!c || !t) return WR_EINVAL;
-    if (t->run_target < 1 || (t->tile_cap != 64 && t->tile_cap != 128 && t->tile_cap != 256 && t->tile_cap != 512) || t->enum_units < 1 ||
+    if (t->run_target < 1 || (t->tile_cap != 128 && t->tile_cap != 256 && t->tile_cap != 512) || t->enum_units < 1 ||
         t->enum_max_units_per_launch < 0 || t->run_target > t->tile_cap)
         return WR_EINVAL;
     RC(set_device(c));
+    if (t->bf_warps != 0 && t->bf_warps != 4 && t->bf_warps != 8) return WR_EINVAL;
+    if (t->tile_cap >= 512 && t->bf_warps == 4) return WR_EINVAL;
     const bool repart = t->run_target != c->tune.run_target || t->tile_cap != c->tune.tile_cap;
+    const bool relaunch = t->bf_warps != c->tune.bf_warps;
     c->tune = *t;
     if (repart && c->has_graph) {
         CK(cudaDeviceSynchronize());
         RC(partition(c));
+    } else if (relaunch && c->has_graph) {
+        RC(wr::bf_prepare(c->hp.tile_cap, c->tune.bf_warps, c->device, &c->bf_info));
     }
     return WR_OK;
 }

@@ -136,13 +136,14 @@ __device__ __forceinline__ void cp_async8_ca(void* smem, const void* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
-// Scan chunks cover 64 consecutive node ids, aligned to multiples of 64, in
-// both passes; a lane owns 2 consecutive nodes of a chunk.  Within each
-// 64-slot block, slot o = 2l + j sits at position 32 j + l, so the 32 lanes
-// reading "their" j-th node touch 32 consecutive 16-byte positions: no bank
-// conflicts and a constant offset per quad.
-constexpr int SPAN = 64;
-__device__ __forceinline__ int pos_of(int i) { return (i & ~63) | ((i & 1) << 5) | ((i >> 1) & 31); }
+// Scan chunks cover SPAN = 32 * SEG consecutive node ids, aligned to
+// multiples of SPAN, in both passes; a lane owns SEG consecutive nodes of a
+// chunk.  Within each SPAN-slot block, slot o = SEG * l + j sits at position
+// 32 j + l, so the 32 lanes reading "their" j-th node touch 32 consecutive
+// 16-byte positions: no bank conflicts and a constant offset per quad.
+constexpr int SEG = 2;
+constexpr int SPAN = 32 * SEG;
+__device__ __forceinline__ int pos_of(int i) { return (i & ~(SPAN - 1)) | ((i % SEG) << 5) | ((i / SEG) & 31); }
 
 __device__ __forceinline__ uint4 addmin4(uint4 x, uint32_t w, uint4 m) {
     return make_uint4(__viaddmin_u32(x.x, w, m.x), __viaddmin_u32(x.y, w, m.y), __viaddmin_u32(x.z, w, m.z),
@@ -157,7 +158,7 @@ __device__ __forceinline__ uint32_t diff4(uint4 a, uint4 b) {
 }
 
 // Fast pass (every arc source a staged tile slot).  The run is walked in
-// 64-node chunks (ascending forward, descending backward); lane l owns two
+// SPAN-node chunks (ascending forward, descending backward); lane l owns SEG
 // consecutive nodes of the chunk in pass order and handles 4 sources at a
 // time.  Per node,
 //   c_v = min(d[v], min over non-carry arcs u -> v of d[u] + w)
@@ -169,33 +170,33 @@ __device__ __forceinline__ uint32_t diff4(uint4 a, uint4 b) {
 // the lanes' (L_last, S_last) pairs gives every lane its x_in, and a fix-up
 // writes min(L, x_in + S).  The forward pass takes arcs from lower ids, the
 // backward pass from higher ids, so every arc is relaxed once per sweep.
-template <int TILE, bool FWD>
-__device__ __forceinline__ bool scan_pass(TileSmem<TILE>& sm, int len, uint32_t x0, int lane) {
+template <int TILE, bool FWD, int NQ>
+__device__ __forceinline__ bool scan_pass(TileSmem<TILE>& sm, int len, uint32_t x0, int lane, int q0) {
     constexpr int NCH = TILE / 32;
     const uint2* xa = sm.xarcs;
     bool changed = false;
     const int nchunks = (len + SPAN - 1) / SPAN;
     for (int cc = 0; cc < nchunks; ++cc) {
-        const int c = FWD ? cc : nchunks - 1 - cc;  // chunk covers ids [64c, 64c + 64)
+        const int c = FWD ? cc : nchunks - 1 - cc;  // chunk covers ids [SPAN c, SPAN c + SPAN)
         if (FWD) {
             const int last_grp = min(NCH - 1, (min(len, (c + 1) * SPAN) - 1) >> 5);
             cp_async_wait_pending(NCH - 1 - last_grp);  // own rows of the chunk have landed
             __syncwarp();
         }
-        int p_own[2], p0[2], p1[2];
-        bool valid[2];
-        uint32_t w[2], S[2], w0[2], w1[2], xb[2], xe[2];
+        int p_own[SEG], p0[SEG], p1[SEG];
+        bool valid[SEG];
+        uint32_t w[SEG], S[SEG], w0[SEG], w1[SEG], xb[SEG], xe[SEG];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            // pass order: forward node 64c + 2l + j, backward node 64c + 63 - 2l - j
-            const int node = FWD ? c * SPAN + 2 * lane + j : c * SPAN + 63 - 2 * lane - j;
+        for (int j = 0; j < SEG; ++j) {
+            // pass order: forward node SPAN c + SEG l + j, backward node SPAN c + SPAN - 1 - SEG l - j
+            const int node = FWD ? c * SPAN + SEG * lane + j : c * SPAN + (SPAN - 1) - SEG * lane - j;
             valid[j] = node < len;
             const int ii = valid[j] ? node : 0;
-            p_own[j] = FWD ? c * SPAN + j * 32 + lane : c * SPAN + (1 - j) * 32 + 31 - lane;
+            p_own[j] = FWD ? c * SPAN + j * 32 + lane : c * SPAN + (SEG - 1 - j) * 32 + 31 - lane;
             const uint4 a = sm.ix[2 * ii];
             const uint4 b = sm.ix[2 * ii + 1];
             w[j] = valid[j] ? min(FWD ? a.x : a.y, INF_U) : INF_U;
-            S[j] = j == 0 ? w[0] : min(S[0] + w[1], INF_U);
+            S[j] = j == 0 ? w[0] : min(S[j > 0 ? j - 1 : 0] + w[j], INF_U);
             p0[j] = pos_of(FWD ? static_cast<int>(b.y & 0xFFFFu) : static_cast<int>(b.z & 0xFFFFu));
             p1[j] = pos_of(static_cast<int>(b.y >> 16));
             w0[j] = valid[j] ? (FWD ? a.z : b.x) : NO_CARRY;
@@ -212,7 +213,7 @@ __device__ __forceinline__ bool scan_pass(TileSmem<TILE>& sm, int len, uint32_t 
         // (lane - 2^k, lane]; lanes below 2^k get INF_U, which never wins
         uint32_t W[5];
         {
-            uint32_t acc = S[1];
+            uint32_t acc = S[SEG - 1];
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 W[k] = lane >= (1 << k) ? acc : INF_U;
@@ -224,57 +225,64 @@ __device__ __forceinline__ bool scan_pass(TileSmem<TILE>& sm, int len, uint32_t 
         const int prev = FWD ? c * SPAN - 1 : (c + 1) * SPAN;
         const bool has_prev = lane == 0 && (FWD ? prev >= 0 : prev < len);
         const int p_prev = pos_of(has_prev ? prev : 0);
-        uint32_t drop0 = 0u, drop1 = 0u;
+        uint32_t drop[SEG];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int j = 0; j < SEG; ++j) drop[j] = 0u;
+#pragma unroll
+        for (int qq = 0; qq < NQ; ++qq) {
+            const int q = q0 + qq;
             const uint4* rq = sm.rows[q];
-            const uint4 cur0 = rq[p_own[0]];
-            const uint4 cur1 = rq[p_own[1]];
-            uint4 L0 = addmin4(rq[p0[0]], w0[0], cur0);
-            uint4 c1 = addmin4(rq[p0[1]], w0[1], cur1);
-            if constexpr (FWD) {
-                L0 = addmin4(rq[p1[0]], w1[0], L0);
-                c1 = addmin4(rq[p1[1]], w1[1], c1);
+            uint4 cur[SEG], L[SEG];
+#pragma unroll
+            for (int j = 0; j < SEG; ++j) {
+                cur[j] = rq[p_own[j]];
+                uint4 cv = addmin4(rq[p0[j]], w0[j], cur[j]);
+                if constexpr (FWD) cv = addmin4(rq[p1[j]], w1[j], cv);
+                for (uint32_t e = xb[j]; e < xe[j]; ++e) cv = addmin4(rq[pos_of(xa[e - x0].x)], xa[e - x0].y, cv);
+                L[j] = j == 0 ? cv : addmin4(L[j > 0 ? j - 1 : 0], w[j], cv);
             }
-            for (uint32_t e = xb[0]; e < xe[0]; ++e) L0 = addmin4(rq[pos_of(xa[e - x0].x)], xa[e - x0].y, L0);
-            for (uint32_t e = xb[1]; e < xe[1]; ++e) c1 = addmin4(rq[pos_of(xa[e - x0].x)], xa[e - x0].y, c1);
-            const uint4 L1 = addmin4(L0, w[1], c1);
             uint4 cin = make_uint4(INF_U, INF_U, INF_U, INF_U);
-            uint4 A = L1;
+            uint4 A = L[SEG - 1];
             if (has_prev) {
                 cin = rq[p_prev];
-                A = addmin4(cin, S[1], A);
+                A = addmin4(cin, S[SEG - 1], A);
             }
 #pragma unroll
             for (int k = 0; k < 5; ++k) A = addmin4(shfl_up4(A, 1 << k), W[k], A);
             uint4 xin = shfl_up4(A, 1);
             if (lane == 0) xin = cin;
-            const uint4 x0v = addmin4(xin, S[0], L0);
-            const uint4 x1v = addmin4(xin, S[1], L1);
-            // x <= cur always; store where valid, note any change
-            if (valid[0]) sm.rows[q][p_own[0]] = x0v;
-            if (valid[1]) sm.rows[q][p_own[1]] = x1v;
-            drop0 |= diff4(x0v, cur0);
-            drop1 |= diff4(x1v, cur1);
+#pragma unroll
+            for (int j = 0; j < SEG; ++j) {
+                // x <= cur always; store where valid, note any change
+                const uint4 x = addmin4(xin, S[j], L[j]);
+                if (valid[j]) sm.rows[q][p_own[j]] = x;
+                drop[j] |= diff4(x, cur[j]);
+            }
         }
-        const bool d0 = valid[0] && drop0 != 0u, d1 = valid[1] && drop1 != 0u;
-        if (__any_sync(FULL_MASK, d0 || d1)) {
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < SEG; ++j) any |= valid[j] && drop[j] != 0u;
+        if (__any_sync(FULL_MASK, any)) {
             changed = true;
-            const int n0 = FWD ? c * SPAN + 2 * lane : c * SPAN + 63 - 2 * lane;
-            if (d0) sm.dirtyb[n0] = 1;
-            if (d1) sm.dirtyb[FWD ? n0 + 1 : n0 - 1] = 1;
+#pragma unroll
+            for (int j = 0; j < SEG; ++j) {
+                if (valid[j] && drop[j] != 0u) {
+                    const int node = FWD ? c * SPAN + SEG * lane + j : c * SPAN + (SPAN - 1) - SEG * lane - j;
+                    sm.dirtyb[node] = 1;
+                }
+            }
         }
         __syncwarp();  // stores of this chunk visible before the next chunk reads them
     }
     return changed;
 }
 
-template <int TILE>
-__device__ __forceinline__ bool passes_fast(TileSmem<TILE>& sm, int len, uint32_t x0, int lane) {
-    const bool f = scan_pass<TILE, true>(sm, len, x0, lane);
+template <int TILE, int NQ>
+__device__ __forceinline__ bool passes_fast(TileSmem<TILE>& sm, int len, uint32_t x0, int lane, int q0) {
+    const bool f = scan_pass<TILE, true, NQ>(sm, len, x0, lane, q0);
     cp_async_wait_pending(0);
     __syncwarp();
-    const bool b = scan_pass<TILE, false>(sm, len, x0, lane);
+    const bool b = scan_pass<TILE, false, NQ>(sm, len, x0, lane, q0);
     return f || b;
 }
 
@@ -334,14 +342,23 @@ __device__ __noinline__ bool passes_generic(const BfParams& p, TileSmem<TILE>& s
     return changed;
 }
 
-// One tile: stage (own rows in 32-node chunks so the forward pass can start
-// on the first chunk while the rest is in flight), forward pass, backward
-// pass, write back the rows that dropped.  Returns true (warp-uniform) if
+// One tile, processed by the whole CTA: NQW warps, warp w owning the 8 / NQW
+// quads (4 sources each) starting at quad w * (8 / NQW).  Every warp stages
+// its own quads of the halo and of the own rows (own rows in 32-node chunks,
+// so the forward pass can start on the first chunk while the rest is in
+// flight); the run's descriptors and extra arcs are staged by all threads.
+// Then each warp runs the forward and backward passes over its quads, and
+// the CTA writes back the rows that dropped.  Returns true (CTA-uniform) if
 // any row dropped.  Each pass relaxes every arc of its direction once.
-template <int TILE>
-__device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, TileSmem<TILE>& sm, int lane,
+template <int TILE, int NQW>
+__device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, TileSmem<TILE>& sm,
                                            unsigned long long& node_visits) {
     constexpr int NCH = TILE / 32;
+    constexpr int NQ = 8 / NQW;      // quads per warp
+    constexpr int NPI = 32 / NQ;     // nodes per warp instruction when staging
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int q0 = warp * NQ;
+    const int qs = q0 + lane % NQ;   // the quad this lane stages
     const int r0 = __ldg(p.g.run_ptr + r);
     const int len = __ldg(p.g.run_ptr + r + 1) - r0;
     const int h0 = __ldg(p.g.halo_ptr + r);
@@ -353,70 +370,74 @@ __device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, Tile
     const uint32_t x0 = __ldg(&p.g.node_ix[2 * static_cast<int64_t>(r0) + 1].w);
     const uint32_t x1 = __ldg(&p.g.node_ix[2 * static_cast<int64_t>(r0 + len) + 1].w);
 
-    // group 0: descriptors, extra arcs, halo rows
+    // group 0: descriptors and extra arcs (all threads), this warp's quads of the halo rows
     if (simple) {
-        for (int i = lane; i < 2 * (len + 1); i += 32) cp_async16(&sm.ix[i], &p.g.node_ix[2 * static_cast<int64_t>(r0) + i]);
-        for (uint32_t q = x0 + lane; q < x1; q += 32) cp_async8_ca(&sm.xarcs[q - x0], &p.g.xarc2[q]);
+        for (int i = tid; i < 2 * (len + 1); i += 32 * NQW)
+            cp_async16(&sm.ix[i], &p.g.node_ix[2 * static_cast<int64_t>(r0) + i]);
+        for (uint32_t q = x0 + tid; q < x1; q += 32 * NQW) cp_async8_ca(&sm.xarcs[q - x0], &p.g.xarc2[q]);
     }
-    for (int i0 = 0; i0 < hn; i0 += 4) {
-        const int i = i0 + (lane >> 3);
-        if (i < hn) {
-            const int node = __ldg(p.g.halo_nodes + h0 + i);
-            cp_async16(&sm.rows[lane & 7][pos_of(len + i)],
-                       rows + static_cast<int64_t>(node) * ld + lane_off + (lane & 7) * 4);
-        }
+    for (int i = lane / NQ; i < hn; i += NPI) {
+        const int node = __ldg(p.g.halo_nodes + h0 + i);
+        cp_async16(&sm.rows[qs][pos_of(len + i)], rows + static_cast<int64_t>(node) * ld + lane_off + qs * 4);
     }
     cp_async_commit();
-    // groups 1..NCH: own rows, 32 nodes each (empty groups complete at once)
+    // groups 1..NCH: this warp's quads of the own rows, 32 nodes each (empty groups complete at once)
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
         const int base = c * 32;
         if (base < len) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int i = base + q * 4 + (lane >> 3);
+            for (int t = 0; t < NQ; ++t) {
+                const int i = base + t * NPI + lane / NQ;
                 if (i < len)
-                    cp_async16(&sm.rows[lane & 7][pos_of(i)],
-                               rows + static_cast<int64_t>(r0 + i) * ld + lane_off + (lane & 7) * 4);
+                    cp_async16(&sm.rows[qs][pos_of(i)], rows + static_cast<int64_t>(r0 + i) * ld + lane_off + qs * 4);
             }
         }
         cp_async_commit();
     }
-    for (int i = lane; i < len; i += 32) sm.dirtyb[i] = 0;
-    // Slots of the last 64-block past the staged rows are read (as nodes that
+    for (int i = tid; i < len; i += 32 * NQW) sm.dirtyb[i] = 0;
+    // Slots of the last SPAN-block past the staged rows are read (as nodes that
     // do not exist) by the chunk scans; they must hold INF, not whatever the
     // shared memory held before: a value above 2^31 plus a blocking INF
     // weight would wrap to a small number.
     {
         const int top = ((len + SPAN - 1) / SPAN) * SPAN;
-        for (int t = len + hn + (lane >> 3); t < top; t += 4)
-            sm.rows[lane & 7][pos_of(t)] = make_uint4(INF_U, INF_U, INF_U, INF_U);
+        for (int t = len + hn + lane / NQ; t < top; t += NPI)
+            sm.rows[qs][pos_of(t)] = make_uint4(INF_U, INF_U, INF_U, INF_U);
     }
-    cp_async_wait_pending(NCH - 1);  // group 0 and the first row chunk landed
-    __syncwarp();
+    cp_async_wait_pending(NCH - 1);  // group 0 and the first row chunk of this thread landed
+    __syncthreads();                 // descriptors staged by other warps are visible
 
-    const bool changed = simple ? passes_fast<TILE>(sm, len, x0, lane) : passes_generic<TILE>(p, sm, r0, len, lane, lane_off);
-    node_visits += static_cast<unsigned long long>(len);
-    __syncwarp();
+    bool mine = false;
+    if (simple) {
+        mine = passes_fast<TILE, NQ>(sm, len, x0, lane, q0);
+    } else {
+        cp_async_wait_pending(0);
+        __syncthreads();  // every quad staged
+        if (warp == 0) mine = passes_generic<TILE>(p, sm, r0, len, lane, lane_off);
+    }
+    const bool changed = __syncthreads_or(mine) != 0;
+    if (tid == 0) node_visits += static_cast<unsigned long long>(len);
     if (changed) {
-        // 4 nodes per step, 8 lanes x 16 bytes per node row
-        const int sub = lane >> 3, q = lane & 7;
-        for (int i0 = 0; i0 < len; i0 += 4) {
+        // 4 * NQW nodes per step, 8 threads x 16 bytes per node row
+        const int sub = tid >> 3, q = tid & 7;
+        for (int i0 = 0; i0 < len; i0 += 4 * NQW) {
             const int i = i0 + sub;
             if (i < len && sm.dirtyb[i])
                 __stcg(reinterpret_cast<uint4*>(rows + static_cast<int64_t>(r0 + i) * ld + lane_off + q * 4),
                        sm.rows[q][pos_of(i)]);
         }
     }
-    __syncwarp();
+    __syncthreads();  // shared memory free for the next tile
     return changed;
 }
 
-template <int TILE>
-__global__ void __launch_bounds__(32) bf_sweeps_kernel(BfParams p) {
+template <int TILE, int NQW>
+// NQW warps per CTA, each owning 8 / NQW quads of a tile's 32 sources.
+__global__ void __launch_bounds__(32 * NQW, NQW == 8 ? 2 : 5) bf_sweeps_kernel(BfParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem<TILE>& sm = *reinterpret_cast<TileSmem<TILE>*>(smem_raw);
-    const int lane = threadIdx.x & 31;
+    __shared__ int s_item;
 
     const int n_lanes = segment_lanes(p.seg);
     const int G = (n_lanes + 31) >> 5;
@@ -450,25 +471,28 @@ __global__ void __launch_bounds__(32) bf_sweeps_kernel(BfParams p) {
         }
         const int32_t* list = cur ? p.w.list1 : p.w.list0;
         for (;;) {
-            int it = 0;
-            if (lane == 0) it = atomicAdd(p.w.counts + 2 + cur, 1);  // dynamic tile scheduling
-            it = __shfl_sync(FULL_MASK, it, 0);
+            if (threadIdx.x == 0) s_item = atomicAdd(p.w.counts + 2 + cur, 1);  // dynamic tile scheduling
+            __syncthreads();
+            const int it = s_item;
+            __syncthreads();
             if (it >= cnt) break;
             const int item = __ldcg(list + it);
             const int r = item / G;
             const int g = item - r * G;
-            const bool ch = sweep_tile<TILE>(p, r, g, sm, lane, nodes);
-            if (ch && lane == 0) p.w.stamp[item] = sweep + 1;
-            ++tiles;
-            bytes += static_cast<unsigned long long>(__ldg(p.g.run_meta_bytes + r)) +
-                     256ull * static_cast<unsigned long long>(__ldg(p.g.run_ptr + r + 1) - __ldg(p.g.run_ptr + r));
+            const bool ch = sweep_tile<TILE, NQW>(p, r, g, sm, nodes);
+            if (threadIdx.x == 0) {
+                if (ch) p.w.stamp[item] = sweep + 1;
+                ++tiles;
+                bytes += static_cast<unsigned long long>(__ldg(p.g.run_meta_bytes + r)) +
+                         256ull * static_cast<unsigned long long>(__ldg(p.g.run_ptr + r + 1) - __ldg(p.g.run_ptr + r));
+            }
         }
         if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) break;
         build_list(p, G, sweep + 1, true, cur ? p.w.list0 : p.w.list1, p.w.counts + (cur ^ 1));
         if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) break;
         cur ^= 1;
     }
-    if (lane == 0 && tiles) {
+    if (threadIdx.x == 0 && tiles) {
         atomicAdd(p.w.stats + 1, tiles);
         atomicAdd(p.w.stats + 2, nodes);
         atomicAdd(p.w.stats + 3, bytes);
@@ -478,29 +502,33 @@ __global__ void __launch_bounds__(32) bf_sweeps_kernel(BfParams p) {
 
 // ---------------------------------------------------------------------------
 
-template <int TILE>
+template <int TILE, int NQW>
 static int prepare_one(int device, BfLaunchInfo* info) {
     const size_t smem = sizeof(TileSmem<TILE>);
-    if (cudaFuncSetAttribute(bf_sweeps_kernel<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem)) != cudaSuccess)
+    auto* fn = bf_sweeps_kernel<TILE, NQW>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
         return WR_ECUDA;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bf_sweeps_kernel<TILE>, 32, smem) != cudaSuccess || occ < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * NQW, smem) != cudaSuccess || occ < 1)
         return WR_ECUDA;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return WR_ECUDA;
     info->blocks = occ * sms;
-    info->threads = 32;
+    info->threads = 32 * NQW;
     info->smem = smem;
+    info->fn = reinterpret_cast<const void*>(fn);
     return WR_OK;
 }
 
-int bf_prepare(int tile_cap, int device, BfLaunchInfo* info) {
-    switch (tile_cap) {
-        case 64: return prepare_one<64>(device, info);
-        case 128: return prepare_one<128>(device, info);
-        case 256: return prepare_one<256>(device, info);
-        case 512: return prepare_one<512>(device, info);
+int bf_prepare(int tile_cap, int warps, int device, BfLaunchInfo* info) {
+    if (warps == 0) warps = tile_cap >= 512 ? 8 : 4;
+    if (warps != 4 && warps != 8) return WR_EINVAL;
+    switch (tile_cap * 16 + warps) {
+        case 128 * 16 + 4: return prepare_one<128, 4>(device, info);
+        case 128 * 16 + 8: return prepare_one<128, 8>(device, info);
+        case 256 * 16 + 4: return prepare_one<256, 4>(device, info);
+        case 256 * 16 + 8: return prepare_one<256, 8>(device, info);
+        case 512 * 16 + 8: return prepare_one<512, 8>(device, info);
         default: return WR_EINVAL;
     }
 }
@@ -515,15 +543,8 @@ cudaError_t bf_launch_sweeps(const DevGraph& g, const BfSegment& seg, const BfWo
                              cudaStream_t s) {
     BfParams p{g, seg, w};
     void* args[] = {&p};
-    const void* fn = nullptr;
-    switch (g.tile_cap) {
-        case 64: fn = reinterpret_cast<const void*>(bf_sweeps_kernel<64>); break;
-        case 128: fn = reinterpret_cast<const void*>(bf_sweeps_kernel<128>); break;
-        case 256: fn = reinterpret_cast<const void*>(bf_sweeps_kernel<256>); break;
-        case 512: fn = reinterpret_cast<const void*>(bf_sweeps_kernel<512>); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaLaunchCooperativeKernel(fn, dim3(info.blocks), dim3(info.threads), args, info.smem, s);
+    if (!info.fn) return cudaErrorInvalidValue;
+    return cudaLaunchCooperativeKernel(info.fn, dim3(info.blocks), dim3(info.threads), args, info.smem, s);
 }
 
 // out[b * ld_out + v] = rows[v * ld + b]: 32 x 32 tiles through shared memory.

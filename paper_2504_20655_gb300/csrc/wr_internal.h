@@ -125,8 +125,10 @@ struct BfLaunchInfo {
     int blocks;
     int threads;
     size_t smem;
+    const void* fn;
 };
-int bf_prepare(int tile_cap, int device, BfLaunchInfo* info);  // occupancy of the sweep kernel
+// picks the sweep kernel for (tile_cap, warps per CTA; 0 = default) and its co-resident grid
+int bf_prepare(int tile_cap, int warps, int device, BfLaunchInfo* info);
 cudaError_t bf_launch_init(const DevGraph& g, const BfSegment& seg, const BfWork& w, cudaStream_t s);
 cudaError_t bf_launch_sweeps(const DevGraph& g, const BfSegment& seg, const BfWork& w,
                              const BfLaunchInfo& info, cudaStream_t s);

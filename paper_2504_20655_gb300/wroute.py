@@ -39,7 +39,7 @@ class wr_config(ctypes.Structure):
 
 class wr_tuning(ctypes.Structure):
     _fields_ = [("run_target", ctypes.c_int32), ("tile_cap", ctypes.c_int32), ("enum_units", ctypes.c_int32),
-                ("enum_max_units_per_launch", ctypes.c_int32)]
+                ("enum_max_units_per_launch", ctypes.c_int32), ("bf_warps", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -20,9 +20,10 @@ using namespace wr;
 namespace {
 
 constexpr int TILE = 256;
-constexpr int SPAN = 64;
+constexpr int SEG = 2;
+constexpr int SPAN = 32 * SEG;
 
-int pos_of(int i) { return (i & ~63) | ((i & 1) << 5) | ((i >> 1) & 31); }
+int pos_of(int i) { return (i & ~(SPAN - 1)) | ((i % SEG) << 5) | ((i / SEG) & 31); }
 
 struct Q4 {
     uint32_t v[4];
@@ -47,9 +48,9 @@ struct Smem {
 };
 
 struct Lane {
-    int p_own[2], p0[2], p1[2];
-    bool valid[2];
-    uint32_t w[2], S[2], w0[2], w1[2], xb[2], xe[2];
+    int p_own[SEG], p0[SEG], p1[SEG];
+    bool valid[SEG];
+    uint32_t w[SEG], S[SEG], w0[SEG], w1[SEG], xb[SEG], xe[SEG];
 };
 
 }  // namespace
@@ -64,14 +65,14 @@ bool scan_pass(Smem& sm, bool fwd, int len, uint32_t x0) {
         const int c = fwd ? cc : nchunks - 1 - cc;
         Lane L[32];
         for (int l = 0; l < 32; ++l) {
-            for (int j = 0; j < 2; ++j) {
-                const int node = fwd ? c * SPAN + 2 * l + j : c * SPAN + 63 - 2 * l - j;
+            for (int j = 0; j < SEG; ++j) {
+                const int node = fwd ? c * SPAN + SEG * l + j : c * SPAN + (SPAN - 1) - SEG * l - j;
                 L[l].valid[j] = node < len;
                 const int ii = L[l].valid[j] ? node : 0;
-                L[l].p_own[j] = fwd ? c * SPAN + j * 32 + l : c * SPAN + (1 - j) * 32 + 31 - l;
+                L[l].p_own[j] = fwd ? c * SPAN + j * 32 + l : c * SPAN + (SEG - 1 - j) * 32 + 31 - l;
                 const uint4 a = sm.ix[2 * ii], b = sm.ix[2 * ii + 1];
                 L[l].w[j] = L[l].valid[j] ? std::min(fwd ? a.x : a.y, INF_U) : INF_U;
-                L[l].S[j] = j == 0 ? L[l].w[0] : std::min(L[l].S[0] + L[l].w[1], INF_U);
+                L[l].S[j] = j == 0 ? L[l].w[0] : std::min(L[l].S[j - 1] + L[l].w[j], INF_U);
                 L[l].p0[j] = pos_of(fwd ? static_cast<int>(b.y & 0xFFFFu) : static_cast<int>(b.z & 0xFFFFu));
                 L[l].p1[j] = pos_of(static_cast<int>(b.y >> 16));
                 L[l].w0[j] = L[l].valid[j] ? (fwd ? a.z : b.x) : NO_CARRY;
@@ -85,7 +86,7 @@ bool scan_pass(Smem& sm, bool fwd, int len, uint32_t x0) {
             }
         }
         uint32_t W[32][5], acc[32];
-        for (int l = 0; l < 32; ++l) acc[l] = L[l].S[1];
+        for (int l = 0; l < 32; ++l) acc[l] = L[l].S[SEG - 1];
         for (int k = 0; k < 5; ++k) {
             uint32_t o[32];
             for (int l = 0; l < 32; ++l) {
@@ -98,30 +99,25 @@ bool scan_pass(Smem& sm, bool fwd, int len, uint32_t x0) {
         const int prev = fwd ? c * SPAN - 1 : (c + 1) * SPAN;
         const bool has_prev = fwd ? prev >= 0 : prev < len;
         const int p_prev = pos_of(has_prev ? prev : 0);
-        uint32_t drop[32][2] = {{0u}};
+        uint32_t drop[32][SEG];
+        std::memset(drop, 0, sizeof(drop));
         for (int q = 0; q < 8; ++q) {
-            Q4 cur0[32], cur1[32], L0[32], L1[32], A[32], cin;
+            Q4 cur[32][SEG], Lc[32][SEG], A[32], cin;
             for (int l = 0; l < 32; ++l) {
-                cur0[l] = sm.rows[q][L[l].p_own[0]];
-                cur1[l] = sm.rows[q][L[l].p_own[1]];
-                Q4 a0 = addmin4(sm.rows[q][L[l].p0[0]], L[l].w0[0], cur0[l]);
-                Q4 c1 = addmin4(sm.rows[q][L[l].p0[1]], L[l].w0[1], cur1[l]);
-                if (fwd) {
-                    a0 = addmin4(sm.rows[q][L[l].p1[0]], L[l].w1[0], a0);
-                    c1 = addmin4(sm.rows[q][L[l].p1[1]], L[l].w1[1], c1);
+                for (int j = 0; j < SEG; ++j) {
+                    cur[l][j] = sm.rows[q][L[l].p_own[j]];
+                    Q4 cv = addmin4(sm.rows[q][L[l].p0[j]], L[l].w0[j], cur[l][j]);
+                    if (fwd) cv = addmin4(sm.rows[q][L[l].p1[j]], L[l].w1[j], cv);
+                    for (uint32_t e = L[l].xb[j]; e < L[l].xe[j]; ++e)
+                        cv = addmin4(sm.rows[q][pos_of(static_cast<int>(sm.xarcs[e - x0].x))], sm.xarcs[e - x0].y, cv);
+                    Lc[l][j] = j == 0 ? cv : addmin4(Lc[l][j - 1], L[l].w[j], cv);
                 }
-                for (uint32_t e = L[l].xb[0]; e < L[l].xe[0]; ++e)
-                    a0 = addmin4(sm.rows[q][pos_of(static_cast<int>(sm.xarcs[e - x0].x))], sm.xarcs[e - x0].y, a0);
-                for (uint32_t e = L[l].xb[1]; e < L[l].xe[1]; ++e)
-                    c1 = addmin4(sm.rows[q][pos_of(static_cast<int>(sm.xarcs[e - x0].x))], sm.xarcs[e - x0].y, c1);
-                L0[l] = a0;
-                L1[l] = addmin4(a0, L[l].w[1], c1);
-                A[l] = L1[l];
+                A[l] = Lc[l][SEG - 1];
             }
             for (int t = 0; t < 4; ++t) cin.v[t] = INF_U;
             if (has_prev) {
                 cin = sm.rows[q][p_prev];
-                A[0] = addmin4(cin, L[0].S[1], A[0]);
+                A[0] = addmin4(cin, L[0].S[SEG - 1], A[0]);
             }
             for (int k = 0; k < 5; ++k) {
                 Q4 o[32];
@@ -130,21 +126,20 @@ bool scan_pass(Smem& sm, bool fwd, int len, uint32_t x0) {
             }
             for (int l = 0; l < 32; ++l) {
                 const Q4 xin = l == 0 ? cin : A[l - 1];
-                const Q4 x0v = addmin4(xin, L[l].S[0], L0[l]);
-                const Q4 x1v = addmin4(xin, L[l].S[1], L1[l]);
-                if (L[l].valid[0]) sm.rows[q][L[l].p_own[0]] = x0v;
-                if (L[l].valid[1]) sm.rows[q][L[l].p_own[1]] = x1v;
-                for (int t = 0; t < 4; ++t) {
-                    drop[l][0] |= x0v.v[t] ^ cur0[l].v[t];
-                    drop[l][1] |= x1v.v[t] ^ cur1[l].v[t];
+                for (int j = 0; j < SEG; ++j) {
+                    const Q4 x = addmin4(xin, L[l].S[j], Lc[l][j]);
+                    if (L[l].valid[j]) sm.rows[q][L[l].p_own[j]] = x;
+                    for (int t = 0; t < 4; ++t) drop[l][j] |= x.v[t] ^ cur[l][j].v[t];
                 }
             }
         }
-        for (int l = 0; l < 32; ++l) {
-            const int n0 = fwd ? c * SPAN + 2 * l : c * SPAN + 63 - 2 * l;
-            if (L[l].valid[0] && drop[l][0]) { sm.dirtyb[n0] = 1; changed = true; }
-            if (L[l].valid[1] && drop[l][1]) { sm.dirtyb[fwd ? n0 + 1 : n0 - 1] = 1; changed = true; }
-        }
+        for (int l = 0; l < 32; ++l)
+            for (int j = 0; j < SEG; ++j)
+                if (L[l].valid[j] && drop[l][j]) {
+                    const int node = fwd ? c * SPAN + SEG * l + j : c * SPAN + (SPAN - 1) - SEG * l - j;
+                    sm.dirtyb[node] = 1;
+                    changed = true;
+                }
     }
     return changed;
 }

@@ -66,7 +66,7 @@ def fast_path_fraction(model, g, run_target, tile_cap):
                                          w.ctypes.data_as(P), run_target, tile_cap))
 
 
-TILINGS = [(96, 128), (32, 64), (200, 256), (1, 64), (64, 64), (400, 512)]
+TILINGS = [(96, 128), (32, 128), (200, 256), (1, 128), (128, 128), (400, 512)]
 
 
 @pytest.mark.parametrize("rt,tc", TILINGS)

@@ -67,9 +67,11 @@ def test_bf_rows_high_in_degree(router, orc):
     assert (router.bf_rows(src) == orc.sssp_rows(g, src)).all()
 
 
-@pytest.mark.parametrize("tune", [dict(run_target=96, tile_cap=128), dict(run_target=32, tile_cap=64),
-                                  dict(run_target=200, tile_cap=256), dict(run_target=1, tile_cap=64),
-                                  dict(run_target=400, tile_cap=512), dict(run_target=256, tile_cap=256)])
+@pytest.mark.parametrize("tune", [dict(run_target=96, tile_cap=128), dict(run_target=32, tile_cap=128),
+                                  dict(run_target=200, tile_cap=256), dict(run_target=1, tile_cap=128),
+                                  dict(run_target=400, tile_cap=512), dict(run_target=256, tile_cap=256),
+                                  dict(run_target=200, tile_cap=256, bf_warps=8),
+                                  dict(run_target=100, tile_cap=128, bf_warps=8)])
 def test_bf_rows_medium_tuning_invariant(router, orc, tune):
     g = synth.medium_layout().build()
     saved = router.tuning()
@@ -267,3 +269,37 @@ def test_batching_sample(router, orc):
     cost, perm, status = router.route_orders(sub.offs, sub.picks)
     c, p, s = orc.route_orders(g, sub, "dijkstra", "heldkarp", NT)
     assert (status == s).all() and (cost == c).all() and (perm[:len(p)] == p).all()
+
+
+def test_scale_submatrix_full_size(wr, orc):
+    """Scale workload at full size, as the benchmark runs it: 4096 sources over
+    V = 1,002,001 under the 2 GiB budget (8 segments).  Sampled rows and their
+    checksums against the oracle; symmetry of the whole 4096 x 4096 submatrix
+    (the layout is undirected) and the triangle inequality on a sample."""
+    import torch
+    g, src = synth.scale_workload()
+    r = wr.Router(device=0, mem_budget_bytes=2 << 30)
+    try:
+        r.load_graph(g)
+        d_src = torch.from_numpy(src).cuda()
+        sub = torch.empty((len(src), len(src)), dtype=torch.int32, device="cuda")
+        check = torch.empty(len(src), dtype=torch.int64, device="cuda")
+        wr.wr_submatrix(r.ctx, d_src, d_src, sub, check)
+        torch.cuda.synchronize()
+        r.sync()
+        assert r.stats()["n_segments"] == 8
+    finally:
+        r.close()
+    sub = sub.cpu().numpy()
+    check = check.cpu().numpy().view(np.uint64)
+    assert (sub == sub.T).all() and (np.diag(sub) == 0).all()
+    pick = [0, 511, 512, 2047, 3000, 4095]  # across segment boundaries
+    rows = orc.sssp_rows(g, src[pick], "dijkstra", NT)
+    weights = (2 * np.arange(g.V, dtype=np.uint64) + 1)
+    for i, p in enumerate(pick):
+        assert (sub[p] == rows[i][src]).all()
+        assert check[p] == np.uint64((rows[i].astype(np.uint64) * weights).sum(dtype=np.uint64))
+    s = synth.distinct_sources(64, len(src), 99)
+    m = sub[np.ix_(s, s)].astype(np.int64)
+    for k in range(len(s)):
+        assert (m <= m[:, k:k + 1] + m[k:k + 1, :]).all()
