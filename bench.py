@@ -195,7 +195,7 @@ def run_scale(args):
     world, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    g, src = synth.scale_workload()
+    g, src = synth.scale_workload(n_src=args.scale_sources)
     n = len(src)
     r = wroute.Router(device=local, mem_budget_bytes=args.budget_gib << 30)
     if args.tune:
@@ -240,7 +240,7 @@ def run_scale(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": "scale: 1000 aisles x 500 slots x 2 levels, 2 cross-aisles (V=1002001, 3007998 arcs); "
-                               "rows of 4096 distinct slot sources consumed as a 4096x4096 submatrix + checksums",
+                               f"rows of {n} distinct slot sources consumed as a {n}x{n} submatrix + checksums",
                    "budget_gib": args.budget_gib, "segments": st["n_segments"], "tuning": r.tuning(),
                    "l2": "rows (2 GiB per segment) exceed L2; 512 MiB flush between steps"},
         "roofline": {"kernel": "bf_sweeps_kernel", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
@@ -379,6 +379,7 @@ def main():
     ap.add_argument("--tune", default="")
     ap.add_argument("--traffic", default="")
     ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--scale-sources", type=int, default=4096, help="sources of the scale workload")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
