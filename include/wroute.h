@@ -176,6 +176,38 @@ int wr_tour_eval_static(int32_t n_orders, const int32_t* k, const int32_t* D, in
                         int32_t* perm, int32_t* status, void* cuda_stream);
 
 int wr_get_stats(wr_ctx* ctx, wr_stats* out);
+
+/* Sweep trace (observability; the paper has no counterpart).  With max_sweeps > 0
+ * every Bellman-Ford segment records, for each sweep t < max_sweeps, the number of
+ * (run, 32-source group) tiles in its frontier and the device clock (ns) at which it
+ * started; one more entry with 0 tiles marks the end.  Each segment overwrites the
+ * previous segment's trace.  0 turns tracing off.  WR_EINVAL above 2^20. */
+int wr_set_trace(wr_ctx* ctx, int32_t max_sweeps);
+/* Copies up to max_entries (tiles, ns) pairs of the last segment's trace to
+ * out[2i], out[2i+1] and sets *n_out to the number recorded (0 when tracing is off). */
+int wr_get_trace(wr_ctx* ctx, int64_t* out, int32_t max_entries, int32_t* n_out);
+/* Batching (the paper has no counterpart).  A plan captures the whole path (a1-a7) for
+ * one batch of n_orders orders into a CUDA graph that is launched again and again on new
+ * batch contents.  offs (n_orders + 1 entries), picks (max_picks), cost (n_orders), perm
+ * (max_picks) and status (n_orders) are DEVICE buffers owned by the caller; every launch
+ * reads offs/picks and writes cost/perm/status exactly as wr_route_orders would.  Each
+ * batch must have offs[0] = 0 and offs[n_orders] <= max_picks (an order whose range leaves
+ * [0, max_picks] comes back WR_ORDER_BAD).  A smaller batch is padded with empty orders
+ * (offs[i+1] = offs[i]), which come back WR_ORDER_BAD.  The plan keeps a private copy of
+ * the context's graph and tuning (taken at creation) and its own work buffers, so later
+ * calls on the context do not disturb it; enum_max_units_per_launch is not used (one
+ * enumeration launch).  Creation runs the path once uncaptured to size every buffer.
+ * Launches of one plan must not overlap on the GPU (they share its work buffers). */
+typedef struct wr_plan wr_plan;
+int wr_plan_create(wr_ctx* ctx, int32_t n_orders, int64_t max_picks, const int64_t* offs, const int32_t* picks,
+                   int32_t* cost, int32_t* perm, int32_t* status, wr_plan** out);
+int wr_plan_launch(wr_plan* plan, void* cuda_stream);
+/* Waits for the plan's last launch and returns any recorded device-side error. */
+int wr_plan_sync(wr_plan* plan);
+/* Counters of the last launch (phase times are not recorded inside the graph: 0). */
+int wr_plan_get_stats(wr_plan* plan, wr_stats* out);
+void wr_plan_destroy(wr_plan* plan);
+
 int wr_get_tuning(wr_ctx* ctx, wr_tuning* out);
 /* Changing run_target or tile_cap re-partitions the loaded graph. */
 int wr_set_tuning(wr_ctx* ctx, const wr_tuning* t);

@@ -57,6 +57,9 @@ struct wr_ctx {
     DBuf node_flag, src_index, src_list, n_src, block_sums;
     DBuf offs, picks, order_status, order_flags, D, unit_off, best, unit_ctr;
     DBuf out_cost, out_perm, out_status, kbuf, dgiven, src_in, sub, check;
+    DBuf trace;          // sweep trace of the last Bellman-Ford segment
+    int32_t trace_cap = 0;
+    bool capturing = false;  // enqueueing into a CUDA graph: no timing events, no host syncs
     // stats
     wr_stats last{};
     std::vector<cudaEvent_t> events;
@@ -111,7 +114,9 @@ struct PhaseTimer {
     cudaStream_t s;
     int phase;
     int b = -1;
-    PhaseTimer(wr_ctx* c_, cudaStream_t s_, int ph) : c(c_), s(s_), phase(ph) { record(c, s, &b); }
+    PhaseTimer(wr_ctx* c_, cudaStream_t s_, int ph) : c(c_), s(s_), phase(ph) {
+        if (!c->capturing) record(c, s, &b);
+    }
     ~PhaseTimer() {
         int e = -1;
         if (b >= 0 && record(c, s, &e) == WR_OK) c->ev_phase[phase].push_back({b, e});
@@ -127,10 +132,14 @@ int begin_call(wr_ctx* c, cudaStream_t s) {
     RC(ensure(c->stats, 8 * sizeof(unsigned long long)));
     RC(ensure(c->err, sizeof(int)));
     CK(cudaMemsetAsync(c->stats.p, 0, 8 * sizeof(unsigned long long), s));
+    if (c->capturing) {
+        c->ev_call_begin = c->ev_call_end = -1;
+        return WR_OK;
+    }
     return record(c, s, &c->ev_call_begin);
 }
 
-int end_call(wr_ctx* c, cudaStream_t s) { return record(c, s, &c->ev_call_end); }
+int end_call(wr_ctx* c, cudaStream_t s) { return c->capturing ? WR_OK : record(c, s, &c->ev_call_end); }
 
 // Returns the recorded device error (and clears it); the stream must be idle.
 int take_device_error(wr_ctx* c) {
@@ -226,12 +235,15 @@ wr::BfWork bf_work(wr_ctx* c, int32_t seg_lanes) {
     w.err = c->err.as<int>();
     w.max_spins = c->cfg.barrier_max_spins ? c->cfg.barrier_max_spins : DEFAULT_SPINS;
     w.stats = c->stats.as<unsigned long long>();
+    w.trace = c->trace_cap > 0 ? c->trace.as<long long>() : nullptr;
+    w.trace_cap = c->trace_cap > 0 ? c->trace_cap : 0;
     return w;
 }
 
 // One Bellman-Ford segment: init + sweeps.
 int run_bf_segment(wr_ctx* c, const wr::BfSegment& seg, cudaStream_t s) {
     wr::BfWork w = bf_work(c, seg.lanes);
+    if (w.trace) CK(cudaMemsetAsync(w.trace, 0xFF, static_cast<size_t>(w.trace_cap) * 16, s));
     {
         PhaseTimer t(c, s, 1);
         CK(wr::bf_launch_init(c->dg, seg, w, s));
@@ -262,7 +274,7 @@ int run_tours(wr_ctx* c, int32_t n, const int32_t* k_dev, const wr::TourBufs& tb
         PhaseTimer t(c, s, 4);
         CK(wr::tour_launch_units(n, k_dev, tb, s, &c->launches));
         const int upt = c->tune.enum_units > 0 ? c->tune.enum_units : 4;
-        if (c->tune.enum_max_units_per_launch > 0) {
+        if (c->tune.enum_max_units_per_launch > 0 && !c->capturing) {
             long long total = 0;
             CK(cudaMemcpyAsync(&total, tb.unit_off + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
@@ -308,6 +320,20 @@ int finish_host_call(wr_ctx* c, cudaStream_t s) {
 }
 
 int check_ptr_kind(int k) { return (k == WR_HOST || k == WR_DEVICE) ? WR_OK : WR_EINVAL; }
+
+// Partition and upload c->hg, size the per-node work arrays.
+int finish_graph(wr_ctx* c) {
+    const int32_t V = c->hg.V;
+    c->has_graph = false;
+    RC(partition(c));
+    RC(ensure(c->node_flag, static_cast<size_t>(V) + 16));
+    RC(ensure(c->src_index, static_cast<size_t>(V) * 4 + 16));
+    RC(ensure(c->src_list, static_cast<size_t>(V) * 4 + 16));
+    RC(ensure(c->n_src, 16));
+    RC(ensure(c->block_sums, (static_cast<size_t>(V) / 4096 + 2) * 4));
+    c->has_graph = true;
+    return WR_OK;
+}
 
 }  // namespace
 
@@ -372,7 +398,7 @@ void wr_destroy(wr_ctx* c) {
                     &c->counts, &c->bar, &c->err, &c->stats, &c->node_flag, &c->src_index, &c->src_list,
                     &c->n_src, &c->block_sums, &c->offs, &c->picks, &c->order_status, &c->order_flags, &c->D,
                     &c->unit_off, &c->best, &c->unit_ctr, &c->out_cost, &c->out_perm, &c->out_status, &c->kbuf,
-                    &c->dgiven, &c->src_in, &c->sub, &c->check};
+                    &c->dgiven, &c->src_in, &c->sub, &c->check, &c->trace};
     for (DBuf* b : bufs) b->release();
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     delete c;
@@ -417,15 +443,55 @@ int wr_load_graph(wr_ctx* c, int32_t V, int64_t E, const int64_t* row_ptr, const
     c->hg.V = g.V;
     c->hg.E = g.E;
     c->hg.depot = g.depot;
-    c->has_graph = false;
-    RC(partition(c));
-    RC(ensure(c->node_flag, static_cast<size_t>(V) + 16));
-    RC(ensure(c->src_index, static_cast<size_t>(V) * 4 + 16));
-    RC(ensure(c->src_list, static_cast<size_t>(V) * 4 + 16));
-    RC(ensure(c->n_src, 16));
-    RC(ensure(c->block_sums, (static_cast<size_t>(V) / 4096 + 2) * 4));
-    c->has_graph = true;
-    return WR_OK;
+    return finish_graph(c);
+}
+
+// a1-a7 for n orders whose offs/picks are on the device, np_bound >= offs[n]:
+// enqueues everything on s with no host synchronisation (the segments are
+// planned for the worst case of np_bound + 1 distinct sources).
+static int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_picks, int64_t np_bound,
+                         int32_t* o_cost, int32_t* o_perm, int32_t* o_status, cudaStream_t s) {
+    const int32_t V = c->dg.V;
+    wr::TourBufs tb{};
+    tb.offs = d_offs;
+    tb.picks = d_picks;
+    RC(ensure_tour_bufs(c, n, tb));
+    // a2: sources = depot + distinct pick nodes of valid orders
+    {
+        PhaseTimer t(c, s, 0);
+        CK(cudaMemsetAsync(c->node_flag.p, 0, static_cast<size_t>(V), s));
+        CK(cudaMemsetAsync(c->order_flags.p, 0, static_cast<size_t>(n) * 4, s));
+        CK(wr::tour_launch_select(n, d_offs, d_picks, V, c->dg.depot, c->cfg.max_k, c->node_flag.as<uint8_t>(),
+                                  tb.order_status, s));
+        c->launches++;
+        CK(wr::tour_launch_compact(V, c->node_flag.as<uint8_t>(), c->src_index.as<int32_t>(),
+                                   c->src_list.as<int32_t>(), c->n_src.as<int32_t>(), c->block_sums.as<int32_t>(), s,
+                                   &c->launches));
+    }
+    // segments of the worst-case source count; empty ones exit on the device
+    const int64_t worst = np_bound + 1 < V ? np_bound + 1 : V;
+    const int32_t lanes_needed = static_cast<int32_t>((worst + 31) / 32 * 32);
+    const int32_t blanes = budget_lanes(c);
+    if (blanes < 32) return WR_ENOMEM;
+    const int32_t seg_lanes = lanes_needed < blanes ? lanes_needed : blanes;
+    const int32_t n_seg = (lanes_needed + seg_lanes - 1) / seg_lanes;
+    RC(ensure_bf(c, seg_lanes));
+    for (int32_t sg = 0; sg < n_seg; ++sg) {
+        wr::BfSegment seg;
+        seg.rows = c->rows.as<uint32_t>();
+        seg.ld = seg_lanes;
+        seg.src = c->src_list.as<int32_t>();
+        seg.n_src_dev = c->n_src.as<int32_t>();
+        seg.n_src_host = 0;
+        seg.first = sg * seg_lanes;
+        seg.lanes = seg_lanes;
+        RC(run_bf_segment(c, seg, s));
+        PhaseTimer t(c, s, 3);
+        CK(wr::tour_launch_gather(n, tb, c->dg.depot, c->src_index.as<int32_t>(), seg, s));
+        c->launches++;
+    }
+    c->last.n_segments = n_seg;
+    return run_tours(c, n, nullptr, tb, o_cost, o_perm, 0, o_status, s);
 }
 
 int wr_route_orders(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* picks, int32_t* cost, int32_t* perm,
@@ -452,7 +518,6 @@ int wr_route_orders(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pi
     if (first != 0 || np < 0) return WR_EINVAL;
     if (np > 0 && (!picks || !perm)) return WR_EINVAL;
     if (n == 0) return WR_OK;
-    const int32_t V = c->dg.V;
     RC(begin_call(c, s));
     // inputs on the device
     const int64_t* d_offs = offs;
@@ -465,10 +530,6 @@ int wr_route_orders(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pi
         d_offs = c->offs.as<int64_t>();
         d_picks = c->picks.as<int32_t>();
     }
-    wr::TourBufs tb{};
-    tb.offs = d_offs;
-    tb.picks = d_picks;
-    RC(ensure_tour_bufs(c, n, tb));
     int32_t* o_cost = cost;
     int32_t* o_perm = perm;
     int32_t* o_status = status;
@@ -480,42 +541,7 @@ int wr_route_orders(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pi
         o_status = c->out_status.as<int32_t>();
         o_perm = c->out_perm.as<int32_t>();
     }
-    // a2: sources = depot + distinct pick nodes of valid orders
-    {
-        PhaseTimer t(c, s, 0);
-        CK(cudaMemsetAsync(c->node_flag.p, 0, static_cast<size_t>(V), s));
-        CK(cudaMemsetAsync(c->order_flags.p, 0, static_cast<size_t>(n) * 4, s));
-        CK(wr::tour_launch_select(n, d_offs, d_picks, V, c->dg.depot, c->cfg.max_k, c->node_flag.as<uint8_t>(),
-                                  tb.order_status, s));
-        c->launches++;
-        CK(wr::tour_launch_compact(V, c->node_flag.as<uint8_t>(), c->src_index.as<int32_t>(),
-                                   c->src_list.as<int32_t>(), c->n_src.as<int32_t>(), c->block_sums.as<int32_t>(), s,
-                                   &c->launches));
-    }
-    // segments of the worst-case source count; empty ones exit on the device
-    const int64_t worst = np + 1 < V ? np + 1 : V;
-    const int32_t lanes_needed = static_cast<int32_t>((worst + 31) / 32 * 32);
-    const int32_t blanes = budget_lanes(c);
-    if (blanes < 32) return WR_ENOMEM;
-    const int32_t seg_lanes = lanes_needed < blanes ? lanes_needed : blanes;
-    const int32_t n_seg = (lanes_needed + seg_lanes - 1) / seg_lanes;
-    RC(ensure_bf(c, seg_lanes));
-    for (int32_t sg = 0; sg < n_seg; ++sg) {
-        wr::BfSegment seg;
-        seg.rows = c->rows.as<uint32_t>();
-        seg.ld = seg_lanes;
-        seg.src = c->src_list.as<int32_t>();
-        seg.n_src_dev = c->n_src.as<int32_t>();
-        seg.n_src_host = 0;
-        seg.first = sg * seg_lanes;
-        seg.lanes = seg_lanes;
-        RC(run_bf_segment(c, seg, s));
-        PhaseTimer t(c, s, 3);
-        CK(wr::tour_launch_gather(n, tb, c->dg.depot, c->src_index.as<int32_t>(), seg, s));
-        c->launches++;
-    }
-    c->last.n_segments = n_seg;
-    RC(run_tours(c, n, nullptr, tb, o_cost, o_perm, 0, o_status, s));
+    RC(enqueue_route(c, n, d_offs, d_picks, np, o_cost, o_perm, o_status, s));
     RC(end_call(c, s));
     c->last.n_orders = n;
     if (ptr_kind == WR_HOST) {
@@ -764,6 +790,32 @@ int wr_get_stats(wr_ctx* c, wr_stats* out) {
     return WR_OK;
 }
 
+int wr_set_trace(wr_ctx* c, int32_t max_sweeps) {
+    if (!c || max_sweeps < 0 || max_sweeps > (1 << 20)) return WR_EINVAL;
+    RC(set_device(c));
+    if (max_sweeps > 0) RC(ensure(c->trace, static_cast<size_t>(max_sweeps) * 16));
+    c->trace_cap = max_sweeps;
+    return WR_OK;
+}
+
+int wr_get_trace(wr_ctx* c, int64_t* out, int32_t max_entries, int32_t* n_out) {
+    if (!c || !n_out || max_entries < 0 || (max_entries > 0 && !out)) return WR_EINVAL;
+    RC(set_device(c));
+    *n_out = 0;
+    if (c->trace_cap <= 0) return WR_OK;
+    CK(cudaStreamSynchronize(c->last_stream));
+    std::vector<long long> h(static_cast<size_t>(c->trace_cap) * 2);
+    CK(cudaMemcpy(h.data(), c->trace.p, h.size() * 8, cudaMemcpyDeviceToHost));
+    int n = 0;
+    while (n < c->trace_cap && h[2 * n] >= 0) ++n;
+    for (int i = 0; i < n && i < max_entries; ++i) {
+        out[2 * i] = h[2 * i];
+        out[2 * i + 1] = h[2 * i + 1];
+    }
+    *n_out = n;
+    return WR_OK;
+}
+
 int wr_get_tuning(wr_ctx* c, wr_tuning* out) {
     if (!c || !out) return WR_EINVAL;
     *out = c->tune;
@@ -787,6 +839,112 @@ int wr_set_tuning(wr_ctx* c, const wr_tuning* t) {
     } else if (relaunch && c->has_graph) {
         RC(wr::bf_prepare(c->hp.tile_cap, c->tune.bf_warps, c->device, &c->bf_info));
     }
+    return WR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batching: the whole path for one fixed-size batch, captured into a CUDA graph.
+
+struct wr_plan {
+    wr_ctx* c = nullptr;      // private context: its own graph copy, tuning and work buffers
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int32_t n = 0;
+    int64_t max_picks = 0;
+    const int64_t* offs = nullptr;
+    const int32_t* picks = nullptr;
+    int32_t *cost = nullptr, *perm = nullptr, *status = nullptr;
+};
+
+void wr_plan_destroy(wr_plan* p) {
+    if (!p) return;
+    if (p->c) cudaSetDevice(p->c->device);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    if (p->c) wr_destroy(p->c);
+    delete p;
+}
+
+int wr_plan_create(wr_ctx* parent, int32_t n, int64_t max_picks, const int64_t* offs, const int32_t* picks,
+                   int32_t* cost, int32_t* perm, int32_t* status, wr_plan** out) {
+    if (!parent || !out || n < 1 || max_picks < 0 || !offs || !cost || !status) return WR_EINVAL;
+    if (max_picks > 0 && (!picks || !perm)) return WR_EINVAL;
+    *out = nullptr;
+    if (!parent->has_graph) return WR_ENOGRAPH;
+    RC(set_device(parent));
+    wr_plan* p = new (std::nothrow) wr_plan();
+    if (!p) return WR_ENOMEM;
+    p->n = n;
+    p->max_picks = max_picks;
+    p->offs = offs;
+    p->picks = picks;
+    p->cost = cost;
+    p->perm = perm;
+    p->status = status;
+    int rc = wr_create(&parent->cfg, &p->c);
+    if (rc == WR_OK) {
+        wr_ctx* c = p->c;
+        c->tune = parent->tune;
+        c->hg = parent->hg;  // host copy of the in-arc graph; re-partitioned and uploaded privately
+        rc = finish_graph(c);
+    }
+    if (rc == WR_OK && cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) rc = WR_ECUDA;
+    // one plain run sizes every buffer, so the captured run allocates nothing
+    if (rc == WR_OK) {
+        wr_ctx* c = p->c;
+        rc = begin_call(c, p->cap);
+        if (rc == WR_OK) rc = enqueue_route(c, n, offs, picks, max_picks, cost, perm, status, p->cap);
+        if (rc == WR_OK) rc = end_call(c, p->cap);
+        if (rc == WR_OK && cudaStreamSynchronize(p->cap) != cudaSuccess) rc = WR_ECUDA;
+        if (rc == WR_OK) rc = take_device_error(c);
+    }
+    if (rc == WR_OK) {
+        wr_ctx* c = p->c;
+        c->capturing = true;
+        if (cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            rc = WR_ECUDA;
+        } else {
+            rc = begin_call(c, p->cap);
+            if (rc == WR_OK) rc = enqueue_route(c, n, offs, picks, max_picks, cost, perm, status, p->cap);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(p->cap, &g);
+            if (rc == WR_OK && e != cudaSuccess) rc = WR_ECUDA;
+            p->graph = g;
+        }
+        c->capturing = false;
+        if (rc == WR_OK && cudaGraphInstantiate(&p->exec, p->graph, 0) != cudaSuccess) rc = WR_ECUDA;
+    }
+    if (rc != WR_OK) {
+        cudaGetLastError();
+        wr_plan_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return WR_OK;
+}
+
+int wr_plan_launch(wr_plan* p, void* stream) {
+    if (!p || !p->exec) return WR_EINVAL;
+    RC(set_device(p->c));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaGraphLaunch(p->exec, s));
+    p->c->last_stream = s;
+    return WR_OK;
+}
+
+int wr_plan_sync(wr_plan* p) {
+    if (!p) return WR_EINVAL;
+    RC(set_device(p->c));
+    CK(cudaStreamSynchronize(p->c->last_stream));
+    return take_device_error(p->c);
+}
+
+int wr_plan_get_stats(wr_plan* p, wr_stats* out) {
+    if (!p || !out) return WR_EINVAL;
+    RC(wr_get_stats(p->c, out));
+    out->n_orders = p->n;
     return WR_OK;
 }
 

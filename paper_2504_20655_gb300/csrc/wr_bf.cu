@@ -100,9 +100,13 @@ __device__ __forceinline__ void build_list(const BfParams& p, int G, int match, 
 
 // Shared memory of one warp: the tile's rows (own nodes then halo), the
 // run's inline node descriptors and extra arcs, and a dirty bit per own node.
+// Each quad plane is padded by one 16-byte slot, so the 8 planes' copies of
+// one position fall in 8 different bank groups (the write-back reads all 8
+// quads of a node in one phase).
 template <int TILE>
 struct TileSmem {
-    uint4 rows[8][TILE];  // quad-major: rows[q][pos(i)] = sources 4q..4q+3 of tile slot i
+    static constexpr int PLANE = TILE + 1;
+    uint4 rows[8][PLANE];  // quad-major: rows[q][pos(i)] = sources 4q..4q+3 of tile slot i
     uint4 ix[2 * (TILE + 1)];
     uint2 xarcs[TILE];
     uint8_t dirtyb[TILE];
@@ -294,7 +298,9 @@ __device__ __noinline__ bool passes_generic(const BfParams& p, TileSmem<TILE>& s
                                             int64_t lane_off) {
     uint32_t* rs = reinterpret_cast<uint32_t*>(&sm.rows[0][0]);
     // word of source lane `lane` of tile slot i in the quad-major layout
-    auto at = [&](int i) -> uint32_t& { return rs[((lane >> 2) * TILE + pos_of(i)) * 4 + (lane & 3)]; };
+    auto at = [&](int i) -> uint32_t& {
+        return rs[((lane >> 2) * TileSmem<TILE>::PLANE + pos_of(i)) * 4 + (lane & 3)];
+    };
     const uint32_t* rows = p.seg.rows;
     const int64_t ld = p.seg.ld;
     bool changed = false;
@@ -358,7 +364,11 @@ __device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, Tile
     constexpr int NPI = 32 / NQ;     // nodes per warp instruction when staging
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int q0 = warp * NQ;
-    const int qs = q0 + lane % NQ;   // the quad this lane stages
+    // Staging: lanes [NPI m', NPI m' + NPI) stage quad q0 + m' of NPI nodes; a
+    // lane's node offset interleaves parities (even nodes on the low half), so
+    // the 8 lanes of a 16-byte access phase hit 8 consecutive positions.
+    const int qs = q0 + lane / NPI;  // the quad this lane stages
+    const int soff = 2 * (lane % (NPI / 2)) + (lane % NPI) / (NPI / 2);
     const int r0 = __ldg(p.g.run_ptr + r);
     const int len = __ldg(p.g.run_ptr + r + 1) - r0;
     const int h0 = __ldg(p.g.halo_ptr + r);
@@ -376,7 +386,9 @@ __device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, Tile
             cp_async16(&sm.ix[i], &p.g.node_ix[2 * static_cast<int64_t>(r0) + i]);
         for (uint32_t q = x0 + tid; q < x1; q += 32 * NQW) cp_async8_ca(&sm.xarcs[q - x0], &p.g.xarc2[q]);
     }
-    for (int i = lane / NQ; i < hn; i += NPI) {
+    for (int i0 = 0; i0 < hn; i0 += NPI) {
+        const int i = i0 + soff;
+        if (i >= hn) break;
         const int node = __ldg(p.g.halo_nodes + h0 + i);
         cp_async16(&sm.rows[qs][pos_of(len + i)], rows + static_cast<int64_t>(node) * ld + lane_off + qs * 4);
     }
@@ -388,7 +400,7 @@ __device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, Tile
         if (base < len) {
 #pragma unroll
             for (int t = 0; t < NQ; ++t) {
-                const int i = base + t * NPI + lane / NQ;
+                const int i = base + t * NPI + soff;
                 if (i < len)
                     cp_async16(&sm.rows[qs][pos_of(i)], rows + static_cast<int64_t>(r0 + i) * ld + lane_off + qs * 4);
             }
@@ -402,7 +414,7 @@ __device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, Tile
     // weight would wrap to a small number.
     {
         const int top = ((len + SPAN - 1) / SPAN) * SPAN;
-        for (int t = len + hn + lane / NQ; t < top; t += NPI)
+        for (int t = len + hn + soff; t < top; t += NPI)
             sm.rows[qs][pos_of(t)] = make_uint4(INF_U, INF_U, INF_U, INF_U);
     }
     cp_async_wait_pending(NCH - 1);  // group 0 and the first row chunk of this thread landed
@@ -460,6 +472,13 @@ __global__ void __launch_bounds__(32 * NQW, NQW == 8 ? 2 : 5) bf_sweeps_kernel(B
     int sweep = 1;
     for (;; ++sweep) {
         const int cnt = ld_volatile(p.w.counts + cur);
+        if (gtid == 0 && sweep <= p.w.trace_cap) {
+            // frontier of this sweep and when it started (the last entry, 0 tiles, is the end)
+            long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            p.w.trace[2 * (sweep - 1)] = cnt;
+            p.w.trace[2 * (sweep - 1) + 1] = t;
+        }
         if (cnt == 0) break;
         if (sweep > p.g.V + 1) {
             if (gtid == 0) atomicCAS(p.w.err, 0, WR_EINTERNAL);

@@ -118,6 +118,8 @@ struct BfWork {
     int* err;
     unsigned long long max_spins;
     unsigned long long* stats;  // [0] sweeps [1] tiles [2] node visits [3] bytes
+    long long* trace;           // optional: per sweep t < trace_cap, [2t] = frontier tiles, [2t+1] = ns
+    int trace_cap;
 };
 
 // launchers (wr_bf.cu)

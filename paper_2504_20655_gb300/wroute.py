@@ -28,7 +28,8 @@ DSTRIDE = 13
 
 EXPORTS = ["wr_create", "wr_destroy", "wr_strerror", "wr_sync", "wr_load_graph", "wr_route_orders", "wr_bf_rows",
            "wr_distance_rows", "wr_submatrix", "wr_tour_eval", "wr_tour_eval_static", "wr_get_stats",
-           "wr_get_tuning", "wr_set_tuning"]
+           "wr_get_tuning", "wr_set_tuning", "wr_set_trace", "wr_get_trace",
+           "wr_plan_create", "wr_plan_launch", "wr_plan_sync", "wr_plan_get_stats", "wr_plan_destroy"]
 WR_STATIC_MAX_ORDERS = 4096
 
 
@@ -92,6 +93,14 @@ def load_library(path: str = LIB_PATH):
     L.wr_get_stats.argtypes = [P, ctypes.POINTER(wr_stats)]
     L.wr_get_tuning.argtypes = [P, ctypes.POINTER(wr_tuning)]
     L.wr_set_tuning.argtypes = [P, ctypes.POINTER(wr_tuning)]
+    L.wr_plan_create.argtypes = [P, i32, i64, P, P, P, P, P, ctypes.POINTER(P)]
+    L.wr_plan_launch.argtypes = [P, P]
+    L.wr_plan_sync.argtypes = [P]
+    L.wr_plan_get_stats.argtypes = [P, ctypes.POINTER(wr_stats)]
+    L.wr_plan_destroy.argtypes = [P]
+    L.wr_plan_destroy.restype = None
+    L.wr_set_trace.argtypes = [P, i32]
+    L.wr_get_trace.argtypes = [P, P, i32, ctypes.POINTER(ctypes.c_int32)]
     for name in EXPORTS:
         if name not in ("wr_destroy", "wr_strerror"):
             getattr(L, name).restype = I
@@ -282,6 +291,78 @@ def wr_set_tuning(ctx, **kw):
     _check(load_library().wr_set_tuning(ctx, ctypes.byref(t)), "wr_set_tuning")
 
 
+def wr_set_trace(ctx, max_sweeps: int):
+    _check(load_library().wr_set_trace(ctx, int(max_sweeps)), "wr_set_trace")
+
+
+def wr_get_trace(ctx, max_entries: int = 1 << 16) -> np.ndarray:
+    """[(frontier tiles, start ns), ...] per sweep of the last segment, then (0, end ns)."""
+    out = np.zeros((max_entries, 2), dtype=np.int64)
+    n = ctypes.c_int32(0)
+    _check(load_library().wr_get_trace(ctx, out.ctypes.data_as(ctypes.c_void_p), max_entries, ctypes.byref(n)),
+           "wr_get_trace")
+    return out[:min(n.value, max_entries)].copy()
+
+
+class Plan:
+    """A batch of n_orders orders captured into a CUDA graph (wr_plan_*).
+
+    The plan owns device tensors offs (n+1), picks (max_picks), cost, perm,
+    status; fill offs/picks (set_batch), launch, then read the outputs."""
+
+    def __init__(self, ctx, n_orders: int, max_picks: int, device=0):
+        import torch
+        dev = torch.device("cuda", device)
+        self.n = int(n_orders)
+        self.max_picks = int(max_picks)
+        self.offs = torch.zeros(self.n + 1, dtype=torch.int64, device=dev)
+        self.picks = torch.zeros(max(self.max_picks, 1), dtype=torch.int32, device=dev)
+        self.cost = torch.empty(self.n, dtype=torch.int32, device=dev)
+        self.perm = torch.empty(max(self.max_picks, 1), dtype=torch.int32, device=dev)
+        self.status = torch.empty(self.n, dtype=torch.int32, device=dev)
+        torch.cuda.synchronize(dev)
+        h = ctypes.c_void_p()
+        _check(load_library().wr_plan_create(ctx, self.n, self.max_picks, self.offs.data_ptr(), self.picks.data_ptr(),
+                                             self.cost.data_ptr(), self.perm.data_ptr(), self.status.data_ptr(),
+                                             ctypes.byref(h)), "wr_plan_create")
+        self.h = h
+
+    def set_batch(self, offs, picks):
+        """Copy a batch (numpy or torch) in; shorter batches are padded with empty orders."""
+        import torch
+        offs = torch.as_tensor(np.asarray(offs, dtype=np.int64) if not _is_torch(offs) else offs)
+        picks = torch.as_tensor(np.asarray(picks, dtype=np.int32) if not _is_torch(picks) else picks)
+        n = offs.shape[0] - 1
+        if n > self.n or int(offs[-1]) > self.max_picks:
+            raise ValueError("batch larger than the plan")
+        self.offs[: n + 1].copy_(offs)
+        self.offs[n + 1:].fill_(int(offs[-1]))
+        if picks.shape[0]:
+            self.picks[: picks.shape[0]].copy_(picks)
+
+    def launch(self, stream=None):
+        _check(load_library().wr_plan_launch(self.h, _stream(stream)), "wr_plan_launch")
+
+    def sync(self):
+        _check(load_library().wr_plan_sync(self.h), "wr_plan_sync")
+
+    def stats(self) -> dict:
+        st = wr_stats()
+        _check(load_library().wr_plan_get_stats(self.h, ctypes.byref(st)), "wr_plan_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self.h is not None:
+            load_library().wr_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------------------
 # convenience wrapper
 # ---------------------------------------------------------------------------
@@ -355,6 +436,15 @@ class Router:
 
     def tuning(self):
         return wr_get_tuning(self.ctx)
+
+    def plan(self, n_orders, max_picks):
+        return Plan(self.ctx, n_orders, max_picks, self.device)
+
+    def set_trace(self, max_sweeps):
+        wr_set_trace(self.ctx, max_sweeps)
+
+    def trace(self):
+        return wr_get_trace(self.ctx)
 
     def set_tuning(self, **kw):
         wr_set_tuning(self.ctx, **kw)

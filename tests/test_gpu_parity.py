@@ -303,3 +303,90 @@ def test_scale_submatrix_full_size(wr, orc):
     m = sub[np.ix_(s, s)].astype(np.int64)
     for k in range(len(s)):
         assert (m <= m[:, k:k + 1] + m[k:k + 1, :]).all()
+
+
+def test_sweep_trace(router, orc):
+    """The sweep trace of a one-segment call: one entry per sweep plus the end marker,
+    frontiers summing to the tile visits, non-decreasing device times; tracing off
+    leaves results unchanged."""
+    g, o = synth.medium_workload(n_orders=64)
+    router.load_graph(g)
+    ref = router.route_orders(o.offs, o.picks)
+    router.set_trace(4096)
+    try:
+        got = router.route_orders(o.offs, o.picks)
+        st = router.stats()
+        tr = router.trace()
+    finally:
+        router.set_trace(0)
+    for a, b in zip(ref, got):
+        assert (np.asarray(a) == np.asarray(b)).all()
+    assert st["n_segments"] == 1
+    assert len(tr) == st["sweeps"] + 1
+    assert tr[-1, 0] == 0 and (tr[:-1, 0] > 0).all()
+    assert int(tr[:, 0].sum()) == st["tile_visits"]
+    assert (np.diff(tr[:, 1]) >= 0).all()
+    assert len(router.trace()) == 0
+
+
+def _plan_run(plan, offs, picks):
+    import torch
+    plan.set_batch(offs, picks)
+    plan.launch()
+    plan.sync()
+    torch.cuda.synchronize()
+    return plan.cost.cpu().numpy(), plan.perm.cpu().numpy(), plan.status.cpu().numpy()
+
+
+def test_plan_graph_matches_direct_calls(router, orc):
+    """A captured plan replays the whole path on new batch contents: each launch equals
+    a direct wr_route_orders call on the same batch, padding orders come back BAD, and
+    loading another graph into the context afterwards does not disturb the plan."""
+    g, o = synth.batching_workload(n_orders=700)
+    router.load_graph(g)
+    a = o.subset(np.arange(0, 500))
+    b = o.subset(np.arange(699, 199, -1))  # other contents, other size
+    np_cap = int(max(a.offs[-1], b.offs[-1])) + 7
+    plan = router.plan(520, np_cap)
+    try:
+        ref_a = router.route_orders(a.offs, a.picks)
+        ref_b = router.route_orders(b.offs, b.picks)
+        tiny = synth.tiny_layout().build()
+        router.load_graph(tiny)  # the plan keeps its own copy of the medium graph
+        for batch, ref in ((a, ref_a), (b, ref_b), (a, ref_a)):
+            cost, perm, status = _plan_run(plan, batch.offs, batch.picks)
+            n, npk = batch.n, int(batch.offs[-1])
+            assert (cost[:n] == ref[0]).all() and (status[:n] == ref[2]).all()
+            assert (perm[:npk] == ref[1][:npk]).all()
+            assert (status[n:] == 2).all()  # padding: empty orders are WR_ORDER_BAD
+        st = plan.stats()
+        assert st["n_orders"] == 520 and st["sequences"] > 0
+    finally:
+        plan.close()
+    c, p, s = orc.route_orders(g, a.subset(np.arange(0, 60)), "dijkstra", "heldkarp", NT)
+    assert (ref_a[0][:60] == c).all() and (ref_a[2][:60] == s).all()
+
+
+def test_plan_batching_full_size(router, orc):
+    """The batching workload at full size through the captured graph the benchmark
+    launches: 20,000 orders, k = 2..12.  Every order against the Held-Karp-lex oracle
+    (cost, argmin, status); brute force on a seeded 5% of the k >= 10 orders."""
+    g, o = synth.batching_workload()
+    router.load_graph(g)
+    plan = router.plan(o.n, int(o.offs[-1]))
+    try:
+        cost, perm, status = _plan_run(plan, o.offs, o.picks)
+    finally:
+        plan.close()
+    c, p, s = orc.route_orders(g, o, "dijkstra", "heldkarp", NT)
+    assert (status == s).all() and (cost == c).all() and (perm[:len(p)] == p).all()
+    k = o.k()
+    big = np.nonzero(k >= 10)[0]
+    rng = np.random.default_rng(2504)
+    pick = np.sort(rng.choice(big, size=max(1, len(big) // 20), replace=False))
+    sub = o.subset(pick)
+    cb, pb, sb = orc.route_orders(g, sub, "dijkstra", "brute", NT)
+    assert (cb == cost[pick]).all() and (sb == status[pick]).all()
+    for j, i in enumerate(pick):
+        lo, hi = o.offs[i], o.offs[i + 1]
+        assert (perm[lo:hi] == pb[sub.offs[j]:sub.offs[j + 1]]).all()
