@@ -74,7 +74,8 @@ typedef struct {
     uint64_t mem_budget_bytes;    /* cap on the distance-row buffer of one source segment */
     int max_k;                    /* largest order size accepted, <= WR_MAX_K */
     uint64_t barrier_max_spins;   /* iteration limit of every device-side wait (0 = default) */
-    const char* tune_path;        /* autotuner table file (NULL = built-in defaults) */
+    const char* tune_path;        /* tuning table file: applied at creation when it exists, written by
+                                     wr_autotune (NULL = built-in defaults, nothing written) */
 } wr_config;
 
 /* Tunables (picked by the autotuner; results never depend on them). */
@@ -83,7 +84,9 @@ typedef struct {
     int32_t tile_cap;       /* nodes (run + halo) staged in shared memory per tile: 128, 256 or 512 */
     int32_t enum_units;     /* sequence units (of 120 sequences) per thread per scheduled chunk */
     int32_t enum_max_units_per_launch; /* rank-range segment: units per enumeration launch (0 = all) */
-    int32_t bf_warps;       /* warps sharing one sweep tile: 4 or 8 (0 = 8 for 512-node tiles, else 4) */
+    int32_t bf_warps;       /* CTA tiling: warps sharing one sweep tile, 4 or 8 (0 = 8 for 512-node tiles, else 4) */
+    int32_t bf_tiling;      /* sweep tiling: 1 = one warp per tile (lane = source; tile_cap 128 or 256),
+                               2 = one CTA per tile (quads of sources per warp); 0 = 2 */
 } wr_tuning;
 
 /* Counters of the last call (device-timed with CUDA events on its stream). */
@@ -204,9 +207,61 @@ int wr_plan_create(wr_ctx* ctx, int32_t n_orders, int64_t max_picks, const int64
 int wr_plan_launch(wr_plan* plan, void* cuda_stream);
 /* Waits for the plan's last launch and returns any recorded device-side error. */
 int wr_plan_sync(wr_plan* plan);
-/* Counters of the last launch (phase times are not recorded inside the graph: 0). */
+/* Counters and phase times of the last launch (the graph holds event-record nodes). */
 int wr_plan_get_stats(wr_plan* plan, wr_stats* out);
 void wr_plan_destroy(wr_plan* plan);
+
+/* Autotuner (the paper has no counterpart).  Times wr_route_orders on the given batch
+ * (median device time of `reps` calls after a warm-up, CUDA events) for each candidate
+ * sweep tiling (warp or CTA tiles, tile_cap, run_target), then for each enumeration
+ * chunk size with the best tiling, and applies the fastest tuning to the context.
+ * Results never depend on the tuning, only the speed does.  When the context was
+ * created with cfg.tune_path, the chosen tuning is written there ("name value"
+ * lines) and read back by wr_create.  Writes the choice to *out when out != NULL.
+ * Each candidate re-partitions the graph on the host. */
+int wr_autotune(wr_ctx* ctx, int32_t n_orders, const int64_t* offs, const int32_t* picks, int ptr_kind,
+                int32_t reps, wr_tuning* out);
+
+/* Serving (the paper has no counterpart).  A server routes a stream of orders that
+ * arrive over time, in real time, with the graph and a cache of distance rows
+ * resident on the device.  Continuous batching: whenever one of n_slots slots is
+ * free, the orders that have arrived (up to max_batch orders and max_batch_picks
+ * picks) form a batch; the rows of its sources the cache lacks are computed by
+ * multi-source Bellman-Ford straight into cache columns (least-recently-used groups
+ * of 32 columns are evicted, never one the batch reads), every order's matrix is
+ * gathered from the cache, and the enumeration runs on the slot's own stream, so
+ * batches overlap on the GPU.  Admission stops growing a batch when its new sources
+ * would not fit the cache.  Every result equals that of wr_route_orders on the
+ * order alone.  The server keeps a private copy of the context's graph and tuning. */
+typedef struct {
+    int32_t max_batch;        /* orders per batch, >= 1 */
+    int64_t max_batch_picks;  /* picks per batch, >= WR_MAX_K; also the largest order accepted */
+    int32_t n_slots;          /* batches in flight, 1..8 */
+    uint64_t cache_bytes;     /* device budget of the row cache: at least 512 rows of V int32 */
+    int32_t plain;            /* 1 = the baseline: one order at a time, rows from scratch, no cache
+                                 (the other fields are ignored) */
+} wr_serve_config;
+
+typedef struct {
+    int64_t orders, batches;
+    int64_t cache_hits;      /* sources of admitted orders found in the cache */
+    int64_t rows_computed;   /* sources whose rows were computed */
+    int64_t evicted_groups;  /* 32-column groups reused */
+    int64_t bf_launches;
+    double wall_s;           /* duration of the last run */
+} wr_serve_stats;
+
+typedef struct wr_server wr_server;
+int wr_serve_create(wr_ctx* ctx, const wr_serve_config* cfg, wr_server** out);
+/* Routes n_orders orders; order i (picks[offs[i] .. offs[i+1])) arrives arrival_s[i]
+ * seconds after the call starts (non-decreasing).  All pointers are host memory.
+ * Writes cost[i], status[i], perm[offs[i] + j] as wr_route_orders does, and done_s[i]
+ * = when its result was on the host (seconds since the call started).  Returns when
+ * every order is done. */
+int wr_serve_run(wr_server* sv, int32_t n_orders, const double* arrival_s, const int64_t* offs, const int32_t* picks,
+                 int32_t* cost, int32_t* perm, int32_t* status, double* done_s);
+int wr_serve_get_stats(wr_server* sv, wr_serve_stats* out);
+void wr_serve_destroy(wr_server* sv);
 
 int wr_get_tuning(wr_ctx* ctx, wr_tuning* out);
 /* Changing run_target or tile_cap re-partitions the loaded graph. */

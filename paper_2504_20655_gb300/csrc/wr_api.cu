@@ -4,89 +4,14 @@
 // enqueues work on the caller's stream.
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
+#include <string>
 #include <vector>
 
-#include "wr_internal.h"
+#include "wr_ctx.h"
 
-namespace {
-
-struct DBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-    bool ensure(size_t need) {
-        if (need <= bytes) return true;
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-        size_t want = need + need / 4 + 256;
-        if (cudaMalloc(&p, want) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        bytes = want;
-        return true;
-    }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    template <class T>
-    T* as() const { return static_cast<T*>(p); }
-};
-
-constexpr unsigned long long DEFAULT_SPINS = 1ull << 24;  // x 64 ns sleeps: about a second
-constexpr uint64_t DEFAULT_BUDGET = 2ull << 30;
-
-}  // namespace
-
-struct wr_ctx {
-    int device = 0;
-    wr_config cfg{};
-    wr_tuning tune{};
-    bool has_graph = false;
-    wr::HostGraph hg;
-    wr::HostPartition hp;
-    wr::DevGraph dg;
-    DBuf g_desc, g_ref, g_w, g_arc2, g_run_ptr, g_halo_ptr, g_halo_nodes, g_rin_ptr, g_rin_list, g_run_of, g_meta, g_flags, g_ix, g_xarc;
-    wr::BfLaunchInfo bf_info{};
-    int enum_blocks = 0;
-    // working buffers
-    DBuf rows, stamp, list0, list1, counts, bar, err, stats;
-    DBuf node_flag, src_index, src_list, n_src, block_sums;
-    DBuf offs, picks, order_status, order_flags, D, unit_off, best, unit_ctr;
-    DBuf out_cost, out_perm, out_status, kbuf, dgiven, src_in, sub, check;
-    DBuf trace;          // sweep trace of the last Bellman-Ford segment
-    int32_t trace_cap = 0;
-    bool capturing = false;  // enqueueing into a CUDA graph: no timing events, no host syncs
-    // stats
-    wr_stats last{};
-    std::vector<cudaEvent_t> events;
-    int n_events_used = 0;
-    int ev_call_begin = -1, ev_call_end = -1;
-    std::vector<std::pair<int, int>> ev_phase[6];  // select, init, bf, gather, enum, finish
-    int launches = 0;
-    cudaStream_t last_stream = nullptr;
-};
-
-namespace {
-
-#define CK(call)                                                                              \
-    do {                                                                                      \
-        cudaError_t e_ = (call);                                                              \
-        if (e_ != cudaSuccess) {                                                              \
-            if (getenv("WROUTE_DEBUG")) fprintf(stderr, "wroute: %s at %s:%d: %s\n", #call, __FILE__, \
-                                                __LINE__, cudaGetErrorString(e_));            \
-            return WR_ECUDA;                                                                  \
-        }                                                                                     \
-    } while (0)
-
-#define RC(call)                      \
-    do {                              \
-        int r_ = (call);              \
-        if (r_ != WR_OK) return r_;   \
-    } while (0)
+namespace wrc {
 
 int ensure(DBuf& b, size_t bytes) { return b.ensure(bytes) ? WR_OK : WR_ENOMEM; }
 
@@ -103,25 +28,18 @@ cudaEvent_t next_event(wr_ctx* c, int* idx) {
 }
 
 int record(wr_ctx* c, cudaStream_t s, int* idx) {
+    if (c->untimed) {
+        *idx = -1;
+        return WR_OK;
+    }
     cudaEvent_t e = next_event(c, idx);
     if (!e) return WR_ECUDA;
-    CK(cudaEventRecord(e, s));
+    // inside a capture the record becomes a node of the graph that stamps the event at replay
+    if (c->capturing) CK(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+    else CK(cudaEventRecord(e, s));
     return WR_OK;
 }
 
-struct PhaseTimer {
-    wr_ctx* c;
-    cudaStream_t s;
-    int phase;
-    int b = -1;
-    PhaseTimer(wr_ctx* c_, cudaStream_t s_, int ph) : c(c_), s(s_), phase(ph) {
-        if (!c->capturing) record(c, s, &b);
-    }
-    ~PhaseTimer() {
-        int e = -1;
-        if (b >= 0 && record(c, s, &e) == WR_OK) c->ev_phase[phase].push_back({b, e});
-    }
-};
 
 int begin_call(wr_ctx* c, cudaStream_t s) {
     c->n_events_used = 0;
@@ -132,14 +50,10 @@ int begin_call(wr_ctx* c, cudaStream_t s) {
     RC(ensure(c->stats, 8 * sizeof(unsigned long long)));
     RC(ensure(c->err, sizeof(int)));
     CK(cudaMemsetAsync(c->stats.p, 0, 8 * sizeof(unsigned long long), s));
-    if (c->capturing) {
-        c->ev_call_begin = c->ev_call_end = -1;
-        return WR_OK;
-    }
     return record(c, s, &c->ev_call_begin);
 }
 
-int end_call(wr_ctx* c, cudaStream_t s) { return c->capturing ? WR_OK : record(c, s, &c->ev_call_end); }
+int end_call(wr_ctx* c, cudaStream_t s) { return record(c, s, &c->ev_call_end); }
 
 // Returns the recorded device error (and clears it); the stream must be idle.
 int take_device_error(wr_ctx* c) {
@@ -154,6 +68,13 @@ int upload(DBuf& b, const void* src, size_t bytes) {
     RC(ensure(b, bytes == 0 ? 4 : bytes));
     if (bytes) CK(cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice));
     return WR_OK;
+}
+
+// Sweep kernel for the context's tiling and tile size.
+int prepare_sweeps(wr_ctx* c) {
+    const int tiling = c->tune.bf_tiling != 0 ? c->tune.bf_tiling : 2;
+    if (tiling == 1) return wr::bf_prepare_warp(c->hp.tile_cap, c->device, &c->bf_info);
+    return wr::bf_prepare(c->hp.tile_cap, c->tune.bf_warps, c->device, &c->bf_info);
 }
 
 int upload_partition(wr_ctx* c) {
@@ -176,6 +97,7 @@ int upload_partition(wr_ctx* c) {
     RC(upload(c->g_flags, p.run_flags.data(), p.run_flags.size() * 4));
     RC(upload(c->g_ix, p.node_ix.data(), p.node_ix.size() * sizeof(uint4)));
     RC(upload(c->g_xarc, p.xarc2.data(), p.xarc2.size() * sizeof(uint2)));
+    RC(upload(c->g_cdesc, p.cdesc.data(), p.cdesc.size() * sizeof(uint4)));
     wr::DevGraph& g = c->dg;
     g.V = p.V;
     g.n_runs = p.n_runs;
@@ -195,7 +117,8 @@ int upload_partition(wr_ctx* c) {
     g.run_flags = c->g_flags.as<int32_t>();
     g.node_ix = c->g_ix.as<uint4>();
     g.xarc2 = c->g_xarc.as<uint2>();
-    return wr::bf_prepare(p.tile_cap, c->tune.bf_warps, c->device, &c->bf_info);
+    g.cdesc = c->g_cdesc.as<uint4>();
+    return prepare_sweeps(c);
 }
 
 int partition(wr_ctx* c) {
@@ -212,9 +135,9 @@ int32_t budget_lanes(const wr_ctx* c) {
 }
 
 // Size the row buffer and frontier arrays for segments of seg_lanes lanes.
-int ensure_bf(wr_ctx* c, int32_t seg_lanes) {
+int ensure_bf(wr_ctx* c, int32_t seg_lanes, bool with_rows) {
     const size_t rows_bytes = static_cast<size_t>(seg_lanes) * static_cast<size_t>(c->dg.V) * 4;
-    RC(ensure(c->rows, rows_bytes));
+    if (with_rows) RC(ensure(c->rows, rows_bytes));
     const size_t items = static_cast<size_t>(c->dg.n_runs) * static_cast<size_t>(seg_lanes / 32);
     RC(ensure(c->stamp, items * 4));
     RC(ensure(c->list0, items * 4));
@@ -321,6 +244,46 @@ int finish_host_call(wr_ctx* c, cudaStream_t s) {
 
 int check_ptr_kind(int k) { return (k == WR_HOST || k == WR_DEVICE) ? WR_OK : WR_EINVAL; }
 
+bool valid_tuning(const wr_tuning* t) {
+    if (t->run_target < 1 || (t->tile_cap != 128 && t->tile_cap != 256 && t->tile_cap != 512) || t->enum_units < 1 ||
+        t->enum_max_units_per_launch < 0 || t->run_target > t->tile_cap)
+        return false;
+    if (t->bf_warps != 0 && t->bf_warps != 4 && t->bf_warps != 8) return false;
+    if (t->tile_cap >= 512 && t->bf_warps == 4) return false;
+    if (t->bf_tiling < 0 || t->bf_tiling > 2 || (t->bf_tiling == 1 && t->tile_cap > 256)) return false;
+    return true;
+}
+
+// Tuning table file: one "name value" pair per line, unknown names ignored.
+bool read_tuning_file(const std::string& path, wr_tuning* t) {
+    FILE* f = std::fopen(path.c_str(), "r");
+    if (!f) return false;
+    char key[64];
+    long long v = 0;
+    int n = 0;
+    while (std::fscanf(f, "%63s %lld", key, &v) == 2) {
+        const std::string k(key);
+        if (k == "run_target") t->run_target = static_cast<int32_t>(v);
+        else if (k == "tile_cap") t->tile_cap = static_cast<int32_t>(v);
+        else if (k == "enum_units") t->enum_units = static_cast<int32_t>(v);
+        else if (k == "enum_max_units_per_launch") t->enum_max_units_per_launch = static_cast<int32_t>(v);
+        else if (k == "bf_warps") t->bf_warps = static_cast<int32_t>(v);
+        else if (k == "bf_tiling") t->bf_tiling = static_cast<int32_t>(v);
+        else continue;
+        ++n;
+    }
+    std::fclose(f);
+    return n > 0;
+}
+
+bool write_tuning_file(const std::string& path, const wr_tuning* t) {
+    FILE* f = std::fopen(path.c_str(), "w");
+    if (!f) return false;
+    std::fprintf(f, "run_target %d\ntile_cap %d\nenum_units %d\nenum_max_units_per_launch %d\nbf_warps %d\nbf_tiling %d\n",
+                 t->run_target, t->tile_cap, t->enum_units, t->enum_max_units_per_launch, t->bf_warps, t->bf_tiling);
+    return std::fclose(f) == 0;
+}
+
 // Partition and upload c->hg, size the per-node work arrays.
 int finish_graph(wr_ctx* c) {
     const int32_t V = c->hg.V;
@@ -335,7 +298,57 @@ int finish_graph(wr_ctx* c) {
     return WR_OK;
 }
 
-}  // namespace
+// a1-a7 for n orders whose offs/picks are on the device, np_bound >= offs[n]:
+// enqueues everything on s with no host synchronisation (the segments are
+// planned for the worst case of np_bound + 1 distinct sources).
+int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_picks, int64_t np_bound,
+                  int32_t* o_cost, int32_t* o_perm, int32_t* o_status, cudaStream_t s) {
+    const int32_t V = c->dg.V;
+    wr::TourBufs tb{};
+    tb.offs = d_offs;
+    tb.picks = d_picks;
+    RC(ensure_tour_bufs(c, n, tb));
+    // a2: sources = depot + distinct pick nodes of valid orders
+    {
+        PhaseTimer t(c, s, 0);
+        CK(cudaMemsetAsync(c->node_flag.p, 0, static_cast<size_t>(V), s));
+        CK(cudaMemsetAsync(c->order_flags.p, 0, static_cast<size_t>(n) * 4, s));
+        CK(wr::tour_launch_select(n, d_offs, d_picks, V, c->dg.depot, c->cfg.max_k, c->node_flag.as<uint8_t>(),
+                                  tb.order_status, s));
+        c->launches++;
+        CK(wr::tour_launch_compact(V, c->node_flag.as<uint8_t>(), c->src_index.as<int32_t>(),
+                                   c->src_list.as<int32_t>(), c->n_src.as<int32_t>(), c->block_sums.as<int32_t>(), s,
+                                   &c->launches));
+    }
+    // segments of the worst-case source count; empty ones exit on the device
+    const int64_t worst = np_bound + 1 < V ? np_bound + 1 : V;
+    const int32_t lanes_needed = static_cast<int32_t>((worst + 31) / 32 * 32);
+    const int32_t blanes = budget_lanes(c);
+    if (blanes < 32) return WR_ENOMEM;
+    const int32_t seg_lanes = lanes_needed < blanes ? lanes_needed : blanes;
+    const int32_t n_seg = (lanes_needed + seg_lanes - 1) / seg_lanes;
+    RC(ensure_bf(c, seg_lanes));
+    for (int32_t sg = 0; sg < n_seg; ++sg) {
+        wr::BfSegment seg;
+        seg.rows = c->rows.as<uint32_t>();
+        seg.ld = seg_lanes;
+        seg.src = c->src_list.as<int32_t>();
+        seg.n_src_dev = c->n_src.as<int32_t>();
+        seg.n_src_host = 0;
+        seg.first = sg * seg_lanes;
+        seg.lanes = seg_lanes;
+        RC(run_bf_segment(c, seg, s));
+        PhaseTimer t(c, s, 3);
+        CK(wr::tour_launch_gather(n, tb, c->dg.depot, c->src_index.as<int32_t>(), seg, s));
+        c->launches++;
+    }
+    c->last.n_segments = n_seg;
+    return run_tours(c, n, nullptr, tb, o_cost, o_perm, 0, o_status, s);
+}
+
+}  // namespace wrc
+
+using namespace wrc;
 
 extern "C" {
 
@@ -380,7 +393,13 @@ int wr_create(const wr_config* cfg, wr_ctx** out) {
     ctx->tune.enum_units = 4;
     ctx->tune.enum_max_units_per_launch = 0;
     ctx->tune.bf_warps = 0;
+    ctx->tune.bf_tiling = 0;
     ctx->enum_blocks = wr::tour_enum_blocks(c.device);
+    if (cfg && cfg->tune_path) {
+        ctx->tune_path = cfg->tune_path;
+        wr_tuning t = ctx->tune;
+        if (read_tuning_file(ctx->tune_path, &t) && valid_tuning(&t)) ctx->tune = t;
+    }
     if (ctx->err.ensure(sizeof(int)) == false || cudaMemset(ctx->err.p, 0, sizeof(int)) != cudaSuccess) {
         delete ctx;
         return WR_ENOMEM;
@@ -394,7 +413,7 @@ void wr_destroy(wr_ctx* c) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     DBuf* bufs[] = {&c->g_desc, &c->g_ref, &c->g_w, &c->g_arc2, &c->g_run_ptr, &c->g_halo_ptr, &c->g_halo_nodes, &c->g_rin_ptr,
-                    &c->g_rin_list, &c->g_run_of, &c->g_meta, &c->g_flags, &c->g_ix, &c->g_xarc, &c->rows, &c->stamp, &c->list0, &c->list1,
+                    &c->g_rin_list, &c->g_run_of, &c->g_meta, &c->g_flags, &c->g_ix, &c->g_xarc, &c->g_cdesc, &c->rows, &c->stamp, &c->list0, &c->list1,
                     &c->counts, &c->bar, &c->err, &c->stats, &c->node_flag, &c->src_index, &c->src_list,
                     &c->n_src, &c->block_sums, &c->offs, &c->picks, &c->order_status, &c->order_flags, &c->D,
                     &c->unit_off, &c->best, &c->unit_ctr, &c->out_cost, &c->out_perm, &c->out_status, &c->kbuf,
@@ -444,54 +463,6 @@ int wr_load_graph(wr_ctx* c, int32_t V, int64_t E, const int64_t* row_ptr, const
     c->hg.E = g.E;
     c->hg.depot = g.depot;
     return finish_graph(c);
-}
-
-// a1-a7 for n orders whose offs/picks are on the device, np_bound >= offs[n]:
-// enqueues everything on s with no host synchronisation (the segments are
-// planned for the worst case of np_bound + 1 distinct sources).
-static int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_picks, int64_t np_bound,
-                         int32_t* o_cost, int32_t* o_perm, int32_t* o_status, cudaStream_t s) {
-    const int32_t V = c->dg.V;
-    wr::TourBufs tb{};
-    tb.offs = d_offs;
-    tb.picks = d_picks;
-    RC(ensure_tour_bufs(c, n, tb));
-    // a2: sources = depot + distinct pick nodes of valid orders
-    {
-        PhaseTimer t(c, s, 0);
-        CK(cudaMemsetAsync(c->node_flag.p, 0, static_cast<size_t>(V), s));
-        CK(cudaMemsetAsync(c->order_flags.p, 0, static_cast<size_t>(n) * 4, s));
-        CK(wr::tour_launch_select(n, d_offs, d_picks, V, c->dg.depot, c->cfg.max_k, c->node_flag.as<uint8_t>(),
-                                  tb.order_status, s));
-        c->launches++;
-        CK(wr::tour_launch_compact(V, c->node_flag.as<uint8_t>(), c->src_index.as<int32_t>(),
-                                   c->src_list.as<int32_t>(), c->n_src.as<int32_t>(), c->block_sums.as<int32_t>(), s,
-                                   &c->launches));
-    }
-    // segments of the worst-case source count; empty ones exit on the device
-    const int64_t worst = np_bound + 1 < V ? np_bound + 1 : V;
-    const int32_t lanes_needed = static_cast<int32_t>((worst + 31) / 32 * 32);
-    const int32_t blanes = budget_lanes(c);
-    if (blanes < 32) return WR_ENOMEM;
-    const int32_t seg_lanes = lanes_needed < blanes ? lanes_needed : blanes;
-    const int32_t n_seg = (lanes_needed + seg_lanes - 1) / seg_lanes;
-    RC(ensure_bf(c, seg_lanes));
-    for (int32_t sg = 0; sg < n_seg; ++sg) {
-        wr::BfSegment seg;
-        seg.rows = c->rows.as<uint32_t>();
-        seg.ld = seg_lanes;
-        seg.src = c->src_list.as<int32_t>();
-        seg.n_src_dev = c->n_src.as<int32_t>();
-        seg.n_src_host = 0;
-        seg.first = sg * seg_lanes;
-        seg.lanes = seg_lanes;
-        RC(run_bf_segment(c, seg, s));
-        PhaseTimer t(c, s, 3);
-        CK(wr::tour_launch_gather(n, tb, c->dg.depot, c->src_index.as<int32_t>(), seg, s));
-        c->launches++;
-    }
-    c->last.n_segments = n_seg;
-    return run_tours(c, n, nullptr, tb, o_cost, o_perm, 0, o_status, s);
 }
 
 int wr_route_orders(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* picks, int32_t* cost, int32_t* perm,
@@ -823,22 +794,106 @@ int wr_get_tuning(wr_ctx* c, wr_tuning* out) {
 }
 
 int wr_set_tuning(wr_ctx* c, const wr_tuning* t) {
-    if (!c || !t) return WR_EINVAL;
-    if (t->run_target < 1 || (t->tile_cap != 128 && t->tile_cap != 256 && t->tile_cap != 512) || t->enum_units < 1 ||
-        t->enum_max_units_per_launch < 0 || t->run_target > t->tile_cap)
-        return WR_EINVAL;
+    if (!c || !t || !valid_tuning(t)) return WR_EINVAL;
     RC(set_device(c));
-    if (t->bf_warps != 0 && t->bf_warps != 4 && t->bf_warps != 8) return WR_EINVAL;
-    if (t->tile_cap >= 512 && t->bf_warps == 4) return WR_EINVAL;
     const bool repart = t->run_target != c->tune.run_target || t->tile_cap != c->tune.tile_cap;
-    const bool relaunch = t->bf_warps != c->tune.bf_warps;
+    const bool relaunch = t->bf_warps != c->tune.bf_warps || t->bf_tiling != c->tune.bf_tiling;
     c->tune = *t;
     if (repart && c->has_graph) {
         CK(cudaDeviceSynchronize());
         RC(partition(c));
     } else if (relaunch && c->has_graph) {
-        RC(wr::bf_prepare(c->hp.tile_cap, c->tune.bf_warps, c->device, &c->bf_info));
+        RC(prepare_sweeps(c));
     }
+    return WR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: times the path on a sample batch for candidate tunings.
+
+int wr_autotune(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* picks, int ptr_kind, int32_t reps,
+                wr_tuning* out) {
+    if (!c || n < 1 || !offs || reps < 1 || reps > 100) return WR_EINVAL;
+    RC(check_ptr_kind(ptr_kind));
+    if (!c->has_graph) return WR_ENOGRAPH;
+    RC(set_device(c));
+    int64_t np = 0;
+    if (ptr_kind == WR_HOST) np = offs[n];
+    else CK(cudaMemcpy(&np, offs + n, 8, cudaMemcpyDeviceToHost));
+    if (np < 0) return WR_EINVAL;
+    // outputs of the trial calls, of the inputs' kind
+    std::vector<int32_t> h_cost, h_perm, h_status;
+    DBuf d_out;
+    int32_t *cost, *perm, *status;
+    if (ptr_kind == WR_HOST) {
+        h_cost.resize(n);
+        h_status.resize(n);
+        h_perm.resize(static_cast<size_t>(np) + 1);
+        cost = h_cost.data();
+        perm = h_perm.data();
+        status = h_status.data();
+    } else {
+        RC(ensure(d_out, (2 * static_cast<size_t>(n) + static_cast<size_t>(np) + 1) * 4));
+        cost = d_out.as<int32_t>();
+        status = cost + n;
+        perm = status + n;
+    }
+    const wr_tuning start = c->tune;
+    // median of reps timed calls (after one warm-up), device time of the whole call
+    auto trial = [&](float* ms) -> int {
+        std::vector<float> t;
+        for (int i = 0; i <= reps; ++i) {
+            RC(wr_route_orders(c, n, offs, picks, cost, perm, status, ptr_kind, nullptr));
+            if (ptr_kind == WR_DEVICE) RC(wr_sync(c));
+            wr_stats st;
+            RC(wr_get_stats(c, &st));
+            if (i > 0) t.push_back(st.ms_total);
+        }
+        std::sort(t.begin(), t.end());
+        *ms = t[t.size() / 2];
+        return WR_OK;
+    };
+    struct BfCand { int tiling, tile_cap, run_target; };
+    const BfCand bf[] = {{1, 256, 200}, {1, 256, 256}, {1, 128, 100}, {1, 128, 128}, {2, 256, 200}, {2, 512, 400}};
+    wr_tuning best = start;
+    float best_ms = 3.4e38f;
+    int rc = WR_OK;
+    for (const BfCand& b : bf) {
+        wr_tuning t = start;
+        t.bf_tiling = b.tiling;
+        t.tile_cap = b.tile_cap;
+        t.run_target = b.run_target;
+        t.bf_warps = 0;
+        if (!valid_tuning(&t)) continue;
+        rc = wr_set_tuning(c, &t);
+        float ms = 0.f;
+        if (rc == WR_OK) rc = trial(&ms);
+        if (rc != WR_OK) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+    }
+    const int units[] = {2, 4, 8, 16};
+    if (rc == WR_OK) rc = wr_set_tuning(c, &best);
+    for (int u : units) {
+        if (rc != WR_OK) break;
+        if (u == best.enum_units) continue;
+        wr_tuning t = best;
+        t.enum_units = u;
+        rc = wr_set_tuning(c, &t);
+        float ms = 0.f;
+        if (rc == WR_OK) rc = trial(&ms);
+        if (rc == WR_OK && ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+    }
+    const int rc2 = wr_set_tuning(c, rc == WR_OK ? &best : &start);
+    if (rc != WR_OK) return rc;
+    RC(rc2);
+    if (out) *out = best;
+    if (!c->tune_path.empty() && !write_tuning_file(c->tune_path, &best)) return WR_EINVAL;
     return WR_OK;
 }
 
@@ -908,6 +963,7 @@ int wr_plan_create(wr_ctx* parent, int32_t n, int64_t max_picks, const int64_t* 
         } else {
             rc = begin_call(c, p->cap);
             if (rc == WR_OK) rc = enqueue_route(c, n, offs, picks, max_picks, cost, perm, status, p->cap);
+            if (rc == WR_OK) rc = end_call(c, p->cap);
             cudaGraph_t g = nullptr;
             const cudaError_t e = cudaStreamEndCapture(p->cap, &g);
             if (rc == WR_OK && e != cudaSuccess) rc = WR_ECUDA;

@@ -18,20 +18,9 @@
 // appends).  The sweep loop lives in one cooperative persistent kernel with
 // bounded grid barriers and stops at the first sweep that changes nothing
 // (early exit on a converged frontier), capped at V+1 sweeps.
-#include "wr_device.cuh"
+#include "wr_bf_common.cuh"
 
 namespace wr {
-
-struct BfParams {
-    DevGraph g;
-    BfSegment seg;
-    BfWork w;
-};
-
-__device__ __forceinline__ int segment_lanes(const BfSegment& seg) {
-    const int n_src = seg.n_src_dev ? ld_l2(seg.n_src_dev) : seg.n_src_host;
-    return min(max(n_src - seg.first, 0), seg.lanes);
-}
 
 // rows := INF except dist(src_b, src_b) = 0; stamps := 0; counters := 0.
 __global__ void bf_init_kernel(BfParams p) {
@@ -51,7 +40,7 @@ __global__ void bf_init_kernel(BfParams p) {
             const int lane = b + q;
             if (lane < n_lanes && p.seg.src[p.seg.first + lane] == v) (&val.x)[q] = 0u;
         }
-        __stcg(reinterpret_cast<uint4*>(p.seg.rows + v * p.seg.ld + b), val);
+        __stcg(reinterpret_cast<uint4*>(p.seg.rows + v * p.seg.ld + seg_col0(p.seg, b >> 5) + (b & 31)), val);
     }
     const int64_t n_items = static_cast<int64_t>(p.g.n_runs) * G;
     for (int64_t i = t0; i < n_items; i += stride) p.w.stamp[i] = 0;
@@ -59,42 +48,6 @@ __global__ void bf_init_kernel(BfParams p) {
     if (t0 == 0) {
         p.w.bar->count = 0;
         p.w.bar->gen = 0;
-    }
-}
-
-// Append the items whose stamp (or, with nbrs, an in-neighbour run's stamp
-// in the same group) equals match.
-__device__ __forceinline__ void build_list(const BfParams& p, int G, int match, bool nbrs, int32_t* out,
-                                           int32_t* count) {
-    const int64_t n_items = static_cast<int64_t>(p.g.n_runs) * G;
-    const int lane = threadIdx.x & 31;
-    for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < n_items;
-         base += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t item = base + threadIdx.x;
-        bool act = false;
-        if (item < n_items) {
-            act = ld_l2(p.w.stamp + item) == match;
-            if (!act && nbrs) {
-                const int r = static_cast<int>(item / G);
-                const int g = static_cast<int>(item - static_cast<int64_t>(r) * G);
-                const int q1 = __ldg(p.g.rin_ptr + r + 1);
-                for (int q = __ldg(p.g.rin_ptr + r); q < q1; ++q) {
-                    const int rr = __ldg(p.g.rin_list + q);
-                    if (ld_l2(p.w.stamp + static_cast<int64_t>(rr) * G + g) == match) {
-                        act = true;
-                        break;
-                    }
-                }
-            }
-        }
-        const unsigned m = __ballot_sync(FULL_MASK, act);
-        if (m) {
-            const int leader = __ffs(m) - 1;
-            int pos = 0;
-            if (lane == leader) pos = atomicAdd(count, __popc(m));
-            pos = __shfl_sync(FULL_MASK, pos, leader);
-            if (act) out[pos + __popc(m & lanemask_lt())] = static_cast<int32_t>(item);
-        }
     }
 }
 
@@ -111,34 +64,6 @@ struct TileSmem {
     uint2 xarcs[TILE];
     uint8_t dirtyb[TILE];
 };
-
-// cp.async.wait_group takes an immediate: dispatch on the pending count.
-__device__ __forceinline__ void cp_async_wait_pending(int n) {
-    switch (n) {
-        case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
-        case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
-        case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
-        case 3: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
-        case 4: asm volatile("cp.async.wait_group 4;\n" ::: "memory"); break;
-        case 5: asm volatile("cp.async.wait_group 5;\n" ::: "memory"); break;
-        case 6: asm volatile("cp.async.wait_group 6;\n" ::: "memory"); break;
-        case 7: asm volatile("cp.async.wait_group 7;\n" ::: "memory"); break;
-        case 8: asm volatile("cp.async.wait_group 8;\n" ::: "memory"); break;
-        case 9: asm volatile("cp.async.wait_group 9;\n" ::: "memory"); break;
-        case 10: asm volatile("cp.async.wait_group 10;\n" ::: "memory"); break;
-        case 11: asm volatile("cp.async.wait_group 11;\n" ::: "memory"); break;
-        case 12: asm volatile("cp.async.wait_group 12;\n" ::: "memory"); break;
-        case 13: asm volatile("cp.async.wait_group 13;\n" ::: "memory"); break;
-        case 14: asm volatile("cp.async.wait_group 14;\n" ::: "memory"); break;
-        case 15: asm volatile("cp.async.wait_group 15;\n" ::: "memory"); break;
-        default: asm volatile("cp.async.wait_group 16;\n" ::: "memory"); break;
-    }
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async8_ca(void* smem, const void* gmem) {
-    unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
 
 // Scan chunks cover SPAN = 32 * SEG consecutive node ids, aligned to
 // multiples of SPAN, in both passes; a lane owns SEG consecutive nodes of a
@@ -375,7 +300,7 @@ __device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, Tile
     const int hn = __ldg(p.g.halo_ptr + r + 1) - h0;
     const bool simple = (__ldg(p.g.run_flags + r) & RUN_SIMPLE) != 0;
     const int64_t ld = p.seg.ld;
-    const int64_t lane_off = static_cast<int64_t>(g) * 32;
+    const int64_t lane_off = seg_col0(p.seg, g);
     uint32_t* rows = p.seg.rows;
     const uint32_t x0 = __ldg(&p.g.node_ix[2 * static_cast<int64_t>(r0) + 1].w);
     const uint32_t x1 = __ldg(&p.g.node_ix[2 * static_cast<int64_t>(r0 + len) + 1].w);

@@ -1,0 +1,393 @@
+// Row a3, warp tiling of the multi-source Bellman-Ford sweeps (Sec. 4.7).
+//
+// Same rows layout, frontier and sweep loop as the CTA tiling in wr_bf.cu;
+// the difference is who owns a (run, 32-source group) tile: here one warp,
+// with lane b holding source b of the group.  Shared memory keeps the tile
+// slot-major (rows[slot][b], one 128-byte line per node), so a lane only
+// ever reads and writes its own column: the relaxation passes need no
+// shuffles, no warp barriers and have no bank conflicts (32 lanes read one
+// line).  Per node and pass a lane does the min-plus step of the paper for
+// the node's in-arcs -- the carry arc from the previous node in pass order
+// through a register, up to two other arcs from the staged tile, addressed
+// by byte offsets precomputed on the host (compact descriptors).
+//
+// Data movement is done by the copy engine of the SM: the tile's lines, its
+// halo lines and its descriptors arrive by bulk asynchronous copies
+// (cp.async.bulk, one 128-byte line per copy, issued 32 at a time by the
+// lanes) that complete on an mbarrier, and lines go back to global memory by
+// bulk stores.  The warp fetches its next tile's index and run metadata
+// while it relaxes the current one.
+//
+// The loads of a block of BLK nodes are issued before the previous block's
+// carry chain runs, so a non-carry arc from a node of the previous block
+// reads the value from before that block: an upper bound, which only defers
+// the improvement to the next sweep (the tile changed, so it is in the next
+// frontier).  The fixpoint, and hence every distance, is unchanged.
+#include "wr_bf_common.cuh"
+
+namespace wr {
+
+template <int TILE>
+struct __align__(128) WarpTile {
+    uint32_t rows[TILE][32];  // slot-major: rows[i][b] = source b of tile slot i (own nodes, then halo)
+    uint4 desc[2 * TILE];     // compact descriptors of the run's nodes: forward, backward
+    unsigned long long bar;   // mbarrier of the tile's inbound copies
+    unsigned long long pad[15];
+};
+
+constexpr int BLK = 8;  // nodes per pipelined block
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// global -> shared, completes `bytes` on the mbarrier
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+// shared -> global, tracked by this thread's bulk groups
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;\n" ::: "memory");
+}
+
+// Bounded wait for the tile's copies; false (and WR_ETIMEOUT recorded) if the
+// limit ran out.  Every lane waits, so every lane sees the landed data.
+__device__ __forceinline__ bool wait_tile(unsigned long long* bar, uint32_t parity, const BfParams& p) {
+    for (unsigned long long spins = 0; !mbar_try_wait(bar, parity); ++spins) {
+        if (spins > p.w.max_spins) {
+            atomicCAS(p.w.err, 0, WR_ETIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Run metadata of one work item (the same in every lane).
+struct TileMeta {
+    int item, r, g, r0, len, h0, hn, flags;
+};
+
+__device__ __forceinline__ TileMeta load_meta(const BfParams& p, const int32_t* list, int it, int G) {
+    TileMeta m;
+    m.item = __ldcg(list + it);
+    m.r = m.item / G;
+    m.g = m.item - m.r * G;
+    m.r0 = __ldg(p.g.run_ptr + m.r);
+    m.len = __ldg(p.g.run_ptr + m.r + 1) - m.r0;
+    m.h0 = __ldg(p.g.halo_ptr + m.r);
+    m.hn = __ldg(p.g.halo_ptr + m.r + 1) - m.h0;
+    m.flags = __ldg(p.g.run_flags + m.r);
+    return m;
+}
+
+// Loads of one block: descriptor, current value and the two arc sources per node.
+struct BlkIn {
+    uint32_t cur[BLK], s0[BLK], s1[BLK], w0[BLK], w1[BLK], cw[BLK];
+};
+
+template <int TILE, bool FWD>
+__device__ __forceinline__ void load_blk(const WarpTile<TILE>& t, const char* cb, int len, int b, BlkIn& in) {
+    uint4 d[BLK];
+#pragma unroll
+    for (int j = 0; j < BLK; ++j) {
+        int i = FWD ? b * BLK + j : len - 1 - (b * BLK + j);
+        i = min(max(i, 0), len - 1);
+        d[j] = t.desc[2 * i + (FWD ? 0 : 1)];
+    }
+#pragma unroll
+    for (int j = 0; j < BLK; ++j) {
+        int i = FWD ? b * BLK + j : len - 1 - (b * BLK + j);
+        i = min(max(i, 0), len - 1);
+        in.cur[j] = *reinterpret_cast<const uint32_t*>(cb + 128 * i);
+        in.s0[j] = *reinterpret_cast<const uint32_t*>(cb + (d[j].y & 0xFFFFu));
+        in.s1[j] = *reinterpret_cast<const uint32_t*>(cb + (d[j].y >> 16));
+        in.w0[j] = d[j].z;
+        in.w1[j] = d[j].w;
+        in.cw[j] = d[j].x;
+    }
+}
+
+// Carry chain of one block; stores the new values, returns the changed bits.
+template <bool FWD>
+__device__ __forceinline__ uint32_t chain_blk(char* cb, int len, int b, const BlkIn& in, uint32_t& xprev) {
+    uint32_t chg = 0;
+#pragma unroll
+    for (int j = 0; j < BLK; ++j) {
+        const int i = FWD ? b * BLK + j : len - 1 - (b * BLK + j);
+        uint32_t m = __viaddmin_u32(in.s0[j], in.w0[j], in.cur[j]);
+        m = __viaddmin_u32(in.s1[j], in.w1[j], m);
+        const uint32_t x = __viaddmin_u32(xprev, in.cw[j], m);
+        if (FWD ? i < len : i >= 0) {
+            *reinterpret_cast<uint32_t*>(cb + 128 * i) = x;
+            chg |= x ^ in.cur[j];
+        }
+        xprev = x;
+    }
+    return chg;
+}
+
+// One pass over the run: blocks of BLK nodes in pass order, the loads of
+// block b + 1 issued before the chain of block b.
+template <int TILE, bool FWD>
+__device__ __forceinline__ uint32_t warp_pass(WarpTile<TILE>& t, int len, int lane) {
+    char* cb = reinterpret_cast<char*>(&t.rows[0][lane]);
+    const int nb = (len + BLK - 1) / BLK;
+    uint32_t xprev = INF_U, chg = 0;
+    BlkIn a, c;
+    load_blk<TILE, FWD>(t, cb, len, 0, a);
+    int b = 0;
+    for (; b + 1 < nb; b += 2) {
+        load_blk<TILE, FWD>(t, cb, len, b + 1, c);
+        chg |= chain_blk<FWD>(cb, len, b, a, xprev);
+        if (b + 2 < nb) load_blk<TILE, FWD>(t, cb, len, b + 2, a);
+        chg |= chain_blk<FWD>(cb, len, b + 1, c, xprev);
+    }
+    if (b < nb) chg |= chain_blk<FWD>(cb, len, b, a, xprev);
+    return chg;
+}
+
+// Runs without compact descriptors (a node with more than two non-carry arcs
+// in a pass, or a halo larger than the tile): descriptors and arcs from global
+// memory, sources from the tile or, past its capacity, from the rows in L2.
+template <int TILE>
+__device__ __noinline__ uint32_t warp_passes_generic(const BfParams& p, WarpTile<TILE>& t, int r0, int len, int lane,
+                                                     int64_t lane_off) {
+    uint32_t* col = &t.rows[0][lane];
+    const uint32_t* rows = p.seg.rows;
+    const int64_t ld = p.seg.ld;
+    uint32_t chg = 0;
+    uint32_t carry = INF_U;
+    for (int i = 0; i < len; ++i) {
+        const int4 d = __ldg(p.g.node_desc + r0 + i);
+        const uint32_t cur = col[32 * i];
+        uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.x), cur);
+        for (int q = d.z; q < d.w; ++q) {
+            const uint2 e = __ldg(p.g.arc2 + q);
+            const uint32_t x = (e.x & GLOBAL_REF) ? ld_l2(rows + static_cast<int64_t>(e.x & ~GLOBAL_REF) * ld + lane_off + lane)
+                                                  : col[32 * e.x];
+            best = __viaddmin_u32(x, e.y, best);
+        }
+        col[32 * i] = best;
+        chg |= best ^ cur;
+        carry = best;
+    }
+    carry = INF_U;
+    for (int i = len - 1; i >= 0; --i) {
+        const int4 d = __ldg(p.g.node_desc + r0 + i);
+        const int end = __ldg(&p.g.node_desc[r0 + i + 1].z);
+        const uint32_t cur = col[32 * i];
+        uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.y), cur);
+        for (int q = d.w; q < end; ++q) {
+            const uint2 e = __ldg(p.g.arc2 + q);
+            best = __viaddmin_u32(col[32 * e.x], e.y, best);
+        }
+        col[32 * i] = best;
+        chg |= best ^ cur;
+        carry = best;
+    }
+    return chg;
+}
+
+// One tile by one warp.  Returns 1 if a row dropped, 0 if not, -1 if a wait
+// ran out (error recorded).  parity is the tile mbarrier's phase bit.
+template <int TILE>
+__device__ __forceinline__ int warp_tile(const BfParams& p, const TileMeta& m, WarpTile<TILE>& t, int lane,
+                                         uint32_t& parity) {
+    const int64_t ld = p.seg.ld;
+    const int64_t lane_off = seg_col0(p.seg, m.g);
+    uint32_t* rows = p.seg.rows;
+    const bool compact = (m.flags & RUN_COMPACT) != 0;
+    const uint32_t bytes = static_cast<uint32_t>(m.len + m.hn) * 128u + (compact ? static_cast<uint32_t>(m.len) * 32u : 0u);
+    if (lane == 0) mbar_arrive_expect_tx(&t.bar, bytes);
+    __syncwarp();
+    // own lines, halo lines (one 128-byte copy per line, 32 per warp instruction), descriptors
+    for (int i = lane; i < m.len; i += 32)
+        bulk_load(&t.rows[i][0], rows + static_cast<int64_t>(m.r0 + i) * ld + lane_off, 128u, &t.bar);
+    for (int h = lane; h < m.hn; h += 32) {
+        const int node = __ldg(p.g.halo_nodes + m.h0 + h);
+        bulk_load(&t.rows[m.len + h][0], rows + static_cast<int64_t>(node) * ld + lane_off, 128u, &t.bar);
+    }
+    if (compact && lane == 0)
+        bulk_load(&t.desc[0], p.g.cdesc + 2 * static_cast<int64_t>(m.r0), static_cast<uint32_t>(m.len) * 32u, &t.bar);
+    if (!wait_tile(&t.bar, parity, p)) {
+        // let the copies already issued land before the shared memory is abandoned
+        for (unsigned long long s = 0; !mbar_try_wait(&t.bar, parity) && s <= p.w.max_spins; ++s) {
+        }
+        return -1;
+    }
+    parity ^= 1u;
+
+    uint32_t chg;
+    if (compact) {
+        chg = warp_pass<TILE, true>(t, m.len, lane);
+        chg |= warp_pass<TILE, false>(t, m.len, lane);
+    } else {
+        chg = warp_passes_generic<TILE>(p, t, m.r0, m.len, lane, lane_off);
+    }
+    const bool changed = __any_sync(FULL_MASK, chg != 0u);
+    if (changed) {
+        // every own line goes back (a visited line is read and written once per sweep)
+        fence_proxy_async_smem();  // this lane's shared stores visible to the copy engine
+        __syncwarp();
+        for (int i = lane; i < m.len; i += 32)
+            bulk_store(rows + static_cast<int64_t>(m.r0 + i) * ld + lane_off, &t.rows[i][0], 128u);
+        bulk_commit();
+        bulk_wait_read_all();  // shared lines read out before the next tile lands on them
+    }
+    __syncwarp();
+    return changed ? 1 : 0;
+}
+
+template <int TILE, int NW>
+__global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpTile<TILE>& t = reinterpret_cast<WarpTile<TILE>*>(smem_raw)[warp];
+
+    const int n_lanes = segment_lanes(p.seg);
+    const int G = (n_lanes + 31) >> 5;
+    if (G == 0) return;  // same decision in every block
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthreads = gridDim.x * blockDim.x;
+    if (lane == 0) mbar_init(&t.bar, 1);
+    fence_proxy_async_smem();
+    __syncwarp();
+    uint32_t parity = 0;
+
+    // seeds: writing d[s][s] = 0 is the change of "sweep 0": the tile holding
+    // each source gets stamp 1, and sweep 1 visits it and the tiles it feeds
+    for (int b = gtid; b < n_lanes; b += nthreads) {
+        const int r = __ldg(p.g.run_of_node + p.seg.src[p.seg.first + b]);
+        p.w.stamp[static_cast<int64_t>(r) * G + (b >> 5)] = 1;
+    }
+    if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) return;
+    build_list(p, G, 1, true, p.w.list0, p.w.counts + 0);
+    if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) return;
+
+    unsigned long long tiles = 0, nodes = 0, bytes = 0;
+    int cur = 0;
+    int sweep = 1;
+    bool failed = false;
+    for (;; ++sweep) {
+        const int cnt = ld_volatile(p.w.counts + cur);
+        if (gtid == 0 && sweep <= p.w.trace_cap) {
+            long long tm;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tm));
+            p.w.trace[2 * (sweep - 1)] = cnt;
+            p.w.trace[2 * (sweep - 1) + 1] = tm;
+        }
+        if (cnt == 0) break;
+        if (sweep > p.g.V + 1) {
+            if (gtid == 0) atomicCAS(p.w.err, 0, WR_EINTERNAL);
+            break;
+        }
+        if (gtid == 0) {
+            p.w.counts[cur ^ 1] = 0;
+            p.w.counts[2 + (cur ^ 1)] = 0;
+        }
+        const int32_t* list = cur ? p.w.list1 : p.w.list0;
+        // dynamic tile scheduling, per warp: the item two ahead is claimed and
+        // the next item's run metadata loaded while the current tile is relaxed
+        int it = 0, it1 = 0;
+        if (lane == 0) {
+            it = atomicAdd(p.w.counts + 2 + cur, 1);
+            it1 = atomicAdd(p.w.counts + 2 + cur, 1);
+        }
+        it = __shfl_sync(FULL_MASK, it, 0);
+        it1 = __shfl_sync(FULL_MASK, it1, 0);
+        TileMeta m{};
+        if (it < cnt) m = load_meta(p, list, it, G);
+        while (it < cnt && !failed) {
+            int it2 = 0;
+            if (lane == 0) it2 = atomicAdd(p.w.counts + 2 + cur, 1);
+            TileMeta m1{};
+            if (it1 < cnt) m1 = load_meta(p, list, it1, G);
+            const int res = warp_tile<TILE>(p, m, t, lane, parity);
+            if (res < 0) {
+                failed = true;
+                break;
+            }
+            if (lane == 0) {
+                if (res) p.w.stamp[m.item] = sweep + 1;
+                ++tiles;
+                nodes += static_cast<unsigned long long>(m.len);
+                bytes += static_cast<unsigned long long>(__ldg(p.g.run_meta_bytes + m.r)) +
+                         256ull * static_cast<unsigned long long>(m.len);
+            }
+            it = it1;
+            m = m1;
+            it1 = __shfl_sync(FULL_MASK, it2, 0);
+        }
+        bulk_wait_all();  // this lane's line stores complete before the sweep barrier
+        fence_proxy_async_global();
+        if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) break;
+        build_list(p, G, sweep + 1, true, cur ? p.w.list0 : p.w.list1, p.w.counts + (cur ^ 1));
+        if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) break;
+        cur ^= 1;
+    }
+    bulk_wait_all();
+    if (lane == 0 && tiles) {
+        atomicAdd(p.w.stats + 1, tiles);
+        atomicAdd(p.w.stats + 2, nodes);
+        atomicAdd(p.w.stats + 3, bytes);
+    }
+    if (gtid == 0) atomicAdd(p.w.stats + 0, static_cast<unsigned long long>(sweep - 1));
+}
+
+template <int TILE, int NW>
+static int prepare_warp_one(int device, BfLaunchInfo* info) {
+    const size_t smem = sizeof(WarpTile<TILE>) * NW;
+    auto* fn = bf_warp_kernel<TILE, NW>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+        return WR_ECUDA;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * NW, smem) != cudaSuccess || occ < 1)
+        return WR_ECUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return WR_ECUDA;
+    info->blocks = occ * sms;
+    info->threads = 32 * NW;
+    info->smem = smem;
+    info->fn = reinterpret_cast<const void*>(fn);
+    return WR_OK;
+}
+
+// Warps per CTA: as many 128- or 256-slot warp tiles as fit 227 KB of shared memory.
+int bf_prepare_warp(int tile_cap, int device, BfLaunchInfo* info) {
+    switch (tile_cap) {
+        case 128: return prepare_warp_one<128, 11>(device, info);
+        case 256: return prepare_warp_one<256, 5>(device, info);
+        default: return WR_EINVAL;
+    }
+}
+
+}  // namespace wr

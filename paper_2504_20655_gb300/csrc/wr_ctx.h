@@ -1,0 +1,127 @@
+// Internal: the library context behind the C ABI and the host-side steps of
+// the launch sequence shared by the API calls, the batching plans and the
+// serving loop.
+#pragma once
+
+#include <cstdio>
+#include <cstdlib>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "wr_internal.h"
+
+namespace wrc {
+
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    bool ensure(size_t need) {
+        if (need <= bytes) return true;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        size_t want = need + need / 4 + 256;
+        if (cudaMalloc(&p, want) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        bytes = want;
+        return true;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+constexpr unsigned long long DEFAULT_SPINS = 1ull << 24;  // x 64 ns sleeps: about a second
+constexpr uint64_t DEFAULT_BUDGET = 2ull << 30;
+
+}  // namespace wrc
+
+struct wr_ctx {
+    int device = 0;
+    wr_config cfg{};
+    wr_tuning tune{};
+    bool has_graph = false;
+    wr::HostGraph hg;
+    wr::HostPartition hp;
+    wr::DevGraph dg;
+    wrc::DBuf g_desc, g_ref, g_w, g_arc2, g_run_ptr, g_halo_ptr, g_halo_nodes, g_rin_ptr, g_rin_list, g_run_of, g_meta, g_flags, g_ix, g_xarc, g_cdesc;
+    wr::BfLaunchInfo bf_info{};
+    int enum_blocks = 0;
+    // working buffers
+    wrc::DBuf rows, stamp, list0, list1, counts, bar, err, stats;
+    wrc::DBuf node_flag, src_index, src_list, n_src, block_sums;
+    wrc::DBuf offs, picks, order_status, order_flags, D, unit_off, best, unit_ctr;
+    wrc::DBuf out_cost, out_perm, out_status, kbuf, dgiven, src_in, sub, check;
+    wrc::DBuf trace;          // sweep trace of the last Bellman-Ford segment
+    int32_t trace_cap = 0;
+    bool capturing = false;  // enqueueing into a CUDA graph: no host syncs, external timing events
+    bool untimed = false;    // no phase events (work from several streams at once: the serving loop)
+    std::string tune_path;   // autotuner table: read at creation, written by wr_autotune
+    // stats
+    wr_stats last{};
+    std::vector<cudaEvent_t> events;
+    int n_events_used = 0;
+    int ev_call_begin = -1, ev_call_end = -1;
+    std::vector<std::pair<int, int>> ev_phase[6];  // select, init, bf, gather, enum, finish
+    int launches = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            if (getenv("WROUTE_DEBUG")) fprintf(stderr, "wroute: %s at %s:%d: %s\n", #call, __FILE__, \
+                                                __LINE__, cudaGetErrorString(e_));            \
+            return WR_ECUDA;                                                                  \
+        }                                                                                     \
+    } while (0)
+
+#define RC(call)                      \
+    do {                              \
+        int r_ = (call);              \
+        if (r_ != WR_OK) return r_;   \
+    } while (0)
+
+namespace wrc {
+
+int ensure(DBuf& b, size_t bytes);
+int set_device(wr_ctx* c);
+int record(wr_ctx* c, cudaStream_t s, int* idx);
+
+// Times one phase of a call with a pair of events on the call's stream.
+struct PhaseTimer {
+    wr_ctx* c;
+    cudaStream_t s;
+    int phase;
+    int b = -1;
+    PhaseTimer(wr_ctx* c_, cudaStream_t s_, int ph) : c(c_), s(s_), phase(ph) { record(c, s, &b); }
+    ~PhaseTimer() {
+        int e = -1;
+        if (b >= 0 && record(c, s, &e) == WR_OK) c->ev_phase[phase].push_back({b, e});
+    }
+};
+
+int begin_call(wr_ctx* c, cudaStream_t s);
+int end_call(wr_ctx* c, cudaStream_t s);
+int take_device_error(wr_ctx* c);
+int32_t budget_lanes(const wr_ctx* c);
+// frontier arrays for segments of seg_lanes lanes, and the segment row buffer unless the rows live elsewhere
+int ensure_bf(wr_ctx* c, int32_t seg_lanes, bool with_rows = true);
+wr::BfWork bf_work(wr_ctx* c, int32_t seg_lanes);
+int run_bf_segment(wr_ctx* c, const wr::BfSegment& seg, cudaStream_t s);
+int run_tours(wr_ctx* c, int32_t n, const int32_t* k_dev, const wr::TourBufs& tb, int32_t* cost, int32_t* perm,
+              int perm_stride, int32_t* status, cudaStream_t s);
+int ensure_tour_bufs(wr_ctx* c, int32_t n, wr::TourBufs& tb);
+int finish_graph(wr_ctx* c);
+int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_picks, int64_t np_bound,
+                  int32_t* o_cost, int32_t* o_perm, int32_t* o_status, cudaStream_t s);
+
+}  // namespace wrc

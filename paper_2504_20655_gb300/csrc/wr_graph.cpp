@@ -77,6 +77,7 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
     p.rin_ptr.push_back(0);
     p.node_desc.resize(static_cast<size_t>(V) + 1);
     p.node_ix.resize(2 * (static_cast<size_t>(V) + 1));
+    p.cdesc.assign(2 * (static_cast<size_t>(V) + 1), make_uint4(NO_CARRY, 0u, NO_CARRY, NO_CARRY));
 
     std::vector<int32_t> halo_mark(static_cast<size_t>(V), -1);  // run id whose halo holds the node
     std::vector<int32_t> slot(static_cast<size_t>(V), 0);        // tile slot within the current run
@@ -133,6 +134,7 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
         // node descriptors and arcs
         int64_t arcs_in_run = 0;
         bool any_not_inline = false;
+        bool compact = true;
         const uint32_t x_first = static_cast<uint32_t>(p.xarc2.size());
         for (int32_t v = s; v < e; ++v) {
             p.run_of_node[v] = run;
@@ -193,6 +195,26 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
             for (size_t q = 2; q < fw.size(); ++q) p.xarc2.push_back(make_uint2(fw[q].first, fw[q].second));
             for (size_t q = 1; q < bw.size(); ++q) p.xarc2.push_back(make_uint2(bw[q].first, bw[q].second));
             if (!inline_ok) any_not_inline = true;
+            // compact form: <= 2 non-carry arcs per pass, all in staged tile slots
+            auto off = [](uint32_t slot) { return slot * 128u; };
+            bool c_ok = fw.size() <= 2 && bw.size() <= 2;
+            for (auto& pr : fw) c_ok = c_ok && !(pr.first & GLOBAL_REF) && pr.first < static_cast<uint32_t>(tile_cap);
+            for (auto& pr : bw) c_ok = c_ok && pr.first < static_cast<uint32_t>(tile_cap);
+            if (c_ok) {
+                uint4 f, bk;
+                f.x = fw_cw;
+                f.y = (fw.size() > 0 ? off(fw[0].first) : 0u) | ((fw.size() > 1 ? off(fw[1].first) : 0u) << 16);
+                f.z = fw.size() > 0 ? fw[0].second : NO_CARRY;
+                f.w = fw.size() > 1 ? fw[1].second : NO_CARRY;
+                bk.x = bw_cw;
+                bk.y = (bw.size() > 0 ? off(bw[0].first) : 0u) | ((bw.size() > 1 ? off(bw[1].first) : 0u) << 16);
+                bk.z = bw.size() > 0 ? bw[0].second : NO_CARRY;
+                bk.w = bw.size() > 1 ? bw[1].second : NO_CARRY;
+                p.cdesc[2 * static_cast<size_t>(v)] = f;
+                p.cdesc[2 * static_cast<size_t>(v) + 1] = bk;
+            } else {
+                compact = false;
+            }
             p.node_ix[2 * static_cast<size_t>(v)] = a;
             p.node_ix[2 * static_cast<size_t>(v) + 1] = b;
         }
@@ -201,7 +223,8 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
             const int64_t extras = static_cast<int64_t>(p.xarc2.size()) - x_first;
             const bool simple = extras <= static_cast<int64_t>(tile_cap) &&
                                 staged == static_cast<int32_t>(halo_all.size()) && !any_not_inline;
-            p.run_flags.push_back(simple ? RUN_SIMPLE : 0);
+            const bool all_staged = staged == static_cast<int32_t>(halo_all.size());
+            p.run_flags.push_back((simple ? RUN_SIMPLE : 0) | (compact && all_staged && tile_cap <= 512 ? RUN_COMPACT : 0));
         }
         p.run_ptr.push_back(e);
         p.halo_ptr.push_back(static_cast<int32_t>(p.halo_nodes.size()));

@@ -20,6 +20,7 @@ constexpr int TAIL = 5;                       // sequences of one unit: ordering
 constexpr int ORDER_FLAG_RANGE = 1;
 constexpr int32_t RUN_SIMPLE = 1;             // run's extra arcs fit the tile buffer, halo fully staged
 constexpr uint32_t IX_EXTRA = 1u << 24;       // node has arcs beyond the inline ones
+constexpr int32_t RUN_COMPACT = 2;            // every node's arcs fit its compact descriptor (warp tiling)
 
 // --------------------------------------------------------------------------
 // graph preprocessing (host, wr_graph.cpp)
@@ -61,7 +62,12 @@ struct HostPartition {
     std::vector<uint4> node_ix;
     std::vector<uint2> xarc2;
     std::vector<int64_t> run_meta_bytes;  // 8 * in-arcs + 8 * nodes of the run
-    std::vector<int32_t> run_flags;       // RUN_SIMPLE
+    std::vector<int32_t> run_flags;       // RUN_SIMPLE | RUN_COMPACT
+    // Compact descriptors of the warp tiling, 2 per node: forward {carry weight,
+    // o0 | o1 << 16, w0, w1} and backward {carry weight, o0 | o1 << 16, w0, w1},
+    // o = tile slot x 128 (byte offset of the slot's line in the slot-major
+    // tile).  Up to two non-carry arcs per pass; absent ones o = 0, w = NO_CARRY.
+    std::vector<uint4> cdesc;
     int64_t n_global_refs = 0;
 };
 
@@ -94,6 +100,7 @@ struct DevGraph {
     int32_t* run_of_node = nullptr;
     int64_t* run_meta_bytes = nullptr;
     int32_t* run_flags = nullptr;
+    uint4* cdesc = nullptr;    // compact descriptors, 2 per node
 };
 
 // One source segment of Bellman-Ford: rows[v * ld + b] holds
@@ -106,6 +113,10 @@ struct BfSegment {
     int32_t n_src_host;
     int32_t first;
     int32_t lanes;             // lane capacity (multiple of 32)
+    // optional: group g (lanes 32g .. 32g+31) lives in row columns
+    // [32 gcol[g], 32 gcol[g] + 32) instead of [32g, 32g + 32) (a row cache
+    // whose free column groups are scattered); nullptr = contiguous
+    const int32_t* gcol = nullptr;
 };
 
 struct BfWork {
@@ -131,6 +142,8 @@ struct BfLaunchInfo {
 };
 // picks the sweep kernel for (tile_cap, warps per CTA; 0 = default) and its co-resident grid
 int bf_prepare(int tile_cap, int warps, int device, BfLaunchInfo* info);
+// the warp-per-tile kernel (wr_bf_warp.cu) for tile_cap 128 or 256
+int bf_prepare_warp(int tile_cap, int device, BfLaunchInfo* info);
 cudaError_t bf_launch_init(const DevGraph& g, const BfSegment& seg, const BfWork& w, cudaStream_t s);
 cudaError_t bf_launch_sweeps(const DevGraph& g, const BfSegment& seg, const BfWork& w,
                              const BfLaunchInfo& info, cudaStream_t s);

@@ -28,7 +28,7 @@ DSTRIDE = 13
 
 EXPORTS = ["wr_create", "wr_destroy", "wr_strerror", "wr_sync", "wr_load_graph", "wr_route_orders", "wr_bf_rows",
            "wr_distance_rows", "wr_submatrix", "wr_tour_eval", "wr_tour_eval_static", "wr_get_stats",
-           "wr_get_tuning", "wr_set_tuning", "wr_set_trace", "wr_get_trace",
+           "wr_get_tuning", "wr_set_tuning", "wr_set_trace", "wr_get_trace", "wr_autotune",
            "wr_plan_create", "wr_plan_launch", "wr_plan_sync", "wr_plan_get_stats", "wr_plan_destroy"]
 WR_STATIC_MAX_ORDERS = 4096
 
@@ -40,7 +40,8 @@ class wr_config(ctypes.Structure):
 
 class wr_tuning(ctypes.Structure):
     _fields_ = [("run_target", ctypes.c_int32), ("tile_cap", ctypes.c_int32), ("enum_units", ctypes.c_int32),
-                ("enum_max_units_per_launch", ctypes.c_int32), ("bf_warps", ctypes.c_int32)]
+                ("enum_max_units_per_launch", ctypes.c_int32), ("bf_warps", ctypes.c_int32),
+                ("bf_tiling", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -99,6 +100,7 @@ def load_library(path: str = LIB_PATH):
     L.wr_plan_get_stats.argtypes = [P, ctypes.POINTER(wr_stats)]
     L.wr_plan_destroy.argtypes = [P]
     L.wr_plan_destroy.restype = None
+    L.wr_autotune.argtypes = [P, i32, P, P, I, i32, ctypes.POINTER(wr_tuning)]
     L.wr_set_trace.argtypes = [P, i32]
     L.wr_get_trace.argtypes = [P, P, i32, ctypes.POINTER(ctypes.c_int32)]
     for name in EXPORTS:
@@ -167,9 +169,10 @@ def _kind(*kinds):
 # C-named wrappers
 # ---------------------------------------------------------------------------
 
-def wr_create(device=0, mem_budget_bytes=2 << 30, max_k=WR_MAX_K, barrier_max_spins=0):
+def wr_create(device=0, mem_budget_bytes=2 << 30, max_k=WR_MAX_K, barrier_max_spins=0, tune_path=None):
     L = load_library()
-    cfg = wr_config(int(device), int(mem_budget_bytes), int(max_k), int(barrier_max_spins), None)
+    cfg = wr_config(int(device), int(mem_budget_bytes), int(max_k), int(barrier_max_spins),
+                    None if tune_path is None else os.fsencode(tune_path))
     ctx = ctypes.c_void_p()
     _check(L.wr_create(ctypes.byref(cfg), ctypes.byref(ctx)), "wr_create")
     return ctx
@@ -291,6 +294,18 @@ def wr_set_tuning(ctx, **kw):
     _check(load_library().wr_set_tuning(ctx, ctypes.byref(t)), "wr_set_tuning")
 
 
+def wr_autotune(ctx, offs, picks, reps=2) -> dict:
+    """Pick and apply the fastest tuning for this batch (host or device arrays)."""
+    po, kind_o, keep_o = _ptr(offs, np.int64)
+    pp, kind_p, keep_p = _ptr(picks, np.int32)
+    if kind_o != kind_p:
+        raise ValueError("offs and picks must both be host or both device arrays")
+    t = wr_tuning()
+    _check(load_library().wr_autotune(ctx, len(offs) - 1, po, pp, kind_o, int(reps), ctypes.byref(t)), "wr_autotune")
+    del keep_o, keep_p
+    return t.as_dict()
+
+
 def wr_set_trace(ctx, max_sweeps: int):
     _check(load_library().wr_set_trace(ctx, int(max_sweeps)), "wr_set_trace")
 
@@ -370,8 +385,8 @@ class Plan:
 class Router:
     """One library context on one device."""
 
-    def __init__(self, device=0, mem_budget_bytes=2 << 30, max_k=WR_MAX_K, barrier_max_spins=0):
-        self.ctx = wr_create(device, mem_budget_bytes, max_k, barrier_max_spins)
+    def __init__(self, device=0, mem_budget_bytes=2 << 30, max_k=WR_MAX_K, barrier_max_spins=0, tune_path=None):
+        self.ctx = wr_create(device, mem_budget_bytes, max_k, barrier_max_spins, tune_path)
         self.device = device
         self.V = None
 
@@ -436,6 +451,9 @@ class Router:
 
     def tuning(self):
         return wr_get_tuning(self.ctx)
+
+    def autotune(self, offs, picks, reps=2):
+        return wr_autotune(self.ctx, offs, picks, reps)
 
     def plan(self, n_orders, max_picks):
         return Plan(self.ctx, n_orders, max_picks, self.device)

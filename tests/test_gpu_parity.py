@@ -43,8 +43,16 @@ def test_bf_rows_tiny_all_sources(router, orc):
     assert st["sweeps"] >= 1 and st["bytes_alg"] > 0
 
 
+@pytest.fixture(params=[2, 1], ids=["cta_tiles", "warp_tiles"])
+def tiling(request, router):
+    saved = router.tuning()
+    router.set_tuning(bf_tiling=request.param)
+    yield request.param
+    router.set_tuning(**saved)
+
+
 @pytest.mark.parametrize("seed", range(8))
-def test_bf_rows_random_graphs(router, orc, seed):
+def test_bf_rows_random_graphs(router, orc, seed, tiling):
     V = [1, 2, 7, 33, 100, 257, 600, 1500][seed]
     g = random_graph(V, max(1, 3 * V), seed + 300, w_lo=0, w_hi=20 if seed % 2 else 1000)
     router.load_graph(g)
@@ -54,7 +62,27 @@ def test_bf_rows_random_graphs(router, orc, seed):
     assert (rows == ref).all()
 
 
-def test_bf_rows_high_in_degree(router, orc):
+def test_bf_rows_chains_both_tilings(router, orc, tiling):
+    """Long chains with sparse extra arcs (mostly compact runs for the warp tiling),
+    directed and with zero weights, many sources."""
+    V = 3000
+    u = np.arange(V - 1, dtype=np.int64)
+    v = u + 1
+    extra_u = synth.uniform_int(91, 400, 0, V - 1)
+    extra_v = synth.uniform_int(92, 400, 0, V - 1)
+    w = np.concatenate([synth.uniform_int(93, V - 1, 0, 30), synth.uniform_int(94, V - 1, 0, 30),
+                        synth.uniform_int(95, 400, 0, 500)])
+    uu = np.concatenate([u, v, extra_u])
+    vv = np.concatenate([v, u[: V - 1] * 0 + u, extra_v])
+    keep = uu != vv
+    rp, col, wt = synth.csr_from_arcs(V, uu[keep], vv[keep], w[keep])
+    g = synth.Graph(V=V, row_ptr=rp, col=col, w=wt, depot=0)
+    router.load_graph(g)
+    src = np.arange(0, V, 23, dtype=np.int32)
+    assert (router.bf_rows(src) == orc.sssp_rows(g, src, "dijkstra", NT)).all()
+
+
+def test_bf_rows_high_in_degree(router, orc, tiling):
     # a node with more in-neighbours than a tile holds: its halo spills to global reads
     V = 700
     u = np.concatenate([np.arange(1, V), np.zeros(V - 1, np.int64)])
@@ -70,8 +98,15 @@ def test_bf_rows_high_in_degree(router, orc):
 @pytest.mark.parametrize("tune", [dict(run_target=96, tile_cap=128), dict(run_target=32, tile_cap=128),
                                   dict(run_target=200, tile_cap=256), dict(run_target=1, tile_cap=128),
                                   dict(run_target=400, tile_cap=512), dict(run_target=256, tile_cap=256),
-                                  dict(run_target=200, tile_cap=256, bf_warps=8),
-                                  dict(run_target=100, tile_cap=128, bf_warps=8)])
+                                  dict(run_target=200, tile_cap=256, bf_tiling=2),
+                                  dict(run_target=200, tile_cap=256, bf_tiling=2, bf_warps=8),
+                                  dict(run_target=100, tile_cap=128, bf_tiling=2, bf_warps=8),
+                                  dict(run_target=96, tile_cap=128, bf_tiling=2),
+                                  dict(run_target=1, tile_cap=128, bf_tiling=2),
+                                  dict(run_target=200, tile_cap=256, bf_tiling=1),
+                                  dict(run_target=256, tile_cap=256, bf_tiling=1),
+                                  dict(run_target=96, tile_cap=128, bf_tiling=1),
+                                  dict(run_target=1, tile_cap=128, bf_tiling=1)])
 def test_bf_rows_medium_tuning_invariant(router, orc, tune):
     g = synth.medium_layout().build()
     saved = router.tuning()
@@ -390,3 +425,30 @@ def test_plan_batching_full_size(router, orc):
     for j, i in enumerate(pick):
         lo, hi = o.offs[i], o.offs[i + 1]
         assert (perm[lo:hi] == pb[sub.offs[j]:sub.offs[j + 1]]).all()
+
+
+def test_autotune_keeps_results(wr, orc, tmp_path):
+    """The autotuner only changes speed: the tuned context routes bit-identically, writes
+    its choice to the tuning file, and a new context reads that file back."""
+    g, o = synth.medium_workload(n_orders=96)
+    path = str(tmp_path / "wroute.tune")
+    r = wr.Router(device=0, tune_path=path)
+    try:
+        r.load_graph(g)
+        ref = r.route_orders(o.offs, o.picks)
+        best = r.autotune(o.offs, o.picks, reps=1)
+        assert r.tuning() == best
+        got = r.route_orders(o.offs, o.picks)
+        for a, b in zip(ref, got):
+            assert (np.asarray(a) == np.asarray(b)).all()
+    finally:
+        r.close()
+    text = open(path).read()
+    assert f"tile_cap {best['tile_cap']}" in text and f"bf_tiling {best['bf_tiling']}" in text
+    r2 = wr.Router(device=0, tune_path=path)
+    try:
+        assert r2.tuning() == best
+    finally:
+        r2.close()
+    c, p, s = orc.route_orders(g, o, "dijkstra", "brute", NT)
+    assert (ref[0] == c).all() and (ref[2] == s).all()
