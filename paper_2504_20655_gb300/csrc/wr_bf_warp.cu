@@ -35,7 +35,7 @@ struct __align__(128) WarpTile {
     unsigned long long pad[15];
 };
 
-constexpr int BLK = 8;  // nodes per pipelined block
+constexpr int BLK = 4;  // nodes per pipelined block
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -109,45 +109,53 @@ __device__ __forceinline__ TileMeta load_meta(const BfParams& p, const int32_t* 
     return m;
 }
 
-// Loads of one block: descriptor, current value and the two arc sources per node.
+// One block's inputs: current value, the best over its non-carry arcs, carry weight.
 struct BlkIn {
-    uint32_t cur[BLK], s0[BLK], s1[BLK], w0[BLK], w1[BLK], cw[BLK];
+    uint32_t cur[BLK], m[BLK], cw[BLK];
 };
 
-template <int TILE, bool FWD>
+// Block b of a pass: nodes ib, ib +- 1, ... (ib = b * BLK forward, len - 1 - b * BLK
+// backward).  PART: the block runs past the run's end and its missing nodes
+// are neutral (infinite value, blocking weights, no loads).
+template <int TILE, bool FWD, bool PART>
 __device__ __forceinline__ void load_blk(const WarpTile<TILE>& t, const char* cb, int len, int b, BlkIn& in) {
+    const int ib = FWD ? b * BLK : len - 1 - b * BLK;
+    const uint4* dp = &t.desc[2 * ib + (FWD ? 0 : 1)];
+    const char* rp = cb + 128 * ib;
     uint4 d[BLK];
+    uint32_t s0[BLK], s1[BLK];
 #pragma unroll
     for (int j = 0; j < BLK; ++j) {
-        int i = FWD ? b * BLK + j : len - 1 - (b * BLK + j);
-        i = min(max(i, 0), len - 1);
-        d[j] = t.desc[2 * i + (FWD ? 0 : 1)];
+        const int st = FWD ? j : -j;
+        const bool valid = !PART || (FWD ? ib + j < len : ib - j >= 0);
+        d[j] = valid ? dp[2 * st] : make_uint4(NO_CARRY, 0u, NO_CARRY, NO_CARRY);
     }
 #pragma unroll
     for (int j = 0; j < BLK; ++j) {
-        int i = FWD ? b * BLK + j : len - 1 - (b * BLK + j);
-        i = min(max(i, 0), len - 1);
-        in.cur[j] = *reinterpret_cast<const uint32_t*>(cb + 128 * i);
-        in.s0[j] = *reinterpret_cast<const uint32_t*>(cb + (d[j].y & 0xFFFFu));
-        in.s1[j] = *reinterpret_cast<const uint32_t*>(cb + (d[j].y >> 16));
-        in.w0[j] = d[j].z;
-        in.w1[j] = d[j].w;
+        const int st = FWD ? j : -j;
+        const bool valid = !PART || (FWD ? ib + j < len : ib - j >= 0);
+        in.cur[j] = valid ? *reinterpret_cast<const uint32_t*>(rp + 128 * st) : INF_U;
+        s0[j] = valid ? *reinterpret_cast<const uint32_t*>(cb + (d[j].y & 0xFFFFu)) : 0u;
+        s1[j] = valid ? *reinterpret_cast<const uint32_t*>(cb + (d[j].y >> 16)) : 0u;
         in.cw[j] = d[j].x;
     }
+#pragma unroll
+    for (int j = 0; j < BLK; ++j)
+        in.m[j] = __viaddmin_u32(s1[j], d[j].w, __viaddmin_u32(s0[j], d[j].z, in.cur[j]));
 }
 
 // Carry chain of one block; stores the new values, returns the changed bits.
-template <bool FWD>
+template <bool FWD, bool PART>
 __device__ __forceinline__ uint32_t chain_blk(char* cb, int len, int b, const BlkIn& in, uint32_t& xprev) {
+    const int ib = FWD ? b * BLK : len - 1 - b * BLK;
+    char* rp = cb + 128 * ib;
     uint32_t chg = 0;
 #pragma unroll
     for (int j = 0; j < BLK; ++j) {
-        const int i = FWD ? b * BLK + j : len - 1 - (b * BLK + j);
-        uint32_t m = __viaddmin_u32(in.s0[j], in.w0[j], in.cur[j]);
-        m = __viaddmin_u32(in.s1[j], in.w1[j], m);
-        const uint32_t x = __viaddmin_u32(xprev, in.cw[j], m);
-        if (FWD ? i < len : i >= 0) {
-            *reinterpret_cast<uint32_t*>(cb + 128 * i) = x;
+        const int st = FWD ? j : -j;
+        const uint32_t x = __viaddmin_u32(xprev, in.cw[j], in.m[j]);
+        if (!PART || (FWD ? ib + j < len : ib - j >= 0)) {
+            *reinterpret_cast<uint32_t*>(rp + 128 * st) = x;
             chg |= x ^ in.cur[j];
         }
         xprev = x;
@@ -155,23 +163,26 @@ __device__ __forceinline__ uint32_t chain_blk(char* cb, int len, int b, const Bl
     return chg;
 }
 
-// One pass over the run: blocks of BLK nodes in pass order, the loads of
-// block b + 1 issued before the chain of block b.
+// One pass over the run: whole blocks of BLK nodes in pass order, the loads
+// of block b + 1 issued before the chain of block b, then the partial block.
 template <int TILE, bool FWD>
 __device__ __forceinline__ uint32_t warp_pass(WarpTile<TILE>& t, int len, int lane) {
     char* cb = reinterpret_cast<char*>(&t.rows[0][lane]);
-    const int nb = (len + BLK - 1) / BLK;
+    const int nf = len / BLK;
     uint32_t xprev = INF_U, chg = 0;
     BlkIn a, c;
-    load_blk<TILE, FWD>(t, cb, len, 0, a);
-    int b = 0;
-    for (; b + 1 < nb; b += 2) {
-        load_blk<TILE, FWD>(t, cb, len, b + 1, c);
-        chg |= chain_blk<FWD>(cb, len, b, a, xprev);
-        if (b + 2 < nb) load_blk<TILE, FWD>(t, cb, len, b + 2, a);
-        chg |= chain_blk<FWD>(cb, len, b + 1, c, xprev);
+    if (nf > 0) load_blk<TILE, FWD, false>(t, cb, len, 0, a);
+#pragma unroll 1
+    for (int b = 0; b < nf; b += 2) {
+        if (b + 1 < nf) load_blk<TILE, FWD, false>(t, cb, len, b + 1, c);
+        chg |= chain_blk<FWD, false>(cb, len, b, a, xprev);
+        if (b + 2 < nf) load_blk<TILE, FWD, false>(t, cb, len, b + 2, a);
+        if (b + 1 < nf) chg |= chain_blk<FWD, false>(cb, len, b + 1, c, xprev);
     }
-    if (b < nb) chg |= chain_blk<FWD>(cb, len, b, a, xprev);
+    if (nf * BLK < len) {
+        load_blk<TILE, FWD, true>(t, cb, len, nf, a);
+        chg |= chain_blk<FWD, true>(cb, len, nf, a, xprev);
+    }
     return chg;
 }
 
@@ -384,7 +395,7 @@ static int prepare_warp_one(int device, BfLaunchInfo* info) {
 // Warps per CTA: as many 128- or 256-slot warp tiles as fit 227 KB of shared memory.
 int bf_prepare_warp(int tile_cap, int device, BfLaunchInfo* info) {
     switch (tile_cap) {
-        case 128: return prepare_warp_one<128, 11>(device, info);
+        case 128: return prepare_warp_one<128, 10>(device, info);
         case 256: return prepare_warp_one<256, 5>(device, info);
         default: return WR_EINVAL;
     }

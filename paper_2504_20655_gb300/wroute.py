@@ -29,8 +29,22 @@ DSTRIDE = 13
 EXPORTS = ["wr_create", "wr_destroy", "wr_strerror", "wr_sync", "wr_load_graph", "wr_route_orders", "wr_bf_rows",
            "wr_distance_rows", "wr_submatrix", "wr_tour_eval", "wr_tour_eval_static", "wr_get_stats",
            "wr_get_tuning", "wr_set_tuning", "wr_set_trace", "wr_get_trace", "wr_autotune",
+           "wr_serve_create", "wr_serve_run", "wr_serve_get_stats", "wr_serve_destroy",
            "wr_plan_create", "wr_plan_launch", "wr_plan_sync", "wr_plan_get_stats", "wr_plan_destroy"]
 WR_STATIC_MAX_ORDERS = 4096
+
+
+class wr_serve_config(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("max_batch_picks", ctypes.c_int64), ("n_slots", ctypes.c_int32),
+                ("cache_bytes", ctypes.c_uint64), ("plain", ctypes.c_int32)]
+
+
+class wr_serve_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("orders", "batches", "cache_hits", "rows_computed", "evicted_groups",
+                                              "bf_launches")] + [("wall_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
 
 
 class wr_config(ctypes.Structure):
@@ -101,6 +115,11 @@ def load_library(path: str = LIB_PATH):
     L.wr_plan_destroy.argtypes = [P]
     L.wr_plan_destroy.restype = None
     L.wr_autotune.argtypes = [P, i32, P, P, I, i32, ctypes.POINTER(wr_tuning)]
+    L.wr_serve_create.argtypes = [P, ctypes.POINTER(wr_serve_config), ctypes.POINTER(P)]
+    L.wr_serve_run.argtypes = [P, i32, P, P, P, P, P, P, P]
+    L.wr_serve_get_stats.argtypes = [P, ctypes.POINTER(wr_serve_stats)]
+    L.wr_serve_destroy.argtypes = [P]
+    L.wr_serve_destroy.restype = None
     L.wr_set_trace.argtypes = [P, i32]
     L.wr_get_trace.argtypes = [P, P, i32, ctypes.POINTER(ctypes.c_int32)]
     for name in EXPORTS:
@@ -319,6 +338,49 @@ def wr_get_trace(ctx, max_entries: int = 1 << 16) -> np.ndarray:
     return out[:min(n.value, max_entries)].copy()
 
 
+class Server:
+    """A serving loop (wr_serve_*) over the context's graph: orders arrive over time,
+    results come back with their completion times."""
+
+    def __init__(self, ctx, max_batch=256, max_batch_picks=4096, n_slots=3, cache_bytes=4 << 30, plain=False):
+        cfg = wr_serve_config(int(max_batch), int(max_batch_picks), int(n_slots), int(cache_bytes), int(bool(plain)))
+        h = ctypes.c_void_p()
+        _check(load_library().wr_serve_create(ctx, ctypes.byref(cfg), ctypes.byref(h)), "wr_serve_create")
+        self.h = h
+
+    def run(self, arrival_s, offs, picks):
+        """Returns (cost, perm, status, done_s) for orders arriving at arrival_s (seconds)."""
+        arrival = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        offs = np.ascontiguousarray(offs, dtype=np.int64)
+        picks = np.ascontiguousarray(picks, dtype=np.int32)
+        n = len(offs) - 1
+        cost = np.empty(n, np.int32)
+        status = np.empty(n, np.int32)
+        perm = np.empty(max(int(offs[-1]), 1), np.int32)
+        done = np.empty(n, np.float64)
+        c = ctypes.c_void_p
+        _check(load_library().wr_serve_run(self.h, n, c(arrival.ctypes.data), c(offs.ctypes.data), c(picks.ctypes.data),
+                                           c(cost.ctypes.data), c(perm.ctypes.data), c(status.ctypes.data),
+                                           c(done.ctypes.data)), "wr_serve_run")
+        return cost, perm, status, done
+
+    def stats(self) -> dict:
+        st = wr_serve_stats()
+        _check(load_library().wr_serve_get_stats(self.h, ctypes.byref(st)), "wr_serve_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self.h is not None:
+            load_library().wr_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Plan:
     """A batch of n_orders orders captured into a CUDA graph (wr_plan_*).
 
@@ -454,6 +516,9 @@ class Router:
 
     def autotune(self, offs, picks, reps=2):
         return wr_autotune(self.ctx, offs, picks, reps)
+
+    def server(self, **kw):
+        return Server(self.ctx, **kw)
 
     def plan(self, n_orders, max_picks):
         return Plan(self.ctx, n_orders, max_picks, self.device)

@@ -452,3 +452,60 @@ def test_autotune_keeps_results(wr, orc, tmp_path):
         r2.close()
     c, p, s = orc.route_orders(g, o, "dijkstra", "brute", NT)
     assert (ref[0] == c).all() and (ref[2] == s).all()
+
+
+def _serve_orders(n, seed=2504, rate=20000.0):
+    lay = synth.serve_layout(seed)
+    g = lay.build()
+    smap = synth.sku_slot_map(50_000, lay.n_slots, seed)
+    k = synth.geometric_k(n, 0.3, 2, 12, seed)
+    o = synth.zipf_orders(n, k, smap, 1.1, seed)
+    return g, o, synth.poisson_arrivals(n, rate, seed)
+
+
+def test_serve_mix_equals_alone(router, orc):
+    """Serving loop with a small row cache (evictions happen): every order's result is
+    the same in the mix as alone, bad orders are reported, completion follows arrival."""
+    g, o, arr = _serve_orders(3000)
+    # two bad orders: a node out of range, an empty order
+    picks = o.picks.copy()
+    picks[o.offs[7]] = g.V + 5
+    offs = o.offs.copy()
+    offs[12:] -= offs[12] - offs[11]
+    picks = np.delete(picks, np.arange(o.offs[11], o.offs[12]))
+    router.load_graph(g)
+    sv = router.server(max_batch=128, max_batch_picks=2048, n_slots=3, cache_bytes=200 << 20)
+    try:
+        cost, perm, status, done = sv.run(arr, offs, picks)
+        st = sv.stats()
+    finally:
+        sv.close()
+    assert st["orders"] == 3000 and st["batches"] > 1
+    assert st["evicted_groups"] > 0 and st["cache_hits"] > 0
+    assert (done >= arr - 1e-9).all()
+    assert status[7] == 2 and status[11] == 2
+    ref = router.route_orders(offs, picks)
+    assert (cost == ref[0]).all() and (status == ref[2]).all() and (perm[:offs[-1]] == ref[1][:offs[-1]]).all()
+    for i in range(0, 3000, 75):  # each alone
+        lo, hi = offs[i], offs[i + 1]
+        c1, p1, s1 = router.route_orders(np.array([0, hi - lo], np.int64), picks[lo:hi])
+        assert c1[0] == cost[i] and s1[0] == status[i] and (p1[:hi - lo] == perm[lo:hi]).all()
+    sub = [i for i in range(0, 3000, 15) if i not in (7, 11)]
+    so = synth.Orders(offs, picks).subset(sub)
+    c, p, s = orc.route_orders(g, so, "dijkstra", "heldkarp", NT)
+    assert (cost[sub] == c).all() and (status[sub] == s).all()
+
+
+def test_serve_plain_baseline(router):
+    """The plain mode (one order at a time, rows from scratch) gives the same results."""
+    g, o, arr = _serve_orders(200, rate=5000.0)
+    router.load_graph(g)
+    sv = router.server(plain=True)
+    try:
+        cost, perm, status, done = sv.run(arr, o.offs, o.picks)
+        st = sv.stats()
+    finally:
+        sv.close()
+    ref = router.route_orders(o.offs, o.picks)
+    assert (cost == ref[0]).all() and (status == ref[2]).all() and (perm == ref[1][:len(perm)]).all()
+    assert st["batches"] == 200 and (done >= arr - 1e-9).all()
