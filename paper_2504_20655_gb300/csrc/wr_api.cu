@@ -87,7 +87,8 @@ int upload_partition(wr_ctx* c) {
         for (size_t i = 0; i < a2.size(); ++i) a2[i] = make_uint2(p.arc_ref[i], p.arc_w[i]);
         RC(upload(c->g_arc2, a2.data(), a2.size() * sizeof(uint2)));
     }
-    RC(upload(c->g_run_ptr, p.run_ptr.data(), p.run_ptr.size() * 4));
+    RC(upload(c->g_run_ptr, p.run_seg.data(), p.run_seg.size() * sizeof(int4)));
+    RC(upload(c->g_run_x, p.run_x.data(), p.run_x.size() * sizeof(int2)));
     RC(upload(c->g_halo_ptr, p.halo_ptr.data(), p.halo_ptr.size() * 4));
     RC(upload(c->g_halo_nodes, p.halo_nodes.data(), p.halo_nodes.size() * 4));
     RC(upload(c->g_rin_ptr, p.rin_ptr.data(), p.rin_ptr.size() * 4));
@@ -107,7 +108,8 @@ int upload_partition(wr_ctx* c) {
     g.arc_ref = c->g_ref.as<uint32_t>();
     g.arc_w = c->g_w.as<uint32_t>();
     g.arc2 = c->g_arc2.as<uint2>();
-    g.run_ptr = c->g_run_ptr.as<int32_t>();
+    g.run_seg = c->g_run_ptr.as<int4>();
+    g.run_x = c->g_run_x.as<int2>();
     g.halo_ptr = c->g_halo_ptr.as<int32_t>();
     g.halo_nodes = c->g_halo_nodes.as<int32_t>();
     g.rin_ptr = c->g_rin_ptr.as<int32_t>();
@@ -412,7 +414,7 @@ void wr_destroy(wr_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    DBuf* bufs[] = {&c->g_desc, &c->g_ref, &c->g_w, &c->g_arc2, &c->g_run_ptr, &c->g_halo_ptr, &c->g_halo_nodes, &c->g_rin_ptr,
+    DBuf* bufs[] = {&c->g_desc, &c->g_ref, &c->g_w, &c->g_arc2, &c->g_run_ptr, &c->g_run_x, &c->g_halo_ptr, &c->g_halo_nodes, &c->g_rin_ptr,
                     &c->g_rin_list, &c->g_run_of, &c->g_meta, &c->g_flags, &c->g_ix, &c->g_xarc, &c->g_cdesc, &c->rows, &c->stamp, &c->list0, &c->list1,
                     &c->counts, &c->bar, &c->err, &c->stats, &c->node_flag, &c->src_index, &c->src_list,
                     &c->n_src, &c->block_sums, &c->offs, &c->picks, &c->order_status, &c->order_flags, &c->D,
@@ -854,7 +856,8 @@ int wr_autotune(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* picks,
         return WR_OK;
     };
     struct BfCand { int tiling, tile_cap, run_target; };
-    const BfCand bf[] = {{1, 256, 200}, {1, 256, 256}, {1, 128, 100}, {1, 128, 128}, {2, 256, 200}, {2, 512, 400}};
+    // run_target about half the tile lets two segments (the faces of an aisle) share one tile
+    const BfCand bf[] = {{1, 256, 120}, {1, 128, 60}, {1, 256, 200}, {2, 256, 120}, {2, 256, 200}, {2, 512, 240}};
     wr_tuning best = start;
     float best_ms = 3.4e38f;
     int rc = WR_OK;

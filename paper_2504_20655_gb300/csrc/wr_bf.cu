@@ -100,7 +100,7 @@ __device__ __forceinline__ uint32_t diff4(uint4 a, uint4 b) {
 // writes min(L, x_in + S).  The forward pass takes arcs from lower ids, the
 // backward pass from higher ids, so every arc is relaxed once per sweep.
 template <int TILE, bool FWD, int NQ>
-__device__ __forceinline__ bool scan_pass(TileSmem<TILE>& sm, int len, uint32_t x0, int lane, int q0) {
+__device__ __forceinline__ bool scan_pass(TileSmem<TILE>& sm, int len, int lane, int q0) {
     constexpr int NCH = TILE / 32;
     const uint2* xa = sm.xarcs;
     bool changed = false;
@@ -135,7 +135,7 @@ __device__ __forceinline__ bool scan_pass(TileSmem<TILE>& sm, int len, uint32_t 
             if (valid[j] && (b.z & IX_EXTRA)) {
                 const uint32_t nfx = (b.z >> 16) & 0xFFu;
                 xb[j] = FWD ? b.w : b.w + nfx;
-                xe[j] = FWD ? b.w + nfx : sm.ix[2 * ii + 3].w;
+                xe[j] = b.w + nfx + (FWD ? 0u : (b.z >> 25) & 0x7Fu);
             }
         }
         // carry-weight prefixes over the lanes: W[k] = summed S over lanes
@@ -167,7 +167,7 @@ __device__ __forceinline__ bool scan_pass(TileSmem<TILE>& sm, int len, uint32_t 
                 cur[j] = rq[p_own[j]];
                 uint4 cv = addmin4(rq[p0[j]], w0[j], cur[j]);
                 if constexpr (FWD) cv = addmin4(rq[p1[j]], w1[j], cv);
-                for (uint32_t e = xb[j]; e < xe[j]; ++e) cv = addmin4(rq[pos_of(xa[e - x0].x)], xa[e - x0].y, cv);
+                for (uint32_t e = xb[j]; e < xe[j]; ++e) cv = addmin4(rq[pos_of(xa[e].x)], xa[e].y, cv);
                 L[j] = j == 0 ? cv : addmin4(L[j > 0 ? j - 1 : 0], w[j], cv);
             }
             uint4 cin = make_uint4(INF_U, INF_U, INF_U, INF_U);
@@ -207,11 +207,11 @@ __device__ __forceinline__ bool scan_pass(TileSmem<TILE>& sm, int len, uint32_t 
 }
 
 template <int TILE, int NQ>
-__device__ __forceinline__ bool passes_fast(TileSmem<TILE>& sm, int len, uint32_t x0, int lane, int q0) {
-    const bool f = scan_pass<TILE, true, NQ>(sm, len, x0, lane, q0);
+__device__ __forceinline__ bool passes_fast(TileSmem<TILE>& sm, int len, int lane, int q0) {
+    const bool f = scan_pass<TILE, true, NQ>(sm, len, lane, q0);
     cp_async_wait_pending(0);
     __syncwarp();
-    const bool b = scan_pass<TILE, false, NQ>(sm, len, x0, lane, q0);
+    const bool b = scan_pass<TILE, false, NQ>(sm, len, lane, q0);
     return f || b;
 }
 
@@ -219,12 +219,12 @@ __device__ __forceinline__ bool passes_fast(TileSmem<TILE>& sm, int len, uint32_
 // in-neighbours than the tile holds): descriptors and arcs from global memory,
 // sources from the tile or, past its capacity, from the rows in L2.
 template <int TILE>
-__device__ __noinline__ bool passes_generic(const BfParams& p, TileSmem<TILE>& sm, int r0, int len, int lane,
+__device__ __noinline__ bool passes_generic(const BfParams& p, TileSmem<TILE>& sm, int4 rs, int len, int lane,
                                             int64_t lane_off) {
-    uint32_t* rs = reinterpret_cast<uint32_t*>(&sm.rows[0][0]);
+    uint32_t* words = reinterpret_cast<uint32_t*>(&sm.rows[0][0]);
     // word of source lane `lane` of tile slot i in the quad-major layout
     auto at = [&](int i) -> uint32_t& {
-        return rs[((lane >> 2) * TileSmem<TILE>::PLANE + pos_of(i)) * 4 + (lane & 3)];
+        return words[((lane >> 2) * TileSmem<TILE>::PLANE + pos_of(i)) * 4 + (lane & 3)];
     };
     const uint32_t* rows = p.seg.rows;
     const int64_t ld = p.seg.ld;
@@ -233,7 +233,7 @@ __device__ __noinline__ bool passes_generic(const BfParams& p, TileSmem<TILE>& s
     __syncwarp();
     uint32_t carry = INF_U;
     for (int i = 0; i < len; ++i) {
-        const int4 d = __ldg(p.g.node_desc + r0 + i);
+        const int4 d = __ldg(p.g.node_desc + run_node(rs, i));
         const uint32_t cur = at(i);
         uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.x), cur);
         for (int q = d.z; q < d.w; ++q) {
@@ -253,8 +253,8 @@ __device__ __noinline__ bool passes_generic(const BfParams& p, TileSmem<TILE>& s
     }
     carry = INF_U;
     for (int i = len - 1; i >= 0; --i) {
-        const int4 d = __ldg(p.g.node_desc + r0 + i);
-        const int end = __ldg(&p.g.node_desc[r0 + i + 1].z);
+        const int4 d = __ldg(p.g.node_desc + run_node(rs, i));
+        const int end = __ldg(&p.g.node_desc[run_node(rs, i) + 1].z);
         const uint32_t cur = at(i);
         uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.y), cur);
         for (int q = d.w; q < end; ++q) {
@@ -294,22 +294,21 @@ __device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, Tile
     // the 8 lanes of a 16-byte access phase hit 8 consecutive positions.
     const int qs = q0 + lane / NPI;  // the quad this lane stages
     const int soff = 2 * (lane % (NPI / 2)) + (lane % NPI) / (NPI / 2);
-    const int r0 = __ldg(p.g.run_ptr + r);
-    const int len = __ldg(p.g.run_ptr + r + 1) - r0;
+    const int4 rs = __ldg(p.g.run_seg + r);
+    const int len = rs.y + rs.w;
     const int h0 = __ldg(p.g.halo_ptr + r);
     const int hn = __ldg(p.g.halo_ptr + r + 1) - h0;
     const bool simple = (__ldg(p.g.run_flags + r) & RUN_SIMPLE) != 0;
     const int64_t ld = p.seg.ld;
     const int64_t lane_off = seg_col0(p.seg, g);
     uint32_t* rows = p.seg.rows;
-    const uint32_t x0 = __ldg(&p.g.node_ix[2 * static_cast<int64_t>(r0) + 1].w);
-    const uint32_t x1 = __ldg(&p.g.node_ix[2 * static_cast<int64_t>(r0 + len) + 1].w);
+    const int2 rx = __ldg(p.g.run_x + r);
 
     // group 0: descriptors and extra arcs (all threads), this warp's quads of the halo rows
     if (simple) {
-        for (int i = tid; i < 2 * (len + 1); i += 32 * NQW)
-            cp_async16(&sm.ix[i], &p.g.node_ix[2 * static_cast<int64_t>(r0) + i]);
-        for (uint32_t q = x0 + tid; q < x1; q += 32 * NQW) cp_async8_ca(&sm.xarcs[q - x0], &p.g.xarc2[q]);
+        for (int i = tid; i < 2 * len; i += 32 * NQW)
+            cp_async16(&sm.ix[i], &p.g.node_ix[2 * static_cast<int64_t>(run_node(rs, i >> 1)) + (i & 1)]);
+        for (int q = rx.x + tid; q < rx.y; q += 32 * NQW) cp_async8_ca(&sm.xarcs[q - rx.x], &p.g.xarc2[q]);
     }
     for (int i0 = 0; i0 < hn; i0 += NPI) {
         const int i = i0 + soff;
@@ -327,7 +326,8 @@ __device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, Tile
             for (int t = 0; t < NQ; ++t) {
                 const int i = base + t * NPI + soff;
                 if (i < len)
-                    cp_async16(&sm.rows[qs][pos_of(i)], rows + static_cast<int64_t>(r0 + i) * ld + lane_off + qs * 4);
+                    cp_async16(&sm.rows[qs][pos_of(i)],
+                               rows + static_cast<int64_t>(run_node(rs, i)) * ld + lane_off + qs * 4);
             }
         }
         cp_async_commit();
@@ -347,11 +347,11 @@ __device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, Tile
 
     bool mine = false;
     if (simple) {
-        mine = passes_fast<TILE, NQ>(sm, len, x0, lane, q0);
+        mine = passes_fast<TILE, NQ>(sm, len, lane, q0);
     } else {
         cp_async_wait_pending(0);
         __syncthreads();  // every quad staged
-        if (warp == 0) mine = passes_generic<TILE>(p, sm, r0, len, lane, lane_off);
+        if (warp == 0) mine = passes_generic<TILE>(p, sm, rs, len, lane, lane_off);
     }
     const bool changed = __syncthreads_or(mine) != 0;
     if (tid == 0) node_visits += static_cast<unsigned long long>(len);
@@ -361,7 +361,7 @@ __device__ __forceinline__ bool sweep_tile(const BfParams& p, int r, int g, Tile
         for (int i0 = 0; i0 < len; i0 += 4 * NQW) {
             const int i = i0 + sub;
             if (i < len && sm.dirtyb[i])
-                __stcg(reinterpret_cast<uint4*>(rows + static_cast<int64_t>(r0 + i) * ld + lane_off + q * 4),
+                __stcg(reinterpret_cast<uint4*>(rows + static_cast<int64_t>(run_node(rs, i)) * ld + lane_off + q * 4),
                        sm.rows[q][pos_of(i)]);
         }
     }
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(32 * NQW, NQW == 8 ? 2 : 5) bf_sweeps_kernel(B
                 if (ch) p.w.stamp[item] = sweep + 1;
                 ++tiles;
                 bytes += static_cast<unsigned long long>(__ldg(p.g.run_meta_bytes + r)) +
-                         256ull * static_cast<unsigned long long>(__ldg(p.g.run_ptr + r + 1) - __ldg(p.g.run_ptr + r));
+                         256ull * static_cast<unsigned long long>(__ldg(&p.g.run_seg[r].y) + __ldg(&p.g.run_seg[r].w));
             }
         }
         if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) break;

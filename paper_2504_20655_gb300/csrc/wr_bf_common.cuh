@@ -12,6 +12,9 @@ struct BfParams {
     BfWork w;
 };
 
+// Node held by tile slot i < alen + blen of a run {a0, alen, b0, blen}.
+__device__ __forceinline__ int run_node(const int4& rs, int i) { return i < rs.y ? rs.x + i : rs.z + (i - rs.y); }
+
 // First row column of the segment's 32-source group g.
 __device__ __forceinline__ int64_t seg_col0(const BfSegment& seg, int g) {
     return seg.gcol ? static_cast<int64_t>(__ldg(seg.gcol + g)) * 32 : static_cast<int64_t>(g) * 32;

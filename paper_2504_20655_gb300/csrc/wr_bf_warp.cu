@@ -93,7 +93,8 @@ __device__ __forceinline__ bool wait_tile(unsigned long long* bar, uint32_t pari
 
 // Run metadata of one work item (the same in every lane).
 struct TileMeta {
-    int item, r, g, r0, len, h0, hn, flags;
+    int item, r, g, len, h0, hn, flags;
+    int4 rs;  // {a0, alen, b0, blen}
 };
 
 __device__ __forceinline__ TileMeta load_meta(const BfParams& p, const int32_t* list, int it, int G) {
@@ -101,8 +102,8 @@ __device__ __forceinline__ TileMeta load_meta(const BfParams& p, const int32_t* 
     m.item = __ldcg(list + it);
     m.r = m.item / G;
     m.g = m.item - m.r * G;
-    m.r0 = __ldg(p.g.run_ptr + m.r);
-    m.len = __ldg(p.g.run_ptr + m.r + 1) - m.r0;
+    m.rs = __ldg(p.g.run_seg + m.r);
+    m.len = m.rs.y + m.rs.w;
     m.h0 = __ldg(p.g.halo_ptr + m.r);
     m.hn = __ldg(p.g.halo_ptr + m.r + 1) - m.h0;
     m.flags = __ldg(p.g.run_flags + m.r);
@@ -190,7 +191,7 @@ __device__ __forceinline__ uint32_t warp_pass(WarpTile<TILE>& t, int len, int la
 // in a pass, or a halo larger than the tile): descriptors and arcs from global
 // memory, sources from the tile or, past its capacity, from the rows in L2.
 template <int TILE>
-__device__ __noinline__ uint32_t warp_passes_generic(const BfParams& p, WarpTile<TILE>& t, int r0, int len, int lane,
+__device__ __noinline__ uint32_t warp_passes_generic(const BfParams& p, WarpTile<TILE>& t, int4 rs, int len, int lane,
                                                      int64_t lane_off) {
     uint32_t* col = &t.rows[0][lane];
     const uint32_t* rows = p.seg.rows;
@@ -198,7 +199,7 @@ __device__ __noinline__ uint32_t warp_passes_generic(const BfParams& p, WarpTile
     uint32_t chg = 0;
     uint32_t carry = INF_U;
     for (int i = 0; i < len; ++i) {
-        const int4 d = __ldg(p.g.node_desc + r0 + i);
+        const int4 d = __ldg(p.g.node_desc + run_node(rs, i));
         const uint32_t cur = col[32 * i];
         uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.x), cur);
         for (int q = d.z; q < d.w; ++q) {
@@ -213,8 +214,8 @@ __device__ __noinline__ uint32_t warp_passes_generic(const BfParams& p, WarpTile
     }
     carry = INF_U;
     for (int i = len - 1; i >= 0; --i) {
-        const int4 d = __ldg(p.g.node_desc + r0 + i);
-        const int end = __ldg(&p.g.node_desc[r0 + i + 1].z);
+        const int4 d = __ldg(p.g.node_desc + run_node(rs, i));
+        const int end = __ldg(&p.g.node_desc[run_node(rs, i) + 1].z);
         const uint32_t cur = col[32 * i];
         uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.y), cur);
         for (int q = d.w; q < end; ++q) {
@@ -242,13 +243,16 @@ __device__ __forceinline__ int warp_tile(const BfParams& p, const TileMeta& m, W
     __syncwarp();
     // own lines, halo lines (one 128-byte copy per line, 32 per warp instruction), descriptors
     for (int i = lane; i < m.len; i += 32)
-        bulk_load(&t.rows[i][0], rows + static_cast<int64_t>(m.r0 + i) * ld + lane_off, 128u, &t.bar);
+        bulk_load(&t.rows[i][0], rows + static_cast<int64_t>(run_node(m.rs, i)) * ld + lane_off, 128u, &t.bar);
     for (int h = lane; h < m.hn; h += 32) {
         const int node = __ldg(p.g.halo_nodes + m.h0 + h);
         bulk_load(&t.rows[m.len + h][0], rows + static_cast<int64_t>(node) * ld + lane_off, 128u, &t.bar);
     }
     if (compact && lane == 0)
-        bulk_load(&t.desc[0], p.g.cdesc + 2 * static_cast<int64_t>(m.r0), static_cast<uint32_t>(m.len) * 32u, &t.bar);
+        bulk_load(&t.desc[0], p.g.cdesc + 2 * static_cast<int64_t>(m.rs.x), static_cast<uint32_t>(m.rs.y) * 32u, &t.bar);
+    if (compact && lane == 1 && m.rs.w > 0)
+        bulk_load(&t.desc[2 * m.rs.y], p.g.cdesc + 2 * static_cast<int64_t>(m.rs.z), static_cast<uint32_t>(m.rs.w) * 32u,
+                  &t.bar);
     if (!wait_tile(&t.bar, parity, p)) {
         // let the copies already issued land before the shared memory is abandoned
         for (unsigned long long s = 0; !mbar_try_wait(&t.bar, parity) && s <= p.w.max_spins; ++s) {
@@ -262,7 +266,7 @@ __device__ __forceinline__ int warp_tile(const BfParams& p, const TileMeta& m, W
         chg = warp_pass<TILE, true>(t, m.len, lane);
         chg |= warp_pass<TILE, false>(t, m.len, lane);
     } else {
-        chg = warp_passes_generic<TILE>(p, t, m.r0, m.len, lane, lane_off);
+        chg = warp_passes_generic<TILE>(p, t, m.rs, m.len, lane, lane_off);
     }
     const bool changed = __any_sync(FULL_MASK, chg != 0u);
     if (changed) {
@@ -270,7 +274,7 @@ __device__ __forceinline__ int warp_tile(const BfParams& p, const TileMeta& m, W
         fence_proxy_async_smem();  // this lane's shared stores visible to the copy engine
         __syncwarp();
         for (int i = lane; i < m.len; i += 32)
-            bulk_store(rows + static_cast<int64_t>(m.r0 + i) * ld + lane_off, &t.rows[i][0], 128u);
+            bulk_store(rows + static_cast<int64_t>(run_node(m.rs, i)) * ld + lane_off, &t.rows[i][0], 128u);
         bulk_commit();
         bulk_wait_read_all();  // shared lines read out before the next tile lands on them
     }

@@ -51,7 +51,7 @@ struct wr_ctx {
     wr::HostGraph hg;
     wr::HostPartition hp;
     wr::DevGraph dg;
-    wrc::DBuf g_desc, g_ref, g_w, g_arc2, g_run_ptr, g_halo_ptr, g_halo_nodes, g_rin_ptr, g_rin_list, g_run_of, g_meta, g_flags, g_ix, g_xarc, g_cdesc;
+    wrc::DBuf g_desc, g_ref, g_w, g_arc2, g_run_ptr, g_run_x, g_halo_ptr, g_halo_nodes, g_rin_ptr, g_rin_list, g_run_of, g_meta, g_flags, g_ix, g_xarc, g_cdesc;
     wr::BfLaunchInfo bf_info{};
     int enum_blocks = 0;
     // working buffers

@@ -37,30 +37,38 @@ struct HostGraph {
     std::vector<int32_t> in_w;
 };
 
-// Sweep tiles: runs of consecutive node ids whose own rows plus the rows of
-// their out-of-run in-neighbours (the halo) fit tile_cap shared-memory slots.
+// Sweep tiles ("runs"): one or two segments of consecutive node ids (two when
+// a segment and the one holding most of its halo fit one tile together, e.g.
+// both faces of an aisle), whose own rows plus the rows of their outside
+// in-neighbours (the halo) fit tile_cap shared-memory slots.  Tile slots:
+// the first segment's nodes, then the second's, then the staged halo.
 struct HostPartition {
     int32_t V = 0, n_runs = 0, tile_cap = 0, max_len = 0;
-    std::vector<int32_t> run_ptr;       // n_runs + 1
+    std::vector<int4> run_seg;          // n_runs: {a0, alen, b0, blen}: nodes a0.. then b0.. (blen may be 0)
     std::vector<int32_t> halo_ptr;      // n_runs + 1 (staged halo only)
     std::vector<int32_t> halo_nodes;
     std::vector<int32_t> rin_ptr;       // runs with an arc into the run
     std::vector<int32_t> rin_list;
     std::vector<int32_t> run_of_node;   // V
-    // per node v (plus a sentinel at V): x = weight of arc v-1 -> v inside the
-    // run (NO_CARRY if none), y = weight of v+1 -> v inside the run, z = first
-    // forward arc, w = first backward arc; backward arcs end at desc[v+1].z.
+    std::vector<int32_t> slot_of_node;  // V: tile slot in its own run
+    // per node v (plus a sentinel at V): x = weight of the carry arc from the
+    // previous tile slot (node v-1, NO_CARRY if none), y = from the next slot
+    // (node v+1), z = first forward arc, w = first backward arc; backward arcs
+    // end at desc[v+1].z (arc lists are in node id order).  Forward arcs come
+    // from lower tile slots or the halo, backward arcs from higher slots.
     std::vector<int4> node_desc;
     std::vector<uint32_t> arc_ref;      // tile slot of the arc's source, or GLOBAL_REF | node
     std::vector<uint32_t> arc_w;
-    // Inline form of the same arcs for the sweep kernel's fast path, two
-    // uint4 per node (plus a sentinel): a = {fw carry w, bw carry w, fw0 w,
-    // fw1 w}, b = {bw0 w, fw0 slot | fw1 slot << 16, bw0 slot | n_fw_extra <<
-    // 16 | IX_EXTRA, first extra}.  Absent inline arcs use slot 0 and weight
-    // NO_CARRY.  Arcs beyond the inline ones are in xarc2: forward extras then
-    // backward extras, ending at the next node's first extra.
+    // Inline form of the same arcs for the CTA tiling, two uint4 per node:
+    // a = {fw carry w, bw carry w, fw0 w, fw1 w}, b = {bw0 w, fw0 slot | fw1
+    // slot << 16, bw0 slot | n_fw_extra << 16 | IX_EXTRA | n_bw_extra << 25,
+    // first extra}.  Absent inline arcs use slot 0 and weight NO_CARRY.  Arcs
+    // beyond the inline ones are the run's extras, xarc2[run_x.x ..
+    // run_x.y), forward then backward per node; "first extra" is relative to
+    // run_x.x.
     std::vector<uint4> node_ix;
     std::vector<uint2> xarc2;
+    std::vector<int2> run_x;
     std::vector<int64_t> run_meta_bytes;  // 8 * in-arcs + 8 * nodes of the run
     std::vector<int32_t> run_flags;       // RUN_SIMPLE | RUN_COMPACT
     // Compact descriptors of the warp tiling, 2 per node: forward {carry weight,
@@ -92,7 +100,8 @@ struct DevGraph {
     uint2* arc2 = nullptr;  // (arc_ref, arc_w) interleaved
     uint4* node_ix = nullptr;  // inline descriptors, 2 per node
     uint2* xarc2 = nullptr;    // extra arcs
-    int32_t* run_ptr = nullptr;
+    int4* run_seg = nullptr;   // {a0, alen, b0, blen} per run
+    int2* run_x = nullptr;     // the run's extras in xarc2
     int32_t* halo_ptr = nullptr;
     int32_t* halo_nodes = nullptr;
     int32_t* rin_ptr = nullptr;

@@ -44,13 +44,15 @@ extern "C" int bfm_rows(int V, long long E, const long long* rp, const int* col,
         if (sweep > V + 1) return 99;
         for (int item : list) {
             const int r = item / G, gg = item % G;
-            const int r0 = p.run_ptr[r], len = p.run_ptr[r + 1] - r0;
+            const int4 rs = p.run_seg[r];
+            const int len = rs.y + rs.w;
+            auto node = [&](int i) { return i < rs.y ? rs.x + i : rs.z + (i - rs.y); };
             const int h0 = p.halo_ptr[r], hn = p.halo_ptr[r + 1] - h0;
             if (len + hn > tile_cap) return 98;
             bool changed = false;
             for (int lane = 0; lane < 32; ++lane) {
                 const size_t c = static_cast<size_t>(gg) * 32 + lane;
-                for (int i = 0; i < len; ++i) tile[i] = rows[static_cast<size_t>(r0 + i) * ld + c];
+                for (int i = 0; i < len; ++i) tile[i] = rows[static_cast<size_t>(node(i)) * ld + c];
                 for (int h = 0; h < hn; ++h) tile[len + h] = rows[static_cast<size_t>(p.halo_nodes[h0 + h]) * ld + c];
                 std::vector<char> dirty(static_cast<size_t>(len), 0);
                 // The kernel walks each pass in chunks of SPAN node ids aligned to
@@ -65,13 +67,13 @@ extern "C" int bfm_rows(int V, long long E, const long long* rp, const int* col,
                 for (int c0 = 0; c0 < len; c0 += SPAN) {
                     const int c1 = std::min(len, c0 + SPAN);
                     for (int i = c0; i < c1; ++i) {
-                        const int4 d = p.node_desc[r0 + i];
+                        const int4 d = p.node_desc[node(i)];
                         uint32_t o = 0xFFFFFFFFu;
                         for (int a = d.z; a < d.w; ++a) o = std::min(src(p.arc_ref[a]) + p.arc_w[a], o);
                         oth[i] = o;
                     }
                     for (int i = c0; i < c1; ++i) {
-                        const uint32_t cw = std::min(static_cast<uint32_t>(p.node_desc[r0 + i].x), INF_U);
+                        const uint32_t cw = std::min(static_cast<uint32_t>(p.node_desc[node(i)].x), INF_U);
                         uint32_t best = std::min(tile[i], oth[i]);
                         if (i > 0) best = std::min(tile[i - 1] + cw, best);
                         if (best < tile[i]) { tile[i] = best; dirty[i] = 1; changed = true; }
@@ -80,20 +82,20 @@ extern "C" int bfm_rows(int V, long long E, const long long* rp, const int* col,
                 for (int cb = ((len - 1) / SPAN) * SPAN; cb >= 0; cb -= SPAN) {
                     const int top = std::min(len - 1, cb + SPAN - 1), bot = cb - 1;
                     for (int i = top; i > bot; --i) {
-                        const int4 d = p.node_desc[r0 + i];
+                        const int4 d = p.node_desc[node(i)];
                         uint32_t o = 0xFFFFFFFFu;
-                        for (int a = d.w; a < p.node_desc[r0 + i + 1].z; ++a) o = std::min(tile[p.arc_ref[a]] + p.arc_w[a], o);
+                        for (int a = d.w; a < p.node_desc[node(i) + 1].z; ++a) o = std::min(tile[p.arc_ref[a]] + p.arc_w[a], o);
                         oth[i] = o;
                     }
                     for (int i = top; i > bot; --i) {
-                        const uint32_t cw = std::min(static_cast<uint32_t>(p.node_desc[r0 + i].y), INF_U);
+                        const uint32_t cw = std::min(static_cast<uint32_t>(p.node_desc[node(i)].y), INF_U);
                         uint32_t best = std::min(tile[i], oth[i]);
                         if (i + 1 < len) best = std::min(tile[i + 1] + cw, best);
                         if (best < tile[i]) { tile[i] = best; dirty[i] = 1; changed = true; }
                     }
                 }
                 for (int i = 0; i < len; ++i)
-                    if (dirty[i]) rows[static_cast<size_t>(r0 + i) * ld + c] = tile[i];
+                    if (dirty[i]) rows[static_cast<size_t>(node(i)) * ld + c] = tile[i];
             }
             if (changed) stamp[item] = sweep + 1;
         }
@@ -113,38 +115,57 @@ extern "C" int bfm_check_partition(int V, long long E, const long long* rp, cons
     HostPartition p;
     build_partition(g, run_target, tile_cap, p);
     *n_runs_out = p.n_runs;
-    if (p.run_ptr.front() != 0 || p.run_ptr.back() != V) return 2;
+    // the runs' segments cover every node once, slots in segment order
+    std::vector<int> seen(static_cast<size_t>(V), 0);
     for (int r = 0; r < p.n_runs; ++r) {
-        const int s = p.run_ptr[r], e = p.run_ptr[r + 1], len = e - s;
-        if (len < 1 || len > run_target) return 3;
+        const int4 rs = p.run_seg[r];
+        if (rs.y < 1 || rs.y > run_target || rs.w < 0 || rs.w > run_target) return 3;
+        for (int i = 0; i < rs.y + rs.w; ++i) {
+            const int v = i < rs.y ? rs.x + i : rs.z + (i - rs.y);
+            if (v < 0 || v >= V || seen[v]++) return 2;
+            if (p.run_of_node[v] != r || p.slot_of_node[v] != i) return 5;
+        }
+    }
+    for (int v = 0; v < V; ++v)
+        if (!seen[v]) return 2;
+    for (int r = 0; r < p.n_runs; ++r) {
+        const int4 rs = p.run_seg[r];
+        const int len = rs.y + rs.w;
+        auto node = [&](int i) { return i < rs.y ? rs.x + i : rs.z + (i - rs.y); };
         const int hn = p.halo_ptr[r + 1] - p.halo_ptr[r];
         if (len + hn > tile_cap) return 4;
-        for (int v = s; v < e; ++v)
-            if (p.run_of_node[v] != r) return 5;
         // every in-arc of the run's nodes appears exactly once, with its weight
         std::vector<int> halo(p.halo_nodes.begin() + p.halo_ptr[r], p.halo_nodes.begin() + p.halo_ptr[r + 1]);
         std::vector<int> runs_in;
-        for (int v = s; v < e; ++v) {
+        for (int i = 0; i < len; ++i) {
+            const int v = node(i);
             const int4 d = p.node_desc[v];
             std::vector<std::pair<int, uint32_t>> got;
-            if (static_cast<uint32_t>(d.x) != NO_CARRY) got.emplace_back(v - 1, static_cast<uint32_t>(d.x));
-            if (static_cast<uint32_t>(d.y) != NO_CARRY) got.emplace_back(v + 1, static_cast<uint32_t>(d.y));
+            // carries come from the neighbouring slots, which must hold v - 1 / v + 1
+            if (static_cast<uint32_t>(d.x) != NO_CARRY) {
+                if (i == 0 || node(i - 1) != v - 1) return 17;
+                got.emplace_back(v - 1, static_cast<uint32_t>(d.x));
+            }
+            if (static_cast<uint32_t>(d.y) != NO_CARRY) {
+                if (i + 1 >= len || node(i + 1) != v + 1) return 17;
+                got.emplace_back(v + 1, static_cast<uint32_t>(d.y));
+            }
             const int end = p.node_desc[v + 1].z;
             for (int a = d.z; a < end; ++a) {
                 const uint32_t ref = p.arc_ref[a];
                 int u;
-                if (ref & GLOBAL_REF) u = static_cast<int>(ref & ~GLOBAL_REF);
-                else if (static_cast<int>(ref) < len) u = s + static_cast<int>(ref);
-                else {
-                    if (static_cast<int>(ref) - len >= hn) return 6;
-                    u = halo[ref - len];
-                }
                 const bool fw = a < d.w;
-                if (u >= s && u < e) {
-                    if (fw && !(u < v)) return 7;   // forward arcs come from lower ids
-                    if (!fw && !(u > v)) return 8;  // backward arcs from higher ids
-                } else if (!fw) {
-                    return 9;  // out-of-run sources are read in the forward pass
+                if (ref & GLOBAL_REF) {
+                    u = static_cast<int>(ref & ~GLOBAL_REF);
+                    if (!fw) return 9;
+                } else if (static_cast<int>(ref) < len) {
+                    u = node(static_cast<int>(ref));
+                    if (fw && !(static_cast<int>(ref) < i)) return 7;   // forward arcs come from lower slots
+                    if (!fw && !(static_cast<int>(ref) > i)) return 8;  // backward arcs from higher slots
+                } else {
+                    if (static_cast<int>(ref) - len >= hn) return 6;
+                    if (!fw) return 9;  // out-of-run sources are read in the forward pass
+                    u = halo[ref - len];
                 }
                 got.emplace_back(u, p.arc_w[a]);
             }
@@ -154,26 +175,27 @@ extern "C" int bfm_check_partition(int V, long long E, const long long* rp, cons
             std::sort(got.begin(), got.end());
             if (got != want) return 10;
             for (auto& pr : want)
-                if (pr.first < s || pr.first >= e) runs_in.push_back(p.run_of_node[pr.first]);
+                if (p.run_of_node[pr.first] != r) runs_in.push_back(p.run_of_node[pr.first]);
         }
         // the inline descriptors of a fast-path run hold the same arcs
         if (p.run_flags[r] & RUN_SIMPLE) {
-            const uint32_t x0 = p.node_ix[2 * static_cast<size_t>(s) + 1].w;
-            const uint32_t x1 = p.node_ix[2 * static_cast<size_t>(e) + 1].w;
-            if (x1 - x0 > static_cast<uint32_t>(tile_cap)) return 12;
-            for (int v = s; v < e; ++v) {
+            const int2 rx = p.run_x[r];
+            if (rx.y - rx.x > tile_cap) return 12;
+            for (int i = 0; i < len; ++i) {
+                const int v = node(i);
                 const uint4 a = p.node_ix[2 * static_cast<size_t>(v)], b = p.node_ix[2 * static_cast<size_t>(v) + 1];
-                const uint4 bn = p.node_ix[2 * static_cast<size_t>(v) + 3];
                 const int4 d = p.node_desc[v];
                 if (a.x != static_cast<uint32_t>(d.x) || a.y != static_cast<uint32_t>(d.y)) return 13;
                 std::vector<std::pair<uint32_t, uint32_t>> fw_ix, bw_ix, fw_l, bw_l;
                 if (a.z != NO_CARRY) fw_ix.emplace_back(b.y & 0xFFFFu, a.z);
                 if (a.w != NO_CARRY) fw_ix.emplace_back(b.y >> 16, a.w);
                 if (b.x != NO_CARRY) bw_ix.emplace_back(b.z & 0xFFFFu, b.x);
-                const uint32_t nfx = (b.z >> 16) & 0xFFu;
-                if (!(b.z & IX_EXTRA) && bn.w != b.w) return 14;
-                for (uint32_t q = b.w; q < b.w + nfx; ++q) fw_ix.emplace_back(p.xarc2[q].x, p.xarc2[q].y);
-                for (uint32_t q = b.w + nfx; q < bn.w; ++q) bw_ix.emplace_back(p.xarc2[q].x, p.xarc2[q].y);
+                const uint32_t nfx = (b.z >> 16) & 0xFFu, nbx = (b.z >> 25) & 0x7Fu;
+                if (!(b.z & IX_EXTRA) && (nfx || nbx)) return 14;
+                const uint32_t x0 = static_cast<uint32_t>(rx.x) + b.w;
+                if (x0 + nfx + nbx > static_cast<uint32_t>(rx.y)) return 14;
+                for (uint32_t q = x0; q < x0 + nfx; ++q) fw_ix.emplace_back(p.xarc2[q].x, p.xarc2[q].y);
+                for (uint32_t q = x0 + nfx; q < x0 + nfx + nbx; ++q) bw_ix.emplace_back(p.xarc2[q].x, p.xarc2[q].y);
                 for (int q = d.z; q < d.w; ++q) fw_l.emplace_back(p.arc_ref[q], p.arc_w[q]);
                 for (int q = d.w; q < p.node_desc[v + 1].z; ++q) bw_l.emplace_back(p.arc_ref[q], p.arc_w[q]);
                 std::sort(fw_ix.begin(), fw_ix.end());
@@ -183,6 +205,27 @@ extern "C" int bfm_check_partition(int V, long long E, const long long* rp, cons
                 if (fw_ix != fw_l || bw_ix != bw_l) return 15;
                 for (auto& pr : fw_ix)
                     if (pr.first >= static_cast<uint32_t>(tile_cap)) return 16;
+            }
+        }
+        // the compact descriptors of a warp-tiling run hold the same arcs
+        if (p.run_flags[r] & RUN_COMPACT) {
+            for (int i = 0; i < len; ++i) {
+                const int v = node(i);
+                const uint4 f = p.cdesc[2 * static_cast<size_t>(v)], bk = p.cdesc[2 * static_cast<size_t>(v) + 1];
+                const int4 d = p.node_desc[v];
+                if (f.x != static_cast<uint32_t>(d.x) || bk.x != static_cast<uint32_t>(d.y)) return 18;
+                std::vector<std::pair<uint32_t, uint32_t>> fc, bc, fw_l, bw_l;
+                if (f.z != NO_CARRY) fc.emplace_back((f.y & 0xFFFFu) / 128u, f.z);
+                if (f.w != NO_CARRY) fc.emplace_back((f.y >> 16) / 128u, f.w);
+                if (bk.z != NO_CARRY) bc.emplace_back((bk.y & 0xFFFFu) / 128u, bk.z);
+                if (bk.w != NO_CARRY) bc.emplace_back((bk.y >> 16) / 128u, bk.w);
+                for (int q = d.z; q < d.w; ++q) fw_l.emplace_back(p.arc_ref[q], p.arc_w[q]);
+                for (int q = d.w; q < p.node_desc[v + 1].z; ++q) bw_l.emplace_back(p.arc_ref[q], p.arc_w[q]);
+                std::sort(fc.begin(), fc.end());
+                std::sort(bc.begin(), bc.end());
+                std::sort(fw_l.begin(), fw_l.end());
+                std::sort(bw_l.begin(), bw_l.end());
+                if (fc != fw_l || bc != bw_l) return 19;
             }
         }
         std::sort(runs_in.begin(), runs_in.end());
@@ -204,4 +247,23 @@ extern "C" double bfm_fast_fraction(int V, long long E, const long long* rp, con
     int simple = 0;
     for (int r = 0; r < p.n_runs; ++r) simple += (p.run_flags[r] & RUN_SIMPLE) ? 1 : 0;
     return static_cast<double>(simple) / p.n_runs;
+}
+
+// Pairing statistics: out[0] = share of runs with two segments, out[1] = staged
+// halo slots per own node, out[2] = share of runs with compact descriptors.
+extern "C" void bfm_pair_stats(int V, long long E, const long long* rp, const int* col, const int* w, int run_target,
+                               int tile_cap, double* out) {
+    HostGraph g;
+    out[0] = out[1] = out[2] = -1.0;
+    if (build_host_graph(V, E, reinterpret_cast<const int64_t*>(rp), col, w, 0, g)) return;
+    HostPartition p;
+    build_partition(g, run_target, tile_cap, p);
+    int paired = 0, compact = 0;
+    for (int r = 0; r < p.n_runs; ++r) {
+        paired += p.run_seg[r].w > 0 ? 1 : 0;
+        compact += (p.run_flags[r] & RUN_COMPACT) ? 1 : 0;
+    }
+    out[0] = static_cast<double>(paired) / p.n_runs;
+    out[1] = static_cast<double>(p.halo_nodes.size()) / V;
+    out[2] = static_cast<double>(compact) / p.n_runs;
 }

@@ -58,7 +58,7 @@ struct Lane {
 namespace {
 
 // One pass over a staged tile (the kernel's scan_pass, all 32 lanes at once).
-bool scan_pass(Smem& sm, bool fwd, int len, uint32_t x0) {
+bool scan_pass(Smem& sm, bool fwd, int len) {
     bool changed = false;
     const int nchunks = (len + SPAN - 1) / SPAN;
     for (int cc = 0; cc < nchunks; ++cc) {
@@ -81,7 +81,7 @@ bool scan_pass(Smem& sm, bool fwd, int len, uint32_t x0) {
                 if (L[l].valid[j] && (b.z & IX_EXTRA)) {
                     const uint32_t nfx = (b.z >> 16) & 0xFFu;
                     L[l].xb[j] = fwd ? b.w : b.w + nfx;
-                    L[l].xe[j] = fwd ? b.w + nfx : sm.ix[2 * ii + 3].w;
+                    L[l].xe[j] = b.w + nfx + (fwd ? 0u : (b.z >> 25) & 0x7Fu);
                 }
             }
         }
@@ -109,7 +109,7 @@ bool scan_pass(Smem& sm, bool fwd, int len, uint32_t x0) {
                     Q4 cv = addmin4(sm.rows[q][L[l].p0[j]], L[l].w0[j], cur[l][j]);
                     if (fwd) cv = addmin4(sm.rows[q][L[l].p1[j]], L[l].w1[j], cv);
                     for (uint32_t e = L[l].xb[j]; e < L[l].xe[j]; ++e)
-                        cv = addmin4(sm.rows[q][pos_of(static_cast<int>(sm.xarcs[e - x0].x))], sm.xarcs[e - x0].y, cv);
+                        cv = addmin4(sm.rows[q][pos_of(static_cast<int>(sm.xarcs[e].x))], sm.xarcs[e].y, cv);
                     Lc[l][j] = j == 0 ? cv : addmin4(Lc[l][j - 1], L[l].w[j], cv);
                 }
                 A[l] = Lc[l][SEG - 1];
@@ -184,17 +184,18 @@ extern "C" int bwm_rows(int V, long long E, const long long* rp, const int* col,
         for (int item : list) {
             const int r = item / G, gg = item % G;
             if (!(p.run_flags[r] & RUN_SIMPLE)) return 97;  // the generic path is not modelled
-            const int r0 = p.run_ptr[r], len = p.run_ptr[r + 1] - r0;
+            const int4 rs = p.run_seg[r];
+            const int len = rs.y + rs.w;
+            auto node = [&](int i) { return i < rs.y ? rs.x + i : rs.z + (i - rs.y); };
             const int h0 = p.halo_ptr[r], hn = p.halo_ptr[r + 1] - h0;
-            const uint32_t x0 = p.node_ix[2 * static_cast<size_t>(r0) + 1].w;
-            const uint32_t x1 = p.node_ix[2 * static_cast<size_t>(r0 + len) + 1].w;
+            const int2 rx = p.run_x[r];
             if (stale)
                 for (int q = 0; q < 8; ++q)
                     for (int i = len + hn; i < TILE; ++i)
                         for (int c = 0; c < 4; ++c)
                             sm.rows[q][pos_of(i)].v[c] = (i % 3 == 0) ? 0x80010000u + static_cast<uint32_t>(i) : 5u;
-            for (int i = 0; i < 2 * (len + 1); ++i) sm.ix[i] = p.node_ix[2 * static_cast<size_t>(r0) + i];
-            for (uint32_t q = x0; q < x1; ++q) sm.xarcs[q - x0] = p.xarc2[q];
+            for (int i = 0; i < 2 * len; ++i) sm.ix[i] = p.node_ix[2 * static_cast<size_t>(node(i >> 1)) + (i & 1)];
+            for (int q = rx.x; q < rx.y; ++q) sm.xarcs[q - rx.x] = p.xarc2[q];
             const size_t off = static_cast<size_t>(gg) * 32;
             for (int i = 0; i < hn; ++i)
                 for (int q = 0; q < 8; ++q)
@@ -203,20 +204,20 @@ extern "C" int bwm_rows(int V, long long E, const long long* rp, const int* col,
             for (int i = 0; i < len; ++i)
                 for (int q = 0; q < 8; ++q)
                     for (int c = 0; c < 4; ++c)
-                        sm.rows[q][pos_of(i)].v[c] = rows[static_cast<size_t>(r0 + i) * ld + off + q * 4 + c];
+                        sm.rows[q][pos_of(i)].v[c] = rows[static_cast<size_t>(node(i)) * ld + off + q * 4 + c];
             for (int i = 0; i < len; ++i) sm.dirtyb[i] = 0;
             if (inf_fill)
                 for (int t = len + hn; t < ((len + SPAN - 1) / SPAN) * SPAN; ++t)
                     for (int q = 0; q < 8; ++q)
                         for (int c = 0; c < 4; ++c) sm.rows[q][pos_of(t)].v[c] = INF_U;
-            const bool f = scan_pass(sm, true, len, x0);
-            const bool b = scan_pass(sm, false, len, x0);
+            const bool f = scan_pass(sm, true, len);
+            const bool b = scan_pass(sm, false, len);
             if (f || b) {
                 for (int i = 0; i < len; ++i)
                     if (sm.dirtyb[i])
                         for (int q = 0; q < 8; ++q)
                             for (int c = 0; c < 4; ++c)
-                                rows[static_cast<size_t>(r0 + i) * ld + off + q * 4 + c] = sm.rows[q][pos_of(i)].v[c];
+                                rows[static_cast<size_t>(node(i)) * ld + off + q * 4 + c] = sm.rows[q][pos_of(i)].v[c];
                 stamp[item] = sweep + 1;
             }
         }

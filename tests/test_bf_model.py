@@ -76,7 +76,7 @@ def test_partition_invariants(model, rt, tc):
     for g in graphs:
         rc, n_runs = check_partition(model, g, rt, tc)
         assert rc == 0, (g.V, rc)
-        assert n_runs >= (g.V + rt - 1) // rt
+        assert n_runs >= (g.V + 2 * rt - 1) // (2 * rt)  # a run holds at most two segments
     # the layouts run entirely on the fast path
     for g in graphs[-2:]:
         assert fast_path_fraction(model, g, rt, tc) == 1.0
@@ -116,3 +116,17 @@ def test_high_in_degree_spills_to_global(model, orc):
     src = np.array([0, 5, 699, 350], np.int32)
     out, _ = model_rows(model, g, src, 96, 128)
     assert (out == orc.sssp_rows(g, src)).all()
+
+
+def test_faces_share_tiles(model):
+    """On a two-level aisle layout the two faces of an aisle stretch pair up: most runs
+    hold two segments and the halo per own node drops well below the one-to-one of
+    unpaired face chains."""
+    g = synth.Layout(A=20, S=100, F=2, C=2, step_lo=50, step_hi=150, face_w=400).build()
+    P = ctypes.c_void_p
+    rp, c, w = _arrs(g)
+    out = np.zeros(3, np.float64)
+    model.bfm_pair_stats(g.V, ctypes.c_longlong(g.E), rp.ctypes.data_as(P), c.ctypes.data_as(P), w.ctypes.data_as(P),
+                         60, 128, out.ctypes.data_as(P))
+    paired, halo_per_node, compact = out
+    assert paired > 0.8 and halo_per_node < 0.25 and compact == 1.0
