@@ -125,9 +125,16 @@ def dist_setup(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        backend = "nccl" if args.impl == "ours" else "gloo"
-        dist.init_process_group(backend)
+        backend = getattr(args, "backend", None) or ("nccl" if args.impl == "ours" else "gloo")
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
     return world, rank, local
+
+
+def replica_value(units_per_rank, ms, world):
+    """Whole-job throughput of `world` replicas that each processed units_per_rank
+    units, timed by the slowest rank (ms = max over ranks)."""
+    return world * units_per_rank / (ms / 1e3)
 
 
 def max_over_ranks(x, world, device=None):
@@ -314,7 +321,7 @@ def run_batching(args):
     barrier(world)
     plan.sync()
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / args.steps, world, dev)
-    value = world * n / (ms / 1e3)
+    value = replica_value(n, ms, world)
     g_cost, g_perm, g_status = plan.cost.cpu().numpy(), plan.perm.cpu().numpy(), plan.status.cpu().numpy()
 
     # the same batch through one direct call, and one plain call per order
@@ -540,7 +547,7 @@ def run_ours(args):
     times = [a.elapsed_time(b) for a, b in zip(e0, e1)]
     ms = sum(times) / len(times)
     ms = max_over_ranks(ms, world, dev)
-    value = world * n / (ms / 1e3)
+    value = replica_value(n, ms, world)
 
     # end to end through the C ABI with pinned host buffers
     h_offs = torch.from_numpy(o.offs).pin_memory()

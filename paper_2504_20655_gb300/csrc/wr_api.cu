@@ -72,7 +72,7 @@ int upload(DBuf& b, const void* src, size_t bytes) {
 
 // Sweep kernel for the context's tiling and tile size.
 int prepare_sweeps(wr_ctx* c) {
-    const int tiling = c->tune.bf_tiling != 0 ? c->tune.bf_tiling : 2;
+    const int tiling = c->tune.bf_tiling != 0 ? c->tune.bf_tiling : (c->hp.tile_cap <= 256 ? 1 : 2);
     if (tiling == 1) return wr::bf_prepare_warp(c->hp.tile_cap, c->device, &c->bf_info);
     return wr::bf_prepare(c->hp.tile_cap, c->tune.bf_warps, c->device, &c->bf_info);
 }
@@ -390,8 +390,8 @@ int wr_create(const wr_config* cfg, wr_ctx** out) {
     ctx->device = c.device;
     ctx->cfg = c;
     ctx->cfg.tune_path = nullptr;
-    ctx->tune.run_target = 200;
-    ctx->tune.tile_cap = 256;
+    ctx->tune.run_target = 60;  // two segments of ~60 nodes (aisle faces) share a 128-slot tile
+    ctx->tune.tile_cap = 128;
     ctx->tune.enum_units = 4;
     ctx->tune.enum_max_units_per_launch = 0;
     ctx->tune.bf_warps = 0;

@@ -11,12 +11,13 @@
 // through a register, up to two other arcs from the staged tile, addressed
 // by byte offsets precomputed on the host (compact descriptors).
 //
-// Data movement is done by the copy engine of the SM: the tile's lines, its
-// halo lines and its descriptors arrive by bulk asynchronous copies
-// (cp.async.bulk, one 128-byte line per copy, issued 32 at a time by the
-// lanes) that complete on an mbarrier, and lines go back to global memory by
-// bulk stores.  The warp fetches its next tile's index and run metadata
-// while it relaxes the current one.
+// Staging: cp.async copies of 16 bytes, 8 lanes per 128-byte line (4 lines
+// per instruction), in two commit groups -- the descriptors, the halo and the
+// first segment, then the second segment -- so the forward pass starts on the
+// first segment while the second is in flight.  Write-back: every own line
+// of a tile that changed, 16-byte stores from 8 lanes per line.  The warp
+// fetches its next tile's index and run metadata while it relaxes the
+// current one.
 //
 // The loads of a block of BLK nodes are issued before the previous block's
 // carry chain runs, so a non-carry arc from a node of the previous block
@@ -31,65 +32,9 @@ template <int TILE>
 struct __align__(128) WarpTile {
     uint32_t rows[TILE][32];  // slot-major: rows[i][b] = source b of tile slot i (own nodes, then halo)
     uint4 desc[2 * TILE];     // compact descriptors of the run's nodes: forward, backward
-    unsigned long long bar;   // mbarrier of the tile's inbound copies
-    unsigned long long pad[15];
 };
 
 constexpr int BLK = 4;  // nodes per pipelined block
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// global -> shared, completes `bytes` on the mbarrier
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-// shared -> global, tracked by this thread's bulk groups
-__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_addr(src)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_global() {
-    asm volatile("fence.proxy.async.global;\n" ::: "memory");
-}
-
-// Bounded wait for the tile's copies; false (and WR_ETIMEOUT recorded) if the
-// limit ran out.  Every lane waits, so every lane sees the landed data.
-__device__ __forceinline__ bool wait_tile(unsigned long long* bar, uint32_t parity, const BfParams& p) {
-    for (unsigned long long spins = 0; !mbar_try_wait(bar, parity); ++spins) {
-        if (spins > p.w.max_spins) {
-            atomicCAS(p.w.err, 0, WR_ETIMEOUT);
-            return false;
-        }
-    }
-    return true;
-}
 
 // Run metadata of one work item (the same in every lane).
 struct TileMeta {
@@ -167,20 +112,39 @@ __device__ __forceinline__ uint32_t chain_blk(char* cb, int len, int b, const Bl
 // One pass over the run: whole blocks of BLK nodes in pass order, the loads
 // of block b + 1 issued before the chain of block b, then the partial block.
 template <int TILE, bool FWD>
-__device__ __forceinline__ uint32_t warp_pass(WarpTile<TILE>& t, int len, int lane) {
+__device__ __forceinline__ uint32_t warp_pass(WarpTile<TILE>& t, int len, int alen, int lane) {
     char* cb = reinterpret_cast<char*>(&t.rows[0][lane]);
     const int nf = len / BLK;
     uint32_t xprev = INF_U, chg = 0;
     BlkIn a, c;
-    if (nf > 0) load_blk<TILE, FWD, false>(t, cb, len, 0, a);
+    // forward: the second segment's lines are waited for before the first block that reaches them
+    bool second = !FWD || alen >= len;
+    auto need = [&](int b) {
+        if (!second && (b + 1) * BLK > alen) {
+            cp_async_wait_pending(0);
+            __syncwarp();
+            second = true;
+        }
+    };
+    if (nf > 0) {
+        need(0);
+        load_blk<TILE, FWD, false>(t, cb, len, 0, a);
+    }
 #pragma unroll 1
     for (int b = 0; b < nf; b += 2) {
-        if (b + 1 < nf) load_blk<TILE, FWD, false>(t, cb, len, b + 1, c);
+        if (b + 1 < nf) {
+            need(b + 1);
+            load_blk<TILE, FWD, false>(t, cb, len, b + 1, c);
+        }
         chg |= chain_blk<FWD, false>(cb, len, b, a, xprev);
-        if (b + 2 < nf) load_blk<TILE, FWD, false>(t, cb, len, b + 2, a);
+        if (b + 2 < nf) {
+            need(b + 2);
+            load_blk<TILE, FWD, false>(t, cb, len, b + 2, a);
+        }
         if (b + 1 < nf) chg |= chain_blk<FWD, false>(cb, len, b + 1, c, xprev);
     }
     if (nf * BLK < len) {
+        need(nf);
         load_blk<TILE, FWD, true>(t, cb, len, nf, a);
         chg |= chain_blk<FWD, true>(cb, len, nf, a, xprev);
     }
@@ -229,57 +193,56 @@ __device__ __noinline__ uint32_t warp_passes_generic(const BfParams& p, WarpTile
     return chg;
 }
 
-// One tile by one warp.  Returns 1 if a row dropped, 0 if not, -1 if a wait
-// ran out (error recorded).  parity is the tile mbarrier's phase bit.
+// One tile by one warp: stage, forward pass, backward pass, write back the
+// own lines.  Returns true (warp-uniform) if a row dropped.
 template <int TILE>
-__device__ __forceinline__ int warp_tile(const BfParams& p, const TileMeta& m, WarpTile<TILE>& t, int lane,
-                                         uint32_t& parity) {
+__device__ __forceinline__ bool warp_tile(const BfParams& p, const TileMeta& m, WarpTile<TILE>& t, int lane) {
     const int64_t ld = p.seg.ld;
     const int64_t lane_off = seg_col0(p.seg, m.g);
     uint32_t* rows = p.seg.rows;
     const bool compact = (m.flags & RUN_COMPACT) != 0;
-    const uint32_t bytes = static_cast<uint32_t>(m.len + m.hn) * 128u + (compact ? static_cast<uint32_t>(m.len) * 32u : 0u);
-    if (lane == 0) mbar_arrive_expect_tx(&t.bar, bytes);
-    __syncwarp();
-    // own lines, halo lines (one 128-byte copy per line, 32 per warp instruction), descriptors
-    for (int i = lane; i < m.len; i += 32)
-        bulk_load(&t.rows[i][0], rows + static_cast<int64_t>(run_node(m.rs, i)) * ld + lane_off, 128u, &t.bar);
-    for (int h = lane; h < m.hn; h += 32) {
+    const int sub = lane >> 3, part = (lane & 7) * 4;  // 8 lanes x 16 bytes per line, 4 lines per instruction
+    // group A: descriptors, halo lines, the first segment's lines
+    if (compact)
+        for (int e = lane; e < 2 * m.len; e += 32)
+            cp_async16(&t.desc[e], p.g.cdesc + 2 * static_cast<int64_t>(run_node(m.rs, e >> 1)) + (e & 1));
+    for (int h = sub; h < m.hn; h += 4) {
         const int node = __ldg(p.g.halo_nodes + m.h0 + h);
-        bulk_load(&t.rows[m.len + h][0], rows + static_cast<int64_t>(node) * ld + lane_off, 128u, &t.bar);
+        cp_async16(&t.rows[m.len + h][part], rows + static_cast<int64_t>(node) * ld + lane_off + part);
     }
-    if (compact && lane == 0)
-        bulk_load(&t.desc[0], p.g.cdesc + 2 * static_cast<int64_t>(m.rs.x), static_cast<uint32_t>(m.rs.y) * 32u, &t.bar);
-    if (compact && lane == 1 && m.rs.w > 0)
-        bulk_load(&t.desc[2 * m.rs.y], p.g.cdesc + 2 * static_cast<int64_t>(m.rs.z), static_cast<uint32_t>(m.rs.w) * 32u,
-                  &t.bar);
-    if (!wait_tile(&t.bar, parity, p)) {
-        // let the copies already issued land before the shared memory is abandoned
-        for (unsigned long long s = 0; !mbar_try_wait(&t.bar, parity) && s <= p.w.max_spins; ++s) {
-        }
-        return -1;
+    {
+        const uint32_t* gp = rows + static_cast<int64_t>(m.rs.x + sub) * ld + lane_off + part;
+        for (int i = sub; i < m.rs.y; i += 4, gp += 4 * ld) cp_async16(&t.rows[i][part], gp);
     }
-    parity ^= 1u;
+    cp_async_commit();
+    // group B: the second segment's lines
+    {
+        const uint32_t* gp = rows + static_cast<int64_t>(m.rs.z + sub) * ld + lane_off + part;
+        for (int i = sub; i < m.rs.w; i += 4, gp += 4 * ld) cp_async16(&t.rows[m.rs.y + i][part], gp);
+    }
+    cp_async_commit();
 
     uint32_t chg;
     if (compact) {
-        chg = warp_pass<TILE, true>(t, m.len, lane);
-        chg |= warp_pass<TILE, false>(t, m.len, lane);
+        cp_async_wait_pending(1);  // group A landed: the forward pass starts on the first segment
+        __syncwarp();
+        chg = warp_pass<TILE, true>(t, m.len, m.rs.y, lane);
+        chg |= warp_pass<TILE, false>(t, m.len, m.rs.y, lane);
     } else {
+        cp_async_wait_pending(0);
+        __syncwarp();
         chg = warp_passes_generic<TILE>(p, t, m.rs, m.len, lane, lane_off);
     }
     const bool changed = __any_sync(FULL_MASK, chg != 0u);
     if (changed) {
         // every own line goes back (a visited line is read and written once per sweep)
-        fence_proxy_async_smem();  // this lane's shared stores visible to the copy engine
         __syncwarp();
-        for (int i = lane; i < m.len; i += 32)
-            bulk_store(rows + static_cast<int64_t>(run_node(m.rs, i)) * ld + lane_off, &t.rows[i][0], 128u);
-        bulk_commit();
-        bulk_wait_read_all();  // shared lines read out before the next tile lands on them
+        for (int i = sub; i < m.len; i += 4)
+            __stcg(reinterpret_cast<uint4*>(rows + static_cast<int64_t>(run_node(m.rs, i)) * ld + lane_off + part),
+                   *reinterpret_cast<const uint4*>(&t.rows[i][part]));
     }
-    __syncwarp();
-    return changed ? 1 : 0;
+    __syncwarp();  // every lane's reads of the tile done before the next staging overwrites it
+    return changed;
 }
 
 template <int TILE, int NW>
@@ -293,10 +256,6 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
     if (G == 0) return;  // same decision in every block
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthreads = gridDim.x * blockDim.x;
-    if (lane == 0) mbar_init(&t.bar, 1);
-    fence_proxy_async_smem();
-    __syncwarp();
-    uint32_t parity = 0;
 
     // seeds: writing d[s][s] = 0 is the change of "sweep 0": the tile holding
     // each source gets stamp 1, and sweep 1 visits it and the tiles it feeds
@@ -311,7 +270,6 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
     unsigned long long tiles = 0, nodes = 0, bytes = 0;
     int cur = 0;
     int sweep = 1;
-    bool failed = false;
     for (;; ++sweep) {
         const int cnt = ld_volatile(p.w.counts + cur);
         if (gtid == 0 && sweep <= p.w.trace_cap) {
@@ -341,18 +299,14 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
         it1 = __shfl_sync(FULL_MASK, it1, 0);
         TileMeta m{};
         if (it < cnt) m = load_meta(p, list, it, G);
-        while (it < cnt && !failed) {
+        while (it < cnt) {
             int it2 = 0;
             if (lane == 0) it2 = atomicAdd(p.w.counts + 2 + cur, 1);
             TileMeta m1{};
             if (it1 < cnt) m1 = load_meta(p, list, it1, G);
-            const int res = warp_tile<TILE>(p, m, t, lane, parity);
-            if (res < 0) {
-                failed = true;
-                break;
-            }
+            const bool ch = warp_tile<TILE>(p, m, t, lane);
             if (lane == 0) {
-                if (res) p.w.stamp[m.item] = sweep + 1;
+                if (ch) p.w.stamp[m.item] = sweep + 1;
                 ++tiles;
                 nodes += static_cast<unsigned long long>(m.len);
                 bytes += static_cast<unsigned long long>(__ldg(p.g.run_meta_bytes + m.r)) +
@@ -362,14 +316,11 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
             m = m1;
             it1 = __shfl_sync(FULL_MASK, it2, 0);
         }
-        bulk_wait_all();  // this lane's line stores complete before the sweep barrier
-        fence_proxy_async_global();
         if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) break;
         build_list(p, G, sweep + 1, true, cur ? p.w.list0 : p.w.list1, p.w.counts + (cur ^ 1));
         if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) break;
         cur ^= 1;
     }
-    bulk_wait_all();
     if (lane == 0 && tiles) {
         atomicAdd(p.w.stats + 1, tiles);
         atomicAdd(p.w.stats + 2, nodes);
