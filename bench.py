@@ -131,6 +131,28 @@ def dist_setup(args):
     return world, rank, local
 
 
+def sweep_kernel_name(tuning):
+    """The Bellman-Ford sweep kernel a tuning selects (warp tiles or CTA tiles)."""
+    warp = tuning["bf_tiling"] == 1 or (tuning["bf_tiling"] == 0 and tuning["tile_cap"] <= 256)
+    return "bf_warp_kernel" if warp else "bf_sweeps_kernel"
+
+
+def cpu_oracle_rows_rate(g, src, budget_s=15.0, n_threads=None):
+    """The oracle's Dijkstra rows on the host's cores for a bounded prefix of the
+    sources; returns (E x sources / s, cores, sample)."""
+    import oracle
+    n_threads = n_threads or os.cpu_count() or 1
+    m = n_threads
+    while True:
+        t0 = time.perf_counter()
+        oracle.sssp_rows(g, src[:m], "dijkstra", n_threads)
+        t = time.perf_counter() - t0
+        if t > budget_s / 3 or m >= len(src):
+            break
+        m = min(len(src), m * max(2, int(budget_s / 3 / max(t, 1e-3))))
+    return g.E * m / t / 1e9, n_threads, f"Dijkstra rows of the first {m} sources ({t:.1f} s on {n_threads} threads)"
+
+
 def replica_value(units_per_rank, ms, world):
     """Whole-job throughput of `world` replicas that each processed units_per_rank
     units, timed by the slowest rank (ms = max over ranks)."""
@@ -250,16 +272,34 @@ def run_scale(args):
                                f"rows of {n} distinct slot sources consumed as a {n}x{n} submatrix + checksums",
                    "budget_gib": args.budget_gib, "segments": st["n_segments"], "tuning": r.tuning(),
                    "l2": "rows (2 GiB per segment) exceed L2; 512 MiB flush between steps"},
-        "roofline": {"kernel": "bf_sweeps_kernel", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"],
-                     "bytes_alg_per_call": st["bytes_alg"], "ms_bf_per_call": bf_ms, "sweeps": st["sweeps"],
-                     "node_visits": st["node_visits"]},
+        "roofline": {"kernel": sweep_kernel_name(r.tuning()), "bound": "hbm", "achieved": achieved,
+                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "peak_source": pk["source"], "bytes_alg_per_call": st["bytes_alg"], "ms_bf_per_call": bf_ms,
+                     "sweeps": st["sweeps"], "node_visits": st["node_visits"]},
         "phases_ms": {k[3:]: statistics.median(s[k] for s in stats_list) for k in
                       ("ms_init", "ms_bf", "ms_total")},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats_list)),
         "clocks": clk.summary(),
         "paper_convention_mteps": paper_mteps(g.V, g.E, n, ms / 1e3),
     }
+    # end to end through the C ABI with host buffers: sources in, submatrix and checksums out
+    h_sub = np.empty((n, n), np.int32)
+    h_check = np.empty(n, np.uint64)
+    e2e = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        wroute.wr_submatrix(r.ctx, src, src, h_sub, h_check)
+        if i >= args.warmup:
+            e2e.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(sum(e2e) / len(e2e), world, dev)
+    line["e2e"] = {"value": g.E * n * world / e2e_s / 1e9, "unit": "Gedges/s", "h2d_bytes_per_step": 8 * n,
+                   "d2h_bytes_per_step": 4 * n * n + 8 * n,
+                   "matches_device_run": bool((h_sub == sub.cpu().numpy()).all())}
+    if rank == 0 and not args.no_cpu:
+        v, cores, sample = cpu_oracle_rows_rate(g, src, budget_s=args.ref_budget)
+        line["cpu_baseline"] = {"value": v, "unit": "Gedges/s", "cores": cores, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line))
     r.close()
@@ -585,8 +625,8 @@ def run_ours(args):
         "dtype": "int32", "data": "synthetic",
         "config": {"workload": desc, "orders_per_step": n, "sources": st["n_sources"], "l2": "flushed (512 MiB write) between steps",
                    "parallelism": f"replicas x{world} (orders are independent)", "tuning": r.tuning()},
-        "roofline": {"kernel": "bf_sweeps_kernel", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+        "roofline": {"kernel": sweep_kernel_name(r.tuning()), "bound": "hbm", "achieved": achieved,
+                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
                      "peak_source": pk["source"], "bytes_alg_per_launch": bytes_alg, "ms_per_launch": bf_ms,
                      "sweeps": st["sweeps"]},
         "roofline_enum": {"kernel": "enum_kernel", "bound": "alu", "sequences": seqs, "ms": enum_ms,
