@@ -131,6 +131,27 @@ def dist_setup(args):
     return world, rank, local
 
 
+# DRAM traffic per launch of the default sweep kernel (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum), from the captures summarised in profiles/bf_warp_kernel_*.txt.
+# A figure holds only while the sources that shape the kernel's traffic are the ones
+# it was taken on (hash below) and the tuning is the default one; otherwise null.
+TRAFFIC_SOURCES = ["paper_2504_20655_gb300/csrc/wr_bf_warp.cu", "paper_2504_20655_gb300/csrc/wr_bf_common.cuh",
+                   "paper_2504_20655_gb300/csrc/wr_graph.cpp"]
+TRAFFIC_HASH = "f85192ecc586583f"
+TRAFFIC = {"medium": 706258688 + 521190400, "scale": 22034982000 + 17681132000}
+
+
+def traffic_for(workload, tuned):
+    import hashlib
+    h = hashlib.sha1()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if tuned or h.hexdigest()[:16] != TRAFFIC_HASH:
+        return None
+    return TRAFFIC.get(workload)
+
+
 def sweep_kernel_name(tuning):
     """The Bellman-Ford sweep kernel a tuning selects (warp tiles or CTA tiles)."""
     warp = tuning["bf_tiling"] == 1 or (tuning["bf_tiling"] == 0 and tuning["tile_cap"] <= 256)
@@ -190,7 +211,15 @@ def cpu_oracle_rate(g, o, budget_s=15.0, n_threads=None):
         if t > budget_s / 3 or n >= o.n:
             break
         n = min(o.n, n * max(2, int(budget_s / 3 / max(t, 1e-3))))
-    return n / t, n_threads, f"first {n} orders of the batch ({t:.1f} s on {n_threads} threads)"
+    reps = 1
+    if n >= o.n and t < budget_s / 3:  # the whole batch is quick: repeat it for a steadier rate
+        reps = max(1, int(budget_s / 3 / max(t, 1e-3)))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            oracle.route_orders(g, sub, "rounds", "brute", n_threads)
+        t = time.perf_counter() - t0
+    what = f"first {n} orders of the batch" if reps == 1 else f"the whole batch of {n} orders x {reps}"
+    return reps * n / t, n_threads, f"{what} ({t:.1f} s on {n_threads} threads)"
 
 
 def run_reference(args):
@@ -273,8 +302,10 @@ def run_scale(args):
                    "budget_gib": args.budget_gib, "segments": st["n_segments"], "tuning": r.tuning(),
                    "l2": "rows (2 GiB per segment) exceed L2; 512 MiB flush between steps"},
         "roofline": {"kernel": sweep_kernel_name(r.tuning()), "bound": "hbm", "achieved": achieved,
-                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                     "peak_source": pk["source"], "bytes_alg_per_call": st["bytes_alg"], "ms_bf_per_call": bf_ms,
+                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                     "traffic": traffic_for("scale", bool(args.tune)) if n == 4096 else None,
+                     "peak_source": pk["source"], "bytes_alg_per_launch": st["bytes_alg"] / st["n_segments"],
+                     "ms_per_launch": bf_ms / st["n_segments"], "launches": st["n_segments"],
                      "sweeps": st["sweeps"], "node_visits": st["node_visits"]},
         "phases_ms": {k[3:]: statistics.median(s[k] for s in stats_list) for k in
                       ("ms_init", "ms_bf", "ms_total")},
@@ -616,9 +647,7 @@ def run_ours(args):
     seqs = st["sequences"]
     clocks = clk.summary()
     int_peak = N_SMS * INT_LANES_PER_SM * pk["sm_max_mhz"] * 1e6 / 1e12  # T lane-ops/s
-    traffic = None
-    if args.traffic:
-        traffic = float(args.traffic)
+    traffic = float(args.traffic) if args.traffic else traffic_for(args.workload, bool(args.tune))
     line = {
         "metric": "exact-routed orders/s", "value": value, "unit": "orders/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
