@@ -198,7 +198,7 @@ int run_tours(wr_ctx* c, int32_t n, const int32_t* k_dev, const wr::TourBufs& tb
     {
         PhaseTimer t(c, s, 4);
         CK(wr::tour_launch_units(n, k_dev, tb, s, &c->launches));
-        const int upt = c->tune.enum_units > 0 ? c->tune.enum_units : 4;
+        const int upt = c->tune.enum_units > 0 ? c->tune.enum_units : 2;
         if (c->tune.enum_max_units_per_launch > 0 && !c->capturing) {
             long long total = 0;
             CK(cudaMemcpyAsync(&total, tb.unit_off + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -392,7 +392,7 @@ int wr_create(const wr_config* cfg, wr_ctx** out) {
     ctx->cfg.tune_path = nullptr;
     ctx->tune.run_target = 60;  // two segments of ~60 nodes (aisle faces) share a 128-slot tile
     ctx->tune.tile_cap = 128;
-    ctx->tune.enum_units = 4;
+    ctx->tune.enum_units = 2;
     ctx->tune.enum_max_units_per_launch = 0;
     ctx->tune.bf_warps = 0;
     ctx->tune.bf_tiling = 0;
@@ -877,7 +877,7 @@ int wr_autotune(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* picks,
             best = t;
         }
     }
-    const int units[] = {2, 4, 8, 16};
+    const int units[] = {1, 2, 4, 8};
     if (rc == WR_OK) rc = wr_set_tuning(c, &best);
     for (int u : units) {
         if (rc != WR_OK) break;

@@ -16,7 +16,8 @@ constexpr uint32_t GLOBAL_REF = 0x80000000u;  // arc source not staged: low 31 b
 constexpr uint32_t TOUR_CAP = 1u << 27;       // unreachable legs are clamped to this in tour sums
 constexpr int DSTRIDE = 13;                   // D blocks are 13 x 13
 constexpr int DBLOCK = DSTRIDE * DSTRIDE;
-constexpr int TAIL = 5;                       // sequences of one unit: orderings of the last 5 picks
+constexpr int TAIL = 5;                       // tail walked by one compile-time unrolled walk
+constexpr int UNIT_TAIL = 6;                  // a unit: a prefix and the 720 orderings of the last 6 picks (k >= 6)
 constexpr int ORDER_FLAG_RANGE = 1;
 constexpr int32_t RUN_SIMPLE = 1;             // run's extra arcs fit the tile buffer, halo fully staged
 constexpr uint32_t IX_EXTRA = 1u << 24;       // node has arcs beyond the inline ones

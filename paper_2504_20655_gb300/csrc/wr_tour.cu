@@ -234,9 +234,9 @@ __device__ __forceinline__ int order_k(const TourBufs& t, const int32_t* k_given
 }
 
 __device__ __forceinline__ long long units_of(int k) {
-    // k! / min(k, TAIL)!
+    // k! / 6! for k >= 6 (a unit is a prefix and the 720 orderings of the last six picks), else 1
     long long u = 1;
-    for (int i = TAIL + 1; i <= k; ++i) u *= i;
+    for (int i = UNIT_TAIL + 1; i <= k; ++i) u *= i;
     return u;
 }
 
@@ -445,98 +445,179 @@ __device__ __forceinline__ int nth_bit(unsigned m, int n) {
     return __ffs(m) - 1;
 }
 
+// One 720-sequence unit (k >= 6): the prefix of cost P ends at x; s[0..5]
+// are the remaining picks in increasing order.  Tables of the six: legs
+// between them (d6), back to the depot folded into two-leg suffixes
+// (tail2[b][c] = d6[b][c] + D[s_c][0]) and from x (xl).  The j-th block of
+// 120 sequences starts with s_j and walks the other five as a 5-tail whose
+// tables are compile-time views of the six's, so no table is loaded twice.
+template <int J>
+__device__ __forceinline__ void tail6_block(const uint32_t (&d6)[6][6], const uint32_t (&tail2)[6][6], uint32_t acc,
+                                            unsigned rank0, uint32_t& best_c, unsigned& best_r) {
+    Tab<5> T;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int ri = i < J ? i : i + 1;
+        T.x[i] = d6[J][ri];
+        T.h[i] = 0u;  // the 5-tail never ends above a two-leg suffix
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const int rq = q < J ? q : q + 1;
+            if (i != q) T.d[i][q] = d6[ri][rq];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 5; ++a)
+#pragma unroll
+        for (int b = 0; b < 5; ++b)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                if (a == b || a == c || b == c) continue;
+                const int ra = a < J ? a : a + 1, rb = b < J ? b : b + 1, rc = c < J ? c : c + 1;
+                T.t3[a][b][c] = d6[ra][rb] + tail2[rb][rc];
+            }
+    uint32_t mins[5];
+    int idx = -1;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) mins[i] = 0xFFFFFFFFu;
+    TopLevel<5, 0>::run(acc, T, mins, idx);
+    uint32_t mn = mins[0];
+#pragma unroll
+    for (int i = 1; i < 5; ++i) mn = min(mn, mins[i]);
+    if (mn < best_c || (mn == best_c && rank0 < best_r)) {
+        Walk<5, 31u, -1, 0, true>::run(acc, T, mn, idx);
+        const unsigned r = rank0 + static_cast<unsigned>(idx);
+        if (mn < best_c || r < best_r) {
+            best_c = mn;
+            best_r = r;
+        }
+    }
+}
+
+template <int J>
+struct Tail6 {
+    static __device__ __forceinline__ void run(const uint32_t (&d6)[6][6], const uint32_t (&tail2)[6][6],
+                                               const uint32_t (&xl)[6], uint32_t P, unsigned rank0, uint32_t& best_c,
+                                               unsigned& best_r) {
+        if constexpr (J < 6) {
+            tail6_block<J>(d6, tail2, P + xl[J], rank0 + 120u * J, best_c, best_r);
+            Tail6<J + 1>::run(d6, tail2, xl, P, rank0, best_c, best_r);
+        }
+    }
+};
+
 // Enumerate the units [ulo, uhi) of one order (k picks, D block Dm); fold
 // the best (cost, rank) into *out.
 __device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, long long ulo, long long uhi,
                                  unsigned long long* out, long long& seqs) {
-    const int L = k < TAIL ? k : TAIL;
-    const int p = k - L;  // prefix length
-    const int lfact = L == 1 ? 1 : L == 2 ? 2 : L == 3 ? 6 : L == 4 ? 24 : 120;
-    // decode the first unit: digits c_i in radix (k - i), i < p
-    unsigned digits = 0;  // 4 bits per position
-    {
-        long long u = ulo;
-        for (int i = p - 1; i >= 0; --i) {
-            const int r = k - i;
-            const int c = static_cast<int>(u % r);
-            u /= r;
-            digits |= static_cast<unsigned>(c) << (4 * i);
-        }
-    }
-    unsigned elems = 0;  // 4 bits per position: pick index 1..k
-    unsigned all = ((1u << k) - 1u) << 1;
-    unsigned avail_last = all;  // available set before the last prefix position
-    uint32_t S = 0;             // cost through position p-2
-    int pos_dirty = 0;          // first prefix position to recompute
     // start from the order's current best (a stale read is only larger, so safe)
     const unsigned long long g0 = __ldcg(out);
     uint32_t best_c = static_cast<uint32_t>(g0 >> 32);
     unsigned best_r = static_cast<unsigned>(g0 & 0xFFFFFFFFull);
-    for (long long u = ulo; u < uhi; ++u) {
-        // (re)build prefix positions >= pos_dirty
-        if (pos_dirty < p) {
-            unsigned av = all;
-            uint32_t cost = 0;
-            int prev = 0;
-            for (int i = 0; i < p; ++i) {
-                int e;
-                if (i < pos_dirty) {
-                    e = (elems >> (4 * i)) & 15;
-                } else {
-                    e = nth_bit(av, (digits >> (4 * i)) & 15);
-                    elems = (elems & ~(15u << (4 * i))) | (static_cast<unsigned>(e) << (4 * i));
-                }
-                if (i == p - 1) {
-                    avail_last = av;
-                    S = cost;
-                }
-                cost += __ldg(Dm + prev * DSTRIDE + e);
-                av &= ~(1u << e);
-                prev = e;
-            }
-        }
-        int x = 0;
-        uint32_t P = 0;
-        unsigned tailset = all;
-        if (p > 0) {
-            x = (elems >> (4 * (p - 1))) & 15;
-            const int xp = p >= 2 ? ((elems >> (4 * (p - 2))) & 15) : 0;
-            P = S + __ldg(Dm + xp * DSTRIDE + x);
-            tailset = avail_last & ~(1u << x);
-        }
+    if (k < UNIT_TAIL) {
+        // one unit: the k! orderings of all picks after the depot
         int t[TAIL];
 #pragma unroll
-        for (int i = 0; i < TAIL; ++i) {
-            t[i] = 0;
-            if (i < L) {
-                t[i] = __ffs(tailset) - 1;
+        for (int i = 0; i < TAIL; ++i) t[i] = i < k ? i + 1 : 0;
+        unit_eval_dispatch(k, Dm, 0u, 0, t, 0u, best_c, best_r);
+        seqs += k == 1 ? 1 : k == 2 ? 2 : k == 3 ? 6 : k == 4 ? 24 : 120;
+    } else {
+        const int p = k - UNIT_TAIL;  // prefix length
+        // decode the first unit: digits c_i in radix (k - i), i < p
+        unsigned digits = 0;  // 4 bits per position
+        {
+            long long u = ulo;
+            for (int i = p - 1; i >= 0; --i) {
+                const int r = k - i;
+                const int c = static_cast<int>(u % r);
+                u /= r;
+                digits |= static_cast<unsigned>(c) << (4 * i);
+            }
+        }
+        unsigned elems = 0;  // 4 bits per position: pick index 1..k
+        const unsigned all = ((1u << k) - 1u) << 1;
+        unsigned avail_last = all;  // available set before the last prefix position
+        uint32_t S = 0;             // cost through position p-2
+        int pos_dirty = 0;          // first prefix position to recompute
+        for (long long u = ulo; u < uhi; ++u) {
+            // (re)build prefix positions >= pos_dirty
+            if (pos_dirty < p) {
+                unsigned av = all;
+                uint32_t cost = 0;
+                int prev = 0;
+                for (int i = 0; i < p; ++i) {
+                    int e;
+                    if (i < pos_dirty) {
+                        e = (elems >> (4 * i)) & 15;
+                    } else {
+                        e = nth_bit(av, (digits >> (4 * i)) & 15);
+                        elems = (elems & ~(15u << (4 * i))) | (static_cast<unsigned>(e) << (4 * i));
+                    }
+                    if (i == p - 1) {
+                        avail_last = av;
+                        S = cost;
+                    }
+                    cost += __ldg(Dm + prev * DSTRIDE + e);
+                    av &= ~(1u << e);
+                    prev = e;
+                }
+            }
+            int x = 0;
+            uint32_t P = 0;
+            unsigned tailset = all;
+            if (p > 0) {
+                x = (elems >> (4 * (p - 1))) & 15;
+                const int xp = p >= 2 ? ((elems >> (4 * (p - 2))) & 15) : 0;
+                P = S + __ldg(Dm + xp * DSTRIDE + x);
+                tailset = avail_last & ~(1u << x);
+            }
+            // the six remaining picks in increasing order and their tables
+            int sx[UNIT_TAIL];
+#pragma unroll
+            for (int i = 0; i < UNIT_TAIL; ++i) {
+                sx[i] = __ffs(tailset) - 1;
                 tailset &= tailset - 1;
             }
-        }
-        unit_eval_dispatch(L, Dm, P, x, t, static_cast<unsigned>(u) * static_cast<unsigned>(lfact), best_c, best_r);
-        // advance the mixed-radix counter of the prefix
-        if (p > 0) {
-            int i = p - 1;
-            for (; i >= 0; --i) {
-                const unsigned c = ((digits >> (4 * i)) & 15) + 1;
-                if (c < static_cast<unsigned>(k - i)) {
-                    digits = (digits & ~(15u << (4 * i))) | (c << (4 * i));
-                    break;
+            uint32_t d6[6][6], tail2[6][6], xl[6], h6[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const uint32_t* row = Dm + sx[i] * DSTRIDE;
+                xl[i] = __ldg(Dm + x * DSTRIDE + sx[i]);
+                h6[i] = __ldg(row);
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+                    if (q != i) d6[i][q] = __ldg(row + sx[q]);
+            }
+#pragma unroll
+            for (int b = 0; b < 6; ++b)
+#pragma unroll
+                for (int c = 0; c < 6; ++c)
+                    if (b != c) tail2[b][c] = d6[b][c] + h6[c];
+            Tail6<0>::run(d6, tail2, xl, P, static_cast<unsigned>(u) * 720u, best_c, best_r);
+            // advance the mixed-radix counter of the prefix
+            if (p > 0) {
+                int i = p - 1;
+                for (; i >= 0; --i) {
+                    const unsigned c = ((digits >> (4 * i)) & 15) + 1;
+                    if (c < static_cast<unsigned>(k - i)) {
+                        digits = (digits & ~(15u << (4 * i))) | (c << (4 * i));
+                        break;
+                    }
+                    digits &= ~(15u << (4 * i));
                 }
-                digits &= ~(15u << (4 * i));
-            }
-            if (i == p - 1) {
-                // only the last prefix element moves: next available pick above it
-                const unsigned above = avail_last & ~((2u << x) - 1u);
-                const int e = __ffs(above) - 1;
-                elems = (elems & ~(15u << (4 * (p - 1)))) | (static_cast<unsigned>(e) << (4 * (p - 1)));
-                pos_dirty = p;
-            } else {
-                pos_dirty = i < 0 ? 0 : i;
+                if (i == p - 1) {
+                    // only the last prefix element moves: next available pick above it
+                    const unsigned above = avail_last & ~((2u << x) - 1u);
+                    const int e = __ffs(above) - 1;
+                    elems = (elems & ~(15u << (4 * (p - 1)))) | (static_cast<unsigned>(e) << (4 * (p - 1)));
+                    pos_dirty = p;
+                } else {
+                    pos_dirty = i < 0 ? 0 : i;
+                }
             }
         }
+        seqs += (uhi - ulo) * 720;
     }
-    seqs += (uhi - ulo) * lfact;
     const unsigned long long packed = (static_cast<unsigned long long>(best_c) << 32) | best_r;
     if (packed < g0) atomicMin(out, packed);
 }
