@@ -447,19 +447,19 @@ __device__ __forceinline__ int nth_bit(unsigned m, int n) {
 
 // One 720-sequence unit (k >= 6): the prefix of cost P ends at x; s[0..5]
 // are the remaining picks in increasing order.  Tables of the six: legs
-// between them (d6), back to the depot folded into two-leg suffixes
-// (tail2[b][c] = d6[b][c] + D[s_c][0]) and from x (xl).  The j-th block of
-// 120 sequences starts with s_j and walks the other five as a 5-tail whose
-// tables are compile-time views of the six's, so no table is loaded twice.
+// between them (d6), from x (xl), and every three-leg suffix ending at the
+// depot (t3f[a][b][c] = D[s_a][s_b] + D[s_b][s_c] + D[s_c][0]), built once per
+// unit.  The j-th block of 120 sequences starts with s_j and walks the other
+// five as a 5-tail whose tables are compile-time views of the six's.
 template <int J>
-__device__ __forceinline__ void tail6_block(const uint32_t (&d6)[6][6], const uint32_t (&tail2)[6][6], uint32_t acc,
+__device__ __forceinline__ void tail6_block(const uint32_t (&d6)[6][6], const uint32_t (&t3f)[6][6][6], uint32_t acc,
                                             unsigned rank0, uint32_t& best_c, unsigned& best_r) {
     Tab<5> T;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         const int ri = i < J ? i : i + 1;
         T.x[i] = d6[J][ri];
-        T.h[i] = 0u;  // the 5-tail never ends above a two-leg suffix
+        T.h[i] = 0u;  // the 5-tail never ends above a three-leg suffix
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             const int rq = q < J ? q : q + 1;
@@ -473,8 +473,7 @@ __device__ __forceinline__ void tail6_block(const uint32_t (&d6)[6][6], const ui
 #pragma unroll
             for (int c = 0; c < 5; ++c) {
                 if (a == b || a == c || b == c) continue;
-                const int ra = a < J ? a : a + 1, rb = b < J ? b : b + 1, rc = c < J ? c : c + 1;
-                T.t3[a][b][c] = d6[ra][rb] + tail2[rb][rc];
+                T.t3[a][b][c] = t3f[a < J ? a : a + 1][b < J ? b : b + 1][c < J ? c : c + 1];
             }
     uint32_t mins[5];
     int idx = -1;
@@ -496,12 +495,12 @@ __device__ __forceinline__ void tail6_block(const uint32_t (&d6)[6][6], const ui
 
 template <int J>
 struct Tail6 {
-    static __device__ __forceinline__ void run(const uint32_t (&d6)[6][6], const uint32_t (&tail2)[6][6],
+    static __device__ __forceinline__ void run(const uint32_t (&d6)[6][6], const uint32_t (&t3f)[6][6][6],
                                                const uint32_t (&xl)[6], uint32_t P, unsigned rank0, uint32_t& best_c,
                                                unsigned& best_r) {
         if constexpr (J < 6) {
-            tail6_block<J>(d6, tail2, P + xl[J], rank0 + 120u * J, best_c, best_r);
-            Tail6<J + 1>::run(d6, tail2, xl, P, rank0, best_c, best_r);
+            tail6_block<J>(d6, t3f, P + xl[J], rank0 + 120u * J, best_c, best_r);
+            Tail6<J + 1>::run(d6, t3f, xl, P, rank0, best_c, best_r);
         }
     }
 };
@@ -578,7 +577,7 @@ __device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, long lo
                 sx[i] = __ffs(tailset) - 1;
                 tailset &= tailset - 1;
             }
-            uint32_t d6[6][6], tail2[6][6], xl[6], h6[6];
+            uint32_t d6[6][6], xl[6], h6[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
                 const uint32_t* row = Dm + sx[i] * DSTRIDE;
@@ -588,12 +587,19 @@ __device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, long lo
                 for (int q = 0; q < 6; ++q)
                     if (q != i) d6[i][q] = __ldg(row + sx[q]);
             }
+            // three-leg suffixes over the six: t3f[a][b][c] = D[a][b] + D[b][c] + D[c][depot]
+            uint32_t t3f[6][6][6];
 #pragma unroll
             for (int b = 0; b < 6; ++b)
 #pragma unroll
-                for (int c = 0; c < 6; ++c)
-                    if (b != c) tail2[b][c] = d6[b][c] + h6[c];
-            Tail6<0>::run(d6, tail2, xl, P, static_cast<unsigned>(u) * 720u, best_c, best_r);
+                for (int c = 0; c < 6; ++c) {
+                    if (b == c) continue;
+                    const uint32_t tail2 = d6[b][c] + h6[c];
+#pragma unroll
+                    for (int a = 0; a < 6; ++a)
+                        if (a != b && a != c) t3f[a][b][c] = d6[a][b] + tail2;
+                }
+            Tail6<0>::run(d6, t3f, xl, P, static_cast<unsigned>(u) * 720u, best_c, best_r);
             // advance the mixed-radix counter of the prefix
             if (p > 0) {
                 int i = p - 1;
