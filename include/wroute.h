@@ -63,7 +63,9 @@ extern "C" {
 #define WR_HOST   0
 #define WR_DEVICE 1
 
-#define WR_MAX_K   12          /* 12! = 479001600 ranks fit int32 */
+#define WR_MAX_K   12          /* exhaustive enumeration: 12! = 479001600 ranks fit int32 */
+#define WR_MAX_K_EXACT 20      /* with max_k above WR_MAX_K, orders of 13..max_k picks are solved exactly by
+                                  Held-Karp (same optimum, same tie rule), wr_route_orders only */
 #define WR_INF     2147483647  /* unreachable distance */
 #define WR_LEG_MAX 10324440    /* 13 legs of at most this stay below 2^27: exact int32 sums */
 
@@ -72,7 +74,7 @@ typedef struct wr_ctx wr_ctx;  /* opaque; owns all device memory it allocates */
 typedef struct {
     int device;                   /* CUDA device ordinal */
     uint64_t mem_budget_bytes;    /* cap on the distance-row buffer of one source segment */
-    int max_k;                    /* largest order size accepted, <= WR_MAX_K */
+    int max_k;                    /* largest order size accepted, <= WR_MAX_K_EXACT (default WR_MAX_K) */
     uint64_t barrier_max_spins;   /* iteration limit of every device-side wait (0 = default) */
     const char* tune_path;        /* tuning table file: applied at creation when it exists, written by
                                      wr_autotune (NULL = built-in defaults, nothing written) */
@@ -157,7 +159,8 @@ int wr_submatrix(wr_ctx* ctx, int32_t n_src, const int32_t* src, int32_t n_dst, 
 
 /* a5-a7 on given matrices -- D is n_orders blocks of 13 x 13 int32 (row-major,
  * the top-left (k+1) x (k+1) used, index 0 = depot, WR_INF = unreachable);
- * k[i] picks per order.  Writes cost[i], status[i] and perm[i * WR_MAX_K + j]. */
+ * k[i] picks per order (k[i] <= WR_MAX_K: larger orders are WR_ORDER_BAD here).  Writes cost[i],
+ * status[i] and perm[i * WR_MAX_K + j]. */
 int wr_tour_eval(wr_ctx* ctx, int32_t n_orders, const int32_t* k, const int32_t* D, int32_t* cost,
                  int32_t* perm, int32_t* status, int ptr_kind, void* cuda_stream);
 
@@ -234,7 +237,8 @@ int wr_autotune(wr_ctx* ctx, int32_t n_orders, const int64_t* offs, const int32_
  * gathered from the cache, and the enumeration runs on the slot's own stream, so
  * batches overlap on the GPU.  Admission stops growing a batch when its new sources
  * would not fit the cache.  Every result equals that of wr_route_orders on the
- * order alone.  The server keeps a private copy of the context's graph and tuning. */
+ * order alone.  The server keeps a private copy of the context's graph and tuning.
+ * It routes orders of up to WR_MAX_K picks (larger ones come back WR_ORDER_BAD). */
 typedef struct {
     int32_t max_batch;        /* orders per batch, >= 1 */
     int64_t max_batch_picks;  /* picks per batch, >= WR_MAX_K; also the largest order accepted */

@@ -18,6 +18,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 
 INF = 2**31 - 1
 MAX_K = 12
+MAX_K_HK = 20
 LEG_MAX = 10324440
 OK, UNREACHABLE, BADORDER, RANGE = 0, 1, 2, 3
 SSSP = {"rounds": 0, "fifo": 1, "dijkstra": 2}
@@ -148,7 +149,10 @@ def tour(D, kind: str = "brute"):
     return int(st), int(cost[0]), perm[:k].copy()
 
 
-def route_orders(g, orders, sssp: str = "dijkstra", tour_kind: str = "brute", n_threads: int = 1):
+def route_orders(g, orders, sssp: str = "dijkstra", tour_kind: str = "brute", n_threads: int = 1, max_k=None):
+    """(cost, perm, status) per order.  Orders above max_k (default: the solver's own
+    limit, 12 for brute force and 20 for Held-Karp) are OR_BADORDER, as in a library
+    context created with that max_k."""
     rp, c, w = _csr(g)
     offs = np.ascontiguousarray(orders.offs, dtype=np.int64)
     picks = np.ascontiguousarray(orders.picks, dtype=np.int32)
@@ -159,6 +163,10 @@ def route_orders(g, orders, sssp: str = "dijkstra", tour_kind: str = "brute", n_
     _check(lib().or_route_orders(g.V, _p(rp), _p(c), _p(w), int(g.depot), n, _p(offs), _p(picks),
                                  SSSP[sssp], TOUR[tour_kind], int(n_threads), _p(cost), _p(perm),
                                  _p(status)), "route_orders")
+    if max_k is not None:
+        for o in np.nonzero(np.diff(offs) > max_k)[0]:
+            cost[o], status[o] = INF, BADORDER
+            perm[offs[o]:offs[o + 1]] = np.arange(offs[o + 1] - offs[o])
     return cost, perm[:int(offs[-1])], status
 
 

@@ -269,7 +269,7 @@ int or_tour_brute(int32_t k, const int32_t* D, int32_t* cost, int32_t* perm) {
  * the optimum at every step, which gives the lexicographically first
  * optimal sequence. */
 int or_tour_held_karp(int32_t k, const int32_t* D, int32_t* cost, int32_t* perm) {
-    if (k < 1 || k > OR_MAX_K) return OR_BADORDER;
+    if (k < 1 || k > OR_MAX_K_HK) return OR_BADORDER;
     if (!range_check(k, D)) { *cost = OR_INF; identity(k, perm); return OR_RANGE; }
     int32_t n = k + 1;
     uint32_t full = (1u << k) - 1u;
@@ -345,14 +345,15 @@ typedef struct {
 
 static void* tour_worker(void* p) {
     tour_job* j = (tour_job*)p;
-    int32_t D[(OR_MAX_K + 1) * (OR_MAX_K + 1)];
-    int32_t pts[OR_MAX_K + 1];
+    int32_t D[(OR_MAX_K_HK + 1) * (OR_MAX_K_HK + 1)];
+    int32_t pts[OR_MAX_K_HK + 1];
+    const int32_t kmax = j->tour_kind == OR_TOUR_HELDKARP ? OR_MAX_K_HK : OR_MAX_K;
     j->rc = 0;
     for (int32_t o = j->tid; o < j->n_orders; o += j->nthr) {
         int64_t b = j->offs[o], e = j->offs[o + 1];
         int64_t k64 = e - b;
         int32_t* perm = j->perm + b;
-        if (k64 < 1 || k64 > OR_MAX_K) {
+        if (k64 < 1 || k64 > kmax) {
             j->cost[o] = OR_INF; j->status[o] = OR_BADORDER;
             for (int64_t i = 0; i < k64; ++i) perm[i] = (int32_t)i;
             continue;
@@ -416,7 +417,7 @@ int or_route_orders(int32_t V, const int64_t* row_ptr, const int32_t* col, const
     nodes[cnt++] = depot;
     for (int32_t o = 0; o < n_orders; ++o) {
         int64_t k = offs[o + 1] - offs[o];
-        if (k < 1 || k > OR_MAX_K) continue;
+        if (k < 1 || k > OR_MAX_K_HK) continue;
         int bad = 0;
         for (int64_t i = offs[o]; i < offs[o + 1]; ++i) if (picks[i] < 0 || picks[i] >= V) bad = 1;
         if (bad) continue;

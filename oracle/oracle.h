@@ -26,7 +26,10 @@
  *   - any finite off-diagonal D entry above OR_LEG_MAX makes the order
  *     OR_RANGE (cost OR_INF, perm = identity): 13 legs of at most
  *     OR_LEG_MAX stay below 2^27, so exact sums fit int32;
- *   - k < 1, k > OR_MAX_K or a node id outside [0, V) is OR_BADORDER;
+ *   - k < 1, k above the solver's limit (OR_MAX_K for brute force, OR_MAX_K_HK
+ *     for Held-Karp) or a node id outside [0, V) is OR_BADORDER;
+ *   - 21 legs of at most OR_LEG_MAX stay below 2^31, so Held-Karp sums for
+ *     k <= 20 are exact in int32 as well;
  *   - perm[j] is the 0-based index into the order's own pick list.
  */
 #ifndef WROUTE_ORACLE_H
@@ -34,7 +37,8 @@
 #include <stdint.h>
 
 #define OR_INF INT32_MAX
-#define OR_MAX_K 12
+#define OR_MAX_K 12      /* brute force: 12! = 479,001,600 sequences, ranks fit int32 */
+#define OR_MAX_K_HK 20   /* Held-Karp: 2^20 x 20 table entries */
 #define OR_LEG_MAX 10324440
 #define OR_OK 0
 #define OR_UNREACHABLE 1

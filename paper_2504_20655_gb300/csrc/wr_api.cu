@@ -322,6 +322,17 @@ int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_
                                    c->src_list.as<int32_t>(), c->n_src.as<int32_t>(), c->block_sums.as<int32_t>(), s,
                                    &c->launches));
     }
+    // orders above WR_MAX_K picks (when the context admits them): Held-Karp
+    const bool hk = c->cfg.max_k > WR_MAX_K;
+    if (hk) {
+        RC(ensure(c->hk_list, static_cast<size_t>(n) * 4 + 4));
+        RC(ensure(c->hk_count, 16));
+        RC(ensure(c->hk_D, static_cast<size_t>(n) * wr::HK_DBLOCK * 4 + 4));
+        RC(ensure(c->hk_h, (static_cast<size_t>(1) << c->cfg.max_k) * static_cast<size_t>(c->cfg.max_k) * 4));
+        CK(cudaMemsetAsync(c->hk_count.p, 0, 4, s));
+        CK(wr::hk_launch_select(n, tb, c->cfg.max_k, c->hk_list.as<int32_t>(), c->hk_count.as<int32_t>(), s));
+        c->launches++;
+    }
     // segments of the worst-case source count; empty ones exit on the device
     const int64_t worst = np_bound + 1 < V ? np_bound + 1 : V;
     const int32_t lanes_needed = static_cast<int32_t>((worst + 31) / 32 * 32);
@@ -343,9 +354,26 @@ int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_
         PhaseTimer t(c, s, 3);
         CK(wr::tour_launch_gather(n, tb, c->dg.depot, c->src_index.as<int32_t>(), seg, s));
         c->launches++;
+        if (hk) {
+            CK(wr::hk_launch_gather(n, c->hk_list.as<int32_t>(), c->hk_count.as<int32_t>(), tb, c->dg.depot,
+                                    c->src_index.as<int32_t>(), seg, c->hk_D.as<uint32_t>(), s));
+            c->launches++;
+        }
     }
     c->last.n_segments = n_seg;
-    return run_tours(c, n, nullptr, tb, o_cost, o_perm, 0, o_status, s);
+    RC(run_tours(c, n, nullptr, tb, o_cost, o_perm, 0, o_status, s));
+    if (hk) {
+        // after the decode of the other orders: these write their own cost, perm and status
+        PhaseTimer t(c, s, 4);
+        RC(ensure(c->bar, sizeof(wr::GridBar)));
+        CK(cudaMemsetAsync(c->bar.p, 0, sizeof(wr::GridBar), s));
+        CK(wr::hk_launch_solve(c->hk_list.as<int32_t>(), c->hk_count.as<int32_t>(), c->hk_D.as<uint32_t>(),
+                               c->hk_h.as<uint32_t>(), tb, o_cost, o_perm, o_status, c->bar.as<wr::GridBar>(),
+                               c->err.as<int>(), c->cfg.barrier_max_spins ? c->cfg.barrier_max_spins : DEFAULT_SPINS,
+                               c->hk_blocks, s));
+        c->launches++;
+    }
+    return WR_OK;
 }
 
 }  // namespace wrc
@@ -377,7 +405,7 @@ int wr_create(const wr_config* cfg, wr_ctx** out) {
     c.barrier_max_spins = DEFAULT_SPINS;
     c.tune_path = nullptr;
     if (cfg) c = *cfg;
-    if (c.max_k < 1 || c.max_k > WR_MAX_K || c.device < 0) return WR_EINVAL;
+    if (c.max_k < 1 || c.max_k > WR_MAX_K_EXACT || c.device < 0) return WR_EINVAL;
     if (c.mem_budget_bytes == 0) return WR_ENOMEM;
     int n_dev = 0;
     if (cudaGetDeviceCount(&n_dev) != cudaSuccess || c.device >= n_dev) {
@@ -397,6 +425,7 @@ int wr_create(const wr_config* cfg, wr_ctx** out) {
     ctx->tune.bf_warps = 0;
     ctx->tune.bf_tiling = 0;
     ctx->enum_blocks = wr::tour_enum_blocks(c.device);
+    ctx->hk_blocks = wr::hk_blocks(c.device);
     if (cfg && cfg->tune_path) {
         ctx->tune_path = cfg->tune_path;
         wr_tuning t = ctx->tune;
@@ -419,7 +448,8 @@ void wr_destroy(wr_ctx* c) {
                     &c->counts, &c->bar, &c->err, &c->stats, &c->node_flag, &c->src_index, &c->src_list,
                     &c->n_src, &c->block_sums, &c->offs, &c->picks, &c->order_status, &c->order_flags, &c->D,
                     &c->unit_off, &c->best, &c->unit_ctr, &c->out_cost, &c->out_perm, &c->out_status, &c->kbuf,
-                    &c->dgiven, &c->src_in, &c->sub, &c->check, &c->trace};
+                    &c->dgiven, &c->src_in, &c->sub, &c->check, &c->trace,
+                    &c->hk_list, &c->hk_count, &c->hk_D, &c->hk_h};
     for (DBuf* b : bufs) b->release();
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     delete c;
@@ -708,7 +738,8 @@ int wr_tour_eval(wr_ctx* c, int32_t n, const int32_t* k, const int32_t* D, int32
     RC(ensure_tour_bufs(c, n, tb));
     {
         PhaseTimer t(c, s, 3);
-        CK(wr::tour_launch_prepare_given(n, d_k, d_D, c->cfg.max_k, tb, s));
+        // given 13 x 13 blocks: exhaustive orders only
+        CK(wr::tour_launch_prepare_given(n, d_k, d_D, c->cfg.max_k < WR_MAX_K ? c->cfg.max_k : WR_MAX_K, tb, s));
         c->launches++;
     }
     int32_t* o_cost = cost;

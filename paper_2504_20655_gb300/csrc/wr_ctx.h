@@ -59,6 +59,8 @@ struct wr_ctx {
     wrc::DBuf node_flag, src_index, src_list, n_src, block_sums;
     wrc::DBuf offs, picks, order_status, order_flags, D, unit_off, best, unit_ctr;
     wrc::DBuf out_cost, out_perm, out_status, kbuf, dgiven, src_in, sub, check;
+    wrc::DBuf hk_list, hk_count, hk_D, hk_h;  // Held-Karp orders (k > WR_MAX_K)
+    int hk_blocks = 0;
     wrc::DBuf trace;          // sweep trace of the last Bellman-Ford segment
     int32_t trace_cap = 0;
     bool capturing = false;  // enqueueing into a CUDA graph: no host syncs, external timing events

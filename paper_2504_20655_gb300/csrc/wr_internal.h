@@ -18,6 +18,9 @@ constexpr int DSTRIDE = 13;                   // D blocks are 13 x 13
 constexpr int DBLOCK = DSTRIDE * DSTRIDE;
 constexpr int TAIL = 5;                       // tail walked by one compile-time unrolled walk
 constexpr int UNIT_TAIL = 6;                  // a unit: a prefix and the 720 orderings of the last 6 picks (k >= 6)
+constexpr int HK_MAX_K = 20;                  // orders of WR_MAX_K+1 .. 20 picks: Held-Karp
+constexpr int HK_DSTRIDE = HK_MAX_K + 1;
+constexpr int HK_DBLOCK = HK_DSTRIDE * HK_DSTRIDE;
 constexpr int ORDER_FLAG_RANGE = 1;
 constexpr int32_t RUN_SIMPLE = 1;             // run's extra arcs fit the tile buffer, halo fully staged
 constexpr uint32_t IX_EXTRA = 1u << 24;       // node has arcs beyond the inline ones
@@ -191,5 +194,15 @@ cudaError_t tour_launch_enum(int32_t n, const int32_t* k_given, const TourBufs& 
 cudaError_t tour_launch_finish(int32_t n, const int32_t* k_given, const TourBufs& t, int32_t* cost,
                                int32_t* perm, int perm_stride, int32_t* status, cudaStream_t s);
 int tour_enum_blocks(int device);
+
+// Held-Karp for orders of WR_MAX_K+1 .. max_k picks (wr_hk.cu)
+cudaError_t hk_launch_select(int32_t n, const TourBufs& t, int32_t max_k, int32_t* list, int32_t* count,
+                             cudaStream_t s);
+cudaError_t hk_launch_gather(int32_t n, const int32_t* list, const int32_t* count, const TourBufs& t, int32_t depot,
+                             const int32_t* src_index, const BfSegment& seg, uint32_t* D21, cudaStream_t s);
+int hk_blocks(int device);
+cudaError_t hk_launch_solve(const int32_t* list, const int32_t* count, const uint32_t* D21, uint32_t* h,
+                            const TourBufs& t, int32_t* cost, int32_t* perm, int32_t* status, GridBar* bar, int* err,
+                            unsigned long long max_spins, int blocks, cudaStream_t s);
 
 }  // namespace wr

@@ -155,7 +155,7 @@ double seconds_since(std::chrono::steady_clock::time_point t0) {
 
 bool order_valid(const wr_server* sv, const int64_t* offs, const int32_t* picks, int32_t i) {
     const int64_t k = offs[i + 1] - offs[i];
-    if (k < 1 || k > sv->c->cfg.max_k) return false;
+    if (k < 1 || k > sv->c->cfg.max_k || k > WR_MAX_K) return false;  // the loop routes exhaustive orders
     for (int64_t q = offs[i]; q < offs[i + 1]; ++q)
         if (picks[q] < 0 || picks[q] >= sv->V) return false;
     return true;
@@ -364,6 +364,7 @@ int wr_serve_create(wr_ctx* parent, const wr_serve_config* cfg, wr_server** out)
     if (rc == WR_OK) {
         sv->c->tune = parent->tune;
         sv->c->tune.enum_max_units_per_launch = 0;  // no host syncs inside a batch
+        if (sv->c->cfg.max_k > WR_MAX_K) sv->c->cfg.max_k = WR_MAX_K;  // the loop routes exhaustive orders
         sv->c->hg = parent->hg;
         rc = finish_graph(sv->c);
     }

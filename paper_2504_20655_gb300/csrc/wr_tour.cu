@@ -161,6 +161,7 @@ __global__ void gather_kernel(int32_t n, TourBufs t, int32_t depot, const int32_
     if (t.order_status[o] != WR_ORDER_OK) return;
     const int64_t b = t.offs[o];
     const int k = static_cast<int>(t.offs[o + 1] - b);
+    if (k > WR_MAX_K) return;  // Held-Karp orders gather into their own blocks
     const int m = k + 1;
     bool range = false;
     for (int e = lane; e < m * m; e += 32) {
@@ -234,7 +235,9 @@ __device__ __forceinline__ int order_k(const TourBufs& t, const int32_t* k_given
 }
 
 __device__ __forceinline__ long long units_of(int k) {
-    // k! / 6! for k >= 6 (a unit is a prefix and the 720 orderings of the last six picks), else 1
+    // k! / 6! for k >= 6 (a unit is a prefix and the 720 orderings of the last six picks), else 1;
+    // orders above WR_MAX_K are solved by Held-Karp instead
+    if (k > WR_MAX_K) return 0;
     long long u = 1;
     for (int i = UNIT_TAIL + 1; i <= k; ++i) u *= i;
     return u;

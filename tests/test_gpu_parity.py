@@ -216,7 +216,7 @@ def test_route_statuses_and_edge_cases(router, orc):
     picks = np.array([x for od in orders for x in od], np.int32)
     o = synth.Orders(offs, picks)
     cost, perm, status = router.route_orders(o.offs, o.picks)
-    c, p, s = orc.route_orders(g, o, "dijkstra", "heldkarp", NT)
+    c, p, s = orc.route_orders(g, o, "dijkstra", "heldkarp", NT, max_k=12)  # the context's default max_k
     assert status.tolist() == s.tolist() == [0, 0, 0, 2, 2, 2, 2, 0, 0]
     assert (cost == c).all() and (perm[:len(p)] == p).all()
 
@@ -509,3 +509,73 @@ def test_serve_plain_baseline(router):
     ref = router.route_orders(o.offs, o.picks)
     assert (cost == ref[0]).all() and (status == ref[2]).all() and (perm == ref[1][:len(perm)]).all()
     assert st["batches"] == 200 and (done >= arr - 1e-9).all()
+
+
+def _big_orders(g, ks, seed):
+    """Orders of the given sizes, distinct uniform slots each."""
+    parts = [synth.uniform_slot_orders(1, int(k), g.n_slots, seed + i) for i, k in enumerate(ks)]
+    offs = np.zeros(len(ks) + 1, np.int64)
+    offs[1:] = np.cumsum(ks)
+    return synth.Orders(offs, np.concatenate([p.picks for p in parts]).astype(np.int32))
+
+
+def test_route_held_karp_large_orders(wr, orc):
+    """Orders of 13..20 picks in a context created with max_k = 20: exact Held-Karp on the
+    GPU against the oracle's Held-Karp (cost, first optimal sequence, status), mixed with
+    exhaustive orders; the same orders are WR_ORDER_BAD under the default max_k = 12,
+    and a captured plan gives the same results."""
+    g = synth.medium_layout().build()
+    ks = [13, 5, 14, 9, 15, 16, 3, 13, 17, 12, 18, 20, 14, 13, 6, 15]
+    o = _big_orders(g, ks, 4242)
+    r = wr.Router(device=0, max_k=20)
+    try:
+        r.load_graph(g)
+        cost, perm, status = r.route_orders(o.offs, o.picks)
+        plan = r.plan(o.n, int(o.offs[-1]))
+        try:
+            pc, pp, ps = _plan_run(plan, o.offs, o.picks)
+        finally:
+            plan.close()
+    finally:
+        r.close()
+    c, p, s = orc.route_orders(g, o, "dijkstra", "heldkarp", NT, max_k=20)
+    assert (status == s).all() and (cost == c).all() and (perm[:len(p)] == p).all()
+    assert (pc == c).all() and (ps == s).all() and (pp[:len(p)] == p).all()
+    assert (s == 0).all()
+    r12 = wr.Router(device=0)
+    try:
+        r12.load_graph(g)
+        c12, _, s12 = r12.route_orders(o.offs, o.picks)
+    finally:
+        r12.close()
+    big = np.array(ks) > 12
+    assert (s12[big] == 2).all() and (s12[~big] == s[~big]).all() and (c12[~big] == c[~big]).all()
+
+
+def test_route_held_karp_unreachable_and_range(wr, orc):
+    """Held-Karp statuses: an order with an unreachable pick, and one with a leg above
+    WR_LEG_MAX, on a small directed graph with heavy arcs."""
+    V = 60
+    u = np.arange(V - 1, dtype=np.int64)
+    w = synth.uniform_int(71, V - 1, 1, 40)
+    w[20] = 20_000_000  # legs across this arc exceed WR_LEG_MAX
+    rp, col, wt = synth.csr_from_arcs(V, np.concatenate([u, u + 1]), np.concatenate([u + 1, u]),
+                                      np.concatenate([w, w]))
+    g = synth.Graph(V=V, row_ptr=rp, col=col, w=wt, depot=0)
+    # node 59 cut off from the depot: drop its arcs
+    keep = (np.repeat(np.arange(V), np.diff(rp)) != 59) & (col != 59)
+    src = np.repeat(np.arange(V), np.diff(rp))[keep]
+    rp2, col2, wt2 = synth.csr_from_arcs(V, src, col[keep], wt[keep])
+    g = synth.Graph(V=V, row_ptr=rp2, col=col2, w=wt2, depot=0)
+    offs = np.array([0, 14, 28, 42], np.int64)
+    picks = np.concatenate([np.arange(1, 15), np.arange(5, 18), [59], np.arange(10, 24) + 1]).astype(np.int32)
+    o = synth.Orders(offs, picks)
+    r = wr.Router(device=0, max_k=16)
+    try:
+        r.load_graph(g)
+        cost, perm, status = r.route_orders(o.offs, o.picks)
+    finally:
+        r.close()
+    c, p, s = orc.route_orders(g, o, "dijkstra", "heldkarp", NT, max_k=16)
+    assert (status == s).all() and (cost == c).all() and (perm[:len(p)] == p).all()
+    assert sorted(s.tolist()) == [0, 1, 3]

@@ -129,3 +129,76 @@ def test_route_orders_statuses(orc):
     assert perm[2:4].tolist() == [0, 1]
     assert perm[4:17].tolist() == list(range(13))
     assert cost[4] == 2 * orc.dijkstra(g, g.depot)[5]
+
+
+# --- Held-Karp above the brute-force limit (k = 13 .. 20) -------------------------------
+
+def line_lex_tour(pos):
+    """Points on a line (depot at 0, pick j at pos[j] > 0, all distinct): a closed tour
+    costs 2 * max(pos) exactly when its positions rise to the maximum and then fall, so
+    the first optimal sequence in lexicographic order is found greedily, taking the
+    smallest pick that still allows such a rise-and-fall completion."""
+    k = len(pos)
+    rest = set(range(k))
+    cur, up, seq = 0, True, []
+    while rest:
+        for j in sorted(rest):
+            others = rest - {j}
+            if up and pos[j] > cur:
+                ok = True  # keep rising: whatever is left below comes on the way down
+            else:          # fall: everything left must lie below j
+                ok = pos[j] < cur and all(pos[q] < pos[j] for q in others)
+            if ok:
+                if pos[j] < cur:
+                    up = False
+                seq.append(j)
+                cur = pos[j]
+                rest.remove(j)
+                break
+        else:
+            raise AssertionError("no feasible step")
+    return 2 * max(pos), seq
+
+
+def line_D(pos):
+    x = np.array([0] + list(pos), dtype=np.int64)
+    return np.abs(x[:, None] - x[None, :]).astype(np.int32)
+
+
+@pytest.mark.parametrize("k", [6, 9, 13, 16, 20])
+def test_held_karp_points_on_a_line(orc, k):
+    """Held-Karp against the closed form and the greedy rule of the line, beyond brute force."""
+    rng = np.random.default_rng(1000 + k)
+    pos = list(rng.choice(np.arange(1, 500), size=k, replace=False) * 3)
+    cost, seq = line_lex_tour(pos)
+    st, c, p = orc.tour(line_D(pos), "heldkarp")
+    assert st == 0 and c == cost and p.tolist() == seq
+    if k <= 9:  # the greedy rule itself against brute force
+        st, c, p = orc.tour(line_D(pos), "brute")
+        assert c == cost and p.tolist() == seq
+
+
+@pytest.mark.parametrize("k", [13, 17, 20])
+def test_held_karp_large_k_consistency(orc, k):
+    """Random asymmetric instances: the returned sequence costs exactly the returned
+    optimum, no random or shifted sequence beats it, and equal legs give the identity."""
+    D = rand_D(k, 500 + k, lo=1, hi=1000)
+    st, c, p = orc.tour(D, "heldkarp")
+    seq = [0] + [x + 1 for x in p.tolist()] + [0]
+    assert st == 0 and sorted(p.tolist()) == list(range(k))
+    assert c == sum(int(D[a, b]) for a, b in zip(seq[:-1], seq[1:]))
+    rng = np.random.default_rng(k)
+    for _ in range(300):
+        q = [0] + list(rng.permutation(k) + 1) + [0]
+        assert c <= sum(int(D[a, b]) for a, b in zip(q[:-1], q[1:]))
+    flat = np.full((k + 1, k + 1), 7, np.int32)
+    np.fill_diagonal(flat, 0)
+    st, c, p = orc.tour(flat, "heldkarp")
+    assert st == 0 and c == 7 * (k + 1) and p.tolist() == list(range(k))
+
+
+def test_held_karp_limits(orc):
+    st, _, _ = orc.tour(rand_D(21, 3), "heldkarp")
+    assert st == 2  # above the Held-Karp limit: bad order
+    st, _, _ = orc.tour(rand_D(13, 3), "brute")
+    assert st == 2  # above the brute-force limit
