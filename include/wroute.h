@@ -63,6 +63,13 @@ extern "C" {
 #define WR_HOST   0
 #define WR_DEVICE 1
 
+/* route shapes (wr_set_route_mode) */
+#define WR_ROUTE_TOUR 0  /* closed tour: depot -> picks -> depot (default) */
+#define WR_ROUTE_OPEN 1  /* open path through the picks: the entrance/exit is not part of the route
+                            (Sec. 3), so the depot's legs are free; one of every reversed pair is
+                            the lexicographically first, so the result is the same as over the
+                            paper's n!/2 undirected routes when D is symmetric */
+
 #define WR_MAX_K   12          /* exhaustive enumeration: 12! = 479001600 ranks fit int32 */
 #define WR_MAX_K_EXACT 20      /* with max_k above WR_MAX_K, orders of 13..max_k picks are solved exactly by
                                   Held-Karp (same optimum, same tie rule), wr_route_orders only */
@@ -268,6 +275,10 @@ int wr_serve_run(wr_server* sv, int32_t n_orders, const double* arrival_s, const
                  int32_t* cost, int32_t* perm, int32_t* status, double* done_s);
 int wr_serve_get_stats(wr_server* sv, wr_serve_stats* out);
 void wr_serve_destroy(wr_server* sv);
+
+/* Route shape of wr_route_orders, plans and servers created afterwards (WR_ROUTE_TOUR or
+ * WR_ROUTE_OPEN); wr_tour_eval uses the matrices as given.  WR_EINVAL otherwise. */
+int wr_set_route_mode(wr_ctx* ctx, int mode);
 
 int wr_get_tuning(wr_ctx* ctx, wr_tuning* out);
 /* Changing run_target or tile_cap re-partitions the loaded graph. */

@@ -23,6 +23,7 @@ LEG_MAX = 10324440
 OK, UNREACHABLE, BADORDER, RANGE = 0, 1, 2, 3
 SSSP = {"rounds": 0, "fifo": 1, "dijkstra": 2}
 TOUR = {"brute": 0, "heldkarp": 1}
+OPEN_PATH = 16
 
 _lib = None
 
@@ -149,7 +150,8 @@ def tour(D, kind: str = "brute"):
     return int(st), int(cost[0]), perm[:k].copy()
 
 
-def route_orders(g, orders, sssp: str = "dijkstra", tour_kind: str = "brute", n_threads: int = 1, max_k=None):
+def route_orders(g, orders, sssp: str = "dijkstra", tour_kind: str = "brute", n_threads: int = 1, max_k=None,
+                 open_path: bool = False):
     """(cost, perm, status) per order.  Orders above max_k (default: the solver's own
     limit, 12 for brute force and 20 for Held-Karp) are OR_BADORDER, as in a library
     context created with that max_k."""
@@ -161,8 +163,8 @@ def route_orders(g, orders, sssp: str = "dijkstra", tour_kind: str = "brute", n_
     perm = np.zeros(max(int(offs[-1]), 1), dtype=np.int32)
     status = np.zeros(n, dtype=np.int32)
     _check(lib().or_route_orders(g.V, _p(rp), _p(c), _p(w), int(g.depot), n, _p(offs), _p(picks),
-                                 SSSP[sssp], TOUR[tour_kind], int(n_threads), _p(cost), _p(perm),
-                                 _p(status)), "route_orders")
+                                 SSSP[sssp], TOUR[tour_kind] | (OPEN_PATH if open_path else 0), int(n_threads),
+                                 _p(cost), _p(perm), _p(status)), "route_orders")
     if max_k is not None:
         for o in np.nonzero(np.diff(offs) > max_k)[0]:
             cost[o], status[o] = INF, BADORDER

@@ -347,7 +347,9 @@ static void* tour_worker(void* p) {
     tour_job* j = (tour_job*)p;
     int32_t D[(OR_MAX_K_HK + 1) * (OR_MAX_K_HK + 1)];
     int32_t pts[OR_MAX_K_HK + 1];
-    const int32_t kmax = j->tour_kind == OR_TOUR_HELDKARP ? OR_MAX_K_HK : OR_MAX_K;
+    const int kind = j->tour_kind & ~OR_OPEN_PATH;
+    const int open_path = (j->tour_kind & OR_OPEN_PATH) != 0;
+    const int32_t kmax = kind == OR_TOUR_HELDKARP ? OR_MAX_K_HK : OR_MAX_K;
     j->rc = 0;
     for (int32_t o = j->tid; o < j->n_orders; o += j->nthr) {
         int64_t b = j->offs[o], e = j->offs[o + 1];
@@ -372,8 +374,10 @@ static void* tour_worker(void* p) {
             for (int32_t c = 0; c < n; ++c)
                 D[a * n + c] = j->rows[(size_t)r * (size_t)j->V + (size_t)pts[c]];
         }
-        int st = (j->tour_kind == OR_TOUR_HELDKARP) ? or_tour_held_karp(k, D, &j->cost[o], perm)
-                                                    : or_tour_brute(k, D, &j->cost[o], perm);
+        if (open_path)
+            for (int32_t a = 0; a < n; ++a) D[a * n] = D[a] = 0;
+        int st = (kind == OR_TOUR_HELDKARP) ? or_tour_held_karp(k, D, &j->cost[o], perm)
+                                            : or_tour_brute(k, D, &j->cost[o], perm);
         if (st < 0) { j->rc = st; return 0; }
         j->status[o] = st;
     }

@@ -50,6 +50,9 @@
 #define OR_SSSP_DIJKSTRA 2
 #define OR_TOUR_BRUTE 0
 #define OR_TOUR_HELDKARP 1
+/* or-ed into tour_kind of the route functions: the route is an open path through the
+ * picks, the entrance/exit (depot) not part of it (Sec. 3): every depot leg costs 0. */
+#define OR_OPEN_PATH 16
 
 #ifdef __cplusplus
 extern "C" {

@@ -352,11 +352,13 @@ int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_
         seg.lanes = seg_lanes;
         RC(run_bf_segment(c, seg, s));
         PhaseTimer t(c, s, 3);
-        CK(wr::tour_launch_gather(n, tb, c->dg.depot, c->src_index.as<int32_t>(), seg, s));
+        CK(wr::tour_launch_gather(n, tb, c->dg.depot, c->src_index.as<int32_t>(), seg, c->route_mode == WR_ROUTE_OPEN,
+                                  s));
         c->launches++;
         if (hk) {
             CK(wr::hk_launch_gather(n, c->hk_list.as<int32_t>(), c->hk_count.as<int32_t>(), tb, c->dg.depot,
-                                    c->src_index.as<int32_t>(), seg, c->hk_D.as<uint32_t>(), s));
+                                    c->src_index.as<int32_t>(), seg, c->hk_D.as<uint32_t>(),
+                                    c->route_mode == WR_ROUTE_OPEN, s));
             c->launches++;
         }
     }
@@ -820,6 +822,12 @@ int wr_get_trace(wr_ctx* c, int64_t* out, int32_t max_entries, int32_t* n_out) {
     return WR_OK;
 }
 
+int wr_set_route_mode(wr_ctx* c, int mode) {
+    if (!c || (mode != WR_ROUTE_TOUR && mode != WR_ROUTE_OPEN)) return WR_EINVAL;
+    c->route_mode = mode;
+    return WR_OK;
+}
+
 int wr_get_tuning(wr_ctx* c, wr_tuning* out) {
     if (!c || !out) return WR_EINVAL;
     *out = c->tune;
@@ -976,6 +984,7 @@ int wr_plan_create(wr_ctx* parent, int32_t n, int64_t max_picks, const int64_t* 
     if (rc == WR_OK) {
         wr_ctx* c = p->c;
         c->tune = parent->tune;
+        c->route_mode = parent->route_mode;
         c->hg = parent->hg;  // host copy of the in-arc graph; re-partitioned and uploaded privately
         rc = finish_graph(c);
     }

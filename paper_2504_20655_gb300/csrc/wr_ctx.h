@@ -61,6 +61,7 @@ struct wr_ctx {
     wrc::DBuf out_cost, out_perm, out_status, kbuf, dgiven, src_in, sub, check;
     wrc::DBuf hk_list, hk_count, hk_D, hk_h;  // Held-Karp orders (k > WR_MAX_K)
     int hk_blocks = 0;
+    int route_mode = WR_ROUTE_TOUR;
     wrc::DBuf trace;          // sweep trace of the last Bellman-Ford segment
     int32_t trace_cap = 0;
     bool capturing = false;  // enqueueing into a CUDA graph: no host syncs, external timing events

@@ -32,7 +32,8 @@ __global__ void hk_select_kernel(int32_t n, TourBufs t, int32_t max_k, int32_t* 
 
 // D of the listed orders, (k+1) x (k+1) at stride HK_DSTRIDE, from one source segment's rows.
 __global__ void hk_gather_kernel(const int32_t* __restrict__ list, const int32_t* __restrict__ count, TourBufs t,
-                                 int32_t depot, const int32_t* __restrict__ src_index, BfSegment seg, uint32_t* D21) {
+                                 int32_t depot, const int32_t* __restrict__ src_index, BfSegment seg, uint32_t* D21,
+                                 int open_path) {
     const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (q >= ld_volatile(count)) return;
@@ -43,6 +44,10 @@ __global__ void hk_gather_kernel(const int32_t* __restrict__ list, const int32_t
     bool range = false;
     for (int e = lane; e < m * m; e += 32) {
         const int i = e / m, j = e - i * m;
+        if (open_path && (i == 0 || j == 0)) {  // open path: free entrance/exit legs
+            D21[static_cast<int64_t>(q) * HK_DBLOCK + i * HK_DSTRIDE + j] = 0u;
+            continue;
+        }
         const int32_t pi = i == 0 ? depot : t.picks[b + i - 1];
         const int32_t si = src_index[pi] - seg.first;
         if (si < 0 || si >= seg.lanes) continue;
@@ -147,8 +152,9 @@ cudaError_t hk_launch_select(int32_t n, const TourBufs& t, int32_t max_k, int32_
 }
 
 cudaError_t hk_launch_gather(int32_t n, const int32_t* list, const int32_t* count, const TourBufs& t, int32_t depot,
-                             const int32_t* src_index, const BfSegment& seg, uint32_t* D21, cudaStream_t s) {
-    hk_gather_kernel<<<(n + 7) / 8, 256, 0, s>>>(list, count, t, depot, src_index, seg, D21);
+                             const int32_t* src_index, const BfSegment& seg, uint32_t* D21, int open_path,
+                             cudaStream_t s) {
+    hk_gather_kernel<<<(n + 7) / 8, 256, 0, s>>>(list, count, t, depot, src_index, seg, D21, open_path);
     return cudaGetLastError();
 }
 

@@ -183,8 +183,9 @@ cudaError_t tour_launch_select(int32_t n, const int64_t* offs, const int32_t* pi
 cudaError_t tour_launch_compact(int32_t V, const uint8_t* node_flag, int32_t* src_index,
                                 int32_t* src_list, int32_t* n_src, int32_t* block_sums,
                                 cudaStream_t s, int* launches);
+// open_path: the depot's legs are free (the route is the path through the picks)
 cudaError_t tour_launch_gather(int32_t n, const TourBufs& t, int32_t depot, const int32_t* src_index,
-                               const BfSegment& seg, cudaStream_t s);
+                               const BfSegment& seg, int open_path, cudaStream_t s);
 cudaError_t tour_launch_prepare_given(int32_t n, const int32_t* k, const int32_t* Din, int32_t max_k,
                                       const TourBufs& t, cudaStream_t s);
 cudaError_t tour_launch_units(int32_t n, const int32_t* k_given, const TourBufs& t, cudaStream_t s,
@@ -199,7 +200,8 @@ int tour_enum_blocks(int device);
 cudaError_t hk_launch_select(int32_t n, const TourBufs& t, int32_t max_k, int32_t* list, int32_t* count,
                              cudaStream_t s);
 cudaError_t hk_launch_gather(int32_t n, const int32_t* list, const int32_t* count, const TourBufs& t, int32_t depot,
-                             const int32_t* src_index, const BfSegment& seg, uint32_t* D21, cudaStream_t s);
+                             const int32_t* src_index, const BfSegment& seg, uint32_t* D21, int open_path,
+                             cudaStream_t s);
 int hk_blocks(int device);
 cudaError_t hk_launch_solve(const int32_t* list, const int32_t* count, const uint32_t* D21, uint32_t* h,
                             const TourBufs& t, int32_t* cost, int32_t* perm, int32_t* status, GridBar* bar, int* err,

@@ -200,7 +200,7 @@ int launch_batch(wr_server* sv, Slot& sl, int32_t n_miss, int32_t n_new_groups) 
     all.n_src_host = sv->C;
     all.first = 0;
     all.lanes = sv->C;
-    CK(wr::tour_launch_gather(sl.n, tb, c->dg.depot, sv->dir.as<int32_t>(), all, s0));
+    CK(wr::tour_launch_gather(sl.n, tb, c->dg.depot, sv->dir.as<int32_t>(), all, c->route_mode == WR_ROUTE_OPEN, s0));
     CK(cudaEventRecord(sl.ev_in, s0));
     // stage 2
     CK(cudaStreamWaitEvent(sl.s, sl.ev_in, 0));
@@ -363,6 +363,7 @@ int wr_serve_create(wr_ctx* parent, const wr_serve_config* cfg, wr_server** out)
     int rc = wr_create(&parent->cfg, &sv->c);
     if (rc == WR_OK) {
         sv->c->tune = parent->tune;
+        sv->c->route_mode = parent->route_mode;
         sv->c->tune.enum_max_units_per_launch = 0;  // no host syncs inside a batch
         if (sv->c->cfg.max_k > WR_MAX_K) sv->c->cfg.max_k = WR_MAX_K;  // the loop routes exhaustive orders
         sv->c->hg = parent->hg;

@@ -154,7 +154,7 @@ cudaError_t tour_launch_compact(int32_t V, const uint8_t* node_flag, int32_t* sr
 // ---------------------------------------------------------------------------
 
 __global__ void gather_kernel(int32_t n, TourBufs t, int32_t depot, const int32_t* __restrict__ src_index,
-                              BfSegment seg) {
+                              BfSegment seg, int open_path) {
     const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (o >= n) return;
@@ -166,6 +166,11 @@ __global__ void gather_kernel(int32_t n, TourBufs t, int32_t depot, const int32_
     bool range = false;
     for (int e = lane; e < m * m; e += 32) {
         const int i = e / m, j = e - i * m;
+        if (open_path && (i == 0 || j == 0)) {
+            // open path: the entrance/exit is not part of the route, its legs are free
+            t.D[static_cast<int64_t>(o) * DBLOCK + i * DSTRIDE + j] = 0u;
+            continue;
+        }
         const int32_t pi = i == 0 ? depot : t.picks[b + i - 1];
         const int32_t si = src_index[pi] - seg.first;
         if (si < 0 || si >= seg.lanes) continue;
@@ -182,8 +187,8 @@ __global__ void gather_kernel(int32_t n, TourBufs t, int32_t depot, const int32_
 }
 
 cudaError_t tour_launch_gather(int32_t n, const TourBufs& t, int32_t depot, const int32_t* src_index,
-                               const BfSegment& seg, cudaStream_t s) {
-    gather_kernel<<<(n + 7) / 8, 256, 0, s>>>(n, t, depot, src_index, seg);
+                               const BfSegment& seg, int open_path, cudaStream_t s) {
+    gather_kernel<<<(n + 7) / 8, 256, 0, s>>>(n, t, depot, src_index, seg, open_path);
     return cudaGetLastError();
 }
 

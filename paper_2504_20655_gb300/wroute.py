@@ -28,7 +28,7 @@ DSTRIDE = 13
 
 EXPORTS = ["wr_create", "wr_destroy", "wr_strerror", "wr_sync", "wr_load_graph", "wr_route_orders", "wr_bf_rows",
            "wr_distance_rows", "wr_submatrix", "wr_tour_eval", "wr_tour_eval_static", "wr_get_stats",
-           "wr_get_tuning", "wr_set_tuning", "wr_set_trace", "wr_get_trace", "wr_autotune",
+           "wr_get_tuning", "wr_set_tuning", "wr_set_trace", "wr_get_trace", "wr_autotune", "wr_set_route_mode",
            "wr_serve_create", "wr_serve_run", "wr_serve_get_stats", "wr_serve_destroy",
            "wr_plan_create", "wr_plan_launch", "wr_plan_sync", "wr_plan_get_stats", "wr_plan_destroy"]
 WR_STATIC_MAX_ORDERS = 4096
@@ -115,6 +115,7 @@ def load_library(path: str = LIB_PATH):
     L.wr_plan_destroy.argtypes = [P]
     L.wr_plan_destroy.restype = None
     L.wr_autotune.argtypes = [P, i32, P, P, I, i32, ctypes.POINTER(wr_tuning)]
+    L.wr_set_route_mode.argtypes = [P, I]
     L.wr_serve_create.argtypes = [P, ctypes.POINTER(wr_serve_config), ctypes.POINTER(P)]
     L.wr_serve_run.argtypes = [P, i32, P, P, P, P, P, P, P]
     L.wr_serve_get_stats.argtypes = [P, ctypes.POINTER(wr_serve_stats)]
@@ -522,6 +523,10 @@ class Router:
 
     def plan(self, n_orders, max_picks):
         return Plan(self.ctx, n_orders, max_picks, self.device)
+
+    def set_route_mode(self, open_path: bool):
+        """Closed tours through the depot (False, the default) or open paths through the picks (True)."""
+        _check(load_library().wr_set_route_mode(self.ctx, 1 if open_path else 0), "wr_set_route_mode")
 
     def set_trace(self, max_sweeps):
         wr_set_trace(self.ctx, max_sweeps)

@@ -579,3 +579,39 @@ def test_route_held_karp_unreachable_and_range(wr, orc):
     c, p, s = orc.route_orders(g, o, "dijkstra", "heldkarp", NT, max_k=16)
     assert (status == s).all() and (cost == c).all() and (perm[:len(p)] == p).all()
     assert sorted(s.tolist()) == [0, 1, 3]
+
+
+def test_route_open_paths(wr, orc):
+    """Open paths (the entrance/exit not part of the route): exhaustive and Held-Karp
+    orders against the oracle's open mode, directly, through a captured plan and through
+    the serving loop (all created after the mode was set)."""
+    g, o = synth.medium_workload(n_orders=200)
+    big = _big_orders(g, [13, 15, 14], 99)
+    offs = np.concatenate([o.offs, o.offs[-1] + big.offs[1:]])
+    picks = np.concatenate([o.picks, big.picks]).astype(np.int32)
+    ob = synth.Orders(offs, picks)
+    r = wr.Router(device=0, max_k=16)
+    try:
+        r.load_graph(g)
+        r.set_route_mode(True)
+        cost, perm, status = r.route_orders(ob.offs, ob.picks)
+        plan = r.plan(ob.n, int(ob.offs[-1]))
+        try:
+            pc, pp, ps = _plan_run(plan, ob.offs, ob.picks)
+        finally:
+            plan.close()
+        sv = r.server(max_batch=64, max_batch_picks=1024, n_slots=2, cache_bytes=256 << 20)
+        try:
+            arr = synth.poisson_arrivals(o.n, 20000.0, 5)
+            sc, sp, ss, _ = sv.run(arr, o.offs, o.picks)
+        finally:
+            sv.close()
+    finally:
+        r.close()
+    c, p, s = orc.route_orders(g, ob, "dijkstra", "heldkarp", NT, max_k=16, open_path=True)
+    assert (status == s).all() and (cost == c).all() and (perm[:len(p)] == p).all()
+    assert (pc == c).all() and (ps == s).all() and (pp[:len(p)] == p).all()
+    n = o.n
+    assert (sc == c[:n]).all() and (ss == s[:n]).all() and (sp[:o.offs[-1]] == p[:o.offs[-1]]).all()
+    cc, _, _ = orc.route_orders(g, o, "dijkstra", "heldkarp", NT)
+    assert (c[:n] <= cc).all() and (c[:n] < cc).any()

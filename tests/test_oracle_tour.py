@@ -202,3 +202,46 @@ def test_held_karp_limits(orc):
     assert st == 2  # above the Held-Karp limit: bad order
     st, _, _ = orc.tour(rand_D(13, 3), "brute")
     assert st == 2  # above the brute-force limit
+
+
+# --- open paths: the entrance/exit is not part of the route (Sec. 3) ---------------------
+
+@pytest.mark.parametrize("k", [2, 5, 8, 14, 20])
+def test_open_path_on_a_line(orc, k):
+    """Open paths through points on a line cost the span exactly when they are monotone,
+    so the first optimal sequence is the lexicographically smaller of the ascending and
+    the descending order.  Brute force (k <= 8) and Held-Karp against that rule; the
+    route functions' open mode gives the same as a matrix with free depot legs."""
+    rng = np.random.default_rng(77 + k)
+    pos = rng.choice(np.arange(1, 900), size=k, replace=False)
+    up = list(np.argsort(pos, kind="stable"))
+    want = min(up, up[::-1])
+    span = int(pos.max() - pos.min())
+    D = line_D(list(pos))
+    D[0, :] = 0
+    D[:, 0] = 0
+    kinds = ["brute", "heldkarp"] if k <= 8 else ["heldkarp"]
+    for kind in kinds:
+        st, c, p = orc.tour(D, kind)
+        assert st == 0 and c == span and p.tolist() == [int(x) for x in want], kind
+
+
+def test_open_path_route_mode(orc):
+    """The route functions' open mode equals closed tours over matrices whose depot legs
+    are free, for brute force and Held-Karp, on a directed layout (one-way aisles)."""
+    g, o = synth.medium_workload(n_orders=40)
+    c1, p1, s1 = orc.route_orders(g, o, "dijkstra", "brute", 4, open_path=True)
+    c2, p2, s2 = orc.route_orders(g, o, "dijkstra", "heldkarp", 4, open_path=True)
+    assert (c1 == c2).all() and (p1 == p2).all() and (s1 == s2).all()
+    cc, _, _ = orc.route_orders(g, o, "dijkstra", "brute", 4)
+    assert (c1 <= cc).all() and (c1 < cc).any()  # dropping the depot legs never costs more
+    rows = orc.sssp_rows(g, np.unique(np.concatenate([[g.depot], o.picks])).astype(np.int32), "dijkstra", 4)
+    nodes = np.unique(np.concatenate([[g.depot], o.picks]))
+    for i in range(0, o.n, 7):
+        pts = np.concatenate([[g.depot], o.order(i)])
+        idx = np.searchsorted(nodes, pts)
+        D = rows[idx][:, pts].astype(np.int64)
+        D[0, :] = 0
+        D[:, 0] = 0
+        st, c, p = orc.tour(D.astype(np.int32), "brute")
+        assert c == c1[i] and p.tolist() == p1[o.offs[i]:o.offs[i + 1]].tolist()
