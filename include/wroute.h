@@ -276,6 +276,24 @@ int wr_serve_run(wr_server* sv, int32_t n_orders, const double* arrival_s, const
 int wr_serve_get_stats(wr_server* sv, wr_serve_stats* out);
 void wr_serve_destroy(wr_server* sv);
 
+/* Node-level routes (the nodes a route passes; the paper has no API for them).  For each
+ * order (picks[offs[i] .. offs[i+1])) and its pick sequence perm[offs[i] + j] (0-based indices
+ * into the order's picks, e.g. from wr_route_orders), the route's nodes: the depot, then the
+ * nodes of each leg after its first, ending at the depot (WR_ROUTE_TOUR), or in WR_ROUTE_OPEN
+ * mode the first pick and then the legs between consecutive picks.  A leg s -> t is the
+ * shortest path whose nodes read backward from t are lexicographically smallest: walking back
+ * from t, the predecessor of v is the smallest node id u with an arc u -> v and
+ * dist(s,u) + w(u,v) = dist(s,v).
+ * Writes node_offs (n_orders + 1 entries; order i's nodes are nodes[node_offs[i] ..
+ * node_offs[i+1])); an order that is invalid (status WR_ORDER_BAD, or perm not a permutation
+ * of 0..k-1) or has an unreachable leg gets no nodes.  With nodes == NULL only node_offs is
+ * written; if node_offs[n_orders] > max_nodes nothing more is written and WR_ENOMEM is
+ * returned (node_offs is valid: call again with a larger buffer).  Requires every arc weight
+ * > 0 (with zero-weight arcs the walk may cycle): WR_EINVAL otherwise.  Recomputes the rows of
+ * the sources (twice for batches needing more than one segment). */
+int wr_route_nodes(wr_ctx* ctx, int32_t n_orders, const int64_t* offs, const int32_t* picks, const int32_t* perm,
+                   int64_t* node_offs, int32_t* nodes, int64_t max_nodes, int ptr_kind, void* cuda_stream);
+
 /* Route shape of wr_route_orders, plans and servers created afterwards (WR_ROUTE_TOUR or
  * WR_ROUTE_OPEN); wr_tour_eval uses the matrices as given.  WR_EINVAL otherwise. */
 int wr_set_route_mode(wr_ctx* ctx, int mode);

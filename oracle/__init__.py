@@ -194,3 +194,58 @@ def factorial(n: int) -> int:
 def patched_route_count(n_j) -> int:
     a = np.ascontiguousarray(n_j, dtype=np.int32)
     return int(lib().or_patched_route_count(a.shape[0], _p(a)))
+
+
+def route_nodes(g, orders, perm, open_path: bool = False, n_threads: int = 1):
+    """Node-level routes (plain Python over the oracle's Dijkstra rows): for each order and
+    its pick sequence, the depot and then each leg's nodes after its first (open path: the
+    first pick, then the legs between picks).  Leg s -> t is walked back from t, taking as
+    the predecessor of v the smallest node id u with an arc u -> v and
+    dist(s,u) + w(u,v) = dist(s,v).  An order with an unreachable leg, an invalid sequence
+    or a bad order gets no nodes.  Returns (node_offs, nodes)."""
+    offs = np.asarray(orders.offs, dtype=np.int64)
+    picks = np.asarray(orders.picks, dtype=np.int64)
+    V = g.V
+    # in-arcs with node ids, the lightest arc per (u, v), no self loops
+    src = np.repeat(np.arange(V), np.diff(g.row_ptr))
+    best = {}
+    for u, v, w in zip(src.tolist(), np.asarray(g.col).tolist(), np.asarray(g.w).tolist()):
+        if u != v and ((u, v) not in best or w < best[(u, v)]):
+            best[(u, v)] = w
+    into = [[] for _ in range(V)]
+    for (u, v), w in best.items():
+        into[v].append((u, w))
+    nodes_needed = np.unique(np.concatenate([[g.depot], picks[(picks >= 0) & (picks < V)]])).astype(np.int32)
+    rows = sssp_rows(g, nodes_needed, "dijkstra", n_threads)
+    row_of = {int(x): i for i, x in enumerate(nodes_needed)}
+
+    def leg(s, t):
+        d = rows[row_of[s]]
+        if d[t] == INF:
+            return None
+        out, v = [], t
+        while v != s:
+            out.append(v)
+            v = min(u for u, w in into[v] if d[u] != INF and int(d[u]) + w == int(d[v]))
+        return out[::-1]
+
+    node_offs, nodes = [0], []
+    for o in range(len(offs) - 1):
+        b, e = int(offs[o]), int(offs[o + 1])
+        k = e - b
+        seq = [int(x) for x in perm[b:e]]
+        route = []
+        ok = 1 <= k <= MAX_K_HK and all(0 <= p < V for p in picks[b:e]) and sorted(seq) == list(range(k))
+        if ok:
+            pts = [int(picks[b + j]) for j in seq]
+            stops = pts if open_path else [g.depot] + pts + [g.depot]
+            route = [stops[0]]
+            for s, t in zip(stops[:-1], stops[1:]):
+                part = leg(s, t)
+                if part is None:
+                    route = []
+                    break
+                route += part
+        nodes += route
+        node_offs.append(len(nodes))
+    return np.array(node_offs, np.int64), np.array(nodes, np.int32)

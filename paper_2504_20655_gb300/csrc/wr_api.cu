@@ -451,7 +451,8 @@ void wr_destroy(wr_ctx* c) {
                     &c->n_src, &c->block_sums, &c->offs, &c->picks, &c->order_status, &c->order_flags, &c->D,
                     &c->unit_off, &c->best, &c->unit_ctr, &c->out_cost, &c->out_perm, &c->out_status, &c->kbuf,
                     &c->dgiven, &c->src_in, &c->sub, &c->check, &c->trace,
-                    &c->hk_list, &c->hk_count, &c->hk_D, &c->hk_h};
+                    &c->hk_list, &c->hk_count, &c->hk_D, &c->hk_h, &c->g_in_ptr, &c->g_in_src, &c->g_in_w,
+                    &c->leg_len, &c->perm_in, &c->node_offs_d, &c->nodes_d};
     for (DBuf* b : bufs) b->release();
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     delete c;
@@ -496,6 +497,8 @@ int wr_load_graph(wr_ctx* c, int32_t V, int64_t E, const int64_t* row_ptr, const
     c->hg.V = g.V;
     c->hg.E = g.E;
     c->hg.depot = g.depot;
+    c->in_csr_uploaded = false;
+    c->positive_weights = std::all_of(c->hg.in_w.begin(), c->hg.in_w.end(), [](int32_t x) { return x > 0; });
     return finish_graph(c);
 }
 
@@ -819,6 +822,125 @@ int wr_get_trace(wr_ctx* c, int64_t* out, int32_t max_entries, int32_t* n_out) {
         out[2 * i + 1] = h[2 * i + 1];
     }
     *n_out = n;
+    return WR_OK;
+}
+
+int wr_route_nodes(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* picks, const int32_t* perm,
+                   int64_t* node_offs, int32_t* nodes, int64_t max_nodes, int ptr_kind, void* stream) {
+    if (!c || n < 0 || !offs || !node_offs || max_nodes < 0) return WR_EINVAL;
+    RC(check_ptr_kind(ptr_kind));
+    if (!c->has_graph) return WR_ENOGRAPH;
+    if (!c->positive_weights) return WR_EINVAL;  // zero-weight arcs: the predecessor rule may cycle
+    RC(set_device(c));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int64_t np = 0, first = 0;
+    if (ptr_kind == WR_HOST) {
+        first = offs[0];
+        np = offs[n];
+        for (int32_t i = 0; i < n; ++i)
+            if (offs[i + 1] < offs[i]) return WR_EINVAL;
+    } else {
+        CK(cudaMemcpyAsync(&first, offs, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&np, offs + n, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    if (first != 0 || np < 0 || (np > 0 && (!picks || !perm))) return WR_EINVAL;
+    if (n == 0) {
+        if (ptr_kind == WR_HOST) node_offs[0] = 0;
+        else CK(cudaMemsetAsync(node_offs, 0, 8, s));
+        return WR_OK;
+    }
+    const int32_t V = c->dg.V;
+    if (!c->in_csr_uploaded) {
+        RC(upload(c->g_in_ptr, c->hg.in_ptr.data(), c->hg.in_ptr.size() * 8));
+        RC(upload(c->g_in_src, c->hg.in_src.data(), c->hg.in_src.size() * 4));
+        RC(upload(c->g_in_w, c->hg.in_w.data(), c->hg.in_w.size() * 4));
+        c->in_csr_uploaded = true;
+    }
+    RC(begin_call(c, s));
+    const int64_t* d_offs = offs;
+    const int32_t* d_picks = picks;
+    const int32_t* d_perm = perm;
+    if (ptr_kind == WR_HOST) {
+        RC(ensure(c->offs, (static_cast<size_t>(n) + 1) * 8));
+        RC(ensure(c->picks, static_cast<size_t>(np) * 4 + 4));
+        RC(ensure(c->perm_in, static_cast<size_t>(np) * 4 + 4));
+        CK(cudaMemcpyAsync(c->offs.p, offs, (static_cast<size_t>(n) + 1) * 8, cudaMemcpyHostToDevice, s));
+        if (np) {
+            CK(cudaMemcpyAsync(c->picks.p, picks, static_cast<size_t>(np) * 4, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(c->perm_in.p, perm, static_cast<size_t>(np) * 4, cudaMemcpyHostToDevice, s));
+        }
+        d_offs = c->offs.as<int64_t>();
+        d_picks = c->picks.as<int32_t>();
+        d_perm = c->perm_in.as<int32_t>();
+    }
+    wr::TourBufs tb{};
+    RC(ensure_tour_bufs(c, n, tb));
+    RC(ensure(c->leg_len, (static_cast<size_t>(np) + n) * 4 + 4));
+    RC(ensure(c->node_offs_d, (static_cast<size_t>(n) + 1) * 8));
+    CK(cudaMemsetAsync(c->node_flag.p, 0, static_cast<size_t>(V), s));
+    CK(wr::tour_launch_select(n, d_offs, d_picks, V, c->dg.depot, c->cfg.max_k, c->node_flag.as<uint8_t>(),
+                              tb.order_status, s));
+    c->launches++;
+    CK(wr::tour_launch_compact(V, c->node_flag.as<uint8_t>(), c->src_index.as<int32_t>(), c->src_list.as<int32_t>(),
+                               c->n_src.as<int32_t>(), c->block_sums.as<int32_t>(), s, &c->launches));
+    const int64_t worst = np + 1 < V ? np + 1 : V;
+    const int32_t lanes_needed = static_cast<int32_t>((worst + 31) / 32 * 32);
+    const int32_t blanes = budget_lanes(c);
+    if (blanes < 32) return WR_ENOMEM;
+    const int32_t seg_lanes = lanes_needed < blanes ? lanes_needed : blanes;
+    const int32_t n_seg = (lanes_needed + seg_lanes - 1) / seg_lanes;
+    RC(ensure_bf(c, seg_lanes));
+    wr::PathsLaunch pl{n, d_offs, d_picks, d_perm, tb.order_status, c->route_mode == WR_ROUTE_OPEN, c->dg.depot,
+                       c->src_index.as<int32_t>(), c->g_in_ptr.as<int64_t>(), c->g_in_src.as<int32_t>(),
+                       c->g_in_w.as<int32_t>(), V, c->leg_len.as<int32_t>()};
+    auto segment = [&](int32_t sg) {
+        wr::BfSegment seg;
+        seg.rows = c->rows.as<uint32_t>();
+        seg.ld = seg_lanes;
+        seg.src = c->src_list.as<int32_t>();
+        seg.n_src_dev = c->n_src.as<int32_t>();
+        seg.n_src_host = 0;
+        seg.first = sg * seg_lanes;
+        seg.lanes = seg_lanes;
+        return seg;
+    };
+    // count pass: every leg's length, in the segment holding its source
+    for (int32_t sg = 0; sg < n_seg; ++sg) {
+        const wr::BfSegment seg = segment(sg);
+        RC(run_bf_segment(c, seg, s));
+        CK(wr::paths_launch(pl, seg, nullptr, nullptr, s));
+        c->launches++;
+    }
+    CK(wr::paths_launch_offsets(pl, c->node_offs_d.as<int64_t>(), s));
+    c->launches++;
+    int64_t total = 0;
+    CK(cudaMemcpyAsync(&total, c->node_offs_d.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, s));
+    if (ptr_kind == WR_HOST)
+        CK(cudaMemcpyAsync(node_offs, c->node_offs_d.p, (static_cast<size_t>(n) + 1) * 8, cudaMemcpyDeviceToHost, s));
+    else
+        CK(cudaMemcpyAsync(node_offs, c->node_offs_d.p, (static_cast<size_t>(n) + 1) * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    RC(take_device_error(c));
+    if (!nodes) return WR_OK;
+    if (total > max_nodes) return WR_ENOMEM;
+    int32_t* d_nodes = nodes;
+    if (ptr_kind == WR_HOST) {
+        RC(ensure(c->nodes_d, static_cast<size_t>(total) * 4 + 4));
+        d_nodes = c->nodes_d.as<int32_t>();
+    }
+    // write pass: the last segment's rows are still in place; earlier ones are computed again
+    for (int32_t sg = n_seg - 1; sg >= 0; --sg) {
+        const wr::BfSegment seg = segment(sg);
+        if (sg != n_seg - 1) RC(run_bf_segment(c, seg, s));
+        CK(wr::paths_launch(pl, seg, d_nodes, c->node_offs_d.as<int64_t>(), s));
+        c->launches++;
+    }
+    RC(end_call(c, s));
+    if (ptr_kind == WR_HOST) {
+        if (total) CK(cudaMemcpyAsync(nodes, d_nodes, static_cast<size_t>(total) * 4, cudaMemcpyDeviceToHost, s));
+        return finish_host_call(c, s);
+    }
     return WR_OK;
 }
 

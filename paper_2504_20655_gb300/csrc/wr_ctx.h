@@ -62,6 +62,9 @@ struct wr_ctx {
     wrc::DBuf hk_list, hk_count, hk_D, hk_h;  // Held-Karp orders (k > WR_MAX_K)
     int hk_blocks = 0;
     int route_mode = WR_ROUTE_TOUR;
+    wrc::DBuf g_in_ptr, g_in_src, g_in_w, leg_len, perm_in, node_offs_d, nodes_d;  // node-level routes
+    bool in_csr_uploaded = false;
+    bool positive_weights = false;  // every arc weight > 0: node-level routes are defined
     wrc::DBuf trace;          // sweep trace of the last Bellman-Ford segment
     int32_t trace_cap = 0;
     bool capturing = false;  // enqueueing into a CUDA graph: no host syncs, external timing events

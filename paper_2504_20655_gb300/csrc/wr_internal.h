@@ -196,6 +196,27 @@ cudaError_t tour_launch_finish(int32_t n, const int32_t* k_given, const TourBufs
                                int32_t* perm, int perm_stride, int32_t* status, cudaStream_t s);
 int tour_enum_blocks(int device);
 
+// Node-level routes (wr_paths.cu)
+struct PathsLaunch {
+    int32_t n;
+    const int64_t* offs;
+    const int32_t* picks;
+    const int32_t* perm;
+    const int32_t* order_status;
+    int open_path;
+    int32_t depot;
+    const int32_t* src_index;
+    const int64_t* in_ptr;  // in-arc CSR with node ids
+    const int32_t* in_src;
+    const int32_t* in_w;
+    int32_t V;
+    int32_t* leg_len;       // offs[n] + n entries
+};
+// count pass (nodes == nullptr) or write pass over the legs whose source lies in seg
+cudaError_t paths_launch(const PathsLaunch& l, const BfSegment& seg, int32_t* nodes, const int64_t* node_offs,
+                         cudaStream_t s);
+cudaError_t paths_launch_offsets(const PathsLaunch& l, int64_t* node_offs, cudaStream_t s);
+
 // Held-Karp for orders of WR_MAX_K+1 .. max_k picks (wr_hk.cu)
 cudaError_t hk_launch_select(int32_t n, const TourBufs& t, int32_t max_k, int32_t* list, int32_t* count,
                              cudaStream_t s);

@@ -28,7 +28,7 @@ DSTRIDE = 13
 
 EXPORTS = ["wr_create", "wr_destroy", "wr_strerror", "wr_sync", "wr_load_graph", "wr_route_orders", "wr_bf_rows",
            "wr_distance_rows", "wr_submatrix", "wr_tour_eval", "wr_tour_eval_static", "wr_get_stats",
-           "wr_get_tuning", "wr_set_tuning", "wr_set_trace", "wr_get_trace", "wr_autotune", "wr_set_route_mode",
+           "wr_get_tuning", "wr_set_tuning", "wr_set_trace", "wr_get_trace", "wr_autotune", "wr_set_route_mode", "wr_route_nodes",
            "wr_serve_create", "wr_serve_run", "wr_serve_get_stats", "wr_serve_destroy",
            "wr_plan_create", "wr_plan_launch", "wr_plan_sync", "wr_plan_get_stats", "wr_plan_destroy"]
 WR_STATIC_MAX_ORDERS = 4096
@@ -116,6 +116,7 @@ def load_library(path: str = LIB_PATH):
     L.wr_plan_destroy.restype = None
     L.wr_autotune.argtypes = [P, i32, P, P, I, i32, ctypes.POINTER(wr_tuning)]
     L.wr_set_route_mode.argtypes = [P, I]
+    L.wr_route_nodes.argtypes = [P, i32, P, P, P, P, P, i64, I, P]
     L.wr_serve_create.argtypes = [P, ctypes.POINTER(wr_serve_config), ctypes.POINTER(P)]
     L.wr_serve_run.argtypes = [P, i32, P, P, P, P, P, P, P]
     L.wr_serve_get_stats.argtypes = [P, ctypes.POINTER(wr_serve_stats)]
@@ -523,6 +524,23 @@ class Router:
 
     def plan(self, n_orders, max_picks):
         return Plan(self.ctx, n_orders, max_picks, self.device)
+
+    def route_nodes(self, offs, picks, perm, stream=None):
+        """Node-level routes of host orders and sequences: (node_offs, nodes)."""
+        offs = np.ascontiguousarray(offs, dtype=np.int64)
+        picks = np.ascontiguousarray(picks, dtype=np.int32)
+        perm = np.ascontiguousarray(perm[: int(offs[-1])], dtype=np.int32)
+        n = len(offs) - 1
+        node_offs = np.zeros(n + 1, np.int64)
+        c = ctypes.c_void_p
+        L = load_library()
+        _check(L.wr_route_nodes(self.ctx, n, c(offs.ctypes.data), c(picks.ctypes.data), c(perm.ctypes.data),
+                                c(node_offs.ctypes.data), None, 0, WR_HOST, _stream(stream)), "wr_route_nodes")
+        nodes = np.zeros(max(int(node_offs[-1]), 1), np.int32)
+        _check(L.wr_route_nodes(self.ctx, n, c(offs.ctypes.data), c(picks.ctypes.data), c(perm.ctypes.data),
+                                c(node_offs.ctypes.data), c(nodes.ctypes.data), int(node_offs[-1]), WR_HOST,
+                                _stream(stream)), "wr_route_nodes")
+        return node_offs, nodes[: int(node_offs[-1])]
 
     def set_route_mode(self, open_path: bool):
         """Closed tours through the depot (False, the default) or open paths through the picks (True)."""

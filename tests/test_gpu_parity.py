@@ -615,3 +615,32 @@ def test_route_open_paths(wr, orc):
     assert (sc == c[:n]).all() and (ss == s[:n]).all() and (sp[:o.offs[-1]] == p[:o.offs[-1]]).all()
     cc, _, _ = orc.route_orders(g, o, "dijkstra", "heldkarp", NT)
     assert (c[:n] <= cc).all() and (c[:n] < cc).any()
+
+
+def test_route_nodes_against_oracle(wr, orc):
+    """Node-level routes (closed tours and open paths, one segment and several) against
+    the oracle's walk of the same predecessor rule, element by element; an invalid
+    sequence gets no nodes; zero-weight arcs are refused."""
+    g, o = synth.medium_workload(n_orders=150)
+    for open_path, budget in ((False, 2 << 30), (True, 2 << 30), (False, 64 * g.V * 4)):
+        r = wr.Router(device=0, mem_budget_bytes=budget)
+        try:
+            r.load_graph(g)
+            r.set_route_mode(open_path)
+            cost, perm, status = r.route_orders(o.offs, o.picks)
+            perm = perm[:o.offs[-1]].copy()
+            perm[o.offs[5]] = perm[o.offs[5] + 1]  # order 5: not a permutation
+            node_offs, nodes = r.route_nodes(o.offs, o.picks, perm)
+        finally:
+            r.close()
+        want_offs, want_nodes = orc.route_nodes(g, o, perm, open_path=open_path, n_threads=NT)
+        assert (node_offs == want_offs).all() and (nodes == want_nodes).all(), (open_path, budget)
+        assert node_offs[6] == node_offs[5]
+    zg = random_graph(50, 150, 7, w_lo=0, w_hi=3)
+    r = wr.Router(device=0)
+    try:
+        r.load_graph(zg)
+        with pytest.raises(wr.WrError):
+            r.route_nodes(np.array([0, 1], np.int64), np.array([3], np.int32), np.array([0], np.int32))
+    finally:
+        r.close()
