@@ -53,6 +53,7 @@ def _configure(L):
     L.or_route_with_rows.argtypes = [i32, i32, i32, P, P, i32, P, P, I, I, P, P, P]
     L.or_factorial.argtypes = [i32]
     L.or_factorial.restype = i64
+    L.or_tour_clustered.argtypes = [i32, P, P, i32, I, P, P]
     L.or_patched_route_count.argtypes = [i32, P]
     L.or_patched_route_count.restype = i64
     return L
@@ -249,3 +250,46 @@ def route_nodes(g, orders, perm, open_path: bool = False, n_threads: int = 1):
         nodes += route
         node_offs.append(len(nodes))
     return np.array(node_offs, np.int64), np.array(nodes, np.int32)
+
+
+def tour_clustered(D, xy, m: int, open_path: bool = False):
+    """(status, cost, perm) of the cluster-patched route (Sec. 3) over D, with the k stops'
+    plan coordinates xy (k x 2) and at most m clusters."""
+    D = np.ascontiguousarray(D, dtype=np.int32)
+    xy = np.ascontiguousarray(xy, dtype=np.int32)
+    k = D.shape[0] - 1
+    cost = np.zeros(1, dtype=np.int32)
+    perm = np.zeros(max(k, 1), dtype=np.int32)
+    st = lib().or_tour_clustered(k, _p(D), _p(xy), int(m), int(bool(open_path)), _p(cost), _p(perm))
+    if st < 0:
+        raise RuntimeError(f"oracle clustered tour failed with {st}")
+    return int(st), int(cost[0]), perm[:k].copy()
+
+
+def route_orders_clustered(g, orders, xy, m: int, open_path: bool = False, n_threads: int = 1):
+    """The cluster-patched route of every order (rows by the oracle's Dijkstra); xy is the
+    (V, 2) plan coordinate array of the graph's nodes.  Orders above MAX_K picks or with a
+    node out of range are BADORDER."""
+    offs = np.asarray(orders.offs, dtype=np.int64)
+    picks = np.asarray(orders.picks, dtype=np.int64)
+    n = len(offs) - 1
+    cost = np.full(n, INF, np.int32)
+    status = np.full(n, BADORDER, np.int32)
+    perm = np.zeros(max(int(offs[-1]), 1), np.int32)
+    ok_nodes = picks[(picks >= 0) & (picks < g.V)]
+    nodes = np.unique(np.concatenate([[g.depot], ok_nodes])).astype(np.int32)
+    rows = sssp_rows(g, nodes, "dijkstra", n_threads)
+    for o in range(n):
+        b, e = int(offs[o]), int(offs[o + 1])
+        k = e - b
+        perm[b:e] = np.arange(k)
+        pts = picks[b:e]
+        if k < 1 or k > MAX_K or (pts < 0).any() or (pts >= g.V).any():
+            continue
+        allp = np.concatenate([[g.depot], pts])
+        idx = np.searchsorted(nodes, allp)
+        D = rows[idx][:, allp]
+        st, c, p = tour_clustered(D, np.asarray(xy)[pts], m, open_path)
+        status[o], cost[o] = st, c
+        perm[b:e] = p
+    return cost, perm[:int(offs[-1])], status

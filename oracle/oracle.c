@@ -323,6 +323,152 @@ int or_tour_held_karp(int32_t k, const int32_t* D, int32_t* cost, int32_t* perm)
     return OR_OK;
 }
 
+/* Cluster-patched approximate route (Sec. 3): the k stops are grouped into
+ * at most m clusters by k-means on their plan coordinates, an optimal open
+ * route is found inside every cluster, and the cluster routes are patched
+ * into one global route by trying every order of the clusters and every
+ * travel direction of each (m! x 2^m candidates; the theorem of Sec. 3
+ * counts m! x 2^(m-1) undirected ones).
+ *
+ * k-means: centres start at stop 0 and then, one by one, at the stop
+ * farthest (squared Euclidean) from the centres so far, ties to the lowest
+ * stop index, up to m centres (fewer if every remaining stop sits on a
+ * centre).  Lloyd steps assign every stop to its nearest centre (ties to the
+ * lowest centre) and move each non-empty centre to the mean of its stops,
+ * until no assignment changes (at most 64 steps).  Distances to a mean
+ * (Sx/c, Sy/c) are compared exactly as (c x - Sx)^2 + (c y - Sy)^2 over c^2.
+ * Cluster route: the lexicographically first optimal open route over the
+ * cluster's stops (legs between stops only).  Patching: the cheapest global
+ * route, the depot legs included for closed tours (free for open paths),
+ * ties to the lexicographically first stop sequence.  Clusters above 10
+ * stops make the order OR_BADORDER. */
+#define CL_MAX 10
+static i64 leg64(const int32_t* D, int32_t n, int32_t a, int32_t b) {
+    return D[a * n + b] == OR_INF ? BIG : (i64)D[a * n + b];
+}
+static int frac_less(i64 num1, i64 den1, i64 num2, i64 den2) { return num1 * den2 < num2 * den1; }
+
+int or_tour_clustered(int32_t k, const int32_t* D, const int32_t* xy, int32_t m, int open_path,
+                      int32_t* cost, int32_t* perm) {
+    if (k < 1 || k > OR_MAX_K || m < 1) return OR_BADORDER;
+    if (!range_check(k, D)) { *cost = OR_INF; identity(k, perm); return OR_RANGE; }
+    const int32_t n = k + 1;
+    /* k-means on the stops' coordinates */
+    int32_t centre_of_init[OR_MAX_K];
+    i64 Sx[OR_MAX_K], Sy[OR_MAX_K], cnt[OR_MAX_K];
+    int32_t nc = 0;
+    centre_of_init[nc] = 0;
+    Sx[nc] = xy[0]; Sy[nc] = xy[1]; cnt[nc] = 1; ++nc;
+    while (nc < m && nc < k) {
+        int32_t best_i = -1;
+        i64 best_d = -1;
+        for (int32_t i = 0; i < k; ++i) {
+            i64 dmin = -1;
+            for (int32_t c = 0; c < nc; ++c) {
+                i64 dx = (i64)xy[2 * i] - Sx[c], dy = (i64)xy[2 * i + 1] - Sy[c];
+                i64 d = dx * dx + dy * dy;
+                if (dmin < 0 || d < dmin) dmin = d;
+            }
+            if (dmin > best_d) { best_d = dmin; best_i = i; }
+        }
+        if (best_d <= 0) break;
+        centre_of_init[nc] = best_i;
+        Sx[nc] = xy[2 * best_i]; Sy[nc] = xy[2 * best_i + 1]; cnt[nc] = 1; ++nc;
+    }
+    int32_t assign[OR_MAX_K];
+    for (int32_t i = 0; i < k; ++i) assign[i] = -1;
+    for (int it = 0; it < 64; ++it) {
+        int changed = 0;
+        for (int32_t i = 0; i < k; ++i) {
+            int32_t bc = 0;
+            i64 bnum = 0, bden = 1;
+            for (int32_t c = 0; c < nc; ++c) {
+                i64 dx = cnt[c] * (i64)xy[2 * i] - Sx[c], dy = cnt[c] * (i64)xy[2 * i + 1] - Sy[c];
+                i64 num = dx * dx + dy * dy, den = cnt[c] * cnt[c];
+                if (c == 0 || frac_less(num, den, bnum, bden)) { bc = c; bnum = num; bden = den; }
+            }
+            if (assign[i] != bc) { assign[i] = bc; changed = 1; }
+        }
+        if (!changed) break;
+        for (int32_t c = 0; c < nc; ++c) {
+            i64 sx = 0, sy = 0, ct = 0;
+            for (int32_t i = 0; i < k; ++i)
+                if (assign[i] == c) { sx += xy[2 * i]; sy += xy[2 * i + 1]; ++ct; }
+            if (ct > 0) { Sx[c] = sx; Sy[c] = sy; cnt[c] = ct; }
+        }
+    }
+    (void)centre_of_init;
+    /* clusters in centre order, stops in increasing index */
+    int32_t members[OR_MAX_K][OR_MAX_K], size[OR_MAX_K], M = 0;
+    for (int32_t c = 0; c < nc; ++c) {
+        int32_t sz = 0;
+        for (int32_t i = 0; i < k; ++i)
+            if (assign[i] == c) members[M][sz++] = i;
+        if (sz == 0) continue;
+        if (sz > CL_MAX) { *cost = OR_INF; identity(k, perm); return OR_BADORDER; }
+        size[M++] = sz;
+    }
+    /* the first optimal open route inside every cluster */
+    int32_t route[OR_MAX_K][OR_MAX_K];
+    i64 fwd[OR_MAX_K], rev[OR_MAX_K];
+    for (int32_t c = 0; c < M; ++c) {
+        int32_t sz = size[c], p[OR_MAX_K], best_p[OR_MAX_K];
+        for (int32_t i = 0; i < sz; ++i) p[i] = i;
+        i64 best = BIG + 1;
+        do {
+            i64 t = 0;
+            for (int32_t i = 0; i + 1 < sz && t < BIG; ++i) {
+                i64 l = leg64(D, n, members[c][p[i]] + 1, members[c][p[i + 1]] + 1);
+                t = l >= BIG ? BIG : t + l;
+            }
+            if (t < best) { best = t; memcpy(best_p, p, sizeof(int32_t) * (size_t)sz); }
+        } while (next_perm(p, sz));
+        for (int32_t i = 0; i < sz; ++i) route[c][i] = members[c][best_p[i]];
+        fwd[c] = best;
+        i64 r = 0;
+        for (int32_t i = sz - 1; i > 0 && r < BIG; --i) {
+            i64 l = leg64(D, n, route[c][i] + 1, route[c][i - 1] + 1);
+            r = l >= BIG ? BIG : r + l;
+        }
+        rev[c] = r;
+    }
+    /* patching: every order of the clusters, every direction of each */
+    int32_t order[OR_MAX_K], seq[OR_MAX_K], best_seq[OR_MAX_K];
+    for (int32_t c = 0; c < M; ++c) order[c] = c;
+    i64 best = BIG;
+    int have = 0;
+    do {
+        for (uint32_t dir = 0; dir < (1u << M); ++dir) {
+            int32_t len = 0;
+            i64 t = 0;
+            for (int32_t q = 0; q < M && t < BIG; ++q) {
+                int32_t c = order[q], r = (dir >> q) & 1u;
+                int32_t head = r ? route[c][size[c] - 1] : route[c][0];
+                i64 inner = r ? rev[c] : fwd[c];
+                i64 link = q == 0 ? (open_path ? 0 : leg64(D, n, 0, head + 1)) : leg64(D, n, seq[len - 1] + 1, head + 1);
+                if (inner >= BIG || link >= BIG) { t = BIG; break; }
+                t += link + inner;
+                for (int32_t i = 0; i < size[c]; ++i) seq[len++] = r ? route[c][size[c] - 1 - i] : route[c][i];
+            }
+            if (t < BIG && !open_path) {
+                i64 back = leg64(D, n, seq[k - 1] + 1, 0);
+                t = back >= BIG ? BIG : t + back;
+            }
+            if (t >= BIG) continue;
+            int better = !have || t < best;
+            if (!better && t == best) {
+                for (int32_t i = 0; i < k; ++i)
+                    if (seq[i] != best_seq[i]) { better = seq[i] < best_seq[i]; break; }
+            }
+            if (better) { best = t; have = 1; memcpy(best_seq, seq, sizeof(int32_t) * (size_t)k); }
+        }
+    } while (next_perm(order, M));
+    if (!have) { *cost = OR_INF; identity(k, perm); return OR_UNREACHABLE; }
+    *cost = (int32_t)best;
+    for (int32_t i = 0; i < k; ++i) perm[i] = best_seq[i];
+    return OR_OK;
+}
+
 /* ------------------------------------------------------------------ */
 /* Whole path                                                          */
 /* ------------------------------------------------------------------ */

@@ -77,6 +77,12 @@ int or_sssp_rows(int32_t V, const int64_t* row_ptr, const int32_t* col, const in
 int or_tour_brute(int32_t k, const int32_t* D, int32_t* cost, int32_t* perm);
 int or_tour_held_karp(int32_t k, const int32_t* D, int32_t* cost, int32_t* perm);
 
+/* Cluster-patched approximate route of Sec. 3 over a (k+1)x(k+1) matrix D; xy holds
+ * the k stops' plan coordinates (x0, y0, x1, y1, ...); at most m clusters of at most
+ * 10 stops (more: OR_BADORDER); open_path != 0 leaves the depot legs out. */
+int or_tour_clustered(int32_t k, const int32_t* D, const int32_t* xy, int32_t m, int open_path,
+                      int32_t* cost, int32_t* perm);
+
 /* Whole path for a batch of orders; picks of order i are picks[offs[i]..offs[i+1]). */
 int or_route_orders(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
                     int32_t depot, int32_t n_orders, const int64_t* offs, const int32_t* picks,

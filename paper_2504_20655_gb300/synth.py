@@ -180,6 +180,27 @@ class Layout:
                 seq.append((0, s))
         return np.array(seq, dtype=np.int64)
 
+    def coords(self) -> np.ndarray:
+        """(V, 2) int32 plan coordinates: slot (a, f, s) at (a, s) -- both faces of a
+        position share it --, cross-aisle node X(a, j) at (a, b_j) with the boundaries on
+        the slot scale shifted by half a slot (2 b_j - 1 on a doubled scale), the depot
+        next to X(0, 0).  Positions are doubled so every coordinate is an integer."""
+        A, S, F, C = self.A, self.S, self.F, self.C
+        xy = np.zeros((self.V, 2), dtype=np.int32)
+        a = np.arange(A)[:, None, None]
+        s = np.arange(S)[None, None, :]
+        f = np.arange(F)[None, :, None]
+        ids = ((a * F + f) * S + s).reshape(-1)
+        xy[ids, 0] = np.broadcast_to(2 * a, (A, F, S)).reshape(-1)
+        xy[ids, 1] = np.broadcast_to(2 * s, (A, F, S)).reshape(-1)
+        b = np.array(self.boundaries())
+        for j in range(C):
+            xid = self.xnode(np.arange(A), j)
+            xy[xid, 0] = 2 * np.arange(A)
+            xy[xid, 1] = 2 * b[j] - 1
+        xy[self.depot] = (0, -3)
+        return xy
+
     def build(self) -> Graph:
         A, S, F, C = self.A, self.S, self.F, self.C
         seq = self.chain_sequence()                       # [S+C, 2]

@@ -37,6 +37,10 @@ MUTANTS = [
     ("dijkstra no decrease", "if (cand < d[v]) { d[v] = cand; hitem x",
      "if (cand < d[v] && d[v] == BIG) { d[v] = cand; hitem x"),
     ("range limit off", "D[i * n + j] > OR_LEG_MAX", "D[i * n + j] > OR_LEG_MAX + 1"),
+    ("patching forward only", "for (uint32_t dir = 0; dir < (1u << M); ++dir) {",
+     "for (uint32_t dir = 0; dir < 1u; ++dir) {"),
+    ("patching last minimiser", "int better = !have || t < best;", "int better = !have || t <= best;"),
+    ("patching no return leg", "t = back >= BIG ? BIG : t + back;", "t = back >= BIG ? BIG : t;"),
 ]
 
 
@@ -78,6 +82,33 @@ def pins_pass() -> bool:
                 b, h = oracle.tour(D, "brute"), oracle.tour(D, "heldkarp")
                 if b[:2] != h[:2] or (b[2] != h[2]).any():
                     return False
+        # cluster-patched route: one stop per cluster is exact; pairs patch to the best
+        # sequence that keeps every pair together
+        import itertools
+        for k in (3, 5):
+            for seed in range(3):
+                n = k + 1
+                D = synth.uniform_int(seed + 31 * k, n * n, 1, 3).reshape(n, n).astype(np.int32)  # ties
+                np.fill_diagonal(D, 0)
+                xy = np.stack([100 * np.arange(k), np.zeros(k, int)], axis=1).astype(np.int32)
+                c1, p1 = oracle.tour_clustered(D, xy, k, False)[1:]
+                c2, p2 = oracle.tour(D, "brute")[1:]
+                if c1 != c2 or p1.tolist() != p2.tolist():
+                    return False
+        xy = np.array([[0, 0], [1, 0], [200, 0], [201, 0]], np.int32)
+        for seed in range(6):
+            D = synth.uniform_int(seed + 77, 25, 1, 30 if seed % 2 else 2).reshape(5, 5).astype(np.int32)
+            np.fill_diagonal(D, 0)
+            best = None
+            for p in itertools.permutations(range(4)):
+                if abs(p.index(0) - p.index(1)) != 1 or abs(p.index(2) - p.index(3)) != 1:
+                    continue
+                c = int(D[0, p[0] + 1]) + sum(int(D[a + 1, b + 1]) for a, b in zip(p[:-1], p[1:])) + int(D[p[-1] + 1, 0])
+                if best is None or c < best[0]:
+                    best = (c, list(p))
+            st, c, pm = oracle.tour_clustered(D, xy, 2, False)
+            if (c, pm.tolist()) != best:
+                return False
         D = np.full((5, 5), 7, dtype=np.int32)
         np.fill_diagonal(D, 0)
         D[1, 2] = oracle.LEG_MAX + 1
