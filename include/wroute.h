@@ -294,6 +294,20 @@ void wr_serve_destroy(wr_server* sv);
 int wr_route_nodes(wr_ctx* ctx, int32_t n_orders, const int64_t* offs, const int32_t* picks, const int32_t* perm,
                    int64_t* node_offs, int32_t* nodes, int64_t max_nodes, int ptr_kind, void* cuda_stream);
 
+/* Cluster-patched approximate routing (Sec. 3; the paper's own method for large orders).
+ * With m > 0, wr_route_orders and plans created afterwards route every order of at most
+ * WR_MAX_K picks by: k-means (at most m clusters) on the picks' plan coordinates
+ * (wr_set_node_coords), the first optimal open route inside every cluster (at most 10
+ * picks, else WR_ORDER_BAD), and the cheapest patching over every order and direction of
+ * the clusters (depot legs included for WR_ROUTE_TOUR), ties to the lexicographically
+ * first sequence.  cost is the patched route's cost (not the optimum).  m = 0 (the
+ * default) routes exactly.  1 <= m <= 6, WR_EINVAL otherwise; wr_route_orders returns
+ * WR_EINVAL while m > 0 and no coordinates are set; servers refuse m > 0. */
+int wr_set_clusters(wr_ctx* ctx, int32_t m);
+/* Plan coordinates of the nodes, xy[2v], xy[2v+1] (int32, |x|, |y| <= 2^20), for the
+ * clustered routing; copied; cleared by wr_load_graph. */
+int wr_set_node_coords(wr_ctx* ctx, const int32_t* xy, int ptr_kind);
+
 /* Route shape of wr_route_orders, plans and servers created afterwards (WR_ROUTE_TOUR or
  * WR_ROUTE_OPEN); wr_tour_eval uses the matrices as given.  WR_EINVAL otherwise. */
 int wr_set_route_mode(wr_ctx* ctx, int mode);

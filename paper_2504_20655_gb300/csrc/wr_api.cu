@@ -322,8 +322,11 @@ int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_
                                    c->src_list.as<int32_t>(), c->n_src.as<int32_t>(), c->block_sums.as<int32_t>(), s,
                                    &c->launches));
     }
-    // orders above WR_MAX_K picks (when the context admits them): Held-Karp
-    const bool hk = c->cfg.max_k > WR_MAX_K;
+    // orders above WR_MAX_K picks (when the context admits them): Held-Karp; the clustered
+    // approximation takes at most WR_MAX_K picks
+    const bool clustered = c->cluster_m > 0;
+    if (clustered && c->coords.size() != 2 * static_cast<size_t>(V)) return WR_EINVAL;
+    const bool hk = c->cfg.max_k > WR_MAX_K && !clustered;
     if (hk) {
         RC(ensure(c->hk_list, static_cast<size_t>(n) * 4 + 4));
         RC(ensure(c->hk_count, 16));
@@ -363,6 +366,13 @@ int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_
         }
     }
     c->last.n_segments = n_seg;
+    if (clustered) {
+        PhaseTimer t(c, s, 4);
+        CK(wr::cluster_launch(n, tb, c->g_coords.as<int32_t>(), c->cluster_m, c->route_mode == WR_ROUTE_OPEN, o_cost,
+                              o_perm, o_status, s));
+        c->launches++;
+        return WR_OK;
+    }
     RC(run_tours(c, n, nullptr, tb, o_cost, o_perm, 0, o_status, s));
     if (hk) {
         // after the decode of the other orders: these write their own cost, perm and status
@@ -452,7 +462,7 @@ void wr_destroy(wr_ctx* c) {
                     &c->unit_off, &c->best, &c->unit_ctr, &c->out_cost, &c->out_perm, &c->out_status, &c->kbuf,
                     &c->dgiven, &c->src_in, &c->sub, &c->check, &c->trace,
                     &c->hk_list, &c->hk_count, &c->hk_D, &c->hk_h, &c->g_in_ptr, &c->g_in_src, &c->g_in_w,
-                    &c->leg_len, &c->perm_in, &c->node_offs_d, &c->nodes_d};
+                    &c->leg_len, &c->perm_in, &c->node_offs_d, &c->nodes_d, &c->g_coords};
     for (DBuf* b : bufs) b->release();
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     delete c;
@@ -498,6 +508,7 @@ int wr_load_graph(wr_ctx* c, int32_t V, int64_t E, const int64_t* row_ptr, const
     c->hg.E = g.E;
     c->hg.depot = g.depot;
     c->in_csr_uploaded = false;
+    c->coords.clear();  // coordinates belong to the previous graph
     c->positive_weights = std::all_of(c->hg.in_w.begin(), c->hg.in_w.end(), [](int32_t x) { return x > 0; });
     return finish_graph(c);
 }
@@ -944,6 +955,33 @@ int wr_route_nodes(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pic
     return WR_OK;
 }
 
+int wr_set_node_coords(wr_ctx* c, const int32_t* xy, int ptr_kind) {
+    if (!c || !xy) return WR_EINVAL;
+    RC(check_ptr_kind(ptr_kind));
+    if (!c->has_graph) return WR_ENOGRAPH;
+    RC(set_device(c));
+    const size_t n = 2 * static_cast<size_t>(c->dg.V);
+    c->coords.resize(n);
+    if (ptr_kind == WR_HOST) {
+        std::memcpy(c->coords.data(), xy, n * 4);
+    } else {
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(c->coords.data(), xy, n * 4, cudaMemcpyDeviceToHost));
+    }
+    for (size_t i = 0; i < n; ++i)
+        if (c->coords[i] < -(1 << 20) || c->coords[i] > (1 << 20)) {
+            c->coords.clear();
+            return WR_EINVAL;
+        }
+    return upload(c->g_coords, c->coords.data(), n * 4);
+}
+
+int wr_set_clusters(wr_ctx* c, int32_t m) {
+    if (!c || m < 0 || m > 6) return WR_EINVAL;
+    c->cluster_m = m;
+    return WR_OK;
+}
+
 int wr_set_route_mode(wr_ctx* c, int mode) {
     if (!c || (mode != WR_ROUTE_TOUR && mode != WR_ROUTE_OPEN)) return WR_EINVAL;
     c->route_mode = mode;
@@ -1107,8 +1145,10 @@ int wr_plan_create(wr_ctx* parent, int32_t n, int64_t max_picks, const int64_t* 
         wr_ctx* c = p->c;
         c->tune = parent->tune;
         c->route_mode = parent->route_mode;
+        c->cluster_m = parent->cluster_m;
         c->hg = parent->hg;  // host copy of the in-arc graph; re-partitioned and uploaded privately
         rc = finish_graph(c);
+        if (rc == WR_OK && !parent->coords.empty()) rc = wr_set_node_coords(c, parent->coords.data(), WR_HOST);
     }
     if (rc == WR_OK && cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) rc = WR_ECUDA;
     // one plain run sizes every buffer, so the captured run allocates nothing

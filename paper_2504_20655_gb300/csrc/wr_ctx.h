@@ -65,6 +65,9 @@ struct wr_ctx {
     wrc::DBuf g_in_ptr, g_in_src, g_in_w, leg_len, perm_in, node_offs_d, nodes_d;  // node-level routes
     bool in_csr_uploaded = false;
     bool positive_weights = false;  // every arc weight > 0: node-level routes are defined
+    int32_t cluster_m = 0;          // > 0: cluster-patched approximate routing with at most this many clusters
+    std::vector<int32_t> coords;    // plan coordinates (2 per node), host copy
+    wrc::DBuf g_coords;
     wrc::DBuf trace;          // sweep trace of the last Bellman-Ford segment
     int32_t trace_cap = 0;
     bool capturing = false;  // enqueueing into a CUDA graph: no host syncs, external timing events

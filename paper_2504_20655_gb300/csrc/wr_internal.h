@@ -217,6 +217,10 @@ cudaError_t paths_launch(const PathsLaunch& l, const BfSegment& seg, int32_t* no
                          cudaStream_t s);
 cudaError_t paths_launch_offsets(const PathsLaunch& l, int64_t* node_offs, cudaStream_t s);
 
+// Cluster-patched approximate routing (wr_cluster.cu); xy: 2 int32 plan coordinates per node
+cudaError_t cluster_launch(int32_t n, const TourBufs& t, const int32_t* xy, int32_t m, int open_path, int32_t* cost,
+                           int32_t* perm, int32_t* status, cudaStream_t s);
+
 // Held-Karp for orders of WR_MAX_K+1 .. max_k picks (wr_hk.cu)
 cudaError_t hk_launch_select(int32_t n, const TourBufs& t, int32_t max_k, int32_t* list, int32_t* count,
                              cudaStream_t s);

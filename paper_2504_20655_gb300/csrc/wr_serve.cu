@@ -349,6 +349,7 @@ int wr_serve_create(wr_ctx* parent, const wr_serve_config* cfg, wr_server** out)
     if (!parent || !cfg || !out) return WR_EINVAL;
     *out = nullptr;
     if (!parent->has_graph) return WR_ENOGRAPH;
+    if (parent->cluster_m > 0) return WR_EINVAL;  // the loop routes exactly
     if (!cfg->plain && (cfg->max_batch < 1 || cfg->max_batch_picks < WR_MAX_K || cfg->n_slots < 1 || cfg->n_slots > 8))
         return WR_EINVAL;
     RC(set_device(parent));

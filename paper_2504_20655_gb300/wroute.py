@@ -28,7 +28,8 @@ DSTRIDE = 13
 
 EXPORTS = ["wr_create", "wr_destroy", "wr_strerror", "wr_sync", "wr_load_graph", "wr_route_orders", "wr_bf_rows",
            "wr_distance_rows", "wr_submatrix", "wr_tour_eval", "wr_tour_eval_static", "wr_get_stats",
-           "wr_get_tuning", "wr_set_tuning", "wr_set_trace", "wr_get_trace", "wr_autotune", "wr_set_route_mode", "wr_route_nodes",
+           "wr_get_tuning", "wr_set_tuning", "wr_set_trace", "wr_get_trace", "wr_autotune", "wr_set_route_mode", "wr_route_nodes", "wr_set_clusters",
+           "wr_set_node_coords",
            "wr_serve_create", "wr_serve_run", "wr_serve_get_stats", "wr_serve_destroy",
            "wr_plan_create", "wr_plan_launch", "wr_plan_sync", "wr_plan_get_stats", "wr_plan_destroy"]
 WR_STATIC_MAX_ORDERS = 4096
@@ -116,6 +117,8 @@ def load_library(path: str = LIB_PATH):
     L.wr_plan_destroy.restype = None
     L.wr_autotune.argtypes = [P, i32, P, P, I, i32, ctypes.POINTER(wr_tuning)]
     L.wr_set_route_mode.argtypes = [P, I]
+    L.wr_set_clusters.argtypes = [P, i32]
+    L.wr_set_node_coords.argtypes = [P, P, I]
     L.wr_route_nodes.argtypes = [P, i32, P, P, P, P, P, i64, I, P]
     L.wr_serve_create.argtypes = [P, ctypes.POINTER(wr_serve_config), ctypes.POINTER(P)]
     L.wr_serve_run.argtypes = [P, i32, P, P, P, P, P, P, P]
@@ -541,6 +544,15 @@ class Router:
                                 c(node_offs.ctypes.data), c(nodes.ctypes.data), int(node_offs[-1]), WR_HOST,
                                 _stream(stream)), "wr_route_nodes")
         return node_offs, nodes[: int(node_offs[-1])]
+
+    def set_clusters(self, m: int, coords=None):
+        """Cluster-patched approximate routing with at most m clusters (0: exact); coords is
+        the (V, 2) int32 plan coordinate array of the loaded graph's nodes."""
+        if coords is not None:
+            xy = np.ascontiguousarray(coords, dtype=np.int32)
+            _check(load_library().wr_set_node_coords(self.ctx, xy.ctypes.data_as(ctypes.c_void_p), WR_HOST),
+                   "wr_set_node_coords")
+        _check(load_library().wr_set_clusters(self.ctx, int(m)), "wr_set_clusters")
 
     def set_route_mode(self, open_path: bool):
         """Closed tours through the depot (False, the default) or open paths through the picks (True)."""

@@ -644,3 +644,33 @@ def test_route_nodes_against_oracle(wr, orc):
             r.route_nodes(np.array([0, 1], np.int64), np.array([3], np.int32), np.array([0], np.int32))
     finally:
         r.close()
+
+
+def test_route_clustered_against_oracle(wr, orc):
+    """Cluster-patched approximate routing (Sec. 3) against the oracle's restatement of
+    the same steps, element by element, for closed tours and open paths and several m;
+    through a captured plan as well; never cheaper than the exact optimum."""
+    lay = synth.medium_layout()
+    g, o = synth.medium_workload(n_orders=300)
+    xy = lay.coords()
+    exact_c, _, _ = orc.route_orders(g, o, "dijkstra", "heldkarp", NT)
+    for m, open_path in ((3, False), (3, True), (2, False), (6, True)):
+        r = wr.Router(device=0)
+        try:
+            r.load_graph(g)
+            r.set_route_mode(open_path)
+            r.set_clusters(m, xy)
+            cost, perm, status = r.route_orders(o.offs, o.picks)
+            if m == 3 and not open_path:
+                plan = r.plan(o.n, int(o.offs[-1]))
+                try:
+                    pc, pp, ps = _plan_run(plan, o.offs, o.picks)
+                finally:
+                    plan.close()
+                assert (pc == cost).all() and (pp[:o.offs[-1]] == perm[:o.offs[-1]]).all() and (ps == status).all()
+        finally:
+            r.close()
+        c, p, s = orc.route_orders_clustered(g, o, xy, m, open_path, NT)
+        assert (status == s).all() and (cost == c).all() and (perm[:len(p)] == p).all(), (m, open_path)
+        if not open_path:
+            assert (c >= exact_c).all()
