@@ -198,7 +198,7 @@ int run_tours(wr_ctx* c, int32_t n, const int32_t* k_dev, const wr::TourBufs& tb
     {
         PhaseTimer t(c, s, 4);
         CK(wr::tour_launch_units(n, k_dev, tb, s, &c->launches));
-        const int upt = c->tune.enum_units > 0 ? c->tune.enum_units : 2;
+        const int upt = c->tune.enum_units > 0 ? c->tune.enum_units : 1;
         if (c->tune.enum_max_units_per_launch > 0 && !c->capturing) {
             long long total = 0;
             CK(cudaMemcpyAsync(&total, tb.unit_off + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -432,7 +432,7 @@ int wr_create(const wr_config* cfg, wr_ctx** out) {
     ctx->cfg.tune_path = nullptr;
     ctx->tune.run_target = 60;  // two segments of ~60 nodes (aisle faces) share a 128-slot tile
     ctx->tune.tile_cap = 128;
-    ctx->tune.enum_units = 2;
+    ctx->tune.enum_units = 1;
     ctx->tune.enum_max_units_per_launch = 0;
     ctx->tune.bf_warps = 0;
     ctx->tune.bf_tiling = 0;
@@ -1204,8 +1204,8 @@ int wr_plan_sync(wr_plan* p) {
 
 int wr_plan_get_stats(wr_plan* p, wr_stats* out) {
     if (!p || !out) return WR_EINVAL;
+    p->c->last.n_orders = p->n;  // the capture saw no host-side order count
     RC(wr_get_stats(p->c, out));
-    out->n_orders = p->n;
     return WR_OK;
 }
 

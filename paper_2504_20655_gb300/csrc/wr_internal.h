@@ -17,7 +17,7 @@ constexpr uint32_t TOUR_CAP = 1u << 27;       // unreachable legs are clamped to
 constexpr int DSTRIDE = 13;                   // D blocks are 13 x 13
 constexpr int DBLOCK = DSTRIDE * DSTRIDE;
 constexpr int TAIL = 5;                       // tail walked by one compile-time unrolled walk
-constexpr int UNIT_TAIL = 6;                  // a unit: a prefix and the 720 orderings of the last 6 picks (k >= 6)
+constexpr int UNIT_TAIL = 6;                  // the 720 orderings of six picks are walked from register tables
 constexpr int HK_MAX_K = 20;                  // orders of WR_MAX_K+1 .. 20 picks: Held-Karp
 constexpr int HK_DSTRIDE = HK_MAX_K + 1;
 constexpr int HK_DBLOCK = HK_DSTRIDE * HK_DSTRIDE;

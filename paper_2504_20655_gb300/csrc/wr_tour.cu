@@ -3,16 +3,17 @@
 //
 // Sec. 4.6 evaluates all n! route permutations, one thread per permutation
 // and an inner loop over the transitions.  Here a thread owns a contiguous
-// range of "units": a unit fixes the first k-5 picks of the sequence (its
-// prefix, decoded from the unit index in the factorial number system) and
-// covers the 5! = 120 orderings of the remaining five picks, all costed in
-// registers from a tiny table of the legs among those picks.  Every one of
-// the k! sequences still gets its full cost computed; shared partial sums
-// only avoid re-adding the same legs.  A thread keeps the minimum of each
-// unit; only when a unit beats the thread's best does it look for the
-// lowest-rank sequence attaining it.  Units are visited in increasing rank,
-// so strict '<' keeps the lowest rank.  Segment minima are merged into one
-// 64-bit word per order, (cost << 32) | rank, with atomicMin: the
+// range of "units": for k >= 7 a unit fixes the first k-7 picks of the
+// sequence (its prefix, decoded from the unit index in the factorial number
+// system) and covers the 5040 orderings of the remaining seven: each of the
+// seven next, then the 720 orderings of the other six, costed in registers
+// from tables of the legs among those six.  Every one of the k! sequences
+// still gets its own cost computed and compared; shared partial sums only
+// avoid re-adding the same legs.  A thread keeps the minimum of each block of
+// 120 sequences; only when a block beats the thread's best does it look for
+// the lowest-rank sequence attaining it.  Blocks are visited in increasing
+// rank, so the first match keeps the lowest rank.  Segment minima are merged
+// into one 64-bit word per order, (cost << 32) | rank, with atomicMin: the
 // lexicographic (cost, rank) minimum, independent of scheduling.
 #include "wr_device.cuh"
 
@@ -240,11 +241,11 @@ __device__ __forceinline__ int order_k(const TourBufs& t, const int32_t* k_given
 }
 
 __device__ __forceinline__ long long units_of(int k) {
-    // k! / 6! for k >= 6 (a unit is a prefix and the 720 orderings of the last six picks), else 1;
-    // orders above WR_MAX_K are solved by Held-Karp instead
+    // k! / 7! for k >= 7 (a unit is a prefix and the 5040 orderings of the last seven picks),
+    // else 1; orders above WR_MAX_K are solved by Held-Karp instead
     if (k > WR_MAX_K) return 0;
     long long u = 1;
-    for (int i = UNIT_TAIL + 1; i <= k; ++i) u *= i;
+    for (int i = UNIT_TAIL + 2; i <= k; ++i) u *= i;
     return u;
 }
 
@@ -324,52 +325,87 @@ struct Bits<0u> {
 
 __host__ __device__ constexpr int cfact(int n) { return n <= 1 ? 1 : n * cfact(n - 1); }
 
-// Walk of the prefix tree below a node: M = tail positions still to visit,
+// Walks of the prefix tree below a node: M = tail positions still to visit,
 // CUR = tail position just visited (-1: the prefix end x), IDX = lexicographic
-// index of the subtree's first sequence within the unit.  Children are visited
+// index of the subtree's first sequence within the walk.  Children are visited
 // in increasing position, i.e. lexicographic order of the sequences.
-// FIND = false: mn = min(mn, cost) over the leaves (fused add-min).
-// FIND = true:  idx = index of the first leaf whose cost equals target.
-template <int L, unsigned M, int CUR, int IDX, bool FIND>
-struct Walk;
+// Scan folds every leaf's cost into one of NACC accumulators with one fused
+// add-min; accumulator a takes the a-th contiguous range of leaves, so the
+// first accumulator holding a block's minimum names the range that holds its
+// lowest-rank minimiser.  Find sets idx to the index of the first leaf whose
+// cost equals target.
+constexpr int NACC = 8;
 
-template <int L, unsigned M, unsigned REST, int CUR, int IDX, bool FIND>
-struct EachChild {
-    static __device__ __forceinline__ void run(uint32_t acc, const Tab<L>& T, uint32_t& mn, int& idx) {
+template <int L>
+struct AccSpan {
+    static constexpr int value = (cfact(L) + NACC - 1) / NACC;  // leaves per accumulator
+};
+
+template <int L, unsigned M, int CUR, int IDX>
+struct Scan;
+
+template <int L, unsigned M, unsigned REST, int CUR, int IDX>
+struct ScanChildren {
+    static __device__ __forceinline__ void run(uint32_t acc, const Tab<L>& T, uint32_t (&mn)[NACC]) {
         if constexpr (REST != 0u) {
             constexpr int i = Bits<REST>::low;
             uint32_t leg;
             if constexpr (CUR < 0) leg = T.x[i];
             else leg = T.d[CUR][i];
-            Walk<L, (M & ~(1u << i)), i, IDX, FIND>::run(acc + leg, T, mn, idx);
-            constexpr int sub = cfact(Bits<M>::count - 1);
-            EachChild<L, M, (REST & ~(1u << i)), CUR, IDX + sub, FIND>::run(acc, T, mn, idx);
+            Scan<L, (M & ~(1u << i)), i, IDX>::run(acc + leg, T, mn);
+            ScanChildren<L, M, (REST & ~(1u << i)), CUR, IDX + cfact(Bits<M>::count - 1)>::run(acc, T, mn);
         }
     }
 };
 
-template <int L, unsigned M, int CUR, int IDX, bool FIND>
-struct Walk {
-    static __device__ __forceinline__ void run(uint32_t acc, const Tab<L>& T, uint32_t& mn, int& idx) {
+template <int L, unsigned M, int CUR, int IDX>
+struct Scan {
+    static __device__ __forceinline__ void run(uint32_t acc, const Tab<L>& T, uint32_t (&mn)[NACC]) {
         constexpr int n = Bits<M>::count;
+        constexpr int S = AccSpan<L>::value;
         if constexpr (n == 0) {
-            if constexpr (FIND) {
-                if (idx < 0 && acc + T.h[CUR] == mn) idx = IDX;
-            } else {
-                mn = __viaddmin_u32(acc, T.h[CUR], mn);
-            }
+            mn[IDX / S] = __viaddmin_u32(acc, T.h[CUR], mn[IDX / S]);
         } else if constexpr (n == 2 && CUR >= 0) {
             constexpr int b = Bits<M>::low;
             constexpr int c = Bits<(M & ~(1u << b))>::low;
-            if constexpr (FIND) {
-                if (idx < 0 && acc + T.t3[CUR][b][c] == mn) idx = IDX;
-                if (idx < 0 && acc + T.t3[CUR][c][b] == mn) idx = IDX + 1;
-            } else {
-                mn = __viaddmin_u32(acc, T.t3[CUR][b][c], mn);
-                mn = __viaddmin_u32(acc, T.t3[CUR][c][b], mn);
-            }
+            mn[IDX / S] = __viaddmin_u32(acc, T.t3[CUR][b][c], mn[IDX / S]);
+            mn[(IDX + 1) / S] = __viaddmin_u32(acc, T.t3[CUR][c][b], mn[(IDX + 1) / S]);
         } else {
-            EachChild<L, M, M, CUR, IDX, FIND>::run(acc, T, mn, idx);
+            ScanChildren<L, M, M, CUR, IDX>::run(acc, T, mn);
+        }
+    }
+};
+
+template <int L, unsigned M, int CUR, int IDX>
+struct Find;
+
+template <int L, unsigned M, unsigned REST, int CUR, int IDX>
+struct FindChildren {
+    static __device__ __forceinline__ void run(uint32_t acc, const Tab<L>& T, uint32_t target, int& idx) {
+        if constexpr (REST != 0u) {
+            constexpr int i = Bits<REST>::low;
+            uint32_t leg;
+            if constexpr (CUR < 0) leg = T.x[i];
+            else leg = T.d[CUR][i];
+            Find<L, (M & ~(1u << i)), i, IDX>::run(acc + leg, T, target, idx);
+            FindChildren<L, M, (REST & ~(1u << i)), CUR, IDX + cfact(Bits<M>::count - 1)>::run(acc, T, target, idx);
+        }
+    }
+};
+
+template <int L, unsigned M, int CUR, int IDX>
+struct Find {
+    static __device__ __forceinline__ void run(uint32_t acc, const Tab<L>& T, uint32_t target, int& idx) {
+        constexpr int n = Bits<M>::count;
+        if constexpr (n == 0) {
+            if (idx < 0 && acc + T.h[CUR] == target) idx = IDX;
+        } else if constexpr (n == 2 && CUR >= 0) {
+            constexpr int b = Bits<M>::low;
+            constexpr int c = Bits<(M & ~(1u << b))>::low;
+            if (idx < 0 && acc + T.t3[CUR][b][c] == target) idx = IDX;
+            if (idx < 0 && acc + T.t3[CUR][c][b] == target) idx = IDX + 1;
+        } else {
+            FindChildren<L, M, M, CUR, IDX>::run(acc, T, target, idx);
         }
     }
 };
@@ -398,37 +434,30 @@ __device__ __forceinline__ void load_tab(Tab<L>& T, const uint32_t* __restrict__
     }
 }
 
-template <int L, int I>
-struct TopLevel {
-    static __device__ __forceinline__ void run(uint32_t P, const Tab<L>& T, uint32_t (&mins)[L], int& idx) {
-        if constexpr (I < L) {
-            Walk<L, (((1u << L) - 1u) & ~(1u << I)), I, I * cfact(L - 1), false>::run(P + T.x[I], T, mins[I], idx);
-            TopLevel<L, I + 1>::run(P, T, mins, idx);
-        }
-    }
-};
+__device__ __forceinline__ uint32_t min_of(const uint32_t (&mn)[NACC]) {
+    uint32_t m = mn[0];
+#pragma unroll
+    for (int i = 1; i < NACC; ++i) m = min(m, mn[i]);
+    return m;
+}
 
-// One unit: the L! orderings of the tail after a prefix of cost P ending at x.
-// Folds (cost, rank) into (best_c, best_r) when the unit holds a sequence that
-// is lexicographically smaller in (cost, rank); rank0 = rank of the unit's first
-// sequence.
+// An order of k <= 5 picks: the L! orderings of all picks after the depot.
+// Folds (cost, rank) into (best_c, best_r) when the order holds a sequence
+// that is lexicographically smaller in (cost, rank).
 template <int L>
-__device__ __forceinline__ void unit_eval(const uint32_t* __restrict__ Dm, uint32_t P, int x, const int (&t)[TAIL],
-                                          unsigned rank0, uint32_t& best_c, unsigned& best_r) {
+__device__ __forceinline__ void unit_eval(const uint32_t* __restrict__ Dm, const int (&t)[TAIL], uint32_t& best_c,
+                                          unsigned& best_r) {
     Tab<L> T;
-    load_tab<L>(T, Dm, x, t);
-    uint32_t mins[L];
-    int idx = -1;
-    // one accumulator per first tail element: L independent add-min chains
+    load_tab<L>(T, Dm, 0, t);
+    uint32_t mins[NACC];
 #pragma unroll
-    for (int i = 0; i < L; ++i) mins[i] = 0xFFFFFFFFu;
-    TopLevel<L, 0>::run(P, T, mins, idx);
-    uint32_t mn = mins[0];
-#pragma unroll
-    for (int i = 1; i < L; ++i) mn = min(mn, mins[i]);
-    if (mn < best_c || (mn == best_c && rank0 < best_r)) {
-        Walk<L, (1u << L) - 1u, -1, 0, true>::run(P, T, mn, idx);
-        const unsigned r = rank0 + static_cast<unsigned>(idx);
+    for (int i = 0; i < NACC; ++i) mins[i] = 0xFFFFFFFFu;
+    Scan<L, (1u << L) - 1u, -1, 0>::run(0u, T, mins);
+    const uint32_t mn = min_of(mins);
+    if (mn < best_c || (mn == best_c && 0u < best_r)) {
+        int idx = -1;
+        Find<L, (1u << L) - 1u, -1, 0>::run(0u, T, mn, idx);
+        const unsigned r = static_cast<unsigned>(idx);
         if (mn < best_c || r < best_r) {
             best_c = mn;
             best_r = r;
@@ -436,14 +465,14 @@ __device__ __forceinline__ void unit_eval(const uint32_t* __restrict__ Dm, uint3
     }
 }
 
-__device__ __forceinline__ void unit_eval_dispatch(int L, const uint32_t* Dm, uint32_t P, int x, const int (&t)[TAIL],
-                                                   unsigned rank0, uint32_t& best_c, unsigned& best_r) {
+__device__ __forceinline__ void unit_eval_dispatch(int L, const uint32_t* Dm, const int (&t)[TAIL], uint32_t& best_c,
+                                                   unsigned& best_r) {
     switch (L) {
-        case 1: unit_eval<1>(Dm, P, x, t, rank0, best_c, best_r); break;
-        case 2: unit_eval<2>(Dm, P, x, t, rank0, best_c, best_r); break;
-        case 3: unit_eval<3>(Dm, P, x, t, rank0, best_c, best_r); break;
-        case 4: unit_eval<4>(Dm, P, x, t, rank0, best_c, best_r); break;
-        default: unit_eval<5>(Dm, P, x, t, rank0, best_c, best_r); break;
+        case 1: unit_eval<1>(Dm, t, best_c, best_r); break;
+        case 2: unit_eval<2>(Dm, t, best_c, best_r); break;
+        case 3: unit_eval<3>(Dm, t, best_c, best_r); break;
+        case 4: unit_eval<4>(Dm, t, best_c, best_r); break;
+        default: unit_eval<5>(Dm, t, best_c, best_r); break;
     }
 }
 
@@ -453,15 +482,53 @@ __device__ __forceinline__ int nth_bit(unsigned m, int n) {
     return __ffs(m) - 1;
 }
 
-// One 720-sequence unit (k >= 6): the prefix of cost P ends at x; s[0..5]
-// are the remaining picks in increasing order.  Tables of the six: legs
-// between them (d6), from x (xl), and every three-leg suffix ending at the
-// depot (t3f[a][b][c] = D[s_a][s_b] + D[s_b][s_c] + D[s_c][0]), built once per
-// unit.  The j-th block of 120 sequences starts with s_j and walks the other
-// five as a 5-tail whose tables are compile-time views of the six's.
+// Lexicographic index, within [lo, hi), of the first ordering of the five
+// picks packed in `five` (4-bit matrix indices, increasing) whose cost after
+// a prefix of cost acc ending at s, back to the depot, equals target.  Runs
+// at most once per thread and unit range, for the block range that recorded
+// the thread's best, so it is a plain loop over D: small code, off the hot
+// path.  Its sums are the hot path's sums regrouped, and exact (no term
+// reaches 2^28, at most 13 terms).
+__device__ __noinline__ int first_of_five(const uint32_t* __restrict__ Dm, uint32_t acc, int s, unsigned five,
+                                          uint32_t target, int lo, int hi) {
+    for (int idx = lo; idx < hi; ++idx) {
+        unsigned rest = five;
+        int r = idx, f = 24, prev = s;
+        uint32_t c = acc;
+        for (int pos = 0; pos < 5; ++pos) {
+            const int d = r / f;
+            r -= d * f;
+            const int e = static_cast<int>((rest >> (4 * d)) & 15u);
+            rest = (rest & ((1u << (4 * d)) - 1u)) | ((rest >> (4 * d + 4)) << (4 * d));
+            c += __ldg(Dm + prev * DSTRIDE + e);
+            prev = e;
+            if (pos < 3) f /= (4 - pos);
+        }
+        c += __ldg(Dm + prev * DSTRIDE);
+        if (c == target) return idx;
+    }
+    return lo;  // not reached: target is the cost of one of these orderings
+}
+
+// The block range that holds a thread's best so far: the five picks after s_J
+// and the cost through s_J, to find the exact rank once at the end.
+struct BlockRec {
+    uint32_t acc;
+    unsigned five, rank0;
+    int sj, lo;
+    bool have;
+};
+
+// One block of 120 sequences of a 720-sequence unit: the six remaining picks
+// s_0 < ... < s_5 (matrix indices packed in sp), s_J next, then the 120
+// orderings of the other five, walked over compile-time views of the six's
+// tables: legs between them (d6) and every three-leg suffix ending at the
+// depot (t3f[a][b][c] = D[s_a][s_b] + D[s_b][s_c] + D[s_c][0]).  acc = cost
+// of the sequence through s_J.
 template <int J>
-__device__ __forceinline__ void tail6_block(const uint32_t (&d6)[6][6], const uint32_t (&t3f)[6][6][6], uint32_t acc,
-                                            unsigned rank0, uint32_t& best_c, unsigned& best_r) {
+__device__ __forceinline__ void tail6_block(const uint32_t (&d6)[6][6], const uint32_t (&t3f)[6][6][6], unsigned sp,
+                                            uint32_t acc, unsigned rank0, uint32_t& cur_c, unsigned& cur_r,
+                                            BlockRec& rec) {
     Tab<5> T;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
@@ -483,154 +550,141 @@ __device__ __forceinline__ void tail6_block(const uint32_t (&d6)[6][6], const ui
                 if (a == b || a == c || b == c) continue;
                 T.t3[a][b][c] = t3f[a < J ? a : a + 1][b < J ? b : b + 1][c < J ? c : c + 1];
             }
-    uint32_t mins[5];
-    int idx = -1;
+    uint32_t mins[NACC];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) mins[i] = 0xFFFFFFFFu;
-    TopLevel<5, 0>::run(acc, T, mins, idx);
-    uint32_t mn = mins[0];
+    for (int i = 0; i < NACC; ++i) mins[i] = 0xFFFFFFFFu;
+    Scan<5, 31u, -1, 0>::run(acc, T, mins);
+    const uint32_t mn = min_of(mins);
+    // cur_r: the exact rank of the order's best, or the first rank of the
+    // recorded range; every later block starts above both
+    if (mn < cur_c || (mn == cur_c && rank0 < cur_r)) {
+        int a = NACC - 1;
 #pragma unroll
-    for (int i = 1; i < 5; ++i) mn = min(mn, mins[i]);
-    if (mn < best_c || (mn == best_c && rank0 < best_r)) {
-        Walk<5, 31u, -1, 0, true>::run(acc, T, mn, idx);
-        const unsigned r = rank0 + static_cast<unsigned>(idx);
-        if (mn < best_c || r < best_r) {
-            best_c = mn;
-            best_r = r;
-        }
+        for (int i = NACC - 2; i >= 0; --i)
+            if (mins[i] == mn) a = i;
+        cur_c = mn;
+        cur_r = rank0 + static_cast<unsigned>(a * AccSpan<5>::value);
+        rec.acc = acc;
+        rec.five = (sp & ((1u << (4 * J)) - 1u)) | ((sp >> (4 * J + 4)) << (4 * J));
+        rec.sj = static_cast<int>((sp >> (4 * J)) & 15u);
+        rec.rank0 = rank0;
+        rec.lo = a * AccSpan<5>::value;
+        rec.have = true;
     }
 }
 
 template <int J>
 struct Tail6 {
     static __device__ __forceinline__ void run(const uint32_t (&d6)[6][6], const uint32_t (&t3f)[6][6][6],
-                                               const uint32_t (&xl)[6], uint32_t P, unsigned rank0, uint32_t& best_c,
-                                               unsigned& best_r) {
+                                               const uint32_t (&xl)[6], unsigned sp, uint32_t P, unsigned rank0,
+                                               uint32_t& cur_c, unsigned& cur_r, BlockRec& rec) {
         if constexpr (J < 6) {
-            tail6_block<J>(d6, t3f, P + xl[J], rank0 + 120u * J, best_c, best_r);
-            Tail6<J + 1>::run(d6, t3f, xl, P, rank0, best_c, best_r);
+            tail6_block<J>(d6, t3f, sp, P + xl[J], rank0 + 120u * J, cur_c, cur_r, rec);
+            Tail6<J + 1>::run(d6, t3f, xl, sp, P, rank0, cur_c, cur_r, rec);
         }
     }
 };
 
+// One 720-sequence unit: a prefix of cost P ending at x (0: the depot), then
+// the 720 orderings of the six picks in `six` (a bit set of matrix indices);
+// rank0 = rank of its first sequence.
+__device__ __forceinline__ void unit720(const uint32_t* __restrict__ Dm, uint32_t P, int x, unsigned six,
+                                        unsigned rank0, uint32_t& cur_c, unsigned& cur_r, BlockRec& rec) {
+    int sx[UNIT_TAIL];
+    unsigned sp = 0;
+#pragma unroll
+    for (int i = 0; i < UNIT_TAIL; ++i) {
+        sx[i] = __ffs(six) - 1;
+        six &= six - 1;
+        sp |= static_cast<unsigned>(sx[i]) << (4 * i);
+    }
+    uint32_t d6[6][6], xl[6], h6[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const uint32_t* row = Dm + sx[i] * DSTRIDE;
+        xl[i] = __ldg(Dm + x * DSTRIDE + sx[i]);
+        h6[i] = __ldg(row);
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+            if (q != i) d6[i][q] = __ldg(row + sx[q]);
+    }
+    uint32_t t3f[6][6][6];
+#pragma unroll
+    for (int b = 0; b < 6; ++b)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            if (b == c) continue;
+            const uint32_t tail2 = d6[b][c] + h6[c];
+#pragma unroll
+            for (int a = 0; a < 6; ++a)
+                if (a != b && a != c) t3f[a][b][c] = d6[a][b] + tail2;
+        }
+    Tail6<0>::run(d6, t3f, xl, sp, P, rank0, cur_c, cur_r, rec);
+}
+
 // Enumerate the units [ulo, uhi) of one order (k picks, D block Dm); fold
-// the best (cost, rank) into *out.
-__device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, long long ulo, long long uhi,
+// the best (cost, rank) into *out.  k <= 5: one unit of k! sequences; k = 6:
+// one unit of 720; k >= 7: unit u fixes the first k-7 picks (the factorial
+// digits of u) and covers the 5040 orderings of the remaining seven, as seven
+// 720-sequence units (each of the seven, in increasing order, next).
+__device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, unsigned ulo, unsigned uhi,
                                  unsigned long long* out, long long& seqs) {
     // start from the order's current best (a stale read is only larger, so safe)
     const unsigned long long g0 = __ldcg(out);
     uint32_t best_c = static_cast<uint32_t>(g0 >> 32);
     unsigned best_r = static_cast<unsigned>(g0 & 0xFFFFFFFFull);
     if (k < UNIT_TAIL) {
-        // one unit: the k! orderings of all picks after the depot
         int t[TAIL];
 #pragma unroll
         for (int i = 0; i < TAIL; ++i) t[i] = i < k ? i + 1 : 0;
-        unit_eval_dispatch(k, Dm, 0u, 0, t, 0u, best_c, best_r);
+        unit_eval_dispatch(k, Dm, t, best_c, best_r);
         seqs += k == 1 ? 1 : k == 2 ? 2 : k == 3 ? 6 : k == 4 ? 24 : 120;
     } else {
-        const int p = k - UNIT_TAIL;  // prefix length
-        // decode the first unit: digits c_i in radix (k - i), i < p
-        unsigned digits = 0;  // 4 bits per position
-        {
-            long long u = ulo;
-            for (int i = p - 1; i >= 0; --i) {
-                const int r = k - i;
-                const int c = static_cast<int>(u % r);
-                u /= r;
-                digits |= static_cast<unsigned>(c) << (4 * i);
-            }
-        }
-        unsigned elems = 0;  // 4 bits per position: pick index 1..k
+        const int q = k - UNIT_TAIL - 1;  // picks fixed by the unit index; -1 for k = 6
         const unsigned all = ((1u << k) - 1u) << 1;
-        unsigned avail_last = all;  // available set before the last prefix position
-        uint32_t S = 0;             // cost through position p-2
-        int pos_dirty = 0;          // first prefix position to recompute
-        for (long long u = ulo; u < uhi; ++u) {
-            // (re)build prefix positions >= pos_dirty
-            if (pos_dirty < p) {
-                unsigned av = all;
-                uint32_t cost = 0;
-                int prev = 0;
-                for (int i = 0; i < p; ++i) {
-                    int e;
-                    if (i < pos_dirty) {
-                        e = (elems >> (4 * i)) & 15;
-                    } else {
-                        e = nth_bit(av, (digits >> (4 * i)) & 15);
-                        elems = (elems & ~(15u << (4 * i))) | (static_cast<unsigned>(e) << (4 * i));
-                    }
-                    if (i == p - 1) {
-                        avail_last = av;
-                        S = cost;
-                    }
-                    cost += __ldg(Dm + prev * DSTRIDE + e);
-                    av &= ~(1u << e);
-                    prev = e;
+        const int nsub = q < 0 ? 1 : UNIT_TAIL + 1;
+        BlockRec rec;
+        rec.have = false;
+#pragma unroll 1
+        for (unsigned u = ulo; u < uhi; ++u) {
+            unsigned avail = all;
+            uint32_t S = 0;
+            int last = 0;
+            if (q > 0) {
+                // factorial digits of u, position i in radix k - i
+                unsigned digits = 0, v = u;
+                for (int i = q - 1; i >= 0; --i) {
+                    const unsigned r = static_cast<unsigned>(k - i);
+                    digits |= (v % r) << (4 * i);
+                    v /= r;
+                }
+                for (int i = 0; i < q; ++i) {
+                    const int e = nth_bit(avail, static_cast<int>((digits >> (4 * i)) & 15u));
+                    S += __ldg(Dm + last * DSTRIDE + e);
+                    avail &= ~(1u << e);
+                    last = e;
                 }
             }
-            int x = 0;
-            uint32_t P = 0;
-            unsigned tailset = all;
-            if (p > 0) {
-                x = (elems >> (4 * (p - 1))) & 15;
-                const int xp = p >= 2 ? ((elems >> (4 * (p - 2))) & 15) : 0;
-                P = S + __ldg(Dm + xp * DSTRIDE + x);
-                tailset = avail_last & ~(1u << x);
-            }
-            // the six remaining picks in increasing order and their tables
-            int sx[UNIT_TAIL];
-#pragma unroll
-            for (int i = 0; i < UNIT_TAIL; ++i) {
-                sx[i] = __ffs(tailset) - 1;
-                tailset &= tailset - 1;
-            }
-            uint32_t d6[6][6], xl[6], h6[6];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                const uint32_t* row = Dm + sx[i] * DSTRIDE;
-                xl[i] = __ldg(Dm + x * DSTRIDE + sx[i]);
-                h6[i] = __ldg(row);
-#pragma unroll
-                for (int q = 0; q < 6; ++q)
-                    if (q != i) d6[i][q] = __ldg(row + sx[q]);
-            }
-            // three-leg suffixes over the six: t3f[a][b][c] = D[a][b] + D[b][c] + D[c][depot]
-            uint32_t t3f[6][6][6];
-#pragma unroll
-            for (int b = 0; b < 6; ++b)
-#pragma unroll
-                for (int c = 0; c < 6; ++c) {
-                    if (b == c) continue;
-                    const uint32_t tail2 = d6[b][c] + h6[c];
-#pragma unroll
-                    for (int a = 0; a < 6; ++a)
-                        if (a != b && a != c) t3f[a][b][c] = d6[a][b] + tail2;
+            unsigned m = avail;
+#pragma unroll 1
+            for (int j = 0; j < nsub; ++j) {
+                int x = 0;
+                unsigned six = all;
+                uint32_t P = 0;
+                if (q >= 0) {
+                    x = __ffs(m) - 1;
+                    m &= m - 1;
+                    six = avail & ~(1u << x);
+                    P = S + __ldg(Dm + last * DSTRIDE + x);
                 }
-            Tail6<0>::run(d6, t3f, xl, P, static_cast<unsigned>(u) * 720u, best_c, best_r);
-            // advance the mixed-radix counter of the prefix
-            if (p > 0) {
-                int i = p - 1;
-                for (; i >= 0; --i) {
-                    const unsigned c = ((digits >> (4 * i)) & 15) + 1;
-                    if (c < static_cast<unsigned>(k - i)) {
-                        digits = (digits & ~(15u << (4 * i))) | (c << (4 * i));
-                        break;
-                    }
-                    digits &= ~(15u << (4 * i));
-                }
-                if (i == p - 1) {
-                    // only the last prefix element moves: next available pick above it
-                    const unsigned above = avail_last & ~((2u << x) - 1u);
-                    const int e = __ffs(above) - 1;
-                    elems = (elems & ~(15u << (4 * (p - 1)))) | (static_cast<unsigned>(e) << (4 * (p - 1)));
-                    pos_dirty = p;
-                } else {
-                    pos_dirty = i < 0 ? 0 : i;
-                }
+                unit720(Dm, P, x, six, (u * static_cast<unsigned>(nsub) + static_cast<unsigned>(j)) * 720u, best_c,
+                        best_r, rec);
             }
         }
-        seqs += (uhi - ulo) * 720;
+        seqs += static_cast<long long>(uhi - ulo) * 720 * nsub;
+        if (rec.have)
+            best_r = rec.rank0 + static_cast<unsigned>(first_of_five(Dm, rec.acc, rec.sj, rec.five, best_c, rec.lo,
+                                                                     rec.lo + AccSpan<5>::value));
     }
     const unsigned long long packed = (static_cast<unsigned long long>(best_c) << 32) | best_r;
     if (packed < g0) atomicMin(out, packed);
@@ -662,7 +716,8 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_kernel(int32_t n, const int
             const long long ob = __ldg(t.unit_off + o), oe = __ldg(t.unit_off + o + 1);
             const long long stop = min(ue, oe);
             const int k = order_k(t, k_given, o);
-            enum_order_range(t.D + static_cast<int64_t>(o) * DBLOCK, k, u - ob, stop - ob, t.best + o, seqs);
+            enum_order_range(t.D + static_cast<int64_t>(o) * DBLOCK, k, static_cast<unsigned>(u - ob),
+                             static_cast<unsigned>(stop - ob), t.best + o, seqs);
             u = stop;
         }
     }

@@ -396,6 +396,7 @@ def test_plan_graph_matches_direct_calls(router, orc):
             assert (status[n:] == 2).all()  # padding: empty orders are WR_ORDER_BAD
         st = plan.stats()
         assert st["n_orders"] == 520 and st["sequences"] > 0
+        assert st["n_sources"] == len(np.unique(np.append(a.picks, g.depot)))  # depot + distinct picks
     finally:
         plan.close()
     c, p, s = orc.route_orders(g, a.subset(np.arange(0, 60)), "dijkstra", "heldkarp", NT)
