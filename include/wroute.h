@@ -96,8 +96,10 @@ typedef struct {
     int32_t enum_max_units_per_launch; /* rank-range segment: units per enumeration launch (0 = all) */
     int32_t bf_warps;       /* CTA tiling: warps sharing one sweep tile, 4 or 8 (0 = 8 for 512-node tiles, else 4) */
     int32_t bf_tiling;      /* sweep tiling: 1 = one warp per tile (lane = source; tile_cap 128 or 256),
-                               2 = one CTA per tile (quads of sources per warp); 0 = 1 up to 256-slot
-                               tiles, else 2.  Defaults: tile_cap 128, run_target 60, warp tiles */
+                               2 = one CTA per tile (quads of sources per warp), 3 = warp tiles driven by
+                               an asynchronous worklist instead of sweeps (tile_cap 128 or 256; no sweep
+                               trace, wr_stats.sweeps = 0); 0 = 1 up to 256-slot tiles, else 2.
+                               Defaults: tile_cap 128, run_target 60, warp tiles */
 } wr_tuning;
 
 /* Counters of the last call (device-timed with CUDA events on its stream). */

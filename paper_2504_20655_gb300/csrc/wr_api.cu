@@ -70,10 +70,15 @@ int upload(DBuf& b, const void* src, size_t bytes) {
     return WR_OK;
 }
 
+// Tiling in effect: the tuned one, else warp tiles up to 256 slots and CTA tiles above.
+int resolved_tiling(const wr_ctx* c) {
+    return c->tune.bf_tiling != 0 ? c->tune.bf_tiling : (c->hp.tile_cap <= 256 ? 1 : 2);
+}
+
 // Sweep kernel for the context's tiling and tile size.
 int prepare_sweeps(wr_ctx* c) {
-    const int tiling = c->tune.bf_tiling != 0 ? c->tune.bf_tiling : (c->hp.tile_cap <= 256 ? 1 : 2);
-    if (tiling == 1) return wr::bf_prepare_warp(c->hp.tile_cap, c->device, &c->bf_info);
+    const int tiling = resolved_tiling(c);
+    if (tiling == 1 || tiling == 3) return wr::bf_prepare_warp(c->hp.tile_cap, tiling == 3, c->device, &c->bf_info);
     return wr::bf_prepare(c->hp.tile_cap, c->tune.bf_warps, c->device, &c->bf_info);
 }
 
@@ -93,6 +98,8 @@ int upload_partition(wr_ctx* c) {
     RC(upload(c->g_halo_nodes, p.halo_nodes.data(), p.halo_nodes.size() * 4));
     RC(upload(c->g_rin_ptr, p.rin_ptr.data(), p.rin_ptr.size() * 4));
     RC(upload(c->g_rin_list, p.rin_list.data(), p.rin_list.size() * 4));
+    RC(upload(c->g_rout_ptr, p.rout_ptr.data(), p.rout_ptr.size() * 4));
+    RC(upload(c->g_rout_list, p.rout_list.data(), p.rout_list.size() * 4));
     RC(upload(c->g_run_of, p.run_of_node.data(), p.run_of_node.size() * 4));
     RC(upload(c->g_meta, p.run_meta_bytes.data(), p.run_meta_bytes.size() * 8));
     RC(upload(c->g_flags, p.run_flags.data(), p.run_flags.size() * 4));
@@ -114,6 +121,8 @@ int upload_partition(wr_ctx* c) {
     g.halo_nodes = c->g_halo_nodes.as<int32_t>();
     g.rin_ptr = c->g_rin_ptr.as<int32_t>();
     g.rin_list = c->g_rin_list.as<int32_t>();
+    g.rout_ptr = c->g_rout_ptr.as<int32_t>();
+    g.rout_list = c->g_rout_list.as<int32_t>();
     g.run_of_node = c->g_run_of.as<int32_t>();
     g.run_meta_bytes = c->g_meta.as<int64_t>();
     g.run_flags = c->g_flags.as<int32_t>();
@@ -146,6 +155,9 @@ int ensure_bf(wr_ctx* c, int32_t seg_lanes, bool with_rows) {
     RC(ensure(c->list1, items * 4));
     RC(ensure(c->counts, 16));
     RC(ensure(c->bar, sizeof(wr::GridBar)));
+    RC(ensure(c->ring, 2 * items * 4));
+    RC(ensure(c->ring_seq, 2 * items * 8));
+    RC(ensure(c->qctl, 4 * sizeof(unsigned long long)));
     return WR_OK;
 }
 
@@ -162,6 +174,10 @@ wr::BfWork bf_work(wr_ctx* c, int32_t seg_lanes) {
     w.stats = c->stats.as<unsigned long long>();
     w.trace = c->trace_cap > 0 ? c->trace.as<long long>() : nullptr;
     w.trace_cap = c->trace_cap > 0 ? c->trace_cap : 0;
+    w.ring = c->ring.as<int32_t>();
+    w.ring_seq = c->ring_seq.as<unsigned long long>();
+    w.qctl = c->qctl.as<unsigned long long>();
+    w.async = resolved_tiling(c) == 3;
     return w;
 }
 
@@ -198,7 +214,7 @@ int run_tours(wr_ctx* c, int32_t n, const int32_t* k_dev, const wr::TourBufs& tb
     {
         PhaseTimer t(c, s, 4);
         CK(wr::tour_launch_units(n, k_dev, tb, s, &c->launches));
-        const int upt = c->tune.enum_units > 0 ? c->tune.enum_units : 1;
+        const int upt = c->tune.enum_units > 0 ? c->tune.enum_units : 2;
         if (c->tune.enum_max_units_per_launch > 0 && !c->capturing) {
             long long total = 0;
             CK(cudaMemcpyAsync(&total, tb.unit_off + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -252,7 +268,8 @@ bool valid_tuning(const wr_tuning* t) {
         return false;
     if (t->bf_warps != 0 && t->bf_warps != 4 && t->bf_warps != 8) return false;
     if (t->tile_cap >= 512 && t->bf_warps == 4) return false;
-    if (t->bf_tiling < 0 || t->bf_tiling > 2 || (t->bf_tiling == 1 && t->tile_cap > 256)) return false;
+    if (t->bf_tiling < 0 || t->bf_tiling > 3 || ((t->bf_tiling == 1 || t->bf_tiling == 3) && t->tile_cap > 256))
+        return false;
     return true;
 }
 
@@ -432,7 +449,7 @@ int wr_create(const wr_config* cfg, wr_ctx** out) {
     ctx->cfg.tune_path = nullptr;
     ctx->tune.run_target = 60;  // two segments of ~60 nodes (aisle faces) share a 128-slot tile
     ctx->tune.tile_cap = 128;
-    ctx->tune.enum_units = 1;
+    ctx->tune.enum_units = 2;
     ctx->tune.enum_max_units_per_launch = 0;
     ctx->tune.bf_warps = 0;
     ctx->tune.bf_tiling = 0;
@@ -456,8 +473,8 @@ void wr_destroy(wr_ctx* c) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     DBuf* bufs[] = {&c->g_desc, &c->g_ref, &c->g_w, &c->g_arc2, &c->g_run_ptr, &c->g_run_x, &c->g_halo_ptr, &c->g_halo_nodes, &c->g_rin_ptr,
-                    &c->g_rin_list, &c->g_run_of, &c->g_meta, &c->g_flags, &c->g_ix, &c->g_xarc, &c->g_cdesc, &c->rows, &c->stamp, &c->list0, &c->list1,
-                    &c->counts, &c->bar, &c->err, &c->stats, &c->node_flag, &c->src_index, &c->src_list,
+                    &c->g_rin_list, &c->g_rout_ptr, &c->g_rout_list, &c->g_run_of, &c->g_meta, &c->g_flags, &c->g_ix, &c->g_xarc, &c->g_cdesc, &c->rows, &c->stamp, &c->list0, &c->list1,
+                    &c->counts, &c->bar, &c->ring, &c->ring_seq, &c->qctl, &c->err, &c->stats, &c->node_flag, &c->src_index, &c->src_list,
                     &c->n_src, &c->block_sums, &c->offs, &c->picks, &c->order_status, &c->order_flags, &c->D,
                     &c->unit_off, &c->best, &c->unit_ctr, &c->out_cost, &c->out_perm, &c->out_status, &c->kbuf,
                     &c->dgiven, &c->src_in, &c->sub, &c->check, &c->trace,
@@ -1056,7 +1073,7 @@ int wr_autotune(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* picks,
     };
     struct BfCand { int tiling, tile_cap, run_target; };
     // run_target about half the tile lets two segments (the faces of an aisle) share one tile
-    const BfCand bf[] = {{1, 256, 120}, {1, 128, 60}, {1, 256, 200}, {2, 256, 120}, {2, 256, 200}, {2, 512, 240}};
+    const BfCand bf[] = {{1, 256, 120}, {1, 128, 60}, {1, 256, 200}, {3, 128, 60}, {2, 256, 120}, {2, 256, 200}, {2, 512, 240}};
     wr_tuning best = start;
     float best_ms = 3.4e38f;
     int rc = WR_OK;
@@ -1076,7 +1093,7 @@ int wr_autotune(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* picks,
             best = t;
         }
     }
-    const int units[] = {1, 2, 4, 8};
+    const int units[] = {1, 2, 4, 8, 16};
     if (rc == WR_OK) rc = wr_set_tuning(c, &best);
     for (int u : units) {
         if (rc != WR_OK) break;

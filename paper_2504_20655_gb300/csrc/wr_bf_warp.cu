@@ -329,10 +329,263 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
     if (gtid == 0) atomicAdd(p.w.stats + 0, static_cast<unsigned long long>(sweep - 1));
 }
 
+// ---------------------------------------------------------------------------
+// Asynchronous worklist (bf_tiling 3): the same warp tiles with no sweeps and
+// no grid barriers after seeding.  Each (run, group) item is idle, queued,
+// running, or running and dirty (an input changed while it ran).  A warp pops
+// an item, relaxes its tile, and when a row dropped pushes the item itself
+// and the items of the runs it feeds (same group); an idle item is queued
+// once (its state is the dedup), a running one is marked dirty and requeued
+// by its runner when it finishes.  So no two warps ever hold the same tile,
+// and each own line has a single writer.  The pending count (queued plus
+// running items) rises before every push and falls only after the finished
+// item's pushes: it reaches zero exactly when nothing can change any more,
+// the fixpoint, which is when every warp stops.
+//
+// The queue is a ring of 2 x items slots with a sequence number per slot:
+// the producer of position t waits for seq == t, writes the item and
+// releases seq = t + 1; the consumer of position h waits for seq == h + 1,
+// takes the item and releases seq = h + cap for the producer one lap later.
+// Consumers may claim positions far ahead of the producers (idle warps); a
+// slot still serves its positions in order.  At most `items` entries wait at
+// any time, so the consumer of position t - cap has always claimed it when
+// the producer of t arrives, and every wait ends.  Every wait is also
+// bounded by max_spins (WR_ETIMEOUT), the kernel by a wall-clock limit, and
+// the total work by (V + 2) x items visits (WR_EINTERNAL).
+// ---------------------------------------------------------------------------
+enum : int32_t { Q_IDLE = 0, Q_QUEUED = 1, Q_RUNNING = 2, Q_DIRTY = 3 };
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+__device__ __forceinline__ bool q_fail(const BfParams& p, int code) {
+    atomicCAS(p.w.err, 0, code);
+    return false;
+}
+
+// Put an item (already counted as pending) into the next ring position.
+__device__ bool q_enqueue(const BfParams& p, int32_t item, unsigned long long cap) {
+    const unsigned long long t = atomicAdd(p.w.qctl + 1, 1ull);
+    const unsigned long long k = t % cap;
+    unsigned long long spins = 0;
+    while (ld_acquire_u64(p.w.ring_seq + k) != t) {  // the slot's previous lap is being taken
+        if (ld_volatile(p.w.err) != 0) return false;
+        if (++spins > p.w.max_spins) return q_fail(p, WR_ETIMEOUT);
+        __nanosleep(32);
+    }
+    *reinterpret_cast<volatile int32_t*>(p.w.ring + k) = item;
+    st_release_u64(p.w.ring_seq + k, t + 1);
+    return true;
+}
+
+// Request a (re)visit of an item: queue it if idle, mark it dirty if running.
+__device__ bool q_push(const BfParams& p, int32_t item, unsigned long long cap) {
+    int32_t* st = p.w.stamp + item;
+    for (int tries = 0; tries < 64; ++tries) {
+        const int32_t s = atomicCAS(st, Q_IDLE, Q_QUEUED);
+        if (s == Q_IDLE) {
+            atomicAdd(p.w.qctl + 2, 1ull);
+            return q_enqueue(p, item, cap);
+        }
+        if (s != Q_RUNNING) return true;  // queued or dirty: a visit is already due
+        if (atomicCAS(st, Q_RUNNING, Q_DIRTY) == Q_RUNNING) return true;
+        // it finished between the two steps: try again from idle
+    }
+    return q_fail(p, WR_EINTERNAL);
+}
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Next item for this warp (lane 0), or -1 when the worklist is exhausted or
+// failed.  Past t_stop (a wall-clock bound far above any legitimate run) the
+// kernel gives up with WR_ETIMEOUT rather than run on.
+__device__ int32_t q_pop(const BfParams& p, unsigned long long cap, unsigned long long limit, long long t_stop) {
+    const unsigned long long h = atomicAdd(p.w.qctl + 0, 1ull);
+    if (h >= limit) {
+        q_fail(p, WR_EINTERNAL);
+        return -1;
+    }
+    if (global_ns() > t_stop) {
+        q_fail(p, WR_ETIMEOUT);
+        return -1;
+    }
+    const unsigned long long k = h % cap;
+    unsigned long long spins = 0;
+    for (;;) {
+        if (ld_acquire_u64(p.w.ring_seq + k) == h + 1) {
+            const int32_t v = *reinterpret_cast<volatile int32_t*>(p.w.ring + k);
+            st_release_u64(p.w.ring_seq + k, h + cap);
+            atomicExch(p.w.stamp + v, Q_RUNNING);  // no one else writes a queued item's state
+            __threadfence();  // the producer's row stores are visible before the tile is staged
+            return v;
+        }
+        if (ld_volatile_u64(p.w.qctl + 2) == 0ull || ld_volatile(p.w.err) != 0) return -1;
+        if (++spins > p.w.max_spins) {
+            q_fail(p, WR_ETIMEOUT);
+            return -1;
+        }
+        __nanosleep(32);
+    }
+}
+
+// The whole warp requests visits of up to n items (cand(j), j < n), one per
+// lane and round: state changes in parallel, then one pending and one ring
+// reservation for all newly queued items of the round.
+template <class Cand>
+__device__ bool q_push_warp(const BfParams& p, int n, unsigned long long cap, int lane, Cand cand) {
+    for (int base = 0; base < n; base += 32) {
+        const int j = base + lane;
+        int32_t item = -1;
+        bool enq = false, ok = true;
+        if (j < n) {
+            item = cand(j);
+            int32_t* st = p.w.stamp + item;
+            int tries = 0;
+            for (; tries < 64; ++tries) {
+                const int32_t s = atomicCAS(st, Q_IDLE, Q_QUEUED);
+                if (s == Q_IDLE) {
+                    enq = true;
+                    break;
+                }
+                if (s != Q_RUNNING) break;  // queued or dirty: a visit is already due
+                if (atomicCAS(st, Q_RUNNING, Q_DIRTY) == Q_RUNNING) break;
+            }
+            if (tries == 64) ok = q_fail(p, WR_EINTERNAL);
+        }
+        const unsigned m = __ballot_sync(FULL_MASK, enq);
+        if (!__all_sync(FULL_MASK, ok)) return false;
+        if (m == 0u) continue;
+        unsigned long long t0 = 0;
+        if (lane == 0) {
+            atomicAdd(p.w.qctl + 2, static_cast<unsigned long long>(__popc(m)));
+            t0 = atomicAdd(p.w.qctl + 1, static_cast<unsigned long long>(__popc(m)));
+        }
+        t0 = __shfl_sync(FULL_MASK, t0, 0);
+        if (enq) {
+            const unsigned long long t = t0 + static_cast<unsigned long long>(__popc(m & lanemask_lt()));
+            const unsigned long long k = t % cap;
+            unsigned long long spins = 0;
+            while (ld_acquire_u64(p.w.ring_seq + k) != t) {
+                if (ld_volatile(p.w.err) != 0) {
+                    ok = false;
+                    break;
+                }
+                if (++spins > p.w.max_spins) {
+                    ok = q_fail(p, WR_ETIMEOUT);
+                    break;
+                }
+                __nanosleep(32);
+            }
+            if (ok) {
+                *reinterpret_cast<volatile int32_t*>(p.w.ring + k) = item;
+                st_release_u64(p.w.ring_seq + k, t + 1);
+            }
+        }
+        if (!__all_sync(FULL_MASK, ok)) return false;
+    }
+    return true;
+}
+
+// After the visit: requeue a dirty item, else retire it from the pending count.
+__device__ bool q_finish(const BfParams& p, int32_t item, unsigned long long cap) {
+    const int32_t s = atomicCAS(p.w.stamp + item, Q_RUNNING, Q_IDLE);
+    if (s == Q_DIRTY) {
+        atomicExch(p.w.stamp + item, Q_QUEUED);
+        return q_enqueue(p, item, cap);
+    }
+    atomicAdd(p.w.qctl + 2, ~0ull);  // -1
+    return true;
+}
+
 template <int TILE, int NW>
+__global__ void __launch_bounds__(32 * NW, 1) bf_warp_async_kernel(BfParams p) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpTile<TILE>& t = reinterpret_cast<WarpTile<TILE>*>(smem_raw)[warp];
+
+    const int n_lanes = segment_lanes(p.seg);
+    const int G = (n_lanes + 31) >> 5;
+    if (G == 0) return;  // same decision in every block
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthreads = gridDim.x * blockDim.x;
+    const unsigned long long n_items = static_cast<unsigned long long>(p.g.n_runs) * static_cast<unsigned long long>(G);
+    const unsigned long long cap = 2ull * n_items;
+    // pops: at most (V + 2) visits per item, plus one last empty pop per warp
+    const unsigned long long limit = (static_cast<unsigned long long>(p.g.V) + 2ull) * n_items +
+                                     static_cast<unsigned long long>(gridDim.x) * (blockDim.x >> 5);
+
+    // seeds: d[s][s] = 0 was written by the init; the tile holding each source
+    // and every tile it feeds get a first visit
+    for (int b = gtid; b < n_lanes; b += nthreads) {
+        const int r = __ldg(p.g.run_of_node + p.seg.src[p.seg.first + b]);
+        const int g = b >> 5;
+        if (!q_push(p, r * G + g, cap)) break;
+        const int q1 = __ldg(p.g.rout_ptr + r + 1);
+        for (int q = __ldg(p.g.rout_ptr + r); q < q1; ++q)
+            if (!q_push(p, __ldg(p.g.rout_list + q) * G + g, cap)) break;
+    }
+    if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) return;
+
+    // wall-clock bound: 1024 ns per allowed spin (about 17 s by default)
+    const long long t_stop = global_ns() + static_cast<long long>(min(p.w.max_spins, 1ull << 40) * 1024ull);
+    unsigned long long tiles = 0, nodes = 0, bytes = 0;
+    for (;;) {
+        int32_t item = -1;
+        if (lane == 0 && ld_volatile(p.w.err) == 0) item = q_pop(p, cap, limit, t_stop);
+        item = __shfl_sync(FULL_MASK, item, 0);
+        if (item < 0) break;
+        __syncwarp();
+        TileMeta m;
+        m.item = item;
+        m.r = item / G;
+        m.g = item - m.r * G;
+        m.rs = __ldg(p.g.run_seg + m.r);
+        m.len = m.rs.y + m.rs.w;
+        m.h0 = __ldg(p.g.halo_ptr + m.r);
+        m.hn = __ldg(p.g.halo_ptr + m.r + 1) - m.h0;
+        m.flags = __ldg(p.g.run_flags + m.r);
+        const bool ch = warp_tile<TILE>(p, m, t, lane);
+        bool ok = true;
+        if (ch) {
+            __threadfence();  // this lane's row stores before the pushes that announce them
+            __syncwarp();
+            // the item itself (running: marked dirty, so it is visited again) and the runs it feeds
+            const int q0 = __ldg(p.g.rout_ptr + m.r), nq = __ldg(p.g.rout_ptr + m.r + 1) - q0;
+            ok = q_push_warp(p, nq + 1, cap, lane,
+                             [&](int j) { return j == 0 ? item : __ldg(p.g.rout_list + q0 + j - 1) * G + m.g; });
+        }
+        if (lane == 0) {
+            if (ok) q_finish(p, item, cap);
+            ++tiles;
+            nodes += static_cast<unsigned long long>(m.len);
+            bytes += static_cast<unsigned long long>(__ldg(p.g.run_meta_bytes + m.r)) +
+                     256ull * static_cast<unsigned long long>(m.len);
+        }
+    }
+    if (lane == 0 && tiles) {
+        atomicAdd(p.w.stats + 1, tiles);
+        atomicAdd(p.w.stats + 2, nodes);
+        atomicAdd(p.w.stats + 3, bytes);
+    }
+}
+
+template <int TILE, int NW, bool ASYNC>
 static int prepare_warp_one(int device, BfLaunchInfo* info) {
     const size_t smem = sizeof(WarpTile<TILE>) * NW;
-    auto* fn = bf_warp_kernel<TILE, NW>;
+    auto* fn = ASYNC ? bf_warp_async_kernel<TILE, NW> : bf_warp_kernel<TILE, NW>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
         return WR_ECUDA;
     int occ = 0;
@@ -348,10 +601,10 @@ static int prepare_warp_one(int device, BfLaunchInfo* info) {
 }
 
 // Warps per CTA: as many 128- or 256-slot warp tiles as fit 227 KB of shared memory.
-int bf_prepare_warp(int tile_cap, int device, BfLaunchInfo* info) {
+int bf_prepare_warp(int tile_cap, bool async, int device, BfLaunchInfo* info) {
     switch (tile_cap) {
-        case 128: return prepare_warp_one<128, 10>(device, info);
-        case 256: return prepare_warp_one<256, 5>(device, info);
+        case 128: return async ? prepare_warp_one<128, 10, true>(device, info) : prepare_warp_one<128, 10, false>(device, info);
+        case 256: return async ? prepare_warp_one<256, 5, true>(device, info) : prepare_warp_one<256, 5, false>(device, info);
         default: return WR_EINVAL;
     }
 }

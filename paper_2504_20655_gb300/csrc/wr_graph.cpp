@@ -401,6 +401,17 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
         p.rin_list.insert(p.rin_list.end(), rin_tmp.begin(), rin_tmp.end());
         p.rin_ptr.push_back(static_cast<int32_t>(p.rin_list.size()));
     }
+    // runs fed by each run: rin transposed, ascending
+    p.rout_ptr.assign(static_cast<size_t>(p.n_runs) + 1, 0);
+    p.rout_list.assign(p.rin_list.size(), 0);
+    for (int32_t r = 0; r < p.n_runs; ++r)
+        for (int32_t q = p.rin_ptr[r]; q < p.rin_ptr[r + 1]; ++q) ++p.rout_ptr[p.rin_list[q] + 1];
+    for (int32_t r = 0; r < p.n_runs; ++r) p.rout_ptr[r + 1] += p.rout_ptr[r];
+    {
+        std::vector<int32_t> fill(p.rout_ptr.begin(), p.rout_ptr.end() - 1);
+        for (int32_t r = 0; r < p.n_runs; ++r)
+            for (int32_t q = p.rin_ptr[r]; q < p.rin_ptr[r + 1]; ++q) p.rout_list[fill[p.rin_list[q]]++] = r;
+    }
     int4 sentinel;
     sentinel.x = static_cast<int>(NO_CARRY);
     sentinel.y = static_cast<int>(NO_CARRY);

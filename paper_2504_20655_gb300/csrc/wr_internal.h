@@ -53,6 +53,8 @@ struct HostPartition {
     std::vector<int32_t> halo_nodes;
     std::vector<int32_t> rin_ptr;       // runs with an arc into the run
     std::vector<int32_t> rin_list;
+    std::vector<int32_t> rout_ptr;      // runs the run has an arc into (rin transposed)
+    std::vector<int32_t> rout_list;
     std::vector<int32_t> run_of_node;   // V
     std::vector<int32_t> slot_of_node;  // V: tile slot in its own run
     // per node v (plus a sentinel at V): x = weight of the carry arc from the
@@ -110,6 +112,8 @@ struct DevGraph {
     int32_t* halo_nodes = nullptr;
     int32_t* rin_ptr = nullptr;
     int32_t* rin_list = nullptr;
+    int32_t* rout_ptr = nullptr;   // runs fed by each run (rin transposed)
+    int32_t* rout_list = nullptr;
     int32_t* run_of_node = nullptr;
     int64_t* run_meta_bytes = nullptr;
     int32_t* run_flags = nullptr;
@@ -144,6 +148,11 @@ struct BfWork {
     unsigned long long* stats;  // [0] sweeps [1] tiles [2] node visits [3] bytes
     long long* trace;           // optional: per sweep t < trace_cap, [2t] = frontier tiles, [2t+1] = ns
     int trace_cap;
+    // asynchronous worklist (bf_tiling 3): stamp holds each item's state
+    int32_t* ring;                // 2 * n_runs * Gcap slots: queued items
+    unsigned long long* ring_seq;  // per slot: the ring position it serves next (see wr_bf_warp.cu)
+    unsigned long long* qctl;      // [0] pop counter, [1] push counter, [2] items queued or running
+    int async;                  // 1: the worklist kernel runs this segment (init fills the ring)
 };
 
 // launchers (wr_bf.cu)
@@ -155,8 +164,9 @@ struct BfLaunchInfo {
 };
 // picks the sweep kernel for (tile_cap, warps per CTA; 0 = default) and its co-resident grid
 int bf_prepare(int tile_cap, int warps, int device, BfLaunchInfo* info);
-// the warp-per-tile kernel (wr_bf_warp.cu) for tile_cap 128 or 256
-int bf_prepare_warp(int tile_cap, int device, BfLaunchInfo* info);
+// the warp-per-tile kernel (wr_bf_warp.cu) for tile_cap 128 or 256: sweeps with grid barriers, or
+// (async) one asynchronous worklist without sweeps
+int bf_prepare_warp(int tile_cap, bool async, int device, BfLaunchInfo* info);
 cudaError_t bf_launch_init(const DevGraph& g, const BfSegment& seg, const BfWork& w, cudaStream_t s);
 cudaError_t bf_launch_sweeps(const DevGraph& g, const BfSegment& seg, const BfWork& w,
                              const BfLaunchInfo& info, cudaStream_t s);

@@ -12,13 +12,86 @@
 
 using namespace wr;
 
+// One tile visit of item (run, 32-source group), as the kernel does it:
+// stage, forward pass, backward pass, write back.  Returns 1 if a row
+// dropped, 0 if not, 98 if the tile does not fit.
+static int relax_item(const HostPartition& p, std::vector<uint32_t>& rows, size_t ld, int G, int tile_cap, int item,
+                      std::vector<uint32_t>& tile) {
+    const int r = item / G, gg = item % G;
+    const int4 rs = p.run_seg[r];
+    const int len = rs.y + rs.w;
+    auto node = [&](int i) { return i < rs.y ? rs.x + i : rs.z + (i - rs.y); };
+    const int h0 = p.halo_ptr[r], hn = p.halo_ptr[r + 1] - h0;
+    if (len + hn > tile_cap) return 98;
+    bool changed = false;
+    for (int lane = 0; lane < 32; ++lane) {
+        const size_t c = static_cast<size_t>(gg) * 32 + lane;
+        for (int i = 0; i < len; ++i) tile[i] = rows[static_cast<size_t>(node(i)) * ld + c];
+        for (int h = 0; h < hn; ++h) tile[len + h] = rows[static_cast<size_t>(p.halo_nodes[h0 + h]) * ld + c];
+        std::vector<char> dirty(static_cast<size_t>(len), 0);
+        // The kernel walks each pass in chunks of SPAN node ids aligned to
+        // multiples of SPAN (ascending forward, descending backward): a node's non-carry
+        // arcs read the tile as it was when its chunk started, then
+        // the carry chain is solved in pass order.
+        constexpr int SPAN = 64;
+        std::vector<uint32_t> oth(static_cast<size_t>(len));
+        auto src = [&](uint32_t ref) {
+            return (ref & GLOBAL_REF) ? rows[static_cast<size_t>(ref & ~GLOBAL_REF) * ld + c] : tile[ref];
+        };
+        for (int c0 = 0; c0 < len; c0 += SPAN) {
+            const int c1 = std::min(len, c0 + SPAN);
+            for (int i = c0; i < c1; ++i) {
+                const int4 d = p.node_desc[node(i)];
+                uint32_t o = 0xFFFFFFFFu;
+                for (int a = d.z; a < d.w; ++a) o = std::min(src(p.arc_ref[a]) + p.arc_w[a], o);
+                oth[i] = o;
+            }
+            for (int i = c0; i < c1; ++i) {
+                const uint32_t cw = std::min(static_cast<uint32_t>(p.node_desc[node(i)].x), INF_U);
+                uint32_t best = std::min(tile[i], oth[i]);
+                if (i > 0) best = std::min(tile[i - 1] + cw, best);
+                if (best < tile[i]) { tile[i] = best; dirty[i] = 1; changed = true; }
+            }
+        }
+        for (int cb = ((len - 1) / SPAN) * SPAN; cb >= 0; cb -= SPAN) {
+            const int top = std::min(len - 1, cb + SPAN - 1), bot = cb - 1;
+            for (int i = top; i > bot; --i) {
+                const int4 d = p.node_desc[node(i)];
+                uint32_t o = 0xFFFFFFFFu;
+                for (int a = d.w; a < p.node_desc[node(i) + 1].z; ++a) o = std::min(tile[p.arc_ref[a]] + p.arc_w[a], o);
+                oth[i] = o;
+            }
+            for (int i = top; i > bot; --i) {
+                const uint32_t cw = std::min(static_cast<uint32_t>(p.node_desc[node(i)].y), INF_U);
+                uint32_t best = std::min(tile[i], oth[i]);
+                if (i + 1 < len) best = std::min(tile[i + 1] + cw, best);
+                if (best < tile[i]) { tile[i] = best; dirty[i] = 1; changed = true; }
+            }
+        }
+        for (int i = 0; i < len; ++i)
+            if (dirty[i]) rows[static_cast<size_t>(node(i)) * ld + c] = tile[i];
+    }
+    return changed ? 1 : 0;
+}
+
+static void setup(int V, long long E, const long long* rp, const int* col, const int* w, int run_target, int tile_cap,
+                  HostGraph& g, HostPartition& p, int& rc) {
+    rc = build_host_graph(V, E, reinterpret_cast<const int64_t*>(rp), col, w, 0, g);
+    if (!rc) build_partition(g, run_target, tile_cap, p);
+}
+
+static void copy_out(const std::vector<uint32_t>& rows, size_t ld, int V, int n_src, int* out) {
+    for (int b = 0; b < n_src; ++b)
+        for (int v = 0; v < V; ++v) out[static_cast<size_t>(b) * V + v] = static_cast<int>(rows[static_cast<size_t>(v) * ld + b]);
+}
+
 extern "C" int bfm_rows(int V, long long E, const long long* rp, const int* col, const int* w, int n_src,
                         const int* src, int run_target, int tile_cap, int* out, int* sweeps_out) {
     HostGraph g;
-    int rc = build_host_graph(V, E, reinterpret_cast<const int64_t*>(rp), col, w, 0, g);
-    if (rc) return rc;
     HostPartition p;
-    build_partition(g, run_target, tile_cap, p);
+    int rc = 0;
+    setup(V, E, rp, col, w, run_target, tile_cap, g, p, rc);
+    if (rc) return rc;
     const int G = (n_src + 31) / 32;
     const size_t ld = static_cast<size_t>(G) * 32;
     std::vector<uint32_t> rows(static_cast<size_t>(V) * ld, INF_U);
@@ -43,67 +116,77 @@ extern "C" int bfm_rows(int V, long long E, const long long* rp, const int* col,
         if (list.empty()) break;
         if (sweep > V + 1) return 99;
         for (int item : list) {
-            const int r = item / G, gg = item % G;
-            const int4 rs = p.run_seg[r];
-            const int len = rs.y + rs.w;
-            auto node = [&](int i) { return i < rs.y ? rs.x + i : rs.z + (i - rs.y); };
-            const int h0 = p.halo_ptr[r], hn = p.halo_ptr[r + 1] - h0;
-            if (len + hn > tile_cap) return 98;
-            bool changed = false;
-            for (int lane = 0; lane < 32; ++lane) {
-                const size_t c = static_cast<size_t>(gg) * 32 + lane;
-                for (int i = 0; i < len; ++i) tile[i] = rows[static_cast<size_t>(node(i)) * ld + c];
-                for (int h = 0; h < hn; ++h) tile[len + h] = rows[static_cast<size_t>(p.halo_nodes[h0 + h]) * ld + c];
-                std::vector<char> dirty(static_cast<size_t>(len), 0);
-                // The kernel walks each pass in chunks of SPAN node ids aligned to
-                // multiples of SPAN (ascending forward, descending backward): a node's non-carry
-                // arcs read the tile as it was when its chunk started, then
-                // the carry chain is solved in pass order.
-                constexpr int SPAN = 64;
-                std::vector<uint32_t> oth(static_cast<size_t>(len));
-                auto src = [&](uint32_t ref) {
-                    return (ref & GLOBAL_REF) ? rows[static_cast<size_t>(ref & ~GLOBAL_REF) * ld + c] : tile[ref];
-                };
-                for (int c0 = 0; c0 < len; c0 += SPAN) {
-                    const int c1 = std::min(len, c0 + SPAN);
-                    for (int i = c0; i < c1; ++i) {
-                        const int4 d = p.node_desc[node(i)];
-                        uint32_t o = 0xFFFFFFFFu;
-                        for (int a = d.z; a < d.w; ++a) o = std::min(src(p.arc_ref[a]) + p.arc_w[a], o);
-                        oth[i] = o;
-                    }
-                    for (int i = c0; i < c1; ++i) {
-                        const uint32_t cw = std::min(static_cast<uint32_t>(p.node_desc[node(i)].x), INF_U);
-                        uint32_t best = std::min(tile[i], oth[i]);
-                        if (i > 0) best = std::min(tile[i - 1] + cw, best);
-                        if (best < tile[i]) { tile[i] = best; dirty[i] = 1; changed = true; }
-                    }
-                }
-                for (int cb = ((len - 1) / SPAN) * SPAN; cb >= 0; cb -= SPAN) {
-                    const int top = std::min(len - 1, cb + SPAN - 1), bot = cb - 1;
-                    for (int i = top; i > bot; --i) {
-                        const int4 d = p.node_desc[node(i)];
-                        uint32_t o = 0xFFFFFFFFu;
-                        for (int a = d.w; a < p.node_desc[node(i) + 1].z; ++a) o = std::min(tile[p.arc_ref[a]] + p.arc_w[a], o);
-                        oth[i] = o;
-                    }
-                    for (int i = top; i > bot; --i) {
-                        const uint32_t cw = std::min(static_cast<uint32_t>(p.node_desc[node(i)].y), INF_U);
-                        uint32_t best = std::min(tile[i], oth[i]);
-                        if (i + 1 < len) best = std::min(tile[i + 1] + cw, best);
-                        if (best < tile[i]) { tile[i] = best; dirty[i] = 1; changed = true; }
-                    }
-                }
-                for (int i = 0; i < len; ++i)
-                    if (dirty[i]) rows[static_cast<size_t>(node(i)) * ld + c] = tile[i];
-            }
-            if (changed) stamp[item] = sweep + 1;
+            const int c = relax_item(p, rows, ld, G, tile_cap, item, tile);
+            if (c > 1) return c;
+            if (c) stamp[item] = sweep + 1;
         }
         list = build(sweep + 1);
     }
     *sweeps_out = sweep - 1;
-    for (int b = 0; b < n_src; ++b)
-        for (int v = 0; v < V; ++v) out[static_cast<size_t>(b) * V + v] = static_cast<int>(rows[static_cast<size_t>(v) * ld + b]);
+    copy_out(rows, ld, V, n_src, out);
+    return 0;
+}
+
+// The asynchronous worklist (bf_tiling 3) replayed one visit at a time: the
+// seeds are each source's run and the runs it feeds (rout); a visit that
+// drops a row requests the item itself and the items of the runs it feeds;
+// an item already waiting is not queued twice.  Visits are taken from the
+// waiting set in a seeded random order (order = 0: first in, first out), so
+// the fixpoint must not depend on the order.  visits_out: tile visits.
+// seed_fed = 0 leaves the fed runs out of the seeds (a planted omission).
+extern "C" int bfm_rows_worklist(int V, long long E, const long long* rp, const int* col, const int* w, int n_src,
+                                 const int* src, int run_target, int tile_cap, unsigned long long order,
+                                 int seed_fed, int* out, long long* visits_out) {
+    HostGraph g;
+    HostPartition p;
+    int rc = 0;
+    setup(V, E, rp, col, w, run_target, tile_cap, g, p, rc);
+    if (rc) return rc;
+    const int G = (n_src + 31) / 32;
+    const size_t ld = static_cast<size_t>(G) * 32;
+    const long long n_items = static_cast<long long>(p.n_runs) * G;
+    std::vector<uint32_t> rows(static_cast<size_t>(V) * ld, INF_U);
+    for (int b = 0; b < n_src; ++b) rows[static_cast<size_t>(src[b]) * ld + b] = 0;
+    std::vector<char> queued(static_cast<size_t>(n_items), 0);
+    std::vector<int> q;
+    auto push = [&](int item) {
+        if (!queued[item]) {
+            queued[item] = 1;
+            q.push_back(item);
+        }
+    };
+    auto push_fed = [&](int r, int gg) {
+        for (int k = p.rout_ptr[r]; k < p.rout_ptr[r + 1]; ++k) push(p.rout_list[k] * G + gg);
+    };
+    for (int b = 0; b < n_src; ++b) {
+        const int r = p.run_of_node[src[b]];
+        push(r * G + b / 32);
+        if (seed_fed) push_fed(r, b / 32);  // 0: a planted omission for the tests
+    }
+    std::vector<uint32_t> tile(static_cast<size_t>(tile_cap));
+    unsigned long long x = order;
+    size_t head = 0;
+    long long visits = 0;
+    while (head < q.size()) {
+        if (visits > (static_cast<long long>(V) + 2) * n_items) return 99;
+        if (order) {  // swap a random waiting item to the front
+            x ^= x << 13;
+            x ^= x >> 7;
+            x ^= x << 17;
+            std::swap(q[head], q[head + x % (q.size() - head)]);
+        }
+        const int item = q[head++];
+        queued[item] = 0;
+        const int c = relax_item(p, rows, ld, G, tile_cap, item, tile);
+        if (c > 1) return c;
+        ++visits;
+        if (c) {
+            push(item);
+            push_fed(item / G, item % G);
+        }
+    }
+    *visits_out = visits;
+    copy_out(rows, ld, V, n_src, out);
     return 0;
 }
 

@@ -130,3 +130,53 @@ def test_faces_share_tiles(model):
                          60, 128, out.ctypes.data_as(P))
     paired, halo_per_node, compact = out
     assert paired > 0.8 and halo_per_node < 0.25 and compact == 1.0
+
+
+def model_rows_worklist(model, g, src, run_target, tile_cap, order=0, seed_fed=1):
+    P = ctypes.c_void_p
+    rp, c, w = _arrs(g)
+    src = np.ascontiguousarray(src, np.int32)
+    out = np.empty((len(src), g.V), np.int32)
+    visits = np.zeros(1, np.int64)
+    rc = model.bfm_rows_worklist(g.V, ctypes.c_longlong(g.E), rp.ctypes.data_as(P), c.ctypes.data_as(P),
+                                 w.ctypes.data_as(P), len(src), src.ctypes.data_as(P), run_target, tile_cap,
+                                 ctypes.c_ulonglong(order), seed_fed, out.ctypes.data_as(P), visits.ctypes.data_as(P))
+    assert rc == 0, rc
+    return out, int(visits[0])
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_worklist_random_graphs_any_order(model, orc, seed):
+    """The asynchronous worklist's rules -- seeds are each source's run and the runs it
+    feeds, a visit that drops a row requests itself and the runs it feeds -- reach the
+    oracle's rows whatever order the waiting visits are taken in."""
+    V = [1, 2, 7, 33, 100, 257, 600, 1500][seed]
+    g = random_graph(V, max(1, 3 * V), seed + 300, w_lo=0, w_hi=20 if seed % 2 else 1000)
+    src = np.arange(0, V, max(1, V // 70), dtype=np.int32)
+    ref = orc.sssp_rows(g, src, "dijkstra", 4)
+    for rt, tc in TILINGS:
+        for order in (0, 0x9E3779B97F4A7C15 + seed, 12345 + seed):
+            out, _ = model_rows_worklist(model, g, src, rt, tc, order)
+            assert (out == ref).all(), (rt, tc, order)
+
+
+def test_worklist_medium_layout(model, orc):
+    g = synth.medium_layout().build()
+    src = synth.distinct_sources(64, g.n_slots, 17)
+    ref = orc.sssp_rows(g, src, "dijkstra", 4)
+    for order in (0, 7):
+        out, visits = model_rows_worklist(model, g, src, 60, 128, order)
+        assert (out == ref).all()
+        assert visits > 0
+
+
+def test_worklist_needs_the_fed_runs_in_its_seeds(model, orc):
+    """Planted omission: with one node per run a source's own visit changes nothing, so
+    without the runs it feeds among the seeds no distance beyond the sources is found."""
+    g = random_graph(100, 300, 301, w_lo=1, w_hi=20)
+    src = np.arange(0, 100, 7, dtype=np.int32)
+    ref = orc.sssp_rows(g, src, "dijkstra", 4)
+    out, _ = model_rows_worklist(model, g, src, 1, 128, 0, seed_fed=0)
+    assert not (out == ref).all()
+    out, _ = model_rows_worklist(model, g, src, 1, 128, 0, seed_fed=1)
+    assert (out == ref).all()

@@ -43,7 +43,7 @@ def test_bf_rows_tiny_all_sources(router, orc):
     assert st["sweeps"] >= 1 and st["bytes_alg"] > 0
 
 
-@pytest.fixture(params=[2, 1], ids=["cta_tiles", "warp_tiles"])
+@pytest.fixture(params=[2, 1, 3], ids=["cta_tiles", "warp_tiles", "warp_worklist"])
 def tiling(request, router):
     saved = router.tuning()
     router.set_tuning(bf_tiling=request.param)
@@ -106,7 +106,10 @@ def test_bf_rows_high_in_degree(router, orc, tiling):
                                   dict(run_target=200, tile_cap=256, bf_tiling=1),
                                   dict(run_target=256, tile_cap=256, bf_tiling=1),
                                   dict(run_target=96, tile_cap=128, bf_tiling=1),
-                                  dict(run_target=1, tile_cap=128, bf_tiling=1)])
+                                  dict(run_target=1, tile_cap=128, bf_tiling=1),
+                                  dict(run_target=60, tile_cap=128, bf_tiling=3),
+                                  dict(run_target=200, tile_cap=256, bf_tiling=3),
+                                  dict(run_target=1, tile_cap=128, bf_tiling=3)])
 def test_bf_rows_medium_tuning_invariant(router, orc, tune):
     g = synth.medium_layout().build()
     saved = router.tuning()
@@ -345,6 +348,8 @@ def test_sweep_trace(router, orc):
     frontiers summing to the tile visits, non-decreasing device times; tracing off
     leaves results unchanged."""
     g, o = synth.medium_workload(n_orders=64)
+    saved = router.tuning()
+    router.set_tuning(bf_tiling=1)  # the trace records sweeps: a sweep tiling
     router.load_graph(g)
     ref = router.route_orders(o.offs, o.picks)
     router.set_trace(4096)
@@ -354,6 +359,7 @@ def test_sweep_trace(router, orc):
         tr = router.trace()
     finally:
         router.set_trace(0)
+        router.set_tuning(**saved)
     for a, b in zip(ref, got):
         assert (np.asarray(a) == np.asarray(b)).all()
     assert st["n_segments"] == 1
