@@ -98,6 +98,8 @@ int upload_partition(wr_ctx* c) {
     RC(upload(c->g_halo_nodes, p.halo_nodes.data(), p.halo_nodes.size() * 4));
     RC(upload(c->g_rin_ptr, p.rin_ptr.data(), p.rin_ptr.size() * 4));
     RC(upload(c->g_rin_list, p.rin_list.data(), p.rin_list.size() * 4));
+    RC(upload(c->g_wx, p.wx.data(), p.wx.size() * sizeof(uint2)));
+    RC(upload(c->g_run_wx, p.run_wx.data(), p.run_wx.size() * sizeof(int4)));
     RC(upload(c->g_rout_ptr, p.rout_ptr.data(), p.rout_ptr.size() * 4));
     RC(upload(c->g_rout_list, p.rout_list.data(), p.rout_list.size() * 4));
     RC(upload(c->g_run_of, p.run_of_node.data(), p.run_of_node.size() * 4));
@@ -121,6 +123,8 @@ int upload_partition(wr_ctx* c) {
     g.halo_nodes = c->g_halo_nodes.as<int32_t>();
     g.rin_ptr = c->g_rin_ptr.as<int32_t>();
     g.rin_list = c->g_rin_list.as<int32_t>();
+    g.wx = c->g_wx.as<uint2>();
+    g.run_wx = c->g_run_wx.as<int4>();
     g.rout_ptr = c->g_rout_ptr.as<int32_t>();
     g.rout_list = c->g_rout_list.as<int32_t>();
     g.run_of_node = c->g_run_of.as<int32_t>();
@@ -153,7 +157,8 @@ int ensure_bf(wr_ctx* c, int32_t seg_lanes, bool with_rows) {
     RC(ensure(c->stamp, items * 4));
     RC(ensure(c->list0, items * 4));
     RC(ensure(c->list1, items * 4));
-    RC(ensure(c->counts, 16));
+    RC(ensure(c->list2, items * 4));
+    RC(ensure(c->counts, 32));
     RC(ensure(c->bar, sizeof(wr::GridBar)));
     RC(ensure(c->ring, 2 * items * 4));
     RC(ensure(c->ring_seq, 2 * items * 8));
@@ -166,6 +171,7 @@ wr::BfWork bf_work(wr_ctx* c, int32_t seg_lanes) {
     w.stamp = c->stamp.as<int32_t>();
     w.list0 = c->list0.as<int32_t>();
     w.list1 = c->list1.as<int32_t>();
+    w.list2 = c->list2.as<int32_t>();
     w.counts = c->counts.as<int32_t>();
     w.gcap = seg_lanes / 32;
     w.bar = c->bar.as<wr::GridBar>();
@@ -473,7 +479,7 @@ void wr_destroy(wr_ctx* c) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     DBuf* bufs[] = {&c->g_desc, &c->g_ref, &c->g_w, &c->g_arc2, &c->g_run_ptr, &c->g_run_x, &c->g_halo_ptr, &c->g_halo_nodes, &c->g_rin_ptr,
-                    &c->g_rin_list, &c->g_rout_ptr, &c->g_rout_list, &c->g_run_of, &c->g_meta, &c->g_flags, &c->g_ix, &c->g_xarc, &c->g_cdesc, &c->rows, &c->stamp, &c->list0, &c->list1,
+                    &c->g_rin_list, &c->g_rout_ptr, &c->g_rout_list, &c->g_wx, &c->g_run_wx, &c->g_run_of, &c->g_meta, &c->g_flags, &c->g_ix, &c->g_xarc, &c->g_cdesc, &c->rows, &c->stamp, &c->list0, &c->list1, &c->list2,
                     &c->counts, &c->bar, &c->ring, &c->ring_seq, &c->qctl, &c->err, &c->stats, &c->node_flag, &c->src_index, &c->src_list,
                     &c->n_src, &c->block_sums, &c->offs, &c->picks, &c->order_status, &c->order_flags, &c->D,
                     &c->unit_off, &c->best, &c->unit_ctr, &c->out_cost, &c->out_perm, &c->out_status, &c->kbuf,

@@ -32,6 +32,7 @@ template <int TILE>
 struct __align__(128) WarpTile {
     uint32_t rows[TILE][32];  // slot-major: rows[i][b] = source b of tile slot i (own nodes, then halo)
     uint4 desc[2 * TILE];     // compact descriptors of the run's nodes: forward, backward
+    uint2 wx[2 * TILE];       // the run's extra arcs: forward, then backward
 };
 
 constexpr int BLK = 4;  // nodes per pipelined block
@@ -40,6 +41,7 @@ constexpr int BLK = 4;  // nodes per pipelined block
 struct TileMeta {
     int item, r, g, len, h0, hn, flags;
     int4 rs;  // {a0, alen, b0, blen}
+    int4 rx;  // extras {first entry, forward count, backward count, 0}
 };
 
 __device__ __forceinline__ TileMeta load_meta(const BfParams& p, const int32_t* list, int it, int G) {
@@ -52,7 +54,26 @@ __device__ __forceinline__ TileMeta load_meta(const BfParams& p, const int32_t* 
     m.h0 = __ldg(p.g.halo_ptr + m.r);
     m.hn = __ldg(p.g.halo_ptr + m.r + 1) - m.h0;
     m.flags = __ldg(p.g.run_flags + m.r);
+    m.rx = __ldg(p.g.run_wx + m.r);
     return m;
+}
+
+// Fold n extra arcs into the tile before a pass: each {dst | src << 16, w}
+// lowers line dst by line src + w in this lane's column.  Returns changed bits.
+template <int TILE>
+__device__ __forceinline__ uint32_t fold_extras(WarpTile<TILE>& t, int e0, int n, int lane) {
+    char* cb = reinterpret_cast<char*>(&t.rows[0][lane]);
+    uint32_t chg = 0;
+#pragma unroll 1
+    for (int e = e0; e < e0 + n; ++e) {
+        const uint2 x = t.wx[e];
+        uint32_t* dst = reinterpret_cast<uint32_t*>(cb + (x.x & 0xFFFFu));
+        const uint32_t cur = *dst;
+        const uint32_t v = __viaddmin_u32(*reinterpret_cast<const uint32_t*>(cb + (x.x >> 16)), x.y, cur);
+        *dst = v;
+        chg |= v ^ cur;
+    }
+    return chg;
 }
 
 // One block's inputs: current value, the best over its non-carry arcs, carry weight.
@@ -202,10 +223,13 @@ __device__ __forceinline__ bool warp_tile(const BfParams& p, const TileMeta& m, 
     uint32_t* rows = p.seg.rows;
     const bool compact = (m.flags & RUN_COMPACT) != 0;
     const int sub = lane >> 3, part = (lane & 7) * 4;  // 8 lanes x 16 bytes per line, 4 lines per instruction
-    // group A: descriptors, halo lines, the first segment's lines
-    if (compact)
+    // group A: descriptors, extras, halo lines, the first segment's lines
+    const int nx = m.rx.y + m.rx.z;
+    if (compact) {
         for (int e = lane; e < 2 * m.len; e += 32)
             cp_async16(&t.desc[e], p.g.cdesc + 2 * static_cast<int64_t>(run_node(m.rs, e >> 1)) + (e & 1));
+        for (int e = lane; 2 * e < nx; e += 32) cp_async16(&t.wx[2 * e], p.g.wx + m.rx.x + 2 * e);
+    }
     for (int h = sub; h < m.hn; h += 4) {
         const int node = __ldg(p.g.halo_nodes + m.h0 + h);
         cp_async16(&t.rows[m.len + h][part], rows + static_cast<int64_t>(node) * ld + lane_off + part);
@@ -222,11 +246,21 @@ __device__ __forceinline__ bool warp_tile(const BfParams& p, const TileMeta& m, 
     }
     cp_async_commit();
 
-    uint32_t chg;
+    uint32_t chg = 0;
     if (compact) {
-        cp_async_wait_pending(1);  // group A landed: the forward pass starts on the first segment
-        __syncwarp();
-        chg = warp_pass<TILE, true>(t, m.len, m.rs.y, lane);
+        int alen = m.rs.y;
+        if (m.rx.y > 0) {
+            // forward extras may touch either segment: everything lands first
+            cp_async_wait_pending(0);
+            __syncwarp();
+            chg = fold_extras<TILE>(t, 0, m.rx.y, lane);
+            alen = m.len;
+        } else {
+            cp_async_wait_pending(1);  // group A landed: the forward pass starts on the first segment
+            __syncwarp();
+        }
+        chg |= warp_pass<TILE, true>(t, m.len, alen, lane);
+        if (m.rx.z > 0) chg |= fold_extras<TILE>(t, m.rx.y, m.rx.z, lane);
         chg |= warp_pass<TILE, false>(t, m.len, m.rs.y, lane);
     } else {
         cp_async_wait_pending(0);
@@ -245,6 +279,44 @@ __device__ __forceinline__ bool warp_tile(const BfParams& p, const TileMeta& m, 
     return changed;
 }
 
+// Push-based frontier of the warp sweeps: sweep s visits list s mod 3.  A
+// tile that changed in sweep s adds itself and the tiles of the runs it feeds
+// (same group) to list s+1; stamp[item] = the last sweep it was listed for,
+// raised with atomicMax, so an item is listed once per sweep.  List s+2 (read
+// in sweep s-1) is cleared during sweep s, before anyone appends to it in
+// sweep s+1.  One grid barrier per sweep.
+__device__ __forceinline__ int32_t* frontier_list(const BfParams& p, int s) {
+    const int i = s % 3;
+    return i == 0 ? p.w.list0 : i == 1 ? p.w.list1 : p.w.list2;
+}
+
+// One thread lists one item for sweep s (seeding).
+__device__ __forceinline__ void frontier_push(const BfParams& p, int32_t item, int s) {
+    if (atomicMax(p.w.stamp + item, s) < s) frontier_list(p, s)[atomicAdd(p.w.counts + s % 3, 1)] = item;
+}
+
+// The warp lists up to n items cand(j) for sweep s: one item per lane and
+// round, one list reservation per round.
+template <class Cand>
+__device__ __forceinline__ void frontier_push_warp(const BfParams& p, int n, int s, int lane, Cand cand) {
+    int32_t* list = frontier_list(p, s);
+    for (int base = 0; base < n; base += 32) {
+        const int j = base + lane;
+        int32_t item = -1;
+        bool add = false;
+        if (j < n) {
+            item = cand(j);
+            add = atomicMax(p.w.stamp + item, s) < s;
+        }
+        const unsigned m = __ballot_sync(FULL_MASK, add);
+        if (m == 0u) continue;
+        int pos = 0;
+        if (lane == 0) pos = atomicAdd(p.w.counts + s % 3, __popc(m));
+        pos = __shfl_sync(FULL_MASK, pos, 0);
+        if (add) list[pos + __popc(m & lanemask_lt())] = item;
+    }
+}
+
 template <int TILE, int NW>
 __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -257,20 +329,21 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthreads = gridDim.x * blockDim.x;
 
-    // seeds: writing d[s][s] = 0 is the change of "sweep 0": the tile holding
-    // each source gets stamp 1, and sweep 1 visits it and the tiles it feeds
+    // seeds: writing d[s][s] = 0 was the change of "sweep 0": sweep 1 visits
+    // the tile holding each source and the tiles it feeds
     for (int b = gtid; b < n_lanes; b += nthreads) {
         const int r = __ldg(p.g.run_of_node + p.seg.src[p.seg.first + b]);
-        p.w.stamp[static_cast<int64_t>(r) * G + (b >> 5)] = 1;
+        const int g = b >> 5;
+        frontier_push(p, r * G + g, 1);
+        const int q1 = __ldg(p.g.rout_ptr + r + 1);
+        for (int q = __ldg(p.g.rout_ptr + r); q < q1; ++q) frontier_push(p, __ldg(p.g.rout_list + q) * G + g, 1);
     }
-    if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) return;
-    build_list(p, G, 1, true, p.w.list0, p.w.counts + 0);
     if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) return;
 
     unsigned long long tiles = 0, nodes = 0, bytes = 0;
-    int cur = 0;
     int sweep = 1;
     for (;; ++sweep) {
+        const int cur = sweep % 3;
         const int cnt = ld_volatile(p.w.counts + cur);
         if (gtid == 0 && sweep <= p.w.trace_cap) {
             long long tm;
@@ -284,16 +357,18 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
             break;
         }
         if (gtid == 0) {
-            p.w.counts[cur ^ 1] = 0;
-            p.w.counts[2 + (cur ^ 1)] = 0;
+            const int nx = (sweep + 2) % 3;  // the list sweep s+2 fills; sweep s-1 read it
+            p.w.counts[nx] = 0;
+            p.w.counts[3 + nx] = 0;
         }
-        const int32_t* list = cur ? p.w.list1 : p.w.list0;
+        const int32_t* list = frontier_list(p, sweep);
+        int* claim = p.w.counts + 3 + cur;
         // dynamic tile scheduling, per warp: the item two ahead is claimed and
         // the next item's run metadata loaded while the current tile is relaxed
         int it = 0, it1 = 0;
         if (lane == 0) {
-            it = atomicAdd(p.w.counts + 2 + cur, 1);
-            it1 = atomicAdd(p.w.counts + 2 + cur, 1);
+            it = atomicAdd(claim, 1);
+            it1 = atomicAdd(claim, 1);
         }
         it = __shfl_sync(FULL_MASK, it, 0);
         it1 = __shfl_sync(FULL_MASK, it1, 0);
@@ -301,12 +376,18 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
         if (it < cnt) m = load_meta(p, list, it, G);
         while (it < cnt) {
             int it2 = 0;
-            if (lane == 0) it2 = atomicAdd(p.w.counts + 2 + cur, 1);
+            if (lane == 0) it2 = atomicAdd(claim, 1);
             TileMeta m1{};
             if (it1 < cnt) m1 = load_meta(p, list, it1, G);
             const bool ch = warp_tile<TILE>(p, m, t, lane);
+            if (ch) {
+                // the tile itself and the runs it feeds, for the next sweep
+                const int q0 = __ldg(p.g.rout_ptr + m.r), nq = __ldg(p.g.rout_ptr + m.r + 1) - q0;
+                const int item = m.item, g = m.g;
+                frontier_push_warp(p, nq + 1, sweep + 1, lane,
+                                   [&](int j) { return j == 0 ? item : __ldg(p.g.rout_list + q0 + j - 1) * G + g; });
+            }
             if (lane == 0) {
-                if (ch) p.w.stamp[m.item] = sweep + 1;
                 ++tiles;
                 nodes += static_cast<unsigned long long>(m.len);
                 bytes += static_cast<unsigned long long>(__ldg(p.g.run_meta_bytes + m.r)) +
@@ -317,9 +398,6 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
             it1 = __shfl_sync(FULL_MASK, it2, 0);
         }
         if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) break;
-        build_list(p, G, sweep + 1, true, cur ? p.w.list0 : p.w.list1, p.w.counts + (cur ^ 1));
-        if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) break;
-        cur ^= 1;
     }
     if (lane == 0 && tiles) {
         atomicAdd(p.w.stats + 1, tiles);
@@ -557,6 +635,7 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_async_kernel(BfParams p) {
         m.h0 = __ldg(p.g.halo_ptr + m.r);
         m.hn = __ldg(p.g.halo_ptr + m.r + 1) - m.h0;
         m.flags = __ldg(p.g.run_flags + m.r);
+        m.rx = __ldg(p.g.run_wx + m.r);
         const bool ch = warp_tile<TILE>(p, m, t, lane);
         bool ok = true;
         if (ch) {

@@ -51,11 +51,11 @@ struct wr_ctx {
     wr::HostGraph hg;
     wr::HostPartition hp;
     wr::DevGraph dg;
-    wrc::DBuf g_desc, g_ref, g_w, g_arc2, g_run_ptr, g_run_x, g_halo_ptr, g_halo_nodes, g_rin_ptr, g_rin_list, g_rout_ptr, g_rout_list, g_run_of, g_meta, g_flags, g_ix, g_xarc, g_cdesc;
+    wrc::DBuf g_desc, g_ref, g_w, g_arc2, g_run_ptr, g_run_x, g_halo_ptr, g_halo_nodes, g_rin_ptr, g_rin_list, g_rout_ptr, g_rout_list, g_wx, g_run_wx, g_run_of, g_meta, g_flags, g_ix, g_xarc, g_cdesc;
     wr::BfLaunchInfo bf_info{};
     int enum_blocks = 0;
     // working buffers
-    wrc::DBuf rows, stamp, list0, list1, counts, bar, err, stats, ring, ring_seq, qctl;
+    wrc::DBuf rows, stamp, list0, list1, list2, counts, bar, err, stats, ring, ring_seq, qctl;
     wrc::DBuf node_flag, src_index, src_list, n_src, block_sums;
     wrc::DBuf offs, picks, order_status, order_flags, D, unit_off, best, unit_ctr;
     wrc::DBuf out_cost, out_perm, out_status, kbuf, dgiven, src_in, sub, check;

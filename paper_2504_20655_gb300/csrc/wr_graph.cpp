@@ -282,6 +282,7 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
     std::vector<int32_t> halo_all, rin_tmp;
     std::vector<uint2> xt;
     std::vector<std::pair<uint32_t, uint32_t>> fw, bw;
+    std::vector<uint2> wxf, wxb;
     auto off = [](uint32_t slot) { return slot * 128u; };
     for (int32_t t = 0; t < T; ++t) {
         const int4 rs = p.run_seg[t];
@@ -367,10 +368,15 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
             for (size_t k = 1; k < bw.size(); ++k) xt.push_back(make_uint2(bw[k].first, bw[k].second));
             p.node_ix[2 * static_cast<size_t>(v)] = ia;
             p.node_ix[2 * static_cast<size_t>(v) + 1] = ib;
-            // compact form (warp tiling): two non-carry arcs per pass, all in staged slots
-            bool c_ok = fw.size() <= 2 && bw.size() <= 2;
+            // compact form (warp tiling): two non-carry arcs per pass in the
+            // descriptor, the rest in the run's extras; all in staged slots
+            bool c_ok = true;
             for (auto& pr : fw) c_ok = c_ok && !(pr.first & GLOBAL_REF) && pr.first < static_cast<uint32_t>(tile_cap);
             for (auto& pr : bw) c_ok = c_ok && pr.first < static_cast<uint32_t>(tile_cap);
+            for (size_t k = 2; c_ok && k < fw.size(); ++k)
+                wxf.push_back(make_uint2(off(sv) | (off(fw[k].first) << 16), fw[k].second));
+            for (size_t k = 2; c_ok && k < bw.size(); ++k)
+                wxb.push_back(make_uint2(off(sv) | (off(bw[k].first) << 16), bw[k].second));
             if (c_ok) {
                 uint4 f, bk;
                 f.x = fw_cw;
@@ -387,6 +393,18 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
                 compact = false;
             }
         }
+        // warp tiling extras: at most 2 x tile_cap entries fit the warp's shared memory
+        if (wxf.size() + wxb.size() > 2 * static_cast<size_t>(tile_cap)) compact = false;
+        p.run_wx.push_back(compact ? make_int4(static_cast<int>(p.wx.size()), static_cast<int>(wxf.size()),
+                                               static_cast<int>(wxb.size()), 0)
+                                   : make_int4(static_cast<int>(p.wx.size()), 0, 0, 0));
+        if (compact) {
+            p.wx.insert(p.wx.end(), wxf.begin(), wxf.end());
+            p.wx.insert(p.wx.end(), wxb.begin(), wxb.end());
+            if (p.wx.size() & 1u) p.wx.push_back(make_uint2(0u, NO_CARRY));  // whole 16-byte pairs per run
+        }
+        wxf.clear();
+        wxb.clear();
         p.run_x[t] = make_int2(static_cast<int>(p.xarc2.size()), static_cast<int>(p.xarc2.size() + xt.size()));
         p.xarc2.insert(p.xarc2.end(), xt.begin(), xt.end());
         p.run_meta_bytes.push_back(8 * arcs_in_run + 8 * static_cast<int64_t>(len));

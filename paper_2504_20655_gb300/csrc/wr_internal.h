@@ -24,7 +24,7 @@ constexpr int HK_DBLOCK = HK_DSTRIDE * HK_DSTRIDE;
 constexpr int ORDER_FLAG_RANGE = 1;
 constexpr int32_t RUN_SIMPLE = 1;             // run's extra arcs fit the tile buffer, halo fully staged
 constexpr uint32_t IX_EXTRA = 1u << 24;       // node has arcs beyond the inline ones
-constexpr int32_t RUN_COMPACT = 2;            // every node's arcs fit its compact descriptor (warp tiling)
+constexpr int32_t RUN_COMPACT = 2;            // every node's arcs are staged: compact descriptors + extras (warp tiling)
 
 // --------------------------------------------------------------------------
 // graph preprocessing (host, wr_graph.cpp)
@@ -82,6 +82,13 @@ struct HostPartition {
     // o = tile slot x 128 (byte offset of the slot's line in the slot-major
     // tile).  Up to two non-carry arcs per pass; absent ones o = 0, w = NO_CARRY.
     std::vector<uint4> cdesc;
+    // A node's non-carry arcs beyond two per pass go to its run's extras, folded
+    // into the tile before the pass (an upper bound, like every stale read):
+    // wx entries {dst o | src o << 16, w}, per run forward extras then backward
+    // extras from run_wx = {first entry, forward count, backward count, 0}; each
+    // run's list starts at an even entry (16-byte copies).
+    std::vector<uint2> wx;
+    std::vector<int4> run_wx;
     int64_t n_global_refs = 0;
 };
 
@@ -118,6 +125,8 @@ struct DevGraph {
     int64_t* run_meta_bytes = nullptr;
     int32_t* run_flags = nullptr;
     uint4* cdesc = nullptr;    // compact descriptors, 2 per node
+    uint2* wx = nullptr;       // compact form: extra arcs per run
+    int4* run_wx = nullptr;
 };
 
 // One source segment of Bellman-Ford: rows[v * ld + b] holds
@@ -140,7 +149,8 @@ struct BfWork {
     int32_t* stamp;   // n_runs * Gcap
     int32_t* list0;   // n_runs * Gcap
     int32_t* list1;
-    int32_t* counts;  // 4
+    int32_t* list2;   // third frontier list (warp sweeps: sweep s reads list s mod 3)
+    int32_t* counts;  // 8: list sizes, then claim counters
     int32_t gcap;
     GridBar* bar;
     int* err;

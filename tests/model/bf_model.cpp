@@ -74,6 +74,126 @@ static int relax_item(const HostPartition& p, std::vector<uint32_t>& rows, size_
     return changed ? 1 : 0;
 }
 
+// One tile visit as the warp tiling (wr_bf_warp.cu) does it, lane by lane:
+// compact runs fold their forward extras, run the forward pass in blocks of 4
+// nodes whose loads precede the previous block's carry chain, fold the
+// backward extras, then the backward pass; other runs take the generic path
+// (descriptors and arcs in node order, sources past the tile from the rows).
+static int relax_item_warp(const HostPartition& p, std::vector<uint32_t>& rows, size_t ld, int G, int tile_cap,
+                           int item, std::vector<uint32_t>& tile) {
+    constexpr int B = 4;
+    const int r = item / G, gg = item % G;
+    const int4 rs = p.run_seg[r];
+    const int len = rs.y + rs.w;
+    auto node = [&](int i) { return i < rs.y ? rs.x + i : rs.z + (i - rs.y); };
+    const int h0 = p.halo_ptr[r], hn = p.halo_ptr[r + 1] - h0;
+    if (len + hn > tile_cap) return 98;
+    const bool compact = (p.run_flags[r] & RUN_COMPACT) != 0;
+    const int4 rx = p.run_wx[r];
+    if (compact && rx.y + rx.z > 2 * tile_cap) return 97;
+    bool changed = false;
+    for (int lane = 0; lane < 32; ++lane) {
+        const size_t c = static_cast<size_t>(gg) * 32 + lane;
+        for (int i = 0; i < len; ++i) tile[i] = rows[static_cast<size_t>(node(i)) * ld + c];
+        for (int h = 0; h < hn; ++h) tile[len + h] = rows[static_cast<size_t>(p.halo_nodes[h0 + h]) * ld + c];
+        uint32_t chg = 0;
+        auto addmin = [](uint32_t a, uint32_t b, uint32_t m) { return std::min(a + b, m); };
+        if (compact) {
+            auto fold = [&](int e0, int n) {
+                for (int e = e0; e < e0 + n; ++e) {
+                    const uint2 x = p.wx[static_cast<size_t>(rx.x + e)];
+                    const uint32_t d = (x.x & 0xFFFFu) / 128u, sidx = (x.x >> 16) / 128u;
+                    if (d >= static_cast<uint32_t>(len) || sidx >= static_cast<uint32_t>(len + hn)) return false;
+                    const uint32_t v = addmin(tile[sidx], x.y, tile[d]);
+                    chg |= v ^ tile[d];
+                    tile[d] = v;
+                }
+                return true;
+            };
+            auto pass = [&](bool fwd) {
+                const int nf = len / B;
+                uint32_t xprev = INF_U;
+                struct Blk { uint32_t cur[B], m[B], cw[B]; bool valid[B]; };
+                auto load = [&](int b, Blk& k) {
+                    const int ib = fwd ? b * B : len - 1 - b * B;
+                    for (int j = 0; j < B; ++j) {
+                        const int i = fwd ? ib + j : ib - j;
+                        k.valid[j] = i >= 0 && i < len;
+                        if (!k.valid[j]) {
+                            k.cur[j] = INF_U;
+                            k.m[j] = INF_U;
+                            k.cw[j] = NO_CARRY;
+                            continue;
+                        }
+                        const uint4 d = p.cdesc[2 * static_cast<size_t>(node(i)) + (fwd ? 0 : 1)];
+                        k.cur[j] = tile[i];
+                        const uint32_t s0 = tile[(d.y & 0xFFFFu) / 128u], s1 = tile[(d.y >> 16) / 128u];
+                        k.cw[j] = d.x;
+                        k.m[j] = addmin(s1, d.w, addmin(s0, d.z, k.cur[j]));
+                    }
+                };
+                auto chain = [&](int b, const Blk& k) {
+                    const int ib = fwd ? b * B : len - 1 - b * B;
+                    for (int j = 0; j < B; ++j) {
+                        const uint32_t x = addmin(xprev, k.cw[j], k.m[j]);
+                        if (k.valid[j]) {
+                            tile[fwd ? ib + j : ib - j] = x;
+                            chg |= x ^ k.cur[j];
+                        }
+                        xprev = x;
+                    }
+                };
+                Blk a, nb;
+                if (nf > 0) load(0, a);
+                for (int b = 0; b < nf; ++b) {
+                    if (b + 1 < nf) load(b + 1, nb);
+                    chain(b, a);
+                    a = nb;
+                }
+                if (nf * B < len) {
+                    load(nf, a);
+                    chain(nf, a);
+                }
+            };
+            if (!fold(0, rx.y)) return 96;
+            pass(true);
+            if (!fold(rx.y, rx.z)) return 96;
+            pass(false);
+        } else {
+            uint32_t carry = INF_U;
+            for (int i = 0; i < len; ++i) {
+                const int4 d = p.node_desc[node(i)];
+                const uint32_t cur = tile[i];
+                uint32_t best = addmin(carry, static_cast<uint32_t>(d.x), cur);
+                for (int a = d.z; a < d.w; ++a) {
+                    const uint32_t ref = p.arc_ref[a];
+                    const uint32_t x = (ref & GLOBAL_REF) ? rows[static_cast<size_t>(ref & ~GLOBAL_REF) * ld + c] : tile[ref];
+                    best = addmin(x, p.arc_w[a], best);
+                }
+                tile[i] = best;
+                chg |= best ^ cur;
+                carry = best;
+            }
+            carry = INF_U;
+            for (int i = len - 1; i >= 0; --i) {
+                const int4 d = p.node_desc[node(i)];
+                const int end = p.node_desc[node(i) + 1].z;
+                const uint32_t cur = tile[i];
+                uint32_t best = addmin(carry, static_cast<uint32_t>(d.y), cur);
+                for (int a = d.w; a < end; ++a) best = addmin(tile[p.arc_ref[a]], p.arc_w[a], best);
+                tile[i] = best;
+                chg |= best ^ cur;
+                carry = best;
+            }
+        }
+        if (chg) {
+            changed = true;
+            for (int i = 0; i < len; ++i) rows[static_cast<size_t>(node(i)) * ld + c] = tile[i];
+        }
+    }
+    return changed ? 1 : 0;
+}
+
 static void setup(int V, long long E, const long long* rp, const int* col, const int* w, int run_target, int tile_cap,
                   HostGraph& g, HostPartition& p, int& rc) {
     rc = build_host_graph(V, E, reinterpret_cast<const int64_t*>(rp), col, w, 0, g);
@@ -123,6 +243,60 @@ extern "C" int bfm_rows(int V, long long E, const long long* rp, const int* col,
         list = build(sweep + 1);
     }
     *sweeps_out = sweep - 1;
+    copy_out(rows, ld, V, n_src, out);
+    return 0;
+}
+
+// The warp tiling's sweeps (default tiling): the frontier of each sweep is
+// the tiles that changed in the previous one and the tiles of the runs they
+// feed (the kernel pushes them; the set is the same), visited one at a time.
+// compact_out: the share of runs on the compact path.
+extern "C" int bfm_rows_warp(int V, long long E, const long long* rp, const int* col, const int* w, int n_src,
+                             const int* src, int run_target, int tile_cap, int* out, int* sweeps_out,
+                             double* compact_out) {
+    HostGraph g;
+    HostPartition p;
+    int rc = 0;
+    setup(V, E, rp, col, w, run_target, tile_cap, g, p, rc);
+    if (rc) return rc;
+    const int G = (n_src + 31) / 32;
+    const size_t ld = static_cast<size_t>(G) * 32;
+    std::vector<uint32_t> rows(static_cast<size_t>(V) * ld, INF_U);
+    for (int b = 0; b < n_src; ++b) rows[static_cast<size_t>(src[b]) * ld + b] = 0;
+    const size_t n_items = static_cast<size_t>(p.n_runs) * G;
+    std::vector<int> stamp(n_items, 0), list;
+    auto push = [&](int item, int s, std::vector<int>& l) {
+        if (stamp[item] < s) {
+            stamp[item] = s;
+            l.push_back(item);
+        }
+    };
+    for (int b = 0; b < n_src; ++b) {
+        const int r = p.run_of_node[src[b]];
+        push(r * G + b / 32, 1, list);
+        for (int k = p.rout_ptr[r]; k < p.rout_ptr[r + 1]; ++k) push(p.rout_list[k] * G + b / 32, 1, list);
+    }
+    std::vector<uint32_t> tile(static_cast<size_t>(tile_cap));
+    int sweep = 1;
+    for (;; ++sweep) {
+        if (list.empty()) break;
+        if (sweep > V + 1) return 99;
+        std::vector<int> next;
+        for (int item : list) {
+            const int c = relax_item_warp(p, rows, ld, G, tile_cap, item, tile);
+            if (c > 1) return c;
+            if (c) {
+                push(item, sweep + 1, next);
+                const int r = item / G;
+                for (int k = p.rout_ptr[r]; k < p.rout_ptr[r + 1]; ++k) push(p.rout_list[k] * G + item % G, sweep + 1, next);
+            }
+        }
+        list.swap(next);
+    }
+    *sweeps_out = sweep - 1;
+    int compact = 0;
+    for (int r = 0; r < p.n_runs; ++r) compact += (p.run_flags[r] & RUN_COMPACT) ? 1 : 0;
+    *compact_out = static_cast<double>(compact) / p.n_runs;
     copy_out(rows, ld, V, n_src, out);
     return 0;
 }
@@ -290,8 +464,18 @@ extern "C" int bfm_check_partition(int V, long long E, const long long* rp, cons
                     if (pr.first >= static_cast<uint32_t>(tile_cap)) return 16;
             }
         }
-        // the compact descriptors of a warp-tiling run hold the same arcs
+        // the compact descriptors of a warp-tiling run, with the run's extras,
+        // hold the same arcs
         if (p.run_flags[r] & RUN_COMPACT) {
+            const int4 rx = p.run_wx[r];
+            if (rx.x & 1 || rx.y + rx.z > 2 * tile_cap || rx.x + rx.y + rx.z > static_cast<int>(p.wx.size())) return 20;
+            std::vector<std::vector<std::pair<uint32_t, uint32_t>>> xf(static_cast<size_t>(len)), xb(static_cast<size_t>(len));
+            for (int e = 0; e < rx.y + rx.z; ++e) {
+                const uint2 x = p.wx[static_cast<size_t>(rx.x + e)];
+                const uint32_t dst = (x.x & 0xFFFFu) / 128u;
+                if ((x.x & 127u) || dst >= static_cast<uint32_t>(len)) return 21;
+                (e < rx.y ? xf : xb)[dst].emplace_back((x.x >> 16) / 128u, x.y);
+            }
             for (int i = 0; i < len; ++i) {
                 const int v = node(i);
                 const uint4 f = p.cdesc[2 * static_cast<size_t>(v)], bk = p.cdesc[2 * static_cast<size_t>(v) + 1];
@@ -302,6 +486,10 @@ extern "C" int bfm_check_partition(int V, long long E, const long long* rp, cons
                 if (f.w != NO_CARRY) fc.emplace_back((f.y >> 16) / 128u, f.w);
                 if (bk.z != NO_CARRY) bc.emplace_back((bk.y & 0xFFFFu) / 128u, bk.z);
                 if (bk.w != NO_CARRY) bc.emplace_back((bk.y >> 16) / 128u, bk.w);
+                if (!xf[i].empty() && fc.size() < 2) return 22;  // extras only beyond two arcs
+                if (!xb[i].empty() && bc.size() < 2) return 22;
+                fc.insert(fc.end(), xf[i].begin(), xf[i].end());
+                bc.insert(bc.end(), xb[i].begin(), xb[i].end());
                 for (int q = d.z; q < d.w; ++q) fw_l.emplace_back(p.arc_ref[q], p.arc_w[q]);
                 for (int q = d.w; q < p.node_desc[v + 1].z; ++q) bw_l.emplace_back(p.arc_ref[q], p.arc_w[q]);
                 std::sort(fc.begin(), fc.end());

@@ -180,3 +180,63 @@ def test_worklist_needs_the_fed_runs_in_its_seeds(model, orc):
     assert not (out == ref).all()
     out, _ = model_rows_worklist(model, g, src, 1, 128, 0, seed_fed=1)
     assert (out == ref).all()
+
+
+def model_rows_warp(model, g, src, run_target, tile_cap):
+    P = ctypes.c_void_p
+    rp, c, w = _arrs(g)
+    src = np.ascontiguousarray(src, np.int32)
+    out = np.empty((len(src), g.V), np.int32)
+    sw = np.zeros(1, np.int32)
+    share = np.zeros(1, np.float64)
+    rc = model.bfm_rows_warp(g.V, ctypes.c_longlong(g.E), rp.ctypes.data_as(P), c.ctypes.data_as(P),
+                             w.ctypes.data_as(P), len(src), src.ctypes.data_as(P), run_target, tile_cap,
+                             out.ctypes.data_as(P), sw.ctypes.data_as(P), share.ctypes.data_as(P))
+    assert rc == 0, rc
+    return out, int(sw[0]), float(share[0])
+
+
+WARP_TILINGS = [(60, 128), (96, 128), (32, 128), (1, 128), (120, 256), (200, 256)]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_warp_model_random_graphs(model, orc, seed):
+    """The warp tiling replayed lane by lane (compact descriptors, extras folded before
+    each pass, blocks of 4 nodes loaded before the previous block's carry chain, the
+    generic path for runs that do not stage every source) reaches the oracle's rows."""
+    V = [1, 2, 7, 33, 100, 257, 600, 1500][seed]
+    g = random_graph(V, max(1, 3 * V), seed + 300, w_lo=0, w_hi=20 if seed % 2 else 1000)
+    src = np.arange(0, V, max(1, V // 70), dtype=np.int32)
+    ref = orc.sssp_rows(g, src, "dijkstra", 4)
+    for rt, tc in WARP_TILINGS:
+        out, sweeps, _ = model_rows_warp(model, g, src, rt, tc)
+        assert (out == ref).all(), (rt, tc)
+        assert sweeps <= V + 1
+
+
+def test_warp_model_layouts_all_compact(model, orc):
+    """On the aisle layouts every run takes the compact path: the cross-aisle nodes'
+    aisle arcs beyond two per pass are the runs' extras.  Rows equal the oracle's."""
+    for lay, n in ((synth.medium_layout(), 64), (synth.Layout(A=20, S=100, F=2, C=2, step_lo=50, step_hi=150,
+                                                              face_w=400), 40)):
+        g = lay.build()
+        src = synth.distinct_sources(n, g.n_slots, 5)
+        ref = orc.sssp_rows(g, src, "dijkstra", 4)
+        for rt, tc in ((60, 128), (120, 256)):
+            out, _, share = model_rows_warp(model, g, src, rt, tc)
+            assert (out == ref).all(), (rt, tc)
+            assert share == 1.0
+
+
+def test_warp_model_high_in_degree(model, orc):
+    """A hub with 699 in-arcs: its run overflows the tile and takes the generic path."""
+    V = 700
+    u = np.concatenate([np.arange(1, V), np.zeros(V - 1, np.int64)])
+    v = np.concatenate([np.zeros(V - 1, np.int64), np.arange(1, V)])
+    w = synth.uniform_int(77, u.shape[0], 1, 50)
+    rp, col, wt = synth.csr_from_arcs(V, u, v, w)
+    g = synth.Graph(V=V, row_ptr=rp, col=col, w=wt, depot=0)
+    src = np.array([0, 5, 699, 350], np.int32)
+    out, _, share = model_rows_warp(model, g, src, 96, 128)
+    assert (out == orc.sssp_rows(g, src)).all()
+    assert share < 1.0
