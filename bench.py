@@ -145,8 +145,8 @@ def dist_setup(args):
 # it was taken on (hash below) and the tuning is the default one; otherwise null.
 TRAFFIC_SOURCES = ["paper_2504_20655_gb300/csrc/wr_bf_warp.cu", "paper_2504_20655_gb300/csrc/wr_bf_common.cuh",
                    "paper_2504_20655_gb300/csrc/wr_graph.cpp"]
-TRAFFIC_HASH = "f85192ecc586583f"
-TRAFFIC = {"medium": 706258688 + 521190400, "scale": 22034982000 + 17681132000}
+TRAFFIC_HASH = "f3d9cbd5395e5ff1"
+TRAFFIC = {"medium": 734220032 + 468953088, "scale": 18333193000 + 9752776000}
 
 
 def traffic_for(workload, tuned):
