@@ -681,3 +681,28 @@ def test_route_clustered_against_oracle(wr, orc):
         assert (status == s).all() and (cost == c).all() and (perm[:len(p)] == p).all(), (m, open_path)
         if not open_path:
             assert (c >= exact_c).all()
+
+
+@pytest.mark.parametrize("tiling", [1, 2, 3], ids=["warp_sweeps", "cta_sweeps", "warp_worklist"])
+def test_wait_limit_reports_timeout_and_device_stays_usable(wr, orc, tiling):
+    """Failure detection without a GPU fault: with a one-spin wait limit the sweep
+    kernel's grid barriers (or worklist waits) give up, every block returns, and the call
+    reports WR_ETIMEOUT; a new context on the same device then computes the oracle's rows."""
+    g = synth.medium_layout().build()
+    src = synth.distinct_sources(64, g.n_slots, 3)
+    r = wr.Router(device=0, barrier_max_spins=1)
+    try:
+        r.set_tuning(bf_tiling=tiling)
+        r.load_graph(g)
+        with pytest.raises(wr.WrError) as e:
+            r.bf_rows(src)
+        assert e.value.code == wr.WR_ETIMEOUT
+    finally:
+        r.close()
+    r2 = wr.Router(device=0)
+    try:
+        r2.set_tuning(bf_tiling=tiling)
+        r2.load_graph(g)
+        assert (r2.bf_rows(src) == orc.sssp_rows(g, src, "dijkstra", NT)).all()
+    finally:
+        r2.close()
