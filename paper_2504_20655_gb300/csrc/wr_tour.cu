@@ -334,7 +334,7 @@ __host__ __device__ constexpr int cfact(int n) { return n <= 1 ? 1 : n * cfact(n
 // first accumulator holding a block's minimum names the range that holds its
 // lowest-rank minimiser.  Find sets idx to the index of the first leaf whose
 // cost equals target.
-constexpr int NACC = 8;
+constexpr int NACC = 4;
 
 template <int L>
 struct AccSpan {
