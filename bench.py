@@ -122,6 +122,15 @@ def workload(name):
     elif name == "tiny":
         g, o = synth.tiny_workload()
         desc = "tiny: 10 aisles x 20 slots x 2 sides (V=421); one order of 6 picks"
+    elif name == "heldkarp":
+        g, o = synth.large_order_workload()
+        desc = "large orders: medium layout (V=20401); 128 orders, k~U{13..20}, Zipf(1.1) over 50k SKUs"
+    elif name in ("open", "clustered", "nodes"):
+        g, o = synth.medium_workload()
+        desc = {"open": "open paths (the entrance/exit not part of the route, Sec. 3): ",
+                "clustered": "cluster-patched approximate routes (Sec. 3), at most 3 clusters: ",
+                "nodes": "node-level routes of the exact sequences: "}[name] + \
+            "medium layout (V=20401); 1024 orders, k~U{4..10}, Zipf(1.1) over 50k SKUs"
     else:
         raise ValueError(name)
     return g, o, desc
@@ -204,17 +213,43 @@ def barrier(world):
         dist.barrier()
 
 
-def cpu_oracle_rate(g, o, budget_s=15.0, n_threads=None):
-    """The oracle (round-based Bellman-Ford + brute force over all k!) on the host's
-    cores, on a bounded prefix of the batch; returns (orders/s, cores, sample)."""
+def oracle_runner(g, o, mode, n_threads):
+    """The oracle's whole path for a prefix of the batch o in the given mode, as it stands
+    (node-level routes: the walk alone, over the oracle's own exact sequences)."""
     import oracle
+    if mode == "heldkarp":
+        return lambda sub: oracle.route_orders(g, sub, "rounds", "heldkarp", n_threads, max_k=20)
+    if mode == "open":
+        return lambda sub: oracle.route_orders(g, sub, "rounds", "brute", n_threads, open_path=True)
+    if mode == "clustered":
+        xy = synth_layout_coords()
+        return lambda sub: oracle.route_orders_clustered(g, sub, xy, 3, False, n_threads)
+    if mode == "nodes":
+        _, perm_all, _ = oracle.route_orders(g, o, "dijkstra", "heldkarp", n_threads)  # untimed: the sequences
+
+        def run(sub):
+            return oracle.route_nodes(g, sub, perm_all[:int(sub.offs[-1])], False, n_threads)
+        return run
+    return lambda sub: oracle.route_orders(g, sub, "rounds", "brute", n_threads)
+
+
+def synth_layout_coords():
+    from paper_2504_20655_gb300 import synth
+    return synth.medium_layout().coords()
+
+
+def cpu_oracle_rate(g, o, budget_s=15.0, n_threads=None, mode="exact"):
+    """The oracle (round-based Bellman-Ford + brute force over all k!, or the mode's own
+    tour step) on the host's cores, on a bounded prefix of the batch; returns
+    (orders/s, cores, sample)."""
     n_threads = n_threads or os.cpu_count() or 1
-    n = 8
+    run = oracle_runner(g, o, mode, n_threads)
+    n = 8 if mode != "heldkarp" else 2
     t = 0.0
     while True:
         sub = o.subset(np.arange(min(n, o.n)))
         t0 = time.perf_counter()
-        oracle.route_orders(g, sub, "rounds", "brute", n_threads)
+        run(sub)
         t = time.perf_counter() - t0
         if t > budget_s / 3 or n >= o.n:
             break
@@ -224,24 +259,47 @@ def cpu_oracle_rate(g, o, budget_s=15.0, n_threads=None):
         reps = max(1, int(budget_s / 3 / max(t, 1e-3)))
         t0 = time.perf_counter()
         for _ in range(reps):
-            oracle.route_orders(g, sub, "rounds", "brute", n_threads)
+            run(sub)
         t = time.perf_counter() - t0
     what = f"first {n} orders of the batch" if reps == 1 else f"the whole batch of {n} orders x {reps}"
     return reps * n / t, n_threads, f"{what} ({t:.1f} s on {n_threads} threads)"
+
+
+METRIC = {"clustered": "approximate-routed orders/s", "nodes": "node-routed orders/s"}
 
 
 def run_reference(args):
     world, rank, local = dist_setup(args)
     if rank != 0:
         return 0
-    g, o, desc = workload(args.workload)
+    if args.workload == "scale":
+        from paper_2504_20655_gb300 import synth
+        g, src = synth.scale_workload(n_src=args.scale_sources)
+        rates = []
+        for i in range(args.warmup + args.steps):
+            v, cores, sample = cpu_oracle_rows_rate(g, src, budget_s=args.ref_budget)
+            if i >= args.warmup:
+                rates.append(v)
+        value = statistics.median(rates)
+        line = {"impl": "reference", "metric": "BF Gedges/s (E x sources / step time)", "value": value,
+                "unit": "Gedges/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * g.E * len(src) / (value * 1e9), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": "scale: rows of the 4096 sources, oracle Dijkstra"},
+                "cpu_baseline": {"value": value, "unit": "Gedges/s", "cores": cores, "kind": "oracle", "sample": sample},
+                "e2e": {"value": value, "unit": "Gedges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+    g, o, desc = workload("medium" if args.workload == "serving" else args.workload)
+    mode = args.workload if args.workload in ("heldkarp", "open", "clustered", "nodes") else "exact"
     rates = []
     for i in range(args.warmup + args.steps):
-        r, cores, sample = cpu_oracle_rate(g, o, budget_s=args.ref_budget)
+        r, cores, sample = cpu_oracle_rate(g, o, budget_s=args.ref_budget, mode=mode)
         if i >= args.warmup:
             rates.append(r)
     value = statistics.median(rates)
-    line = {"impl": "reference", "metric": "exact-routed orders/s", "value": value, "unit": "orders/s",
+    line = {"impl": "reference", "metric": METRIC.get(args.workload, "exact-routed orders/s"), "value": value,
+            "unit": "orders/s",
             "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * o.n / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "config": {"workload": desc},
@@ -690,13 +748,199 @@ def run_ours(args):
     return 0
 
 
+def hk_transitions(k):
+    """Held-Karp transitions of one order of k picks: a set S of visited picks with its
+    last pick c and a next pick j outside S (k(k-1)2^(k-2) of them), plus the k legs
+    from the depot and the k legs back.  Each is one saturating add and one min."""
+    return k * (k - 1) * (1 << (k - 2)) + 2 * k
+
+
+def hk_table_bytes(k):
+    """Algorithmic table traffic of Held-Karp for one order of k picks: every word
+    h(S, c) of the 2^k x k table written once, and read once by the level below
+    (h(S + j, j) for each S without j), 4 bytes each: k 2^(k-1) words each way."""
+    return 2 * 4 * k * (1 << (k - 1))
+
+
+def run_next(args):
+    """The rows past the core of the path, each to the same bar as the medium line:
+    Held-Karp for orders of 13..20 picks, open paths, cluster-patched approximate routes
+    and node-level routes.  Timing (CUDA events on the launching stream, L2 flushed
+    between steps), end to end through the C ABI with host buffers, the oracle in the
+    same mode on the host's cores, the dominant kernel against its roofline."""
+    import torch
+
+    from paper_2504_20655_gb300 import synth, wroute
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = args.workload
+    g, o, desc = workload(w)
+    r = wroute.Router(device=local, mem_budget_bytes=args.budget_gib << 30, max_k=20 if w == "heldkarp" else 12)
+    if args.tune:
+        r.set_tuning(**json.loads(args.tune))
+    r.load_graph(g)
+    if w == "open":
+        r.set_route_mode(True)
+    if w == "clustered":
+        r.set_clusters(3, synth.medium_layout().coords())
+    stream = torch.cuda.current_stream(dev)
+    n, np_ = o.n, int(o.offs[-1])
+    offs = torch.from_numpy(o.offs).to(dev)
+    picks = torch.from_numpy(o.picks).to(dev)
+    cost = torch.empty(n, dtype=torch.int32, device=dev)
+    perm = torch.empty(max(np_, 1), dtype=torch.int32, device=dev)
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    if w == "nodes":
+        # the exact sequences first (untimed), then their node-level routes
+        wroute.wr_route_orders(r.ctx, offs, picks, cost, perm, status, stream.cuda_stream)
+        node_offs = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+        wroute.wr_route_nodes(r.ctx, offs, picks, perm, node_offs, None, 0, stream.cuda_stream)
+        torch.cuda.synchronize()
+        n_nodes = int(node_offs[-1].item())
+        nodes = torch.empty(max(n_nodes, 1), dtype=torch.int32, device=dev)
+
+        def step():
+            wroute.wr_route_nodes(r.ctx, offs, picks, perm, node_offs, nodes, n_nodes, stream.cuda_stream)
+    else:
+        def step():
+            wroute.wr_route_orders(r.ctx, offs, picks, cost, perm, status, stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    r.sync()
+    stats_list = []
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            e0[i].record(stream)
+            step()
+            e1[i].record(stream)
+            stats_list.append(r.stats())  # syncs; outside the event pair
+        torch.cuda.synchronize()
+    barrier(world)
+    r.sync()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / args.steps, world, dev)
+    value = replica_value(n, ms, world)
+
+    # end to end with pinned host buffers
+    h_offs = torch.from_numpy(o.offs).pin_memory()
+    h_picks = torch.from_numpy(o.picks).pin_memory()
+    if w == "nodes":
+        h_perm_in = perm[:max(np_, 1)].cpu().pin_memory()
+        h_noffs = torch.zeros(n + 1, dtype=torch.int64).pin_memory()
+        h_nodes = torch.empty(max(n_nodes, 1), dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            wroute.wr_route_nodes(r.ctx, h_offs, h_picks, h_perm_in, h_noffs, h_nodes, n_nodes, stream.cuda_stream)
+        h2d, d2h = 8 * (n + 1) + 8 * np_, 8 * (n + 1) + 4 * n_nodes
+    else:
+        h_cost = torch.empty(n, dtype=torch.int32).pin_memory()
+        h_perm = torch.empty(max(np_, 1), dtype=torch.int32).pin_memory()
+        h_status = torch.empty(n, dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            wroute.wr_route_orders(r.ctx, h_offs, h_picks, h_cost, h_perm, h_status, stream.cuda_stream)
+        h2d, d2h = 8 * (n + 1) + 4 * np_, 8 * n + 4 * np_
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_times.append(t1 - t0)
+    e2e_s = max_over_ranks(sum(e2e_times) / len(e2e_times), world, dev)
+    if w == "nodes":
+        ok = bool((h_noffs.numpy() == node_offs.cpu().numpy()).all()
+                  and (h_nodes.numpy()[:n_nodes] == nodes.cpu().numpy()[:n_nodes]).all())
+    else:
+        ok = bool((h_cost.numpy() == cost.cpu().numpy()).all() and (h_status.numpy() == status.cpu().numpy()).all())
+
+    st = stats_list[-1]
+    pk = peaks()
+    phases = {k[3:]: statistics.median(s[k] for s in stats_list) for k in
+              ("ms_select", "ms_init", "ms_bf", "ms_gather", "ms_enum", "ms_finish", "ms_total")}
+    bf_ms = phases["bf"]
+    bf_gbs = st["bytes_alg"] / (bf_ms / 1e3) / 1e9 if bf_ms > 0 else 0.0
+    bf_roof = {"kernel": sweep_kernel_name(r.tuning()), "bound": "hbm", "achieved": bf_gbs, "peak": pk["hbm_gbs"],
+               "unit": "GB/s", "frac": bf_gbs / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"],
+               "bytes_alg_per_launch": st["bytes_alg"], "ms_per_launch": bf_ms, "sweeps": st["sweeps"]}
+    alu_peak = alu_min_peak(pk)
+    extra = {}
+    if w == "heldkarp":
+        # the solve kernel dominates; its tables (2^k x k words per order) stream through HBM
+        # once each way, which binds before the ALU pipe does (2 operations per transition)
+        k = o.k()
+        trans = float(sum(hk_transitions(int(kk)) for kk in k))
+        tbytes = float(sum(hk_table_bytes(int(kk)) for kk in k))
+        hk_ms = phases["enum"]
+        achieved = tbytes / (hk_ms / 1e3) / 1e9 if hk_ms > 0 else 0.0
+        roof = {"kernel": "hk_solve_kernel", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"],
+                "bytes_alg_per_launch": tbytes, "ms_per_launch": hk_ms, "transitions_per_launch": trans,
+                "transitions_per_s": trans / (hk_ms / 1e3) if hk_ms > 0 else 0.0,
+                "alu_frac": (2 * trans / (hk_ms / 1e3) / 1e12) / alu_peak if hk_ms > 0 else 0.0}
+        extra["roofline_bf"] = bf_roof
+        metric = "exact-routed orders/s"
+    else:
+        roof = bf_roof
+        metric = METRIC.get(w, "exact-routed orders/s")
+        if w == "clustered":
+            extra["cluster_kernel_ms"] = phases["enum"]
+            # context: the approximate costs against the exact ones (same GPU, exact routing)
+            rx = wroute.Router(device=local, mem_budget_bytes=args.budget_gib << 30)
+            rx.load_graph(g)
+            cx, _, sx = rx.route_orders(o.offs, o.picks)
+            rx.close()
+            ca = cost.cpu().numpy()
+            okm = (sx == 0) & (status.cpu().numpy() == 0)
+            extra["cost_ratio_vs_exact"] = {"mean": float(np.mean(ca[okm] / cx[okm])),
+                                            "max": float(np.max(ca[okm] / cx[okm])),
+                                            "exact_share": float(np.mean(ca[okm] == cx[okm]))}
+        if w == "nodes":
+            extra["nodes_per_step"] = n_nodes
+            extra["walk_ms"] = phases["finish"]
+    line = {
+        "metric": metric, "value": value, "unit": "orders/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": desc, "orders_per_step": n, "sources": st["n_sources"],
+                   "l2": "flushed (512 MiB write) between steps",
+                   "parallelism": f"replicas x{world} (orders are independent)", "tuning": r.tuning()},
+        "roofline": roof,
+        "phases_ms": phases,
+        "e2e": {"value": world * n / e2e_s, "unit": "orders/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "matches_device_run": ok},
+        "gpu_launches": int(sum(s["kernel_launches"] for s in stats_list)),
+        "clocks": clk.summary(),
+    }
+    line.update(extra)
+    if rank == 0 and not args.no_cpu:
+        mode = w
+        v, cores, sample = cpu_oracle_rate(g, o, budget_s=args.ref_budget, mode=mode)
+        line["cpu_baseline"] = {"value": v, "unit": "orders/s", "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line))
+    r.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="medium", choices=["medium", "batching", "tiny", "scale", "serving"])
+    ap.add_argument("--workload", default="medium",
+                    choices=["medium", "batching", "tiny", "scale", "serving", "heldkarp", "open", "clustered", "nodes"])
     ap.add_argument("--budget-gib", type=int, default=2)
     ap.add_argument("--tune", default="")
     ap.add_argument("--traffic", default="")
@@ -722,6 +966,8 @@ def main():
         return run_batching(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload in ("heldkarp", "open", "clustered", "nodes"):
+        return run_next(args)
     return run_ours(args)
 
 

@@ -354,7 +354,9 @@ int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_
         RC(ensure(c->hk_list, static_cast<size_t>(n) * 4 + 4));
         RC(ensure(c->hk_count, 16));
         RC(ensure(c->hk_D, static_cast<size_t>(n) * wr::HK_DBLOCK * 4 + 4));
-        RC(ensure(c->hk_h, (static_cast<size_t>(1) << c->cfg.max_k) * static_cast<size_t>(c->cfg.max_k) * 4));
+        // tables of a batch of orders solved together: at least one of max_k picks, up to the budget
+        const size_t one = (static_cast<size_t>(1) << c->cfg.max_k) * static_cast<size_t>(c->cfg.max_k) * 4;
+        RC(ensure(c->hk_h, one > c->cfg.mem_budget_bytes ? one : static_cast<size_t>(c->cfg.mem_budget_bytes)));
         CK(cudaMemsetAsync(c->hk_count.p, 0, 4, s));
         CK(wr::hk_launch_select(n, tb, c->cfg.max_k, c->hk_list.as<int32_t>(), c->hk_count.as<int32_t>(), s));
         c->launches++;
@@ -390,10 +392,45 @@ int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_
     }
     c->last.n_segments = n_seg;
     if (clustered) {
-        PhaseTimer t(c, s, 4);
-        CK(wr::cluster_launch(n, tb, c->g_coords.as<int32_t>(), c->cluster_m, c->route_mode == WR_ROUTE_OPEN, o_cost,
-                              o_perm, o_status, s));
-        c->launches++;
+        // every cluster an order has becomes a sub-order with free depot legs, routed by the
+        // exhaustive enumeration; then the patching of the cluster routes
+        const int32_t m = c->cluster_m;
+        const size_t ns = static_cast<size_t>(n) * static_cast<size_t>(m);
+        RC(ensure(c->cl_k, ns * 4 + 4));
+        RC(ensure(c->cl_status, ns * 4 + 4));
+        RC(ensure(c->cl_flags, ns * 4 + 4));
+        RC(ensure(c->cl_D, ns * wr::DBLOCK * 4 + 4));
+        RC(ensure(c->cl_mem, ns * 8 + 8));
+        RC(ensure(c->cl_perm, ns * WR_MAX_K * 4 + 4));
+        RC(ensure(c->cl_state, static_cast<size_t>(n) * 4 + 4));
+        RC(ensure(c->cl_nc, static_cast<size_t>(n) * 4 + 4));
+        RC(ensure(c->cl_unit_off, (ns + 1) * 8));
+        RC(ensure(c->cl_best, ns * 8 + 8));
+        RC(ensure(c->cl_cost, ns * 4 + 4));
+        RC(ensure(c->cl_ostatus, ns * 4 + 4));
+        wr::ClusterBufs cb{c->cl_k.as<int32_t>(), c->cl_status.as<int32_t>(), c->cl_flags.as<int32_t>(),
+                           c->cl_D.as<uint32_t>(), c->cl_mem.as<unsigned long long>(), c->cl_perm.as<int32_t>(),
+                           c->cl_state.as<int32_t>(), c->cl_nc.as<int32_t>()};
+        {
+            PhaseTimer t(c, s, 3);
+            CK(wr::cluster_launch_split(n, tb, c->g_coords.as<int32_t>(), m, cb, s));
+            c->launches++;
+        }
+        wr::TourBufs sb{};
+        sb.order_status = cb.sub_status;
+        sb.order_flags = cb.sub_flags;
+        sb.D = cb.sub_D;
+        sb.unit_off = c->cl_unit_off.as<long long>();
+        sb.best = c->cl_best.as<unsigned long long>();
+        sb.unit_ctr = tb.unit_ctr;
+        sb.seq_count = tb.seq_count;
+        RC(run_tours(c, static_cast<int32_t>(ns), cb.sub_k, sb, c->cl_cost.as<int32_t>(), cb.sub_perm, WR_MAX_K,
+                     c->cl_ostatus.as<int32_t>(), s));
+        {
+            PhaseTimer t(c, s, 5);
+            CK(wr::cluster_launch_patch(n, tb, m, c->route_mode == WR_ROUTE_OPEN, cb, o_cost, o_perm, o_status, s));
+            c->launches++;
+        }
         return WR_OK;
     }
     RC(run_tours(c, n, nullptr, tb, o_cost, o_perm, 0, o_status, s));
@@ -403,7 +440,8 @@ int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_
         RC(ensure(c->bar, sizeof(wr::GridBar)));
         CK(cudaMemsetAsync(c->bar.p, 0, sizeof(wr::GridBar), s));
         CK(wr::hk_launch_solve(c->hk_list.as<int32_t>(), c->hk_count.as<int32_t>(), c->hk_D.as<uint32_t>(),
-                               c->hk_h.as<uint32_t>(), tb, o_cost, o_perm, o_status, c->bar.as<wr::GridBar>(),
+                               c->hk_h.as<uint32_t>(), c->hk_h.bytes / 4, tb, o_cost, o_perm, o_status,
+                               c->bar.as<wr::GridBar>(),
                                c->err.as<int>(), c->cfg.barrier_max_spins ? c->cfg.barrier_max_spins : DEFAULT_SPINS,
                                c->hk_blocks, s));
         c->launches++;
@@ -485,7 +523,9 @@ void wr_destroy(wr_ctx* c) {
                     &c->unit_off, &c->best, &c->unit_ctr, &c->out_cost, &c->out_perm, &c->out_status, &c->kbuf,
                     &c->dgiven, &c->src_in, &c->sub, &c->check, &c->trace,
                     &c->hk_list, &c->hk_count, &c->hk_D, &c->hk_h, &c->g_in_ptr, &c->g_in_src, &c->g_in_w,
-                    &c->leg_len, &c->perm_in, &c->node_offs_d, &c->nodes_d, &c->g_coords};
+                    &c->leg_len, &c->perm_in, &c->node_offs_d, &c->nodes_d, &c->g_coords,
+                    &c->cl_k, &c->cl_status, &c->cl_flags, &c->cl_D, &c->cl_mem, &c->cl_perm, &c->cl_state, &c->cl_nc,
+                    &c->cl_unit_off, &c->cl_best, &c->cl_cost, &c->cl_ostatus};
     for (DBuf* b : bufs) b->release();
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     delete c;
@@ -943,11 +983,15 @@ int wr_route_nodes(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pic
     for (int32_t sg = 0; sg < n_seg; ++sg) {
         const wr::BfSegment seg = segment(sg);
         RC(run_bf_segment(c, seg, s));
+        PhaseTimer t(c, s, 5);  // the walks are the decode of routes into nodes
         CK(wr::paths_launch(pl, seg, nullptr, nullptr, s));
         c->launches++;
     }
-    CK(wr::paths_launch_offsets(pl, c->node_offs_d.as<int64_t>(), s));
-    c->launches++;
+    {
+        PhaseTimer t(c, s, 5);
+        CK(wr::paths_launch_offsets(pl, c->node_offs_d.as<int64_t>(), s));
+        c->launches++;
+    }
     int64_t total = 0;
     CK(cudaMemcpyAsync(&total, c->node_offs_d.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, s));
     if (ptr_kind == WR_HOST)
@@ -967,6 +1011,7 @@ int wr_route_nodes(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pic
     for (int32_t sg = n_seg - 1; sg >= 0; --sg) {
         const wr::BfSegment seg = segment(sg);
         if (sg != n_seg - 1) RC(run_bf_segment(c, seg, s));
+        PhaseTimer t(c, s, 5);
         CK(wr::paths_launch(pl, seg, d_nodes, c->node_offs_d.as<int64_t>(), s));
         c->launches++;
     }

@@ -68,6 +68,9 @@ struct wr_ctx {
     int32_t cluster_m = 0;          // > 0: cluster-patched approximate routing with at most this many clusters
     std::vector<int32_t> coords;    // plan coordinates (2 per node), host copy
     wrc::DBuf g_coords;
+    // clustered routing: per order and cluster slot (n * cluster_m sub-orders)
+    wrc::DBuf cl_k, cl_status, cl_flags, cl_D, cl_mem, cl_perm, cl_state, cl_nc, cl_unit_off, cl_best, cl_cost,
+        cl_ostatus;
     wrc::DBuf trace;          // sweep trace of the last Bellman-Ford segment
     int32_t trace_cap = 0;
     bool capturing = false;  // enqueueing into a CUDA graph: no host syncs, external timing events

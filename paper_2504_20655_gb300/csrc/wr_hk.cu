@@ -13,11 +13,12 @@
 // and the sequence is rebuilt from the depot by taking, at every step, the
 // smallest pick index j whose D[cur][j] + h(S + j, j) equals what remains.
 //
-// One cooperative persistent kernel works through the orders one at a time:
-// the table of an order (2^k x k words) is filled level by level (subsets of
-// k picks, then k-1, ... 1), all blocks sharing each level, with a bounded
-// grid barrier between levels; block 0 rebuilds the sequence.  Arithmetic is
-// uint32 with WR_INF saturation; finite sums stay below 21 x WR_LEG_MAX < 2^31.
+// One cooperative persistent kernel fills the tables (2^k x k words per order)
+// level by level (subsets of k picks, then k-1, ... 1) for a whole batch of
+// orders at once, all blocks sharing each level, with one bounded grid
+// barrier per level; then every order's sequence is rebuilt by one thread.
+// Arithmetic is uint32 with WR_INF saturation; finite sums stay below
+// 21 x WR_LEG_MAX < 2^31.
 #include "wr_bf_common.cuh"
 
 namespace wr {
@@ -65,7 +66,8 @@ struct HkParams {
     const int32_t* list;
     const int32_t* count;
     const uint32_t* D21;
-    uint32_t* h;  // 2^max_k x max_k words
+    uint32_t* h;                 // table buffer
+    unsigned long long h_words;  // its capacity in words (at least one table of max_k picks)
     TourBufs t;
     int32_t* cost;
     int32_t* perm;
@@ -75,45 +77,123 @@ struct HkParams {
     unsigned long long max_spins;
 };
 
+constexpr int HK_BATCH = 512;  // orders solved together, at most
+
+// Picks of listed order q (0 for an order whose D holds an out-of-range leg:
+// its status comes from the decode of the other orders).
+__device__ __forceinline__ int hk_k(const HkParams& p, int q) {
+    const int o = p.list[q];
+    if (p.t.order_flags[o] & ORDER_FLAG_RANGE) return 0;
+    return static_cast<int>(p.t.offs[o + 1] - p.t.offs[o]);
+}
+
+// Orders are solved in batches whose tables (2^k x k words each) fit the buffer;
+// within a batch all orders share every level: level L holds, for every order of
+// k >= L picks, its C(k, L) subsets S of size L, in increasing bitmask order per
+// order, orders one after another.  Consecutive threads take consecutive items
+// (grid-stride), each unranking its subset (combinatorial number system), and a
+// table is pick-major, h[c][S], so the lanes of a warp read and write
+// neighbouring words.  One grid barrier per level; then one thread per order
+// rebuilds its first optimal sequence.
 __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
-    __shared__ uint32_t D[HK_DBLOCK];
+    __shared__ uint32_t binom[HK_MAX_K + 1][HK_MAX_K + 1];
+    __shared__ unsigned long long pre[HK_BATCH + 1];  // level prefix of C(k_q, L)
+    __shared__ unsigned long long base[HK_BATCH + 1];  // table offsets (words)
+    __shared__ int kq[HK_BATCH];
+    __shared__ int nb_s;
+    for (int i = threadIdx.x; i < (HK_MAX_K + 1) * (HK_MAX_K + 1); i += blockDim.x) {
+        const int n = i / (HK_MAX_K + 1), r = i % (HK_MAX_K + 1);
+        unsigned long long c = 1;  // C(n, r) by the multiplicative formula (exact at each step)
+        if (r > n) c = 0;
+        for (int j = 1; j <= r && j <= n; ++j) c = c * static_cast<unsigned long long>(n - r + j) / j;
+        binom[n][r] = static_cast<uint32_t>(c);
+    }
     const int n_big = ld_volatile(p.count);
     const long long gtid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     const long long nthreads = static_cast<long long>(gridDim.x) * blockDim.x;
-    for (int q = 0; q < n_big; ++q) {
-        const int o = p.list[q];
-        const int64_t b = p.t.offs[o];
-        const int k = static_cast<int>(p.t.offs[o + 1] - b);
-        if (p.t.order_flags[o] & ORDER_FLAG_RANGE) continue;  // decided by the decode of the other orders
-        for (int e = threadIdx.x; e < HK_DBLOCK; e += blockDim.x) D[e] = p.D21[static_cast<int64_t>(q) * HK_DBLOCK + e];
+    int q0 = 0;
+    while (q0 < n_big) {
+        // the batch: orders q0 .. q1-1 whose tables fit (the same in every block)
         __syncthreads();
-        const unsigned full = (1u << k) - 1u;
-        for (int L = k; L >= 1; --L) {
-            for (long long S = gtid; S <= full; S += nthreads) {
-                const unsigned s = static_cast<unsigned>(S);
-                if (__popc(s) != L) continue;
-                uint32_t* hs = p.h + static_cast<int64_t>(s) * k;
+        if (threadIdx.x == 0) {
+            unsigned long long acc = 0;
+            int q = q0;
+            base[0] = 0;
+            while (q < n_big && q - q0 < HK_BATCH) {
+                const int k = hk_k(p, q);
+                const unsigned long long sz = k > 0 ? (1ull << k) * static_cast<unsigned long long>(k) : 0ull;
+                if (q > q0 && acc + sz > p.h_words) break;
+                kq[q - q0] = k;
+                acc += sz;
+                base[q - q0 + 1] = acc;
+                ++q;
+            }
+            nb_s = q - q0;  // batch size
+        }
+        __syncthreads();
+        const int nb = nb_s;
+        int kmax = 0;
+        for (int i = 0; i < nb; ++i) kmax = max(kmax, kq[i]);
+        for (int L = kmax; L >= 1; --L) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                pre[0] = 0;
+                for (int i = 0; i < nb; ++i) pre[i + 1] = pre[i] + (kq[i] >= L ? binom[kq[i]][L] : 0u);
+            }
+            __syncthreads();
+            const unsigned long long total = pre[nb];
+            int qi = 0;
+            for (unsigned long long w = static_cast<unsigned long long>(gtid); w < total;
+                 w += static_cast<unsigned long long>(nthreads)) {
+                while (pre[qi + 1] <= w) ++qi;  // the order holding item w
+                const int k = kq[qi];
+                // unrank: the subset of rank w - pre[qi] among the L-subsets of k picks
+                unsigned s = 0;
+                unsigned long long rr = w - pre[qi];
+                for (int i = L; i >= 1; --i) {
+                    int c = i - 1;
+                    while (c + 1 < k && binom[c + 1][i] <= rr) ++c;
+                    s |= 1u << c;
+                    rr -= binom[c][i];
+                }
+                const unsigned full = (1u << k) - 1u;
+                const int64_t side = static_cast<int64_t>(1) << k;  // words per pick in the table
+                const uint32_t* D = p.D21 + static_cast<int64_t>(q0 + qi) * HK_DBLOCK;
+                uint32_t* hq = p.h + base[qi];
+                // h(S + j, j) for every pick j outside S, all loads in flight together
+                uint32_t hv[HK_MAX_K];
+#pragma unroll
+                for (int j = 0; j < HK_MAX_K; ++j)
+                    hv[j] = (j < k && !((s >> j) & 1u)) ? __ldcg(hq + j * side + (s | (1u << j))) : INF_U;
                 for (unsigned cm = s; cm; cm &= cm - 1) {
                     const int c = __ffs(cm) - 1;
+                    const uint32_t* Dr = D + (c + 1) * HK_DSTRIDE;
                     uint32_t best;
                     if (s == full) {
-                        best = D[(c + 1) * HK_DSTRIDE];
+                        best = __ldg(Dr);
                     } else {
                         best = INF_U;
-                        for (unsigned jm = full & ~s; jm; jm &= jm - 1) {
-                            const int j = __ffs(jm) - 1;
-                            best = min(best, sat_add(D[(c + 1) * HK_DSTRIDE + j + 1],
-                                                     __ldcg(p.h + static_cast<int64_t>(s | (1u << j)) * k + j)));
-                        }
+#pragma unroll
+                        for (int j = 0; j < HK_MAX_K; ++j)
+                            if (j < k && !((s >> j) & 1u)) best = min(best, sat_add(__ldg(Dr + j + 1), hv[j]));
                     }
-                    __stcg(hs + c, best);
+                    __stcg(hq + c * side + s, best);
                 }
             }
             if (!grid_sync(p.bar, p.err, p.max_spins)) return;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // rebuild: one thread per order, lexicographically first optimal sequence
+        for (long long qi = gtid; qi < nb; qi += nthreads) {
+            const int q = q0 + static_cast<int>(qi);
+            const int k = kq[qi];
+            if (k == 0) continue;
+            const int o = p.list[q];
+            const int64_t b = p.t.offs[o];
+            const uint32_t* D = p.D21 + static_cast<int64_t>(q) * HK_DBLOCK;
+            const uint32_t* hq = p.h + base[qi];
+            const int64_t side = static_cast<int64_t>(1) << k;
             uint32_t best = INF_U;
-            for (int j = 0; j < k; ++j) best = min(best, sat_add(D[j + 1], __ldcg(p.h + static_cast<int64_t>(1u << j) * k + j)));
+            for (int j = 0; j < k; ++j) best = min(best, sat_add(__ldg(D + j + 1), __ldcg(hq + j * side + (1u << j))));
             int32_t* pp = p.perm + b;
             if (best >= INF_U) {
                 p.cost[o] = WR_INF;
@@ -128,8 +208,8 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
                 for (int pos = 0; pos < k; ++pos) {
                     for (int j = 0; j < k; ++j) {
                         if (s & (1u << j)) continue;
-                        const uint32_t r = __ldcg(p.h + static_cast<int64_t>(s | (1u << j)) * k + j);
-                        if (sat_add(D[cur * HK_DSTRIDE + j + 1], r) == rem) {
+                        const uint32_t r = __ldcg(hq + j * side + (s | (1u << j)));
+                        if (sat_add(__ldg(D + cur * HK_DSTRIDE + j + 1), r) == rem) {
                             pp[pos] = j;
                             s |= 1u << j;
                             rem = r;
@@ -140,8 +220,9 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
                 }
             }
         }
-        // the table and the shared matrix are reused by the next order
+        // the table buffer is reused by the next batch
         if (!grid_sync(p.bar, p.err, p.max_spins)) return;
+        q0 += nb;
     }
 }
 
@@ -166,9 +247,10 @@ int hk_blocks(int device) {
 }
 
 cudaError_t hk_launch_solve(const int32_t* list, const int32_t* count, const uint32_t* D21, uint32_t* h,
-                            const TourBufs& t, int32_t* cost, int32_t* perm, int32_t* status, GridBar* bar, int* err,
-                            unsigned long long max_spins, int blocks, cudaStream_t s) {
-    HkParams p{list, count, D21, h, t, cost, perm, status, bar, err, max_spins};
+                            unsigned long long h_words, const TourBufs& t, int32_t* cost, int32_t* perm,
+                            int32_t* status, GridBar* bar, int* err, unsigned long long max_spins, int blocks,
+                            cudaStream_t s) {
+    HkParams p{list, count, D21, h, h_words, t, cost, perm, status, bar, err, max_spins};
     void* args[] = {&p};
     return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(hk_solve_kernel), dim3(blocks), dim3(256), args, 0,
                                        s);

@@ -237,9 +237,24 @@ cudaError_t paths_launch(const PathsLaunch& l, const BfSegment& seg, int32_t* no
                          cudaStream_t s);
 cudaError_t paths_launch_offsets(const PathsLaunch& l, int64_t* node_offs, cudaStream_t s);
 
-// Cluster-patched approximate routing (wr_cluster.cu); xy: 2 int32 plan coordinates per node
-cudaError_t cluster_launch(int32_t n, const TourBufs& t, const int32_t* xy, int32_t m, int open_path, int32_t* cost,
-                           int32_t* perm, int32_t* status, cudaStream_t s);
+// Cluster-patched approximate routing (wr_cluster.cu); xy: 2 int32 plan coordinates per node.
+// Order o's clusters are sub-orders o*m .. o*m + m-1 routed by the exhaustive enumeration.
+constexpr int CL_MAX = 10;   // stops per cluster
+constexpr int CL_MAX_M = 6;  // clusters per order
+struct ClusterBufs {
+    int32_t* sub_k;               // n*m: stops of each cluster (0: empty slot)
+    int32_t* sub_status;          // n*m: WR_ORDER_OK for a cluster, else BAD (no units)
+    int32_t* sub_flags;           // n*m: 0
+    uint32_t* sub_D;              // n*m * DBLOCK: the cluster's legs, free depot legs
+    unsigned long long* members;  // n*m: pick indices (4 bits each) | count << 60
+    int32_t* sub_perm;            // n*m * WR_MAX_K: the clusters' routes (sub-order sequences)
+    int32_t* order_state;         // n: the order's status before patching
+    int32_t* n_clusters;          // n
+};
+cudaError_t cluster_launch_split(int32_t n, const TourBufs& t, const int32_t* xy, int32_t m, const ClusterBufs& cb,
+                                 cudaStream_t s);
+cudaError_t cluster_launch_patch(int32_t n, const TourBufs& t, int32_t m, int open_path, const ClusterBufs& cb,
+                                 int32_t* cost, int32_t* perm, int32_t* status, cudaStream_t s);
 
 // Held-Karp for orders of WR_MAX_K+1 .. max_k picks (wr_hk.cu)
 cudaError_t hk_launch_select(int32_t n, const TourBufs& t, int32_t max_k, int32_t* list, int32_t* count,
@@ -249,7 +264,8 @@ cudaError_t hk_launch_gather(int32_t n, const int32_t* list, const int32_t* coun
                              cudaStream_t s);
 int hk_blocks(int device);
 cudaError_t hk_launch_solve(const int32_t* list, const int32_t* count, const uint32_t* D21, uint32_t* h,
-                            const TourBufs& t, int32_t* cost, int32_t* perm, int32_t* status, GridBar* bar, int* err,
-                            unsigned long long max_spins, int blocks, cudaStream_t s);
+                            unsigned long long h_words, const TourBufs& t, int32_t* cost, int32_t* perm,
+                            int32_t* status, GridBar* bar, int* err, unsigned long long max_spins, int blocks,
+                            cudaStream_t s);
 
 }  // namespace wr

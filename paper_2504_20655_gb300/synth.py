@@ -417,6 +417,17 @@ def batching_workload(seed: int = SEED_BASE, n_orders: int = 20_000, n_sku: int 
     return g, zipf_orders(n_orders, k, smap, 1.1, seed)
 
 
+def large_order_workload(seed: int = SEED_BASE, n_orders: int = 128, k_lo: int = 13, k_hi: int = 20,
+                         n_sku: int = 50_000):
+    """Medium layout; orders of k ~ U{k_lo..k_hi} distinct Zipf(1.1) picks: orders too large
+    for exhaustive enumeration, routed exactly by Held-Karp."""
+    lay = medium_layout(seed)
+    g = lay.build()
+    smap = sku_slot_map(n_sku, lay.n_slots, seed)
+    k = uniform_k(n_orders, k_lo, k_hi, seed)
+    return g, zipf_orders(n_orders, k, smap, 1.1, seed, width=160)
+
+
 def scale_workload(seed: int = SEED_BASE, n_src: int = 4096):
     lay = scale_layout(seed)
     g = lay.build()

@@ -233,6 +233,24 @@ def wr_route_orders(ctx, offs, picks, cost, perm, status, stream=None):
            "wr_route_orders")
 
 
+def wr_route_nodes(ctx, offs, picks, perm, node_offs, nodes=None, max_nodes=0, stream=None):
+    """Node-level routes into caller buffers (numpy or torch, all host or all device):
+    node_offs (n+1) always, nodes (max_nodes) unless None (count only)."""
+    n = int(len(offs)) - 1
+    po, k1, a1 = _ptr(offs, np.int64)
+    pp, k2, a2 = _ptr(picks, np.int32)
+    pm, k3, a3 = _ptr(perm, np.int32)
+    pn, k4, a4 = _ptr(node_offs, np.int64)
+    pd, k5, a5 = _ptr(nodes, np.int32)
+    for x, a in ((node_offs, a4), (nodes, a5)):
+        if isinstance(x, np.ndarray) and a is not x:
+            raise ValueError("output numpy arrays must be contiguous")
+    kinds = (k1, k2, k3, k4) + ((k5,) if nodes is not None else ())
+    c = ctypes.c_void_p
+    _check(load_library().wr_route_nodes(ctx, n, c(po), c(pp), c(pm), c(pn), c(pd) if pd else None,
+                                         int(max_nodes), _kind(*kinds), _stream(stream)), "wr_route_nodes")
+
+
 def wr_bf_rows(ctx, src, rows, ld, stream=None):
     p_s, k1, a1 = _ptr(src, np.int32)
     p_r, k2, a2 = _ptr(rows, np.int32)

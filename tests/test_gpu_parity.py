@@ -706,3 +706,42 @@ def test_wait_limit_reports_timeout_and_device_stays_usable(wr, orc, tiling):
         assert (r2.bf_rows(src) == orc.sssp_rows(g, src, "dijkstra", NT)).all()
     finally:
         r2.close()
+
+
+def test_route_clustered_uneven_orders(wr, orc):
+    """Clustered routing of orders of 2..12 picks: with one cluster the orders above ten
+    stops are WR_ORDER_BAD on both sides, with four clusters every order is routed; the
+    results equal the oracle's element by element."""
+    lay = synth.medium_layout()
+    g, o = synth.batching_workload(n_orders=400)
+    xy = lay.coords()
+    assert (o.k() > 10).any()
+    for m in (1, 4):
+        r = wr.Router(device=0)
+        try:
+            r.load_graph(g)
+            r.set_clusters(m, xy)
+            cost, perm, status = r.route_orders(o.offs, o.picks)
+        finally:
+            r.close()
+        c, p, s = orc.route_orders_clustered(g, o, xy, m, False, NT)
+        assert (status == s).all() and (cost == c).all() and (perm[:len(p)] == p).all(), m
+        if m == 1:
+            assert (s[o.k() > 10] == 2).all()
+
+
+def test_route_held_karp_full_batch_and_small_budget(wr, orc):
+    """The large-order workload (128 orders of 13..20 picks) through batched Held-Karp
+    against the oracle's Held-Karp; then again under a 64 MiB budget, where the tables
+    are solved in many small batches and the rows in several segments: same results."""
+    g, o = synth.large_order_workload()
+    c, p, s = orc.route_orders(g, o, "dijkstra", "heldkarp", NT, max_k=20)
+    assert (s == 0).all()
+    for budget in (2 << 30, 64 << 20):
+        r = wr.Router(device=0, max_k=20, mem_budget_bytes=budget)
+        try:
+            r.load_graph(g)
+            cost, perm, status = r.route_orders(o.offs, o.picks)
+        finally:
+            r.close()
+        assert (status == s).all() and (cost == c).all() and (perm[:len(p)] == p).all(), budget
