@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -63,7 +64,7 @@ class ClockSampler:
     def __init__(self, index=0):
         self.proc = None
         self.index = index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"wroute_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
