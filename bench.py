@@ -171,9 +171,12 @@ def traffic_for(workload, tuned):
 
 
 def sweep_kernel_name(tuning):
-    """The Bellman-Ford sweep kernel a tuning selects (warp tiles or CTA tiles)."""
-    warp = tuning["bf_tiling"] == 1 or (tuning["bf_tiling"] == 0 and tuning["tile_cap"] <= 256)
-    return "bf_warp_kernel" if warp else "bf_sweeps_kernel"
+    """The Bellman-Ford kernel a tuning selects (warp tiles, one or two source groups per warp;
+    the warp worklist; CTA tiles)."""
+    t = tuning["bf_tiling"]
+    if t == 0:
+        t = 1 if tuning["tile_cap"] <= 256 else 2
+    return {1: "bf_warp_kernel", 4: "bf_warp_kernel", 3: "bf_warp_async_kernel"}.get(t, "bf_sweeps_kernel")
 
 
 def cpu_oracle_rows_rate(g, src, budget_s=15.0, n_threads=None):

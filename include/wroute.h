@@ -98,7 +98,8 @@ typedef struct {
     int32_t bf_tiling;      /* sweep tiling: 1 = one warp per tile (lane = source; tile_cap 128 or 256),
                                2 = one CTA per tile (quads of sources per warp), 3 = warp tiles driven by
                                an asynchronous worklist instead of sweeps (tile_cap 128 or 256; no sweep
-                               trace, wr_stats.sweeps = 0); 0 = 1 up to 256-slot tiles, else 2.
+                               trace, wr_stats.sweeps = 0), 4 = warp tiles of two 32-source groups
+                               (lane = source of each; tile_cap 128); 0 = 1 up to 256-slot tiles, else 2.
                                Defaults: tile_cap 128, run_target 60, warp tiles */
 } wr_tuning;
 

@@ -78,7 +78,10 @@ int resolved_tiling(const wr_ctx* c) {
 // Sweep kernel for the context's tiling and tile size.
 int prepare_sweeps(wr_ctx* c) {
     const int tiling = resolved_tiling(c);
-    if (tiling == 1 || tiling == 3) return wr::bf_prepare_warp(c->hp.tile_cap, tiling == 3, c->device, &c->bf_info);
+    if (tiling == 1 || tiling == 3 || tiling == 4)
+        return wr::bf_prepare_warp(c->hp.tile_cap,
+                                   tiling == 3 ? wr::WARP_ASYNC : tiling == 4 ? wr::WARP_PAIRS : wr::WARP_SWEEPS,
+                                   c->device, &c->bf_info);
     return wr::bf_prepare(c->hp.tile_cap, c->tune.bf_warps, c->device, &c->bf_info);
 }
 
@@ -274,7 +277,8 @@ bool valid_tuning(const wr_tuning* t) {
         return false;
     if (t->bf_warps != 0 && t->bf_warps != 4 && t->bf_warps != 8) return false;
     if (t->tile_cap >= 512 && t->bf_warps == 4) return false;
-    if (t->bf_tiling < 0 || t->bf_tiling > 3 || ((t->bf_tiling == 1 || t->bf_tiling == 3) && t->tile_cap > 256))
+    if (t->bf_tiling < 0 || t->bf_tiling > 4 || ((t->bf_tiling == 1 || t->bf_tiling == 3) && t->tile_cap > 256) ||
+        (t->bf_tiling == 4 && t->tile_cap != 128))
         return false;
     return true;
 }
@@ -1124,7 +1128,7 @@ int wr_autotune(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* picks,
     };
     struct BfCand { int tiling, tile_cap, run_target; };
     // run_target about half the tile lets two segments (the faces of an aisle) share one tile
-    const BfCand bf[] = {{1, 256, 120}, {1, 128, 60}, {1, 256, 200}, {3, 128, 60}, {2, 256, 120}, {2, 256, 200}, {2, 512, 240}};
+    const BfCand bf[] = {{1, 256, 120}, {1, 128, 60}, {4, 128, 60}, {1, 256, 200}, {3, 128, 60}, {2, 256, 120}, {2, 256, 200}, {2, 512, 240}};
     wr_tuning best = start;
     float best_ms = 3.4e38f;
     int rc = WR_OK;

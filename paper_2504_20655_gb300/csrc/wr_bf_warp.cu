@@ -28,11 +28,13 @@
 
 namespace wr {
 
-template <int TILE>
+// GPW source groups per warp: lane b holds source b of each group, the
+// groups' lines side by side in one slot (a 128 x GPW-byte row per slot).
+template <int TILE, int GPW = 1>
 struct __align__(128) WarpTile {
-    uint32_t rows[TILE][32];  // slot-major: rows[i][b] = source b of tile slot i (own nodes, then halo)
-    uint4 desc[2 * TILE];     // compact descriptors of the run's nodes: forward, backward
-    uint2 wx[2 * TILE];       // the run's extra arcs: forward, then backward
+    uint32_t rows[TILE][32 * GPW];  // slot-major: rows[i][32 g + b] = source b of group g at tile slot i
+    uint4 desc[2 * TILE];           // compact descriptors of the run's nodes: forward, backward
+    uint2 wx[2 * TILE];             // the run's extra arcs: forward, then backward
 };
 
 constexpr int BLK = 4;  // nodes per pipelined block
@@ -40,15 +42,20 @@ constexpr int BLK = 4;  // nodes per pipelined block
 // Run metadata of one work item (the same in every lane).
 struct TileMeta {
     int item, r, g, len, h0, hn, flags;
+    int ng;   // source groups of the item (GPW, or fewer for the last item of a run)
     int4 rs;  // {a0, alen, b0, blen}
     int4 rx;  // extras {first entry, forward count, backward count, 0}
 };
 
+// Item = run x items_per_run + j, its groups GPW j .. GPW j + GPW - 1 (those below G).
+template <int GPW>
 __device__ __forceinline__ TileMeta load_meta(const BfParams& p, const int32_t* list, int it, int G) {
+    const int ipr = (G + GPW - 1) / GPW;
     TileMeta m;
     m.item = __ldcg(list + it);
-    m.r = m.item / G;
-    m.g = m.item - m.r * G;
+    m.r = m.item / ipr;
+    m.g = (m.item - m.r * ipr) * GPW;
+    m.ng = min(GPW, G - m.g);
     m.rs = __ldg(p.g.run_seg + m.r);
     m.len = m.rs.y + m.rs.w;
     m.h0 = __ldg(p.g.halo_ptr + m.r);
@@ -58,39 +65,52 @@ __device__ __forceinline__ TileMeta load_meta(const BfParams& p, const int32_t* 
     return m;
 }
 
+// Byte offset of a descriptor's slot offset (slot x 128) in a GPW-group tile.
+template <int GPW>
+__device__ __forceinline__ uint32_t line_off(uint32_t o) {
+    return GPW == 1 ? o : o * GPW;
+}
+
 // Fold n extra arcs into the tile before a pass: each {dst | src << 16, w}
-// lowers line dst by line src + w in this lane's column.  Returns changed bits.
-template <int TILE>
-__device__ __forceinline__ uint32_t fold_extras(WarpTile<TILE>& t, int e0, int n, int lane) {
+// lowers line dst by line src + w in this lane's columns; changed bits per group.
+template <int TILE, int GPW>
+__device__ __forceinline__ void fold_extras(WarpTile<TILE, GPW>& t, int e0, int n, int lane, uint32_t (&chg)[GPW]) {
     char* cb = reinterpret_cast<char*>(&t.rows[0][lane]);
-    uint32_t chg = 0;
 #pragma unroll 1
     for (int e = e0; e < e0 + n; ++e) {
         const uint2 x = t.wx[e];
-        uint32_t* dst = reinterpret_cast<uint32_t*>(cb + (x.x & 0xFFFFu));
-        const uint32_t cur = *dst;
-        const uint32_t v = __viaddmin_u32(*reinterpret_cast<const uint32_t*>(cb + (x.x >> 16)), x.y, cur);
-        *dst = v;
-        chg |= v ^ cur;
+        char* dp = cb + line_off<GPW>(x.x & 0xFFFFu);
+        const char* sp = cb + line_off<GPW>(x.x >> 16);
+#pragma unroll
+        for (int g = 0; g < GPW; ++g) {
+            uint32_t* dst = reinterpret_cast<uint32_t*>(dp + 128 * g);
+            const uint32_t cur = *dst;
+            const uint32_t v = __viaddmin_u32(*reinterpret_cast<const uint32_t*>(sp + 128 * g), x.y, cur);
+            *dst = v;
+            chg[g] |= v ^ cur;
+        }
     }
-    return chg;
 }
 
-// One block's inputs: current value, the best over its non-carry arcs, carry weight.
+// One block's inputs: current values, the best over the non-carry arcs, carry weight.
+template <int GPW>
 struct BlkIn {
-    uint32_t cur[BLK], m[BLK], cw[BLK];
+    uint32_t cur[BLK][GPW], m[BLK][GPW], cw[BLK];
 };
 
 // Block b of a pass: nodes ib, ib +- 1, ... (ib = b * BLK forward, len - 1 - b * BLK
 // backward).  PART: the block runs past the run's end and its missing nodes
-// are neutral (infinite value, blocking weights, no loads).
-template <int TILE, bool FWD, bool PART>
-__device__ __forceinline__ void load_blk(const WarpTile<TILE>& t, const char* cb, int len, int b, BlkIn& in) {
+// are neutral (infinite value, blocking weights, no loads).  The descriptor
+// and the arc addresses of a node serve all GPW groups.
+template <int TILE, int GPW, bool FWD, bool PART>
+__device__ __forceinline__ void load_blk(const WarpTile<TILE, GPW>& t, const char* cb, int len, int b,
+                                         BlkIn<GPW>& in) {
+    constexpr int LINE = 128 * GPW;
     const int ib = FWD ? b * BLK : len - 1 - b * BLK;
     const uint4* dp = &t.desc[2 * ib + (FWD ? 0 : 1)];
-    const char* rp = cb + 128 * ib;
+    const char* rp = cb + LINE * ib;
     uint4 d[BLK];
-    uint32_t s0[BLK], s1[BLK];
+    uint32_t s0[BLK][GPW], s1[BLK][GPW];
 #pragma unroll
     for (int j = 0; j < BLK; ++j) {
         const int st = FWD ? j : -j;
@@ -101,43 +121,56 @@ __device__ __forceinline__ void load_blk(const WarpTile<TILE>& t, const char* cb
     for (int j = 0; j < BLK; ++j) {
         const int st = FWD ? j : -j;
         const bool valid = !PART || (FWD ? ib + j < len : ib - j >= 0);
-        in.cur[j] = valid ? *reinterpret_cast<const uint32_t*>(rp + 128 * st) : INF_U;
-        s0[j] = valid ? *reinterpret_cast<const uint32_t*>(cb + (d[j].y & 0xFFFFu)) : 0u;
-        s1[j] = valid ? *reinterpret_cast<const uint32_t*>(cb + (d[j].y >> 16)) : 0u;
+        const char* a0 = cb + line_off<GPW>(d[j].y & 0xFFFFu);
+        const char* a1 = cb + line_off<GPW>(d[j].y >> 16);
+#pragma unroll
+        for (int g = 0; g < GPW; ++g) {
+            in.cur[j][g] = valid ? *reinterpret_cast<const uint32_t*>(rp + LINE * st + 128 * g) : INF_U;
+            s0[j][g] = valid ? *reinterpret_cast<const uint32_t*>(a0 + 128 * g) : 0u;
+            s1[j][g] = valid ? *reinterpret_cast<const uint32_t*>(a1 + 128 * g) : 0u;
+        }
         in.cw[j] = d[j].x;
     }
 #pragma unroll
     for (int j = 0; j < BLK; ++j)
-        in.m[j] = __viaddmin_u32(s1[j], d[j].w, __viaddmin_u32(s0[j], d[j].z, in.cur[j]));
+#pragma unroll
+        for (int g = 0; g < GPW; ++g)
+            in.m[j][g] = __viaddmin_u32(s1[j][g], d[j].w, __viaddmin_u32(s0[j][g], d[j].z, in.cur[j][g]));
 }
 
-// Carry chain of one block; stores the new values, returns the changed bits.
-template <bool FWD, bool PART>
-__device__ __forceinline__ uint32_t chain_blk(char* cb, int len, int b, const BlkIn& in, uint32_t& xprev) {
+// Carry chains of one block (one per group); stores the new values, folds the
+// changed bits into chg (per group).
+template <int GPW, bool FWD, bool PART>
+__device__ __forceinline__ void chain_blk(char* cb, int len, int b, const BlkIn<GPW>& in, uint32_t (&xprev)[GPW],
+                                          uint32_t (&chg)[GPW]) {
+    constexpr int LINE = 128 * GPW;
     const int ib = FWD ? b * BLK : len - 1 - b * BLK;
-    char* rp = cb + 128 * ib;
-    uint32_t chg = 0;
+    char* rp = cb + LINE * ib;
 #pragma unroll
     for (int j = 0; j < BLK; ++j) {
         const int st = FWD ? j : -j;
-        const uint32_t x = __viaddmin_u32(xprev, in.cw[j], in.m[j]);
-        if (!PART || (FWD ? ib + j < len : ib - j >= 0)) {
-            *reinterpret_cast<uint32_t*>(rp + 128 * st) = x;
-            chg |= x ^ in.cur[j];
+#pragma unroll
+        for (int g = 0; g < GPW; ++g) {
+            const uint32_t x = __viaddmin_u32(xprev[g], in.cw[j], in.m[j][g]);
+            if (!PART || (FWD ? ib + j < len : ib - j >= 0)) {
+                *reinterpret_cast<uint32_t*>(rp + LINE * st + 128 * g) = x;
+                chg[g] |= x ^ in.cur[j][g];
+            }
+            xprev[g] = x;
         }
-        xprev = x;
     }
-    return chg;
 }
 
 // One pass over the run: whole blocks of BLK nodes in pass order, the loads
 // of block b + 1 issued before the chain of block b, then the partial block.
-template <int TILE, bool FWD>
-__device__ __forceinline__ uint32_t warp_pass(WarpTile<TILE>& t, int len, int alen, int lane) {
+template <int TILE, int GPW, bool FWD>
+__device__ __forceinline__ void warp_pass(WarpTile<TILE, GPW>& t, int len, int alen, int lane, uint32_t (&chg)[GPW]) {
     char* cb = reinterpret_cast<char*>(&t.rows[0][lane]);
     const int nf = len / BLK;
-    uint32_t xprev = INF_U, chg = 0;
-    BlkIn a, c;
+    uint32_t xprev[GPW];
+#pragma unroll
+    for (int g = 0; g < GPW; ++g) xprev[g] = INF_U;
+    BlkIn<GPW> a, c;
     // forward: the second segment's lines are waited for before the first block that reaches them
     bool second = !FWD || alen >= len;
     auto need = [&](int b) {
@@ -149,80 +182,91 @@ __device__ __forceinline__ uint32_t warp_pass(WarpTile<TILE>& t, int len, int al
     };
     if (nf > 0) {
         need(0);
-        load_blk<TILE, FWD, false>(t, cb, len, 0, a);
+        load_blk<TILE, GPW, FWD, false>(t, cb, len, 0, a);
     }
 #pragma unroll 1
     for (int b = 0; b < nf; b += 2) {
         if (b + 1 < nf) {
             need(b + 1);
-            load_blk<TILE, FWD, false>(t, cb, len, b + 1, c);
+            load_blk<TILE, GPW, FWD, false>(t, cb, len, b + 1, c);
         }
-        chg |= chain_blk<FWD, false>(cb, len, b, a, xprev);
+        chain_blk<GPW, FWD, false>(cb, len, b, a, xprev, chg);
         if (b + 2 < nf) {
             need(b + 2);
-            load_blk<TILE, FWD, false>(t, cb, len, b + 2, a);
+            load_blk<TILE, GPW, FWD, false>(t, cb, len, b + 2, a);
         }
-        if (b + 1 < nf) chg |= chain_blk<FWD, false>(cb, len, b + 1, c, xprev);
+        if (b + 1 < nf) chain_blk<GPW, FWD, false>(cb, len, b + 1, c, xprev, chg);
     }
     if (nf * BLK < len) {
         need(nf);
-        load_blk<TILE, FWD, true>(t, cb, len, nf, a);
-        chg |= chain_blk<FWD, true>(cb, len, nf, a, xprev);
+        load_blk<TILE, GPW, FWD, true>(t, cb, len, nf, a);
+        chain_blk<GPW, FWD, true>(cb, len, nf, a, xprev, chg);
     }
-    return chg;
 }
 
 // Runs without compact descriptors (a node with more than two non-carry arcs
 // in a pass, or a halo larger than the tile): descriptors and arcs from global
 // memory, sources from the tile or, past its capacity, from the rows in L2.
-template <int TILE>
-__device__ __noinline__ uint32_t warp_passes_generic(const BfParams& p, WarpTile<TILE>& t, int4 rs, int len, int lane,
-                                                     int64_t lane_off) {
-    uint32_t* col = &t.rows[0][lane];
+template <int TILE, int GPW>
+__device__ __noinline__ uint32_t warp_passes_generic(const BfParams& p, WarpTile<TILE, GPW>& t, int4 rs, int len,
+                                                     int lane, const TileMeta& m, int G) {
     const uint32_t* rows = p.seg.rows;
     const int64_t ld = p.seg.ld;
     uint32_t chg = 0;
-    uint32_t carry = INF_U;
-    for (int i = 0; i < len; ++i) {
-        const int4 d = __ldg(p.g.node_desc + run_node(rs, i));
-        const uint32_t cur = col[32 * i];
-        uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.x), cur);
-        for (int q = d.z; q < d.w; ++q) {
-            const uint2 e = __ldg(p.g.arc2 + q);
-            const uint32_t x = (e.x & GLOBAL_REF) ? ld_l2(rows + static_cast<int64_t>(e.x & ~GLOBAL_REF) * ld + lane_off + lane)
-                                                  : col[32 * e.x];
-            best = __viaddmin_u32(x, e.y, best);
+#pragma unroll 1
+    for (int g = 0; g < m.ng; ++g) {
+        uint32_t* col = &t.rows[0][32 * g + lane];
+        const int64_t lane_off = seg_col0(p.seg, m.g + g);
+        uint32_t carry = INF_U;
+        for (int i = 0; i < len; ++i) {
+            const int4 d = __ldg(p.g.node_desc + run_node(rs, i));
+            const uint32_t cur = col[32 * GPW * i];
+            uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.x), cur);
+            for (int q = d.z; q < d.w; ++q) {
+                const uint2 e = __ldg(p.g.arc2 + q);
+                const uint32_t x = (e.x & GLOBAL_REF)
+                                       ? ld_l2(rows + static_cast<int64_t>(e.x & ~GLOBAL_REF) * ld + lane_off + lane)
+                                       : col[32 * GPW * e.x];
+                best = __viaddmin_u32(x, e.y, best);
+            }
+            col[32 * GPW * i] = best;
+            chg |= best ^ cur;
+            carry = best;
         }
-        col[32 * i] = best;
-        chg |= best ^ cur;
-        carry = best;
-    }
-    carry = INF_U;
-    for (int i = len - 1; i >= 0; --i) {
-        const int4 d = __ldg(p.g.node_desc + run_node(rs, i));
-        const int end = __ldg(&p.g.node_desc[run_node(rs, i) + 1].z);
-        const uint32_t cur = col[32 * i];
-        uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.y), cur);
-        for (int q = d.w; q < end; ++q) {
-            const uint2 e = __ldg(p.g.arc2 + q);
-            best = __viaddmin_u32(col[32 * e.x], e.y, best);
+        carry = INF_U;
+        for (int i = len - 1; i >= 0; --i) {
+            const int4 d = __ldg(p.g.node_desc + run_node(rs, i));
+            const int end = __ldg(&p.g.node_desc[run_node(rs, i) + 1].z);
+            const uint32_t cur = col[32 * GPW * i];
+            uint32_t best = __viaddmin_u32(carry, static_cast<uint32_t>(d.y), cur);
+            for (int q = d.w; q < end; ++q) {
+                const uint2 e = __ldg(p.g.arc2 + q);
+                best = __viaddmin_u32(col[32 * GPW * e.x], e.y, best);
+            }
+            col[32 * GPW * i] = best;
+            chg |= best ^ cur;
+            carry = best;
         }
-        col[32 * i] = best;
-        chg |= best ^ cur;
-        carry = best;
     }
     return chg;
 }
 
 // One tile by one warp: stage, forward pass, backward pass, write back the
-// own lines.  Returns true (warp-uniform) if a row dropped.
-template <int TILE>
-__device__ __forceinline__ bool warp_tile(const BfParams& p, const TileMeta& m, WarpTile<TILE>& t, int lane) {
+// own lines.  Returns true (warp-uniform) if a row dropped.  A group slot
+// past G (ng < GPW) is neither staged nor written back; its columns hold
+// stale values that only feed its own discarded chains.
+template <int TILE, int GPW>
+__device__ __forceinline__ bool warp_tile(const BfParams& p, const TileMeta& m, WarpTile<TILE, GPW>& t, int lane) {
     const int64_t ld = p.seg.ld;
-    const int64_t lane_off = seg_col0(p.seg, m.g);
     uint32_t* rows = p.seg.rows;
     const bool compact = (m.flags & RUN_COMPACT) != 0;
-    const int sub = lane >> 3, part = (lane & 7) * 4;  // 8 lanes x 16 bytes per line, 4 lines per instruction
+    // 8 lanes x 16 bytes per 128-byte line; 4 / GPW slots per instruction
+    constexpr int LPS = 8 * GPW;  // lanes per slot
+    const int sub = lane / LPS, gq = (lane % LPS) / 8, part = (lane & 7) * 4;
+    constexpr int SPI = 32 / LPS;  // slots per instruction
+    const bool act = gq < m.ng;
+    const int64_t col0 = act ? seg_col0(p.seg, m.g + gq) : 0;
+    const int cpart = 32 * gq + part;
     // group A: descriptors, extras, halo lines, the first segment's lines
     const int nx = m.rx.y + m.rx.z;
     if (compact) {
@@ -230,50 +274,58 @@ __device__ __forceinline__ bool warp_tile(const BfParams& p, const TileMeta& m, 
             cp_async16(&t.desc[e], p.g.cdesc + 2 * static_cast<int64_t>(run_node(m.rs, e >> 1)) + (e & 1));
         for (int e = lane; 2 * e < nx; e += 32) cp_async16(&t.wx[2 * e], p.g.wx + m.rx.x + 2 * e);
     }
-    for (int h = sub; h < m.hn; h += 4) {
-        const int node = __ldg(p.g.halo_nodes + m.h0 + h);
-        cp_async16(&t.rows[m.len + h][part], rows + static_cast<int64_t>(node) * ld + lane_off + part);
-    }
-    {
-        const uint32_t* gp = rows + static_cast<int64_t>(m.rs.x + sub) * ld + lane_off + part;
-        for (int i = sub; i < m.rs.y; i += 4, gp += 4 * ld) cp_async16(&t.rows[i][part], gp);
+    if (act) {
+        for (int h = sub; h < m.hn; h += SPI) {
+            const int node = __ldg(p.g.halo_nodes + m.h0 + h);
+            cp_async16(&t.rows[m.len + h][cpart], rows + static_cast<int64_t>(node) * ld + col0 + part);
+        }
+        const uint32_t* gp = rows + static_cast<int64_t>(m.rs.x + sub) * ld + col0 + part;
+        for (int i = sub; i < m.rs.y; i += SPI, gp += SPI * ld) cp_async16(&t.rows[i][cpart], gp);
     }
     cp_async_commit();
     // group B: the second segment's lines
-    {
-        const uint32_t* gp = rows + static_cast<int64_t>(m.rs.z + sub) * ld + lane_off + part;
-        for (int i = sub; i < m.rs.w; i += 4, gp += 4 * ld) cp_async16(&t.rows[m.rs.y + i][part], gp);
+    if (act) {
+        const uint32_t* gp = rows + static_cast<int64_t>(m.rs.z + sub) * ld + col0 + part;
+        for (int i = sub; i < m.rs.w; i += SPI, gp += SPI * ld) cp_async16(&t.rows[m.rs.y + i][cpart], gp);
     }
     cp_async_commit();
 
     uint32_t chg = 0;
     if (compact) {
+        uint32_t cg[GPW];
+#pragma unroll
+        for (int g = 0; g < GPW; ++g) cg[g] = 0;
         int alen = m.rs.y;
         if (m.rx.y > 0) {
             // forward extras may touch either segment: everything lands first
             cp_async_wait_pending(0);
             __syncwarp();
-            chg = fold_extras<TILE>(t, 0, m.rx.y, lane);
+            fold_extras<TILE, GPW>(t, 0, m.rx.y, lane, cg);
             alen = m.len;
         } else {
             cp_async_wait_pending(1);  // group A landed: the forward pass starts on the first segment
             __syncwarp();
         }
-        chg |= warp_pass<TILE, true>(t, m.len, alen, lane);
-        if (m.rx.z > 0) chg |= fold_extras<TILE>(t, m.rx.y, m.rx.z, lane);
-        chg |= warp_pass<TILE, false>(t, m.len, m.rs.y, lane);
+        warp_pass<TILE, GPW, true>(t, m.len, alen, lane, cg);
+        if (m.rx.z > 0) fold_extras<TILE, GPW>(t, m.rx.y, m.rx.z, lane, cg);
+        warp_pass<TILE, GPW, false>(t, m.len, m.rs.y, lane, cg);
+        // an absent group's columns hold stale values: only the present groups count
+#pragma unroll
+        for (int g = 0; g < GPW; ++g)
+            if (g < m.ng) chg |= cg[g];
     } else {
         cp_async_wait_pending(0);
         __syncwarp();
-        chg = warp_passes_generic<TILE>(p, t, m.rs, m.len, lane, lane_off);
+        chg = warp_passes_generic<TILE, GPW>(p, t, m.rs, m.len, lane, m, 0);
     }
     const bool changed = __any_sync(FULL_MASK, chg != 0u);
     if (changed) {
         // every own line goes back (a visited line is read and written once per sweep)
         __syncwarp();
-        for (int i = sub; i < m.len; i += 4)
-            __stcg(reinterpret_cast<uint4*>(rows + static_cast<int64_t>(run_node(m.rs, i)) * ld + lane_off + part),
-                   *reinterpret_cast<const uint4*>(&t.rows[i][part]));
+        if (act)
+            for (int i = sub; i < m.len; i += SPI)
+                __stcg(reinterpret_cast<uint4*>(rows + static_cast<int64_t>(run_node(m.rs, i)) * ld + col0 + part),
+                       *reinterpret_cast<const uint4*>(&t.rows[i][cpart]));
     }
     __syncwarp();  // every lane's reads of the tile done before the next staging overwrites it
     return changed;
@@ -317,15 +369,16 @@ __device__ __forceinline__ void frontier_push_warp(const BfParams& p, int n, int
     }
 }
 
-template <int TILE, int NW>
+template <int TILE, int NW, int GPW>
 __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpTile<TILE>& t = reinterpret_cast<WarpTile<TILE>*>(smem_raw)[warp];
+    WarpTile<TILE, GPW>& t = reinterpret_cast<WarpTile<TILE, GPW>*>(smem_raw)[warp];
 
     const int n_lanes = segment_lanes(p.seg);
     const int G = (n_lanes + 31) >> 5;
     if (G == 0) return;  // same decision in every block
+    const int ipr = (G + GPW - 1) / GPW;  // items per run: GPW groups each
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthreads = gridDim.x * blockDim.x;
 
@@ -333,10 +386,10 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
     // the tile holding each source and the tiles it feeds
     for (int b = gtid; b < n_lanes; b += nthreads) {
         const int r = __ldg(p.g.run_of_node + p.seg.src[p.seg.first + b]);
-        const int g = b >> 5;
-        frontier_push(p, r * G + g, 1);
+        const int g = (b >> 5) / GPW;
+        frontier_push(p, r * ipr + g, 1);
         const int q1 = __ldg(p.g.rout_ptr + r + 1);
-        for (int q = __ldg(p.g.rout_ptr + r); q < q1; ++q) frontier_push(p, __ldg(p.g.rout_list + q) * G + g, 1);
+        for (int q = __ldg(p.g.rout_ptr + r); q < q1; ++q) frontier_push(p, __ldg(p.g.rout_list + q) * ipr + g, 1);
     }
     if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) return;
 
@@ -373,25 +426,25 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
         it = __shfl_sync(FULL_MASK, it, 0);
         it1 = __shfl_sync(FULL_MASK, it1, 0);
         TileMeta m{};
-        if (it < cnt) m = load_meta(p, list, it, G);
+        if (it < cnt) m = load_meta<GPW>(p, list, it, G);
         while (it < cnt) {
             int it2 = 0;
             if (lane == 0) it2 = atomicAdd(claim, 1);
             TileMeta m1{};
-            if (it1 < cnt) m1 = load_meta(p, list, it1, G);
-            const bool ch = warp_tile<TILE>(p, m, t, lane);
+            if (it1 < cnt) m1 = load_meta<GPW>(p, list, it1, G);
+            const bool ch = warp_tile<TILE, GPW>(p, m, t, lane);
             if (ch) {
                 // the tile itself and the runs it feeds, for the next sweep
                 const int q0 = __ldg(p.g.rout_ptr + m.r), nq = __ldg(p.g.rout_ptr + m.r + 1) - q0;
-                const int item = m.item, g = m.g;
+                const int item = m.item, g = m.g / GPW;
                 frontier_push_warp(p, nq + 1, sweep + 1, lane,
-                                   [&](int j) { return j == 0 ? item : __ldg(p.g.rout_list + q0 + j - 1) * G + g; });
+                                   [&](int j) { return j == 0 ? item : __ldg(p.g.rout_list + q0 + j - 1) * ipr + g; });
             }
             if (lane == 0) {
                 ++tiles;
-                nodes += static_cast<unsigned long long>(m.len);
+                nodes += static_cast<unsigned long long>(m.len) * m.ng;
                 bytes += static_cast<unsigned long long>(__ldg(p.g.run_meta_bytes + m.r)) +
-                         256ull * static_cast<unsigned long long>(m.len);
+                         256ull * static_cast<unsigned long long>(m.len) * m.ng;
             }
             it = it1;
             m = m1;
@@ -592,7 +645,7 @@ template <int TILE, int NW>
 __global__ void __launch_bounds__(32 * NW, 1) bf_warp_async_kernel(BfParams p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpTile<TILE>& t = reinterpret_cast<WarpTile<TILE>*>(smem_raw)[warp];
+    WarpTile<TILE, 1>& t = reinterpret_cast<WarpTile<TILE, 1>*>(smem_raw)[warp];
 
     const int n_lanes = segment_lanes(p.seg);
     const int G = (n_lanes + 31) >> 5;
@@ -630,13 +683,14 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_async_kernel(BfParams p) {
         m.item = item;
         m.r = item / G;
         m.g = item - m.r * G;
+        m.ng = 1;
         m.rs = __ldg(p.g.run_seg + m.r);
         m.len = m.rs.y + m.rs.w;
         m.h0 = __ldg(p.g.halo_ptr + m.r);
         m.hn = __ldg(p.g.halo_ptr + m.r + 1) - m.h0;
         m.flags = __ldg(p.g.run_flags + m.r);
         m.rx = __ldg(p.g.run_wx + m.r);
-        const bool ch = warp_tile<TILE>(p, m, t, lane);
+        const bool ch = warp_tile<TILE, 1>(p, m, t, lane);
         bool ok = true;
         if (ch) {
             __threadfence();  // this lane's row stores before the pushes that announce them
@@ -661,10 +715,10 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_async_kernel(BfParams p) {
     }
 }
 
-template <int TILE, int NW, bool ASYNC>
+template <int TILE, int NW, bool ASYNC, int GPW = 1>
 static int prepare_warp_one(int device, BfLaunchInfo* info) {
-    const size_t smem = sizeof(WarpTile<TILE>) * NW;
-    auto* fn = ASYNC ? bf_warp_async_kernel<TILE, NW> : bf_warp_kernel<TILE, NW>;
+    const size_t smem = sizeof(WarpTile<TILE, GPW>) * NW;
+    auto* fn = ASYNC ? bf_warp_async_kernel<TILE, NW> : bf_warp_kernel<TILE, NW, GPW>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
         return WR_ECUDA;
     int occ = 0;
@@ -679,11 +733,18 @@ static int prepare_warp_one(int device, BfLaunchInfo* info) {
     return WR_OK;
 }
 
-// Warps per CTA: as many 128- or 256-slot warp tiles as fit 227 KB of shared memory.
-int bf_prepare_warp(int tile_cap, bool async, int device, BfLaunchInfo* info) {
+// Warps per CTA: as many warp tiles as fit 227 KB of shared memory: 128-slot
+// tiles of one source group (10 warps) or two (5 warps), 256-slot tiles of one (5).
+int bf_prepare_warp(int tile_cap, int mode, int device, BfLaunchInfo* info) {
     switch (tile_cap) {
-        case 128: return async ? prepare_warp_one<128, 10, true>(device, info) : prepare_warp_one<128, 10, false>(device, info);
-        case 256: return async ? prepare_warp_one<256, 5, true>(device, info) : prepare_warp_one<256, 5, false>(device, info);
+        case 128:
+            if (mode == WARP_ASYNC) return prepare_warp_one<128, 10, true>(device, info);
+            if (mode == WARP_PAIRS) return prepare_warp_one<128, 5, false, 2>(device, info);
+            return prepare_warp_one<128, 10, false>(device, info);
+        case 256:
+            if (mode == WARP_ASYNC) return prepare_warp_one<256, 5, true>(device, info);
+            if (mode == WARP_PAIRS) return WR_EINVAL;
+            return prepare_warp_one<256, 5, false>(device, info);
         default: return WR_EINVAL;
     }
 }

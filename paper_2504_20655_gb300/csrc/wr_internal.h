@@ -174,9 +174,11 @@ struct BfLaunchInfo {
 };
 // picks the sweep kernel for (tile_cap, warps per CTA; 0 = default) and its co-resident grid
 int bf_prepare(int tile_cap, int warps, int device, BfLaunchInfo* info);
-// the warp-per-tile kernel (wr_bf_warp.cu) for tile_cap 128 or 256: sweeps with grid barriers, or
-// (async) one asynchronous worklist without sweeps
-int bf_prepare_warp(int tile_cap, bool async, int device, BfLaunchInfo* info);
+// the warp-per-tile kernel (wr_bf_warp.cu) for tile_cap 128 or 256: sweeps with grid barriers
+// (WARP_SWEEPS), the same with two source groups per warp (WARP_PAIRS, tile_cap 128), or one
+// asynchronous worklist without sweeps (WARP_ASYNC)
+constexpr int WARP_SWEEPS = 0, WARP_ASYNC = 1, WARP_PAIRS = 2;
+int bf_prepare_warp(int tile_cap, int mode, int device, BfLaunchInfo* info);
 cudaError_t bf_launch_init(const DevGraph& g, const BfSegment& seg, const BfWork& w, cudaStream_t s);
 cudaError_t bf_launch_sweeps(const DevGraph& g, const BfSegment& seg, const BfWork& w,
                              const BfLaunchInfo& info, cudaStream_t s);

@@ -43,7 +43,7 @@ def test_bf_rows_tiny_all_sources(router, orc):
     assert st["sweeps"] >= 1 and st["bytes_alg"] > 0
 
 
-@pytest.fixture(params=[2, 1, 3], ids=["cta_tiles", "warp_tiles", "warp_worklist"])
+@pytest.fixture(params=[2, 1, 3, 4], ids=["cta_tiles", "warp_tiles", "warp_worklist", "warp_pairs"])
 def tiling(request, router):
     saved = router.tuning()
     router.set_tuning(bf_tiling=request.param)
@@ -109,7 +109,10 @@ def test_bf_rows_high_in_degree(router, orc, tiling):
                                   dict(run_target=1, tile_cap=128, bf_tiling=1),
                                   dict(run_target=60, tile_cap=128, bf_tiling=3),
                                   dict(run_target=200, tile_cap=256, bf_tiling=3),
-                                  dict(run_target=1, tile_cap=128, bf_tiling=3)])
+                                  dict(run_target=1, tile_cap=128, bf_tiling=3),
+                                  dict(run_target=60, tile_cap=128, bf_tiling=4),
+                                  dict(run_target=96, tile_cap=128, bf_tiling=4),
+                                  dict(run_target=1, tile_cap=128, bf_tiling=4)])
 def test_bf_rows_medium_tuning_invariant(router, orc, tune):
     g = synth.medium_layout().build()
     saved = router.tuning()
@@ -683,7 +686,7 @@ def test_route_clustered_against_oracle(wr, orc):
             assert (c >= exact_c).all()
 
 
-@pytest.mark.parametrize("tiling", [1, 2, 3], ids=["warp_sweeps", "cta_sweeps", "warp_worklist"])
+@pytest.mark.parametrize("tiling", [1, 2, 3, 4], ids=["warp_sweeps", "cta_sweeps", "warp_worklist", "warp_pairs"])
 def test_wait_limit_reports_timeout_and_device_stays_usable(wr, orc, tiling):
     """Failure detection without a GPU fault: with a one-spin wait limit the sweep
     kernel's grid barriers (or worklist waits) give up, every block returns, and the call
