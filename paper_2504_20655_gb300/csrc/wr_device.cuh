@@ -29,29 +29,31 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Grid-wide barrier for a co-resident (cooperative) grid.  Every wait is
-// bounded by max_spins iterations; on expiry it records WR_ETIMEOUT in *err
-// and returns false, and every block then leaves the kernel.
+// Grid-wide barrier for a co-resident (cooperative) grid.  The barrier's two
+// words, count (low) and generation (high), are one 64-bit word: a block
+// arrives with one atomic add, and the last arrival resets the count and
+// advances the generation with a second one.  Every wait is bounded by
+// max_spins iterations; on expiry it records WR_ETIMEOUT in *err and returns
+// false, and every block then leaves the kernel.
 __device__ __forceinline__ bool grid_sync(GridBar* bar, int* err, unsigned long long max_spins) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned gen = ld_volatile(&bar->gen);
+        unsigned long long* word = reinterpret_cast<unsigned long long*>(bar);
         __threadfence();
-        const unsigned arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
+        const unsigned long long old = atomicAdd(word, 1ull);
+        const unsigned gen = static_cast<unsigned>(old >> 32);
+        if (static_cast<unsigned>(old) == gridDim.x - 1) {
+            atomicAdd(word, (1ull << 32) - gridDim.x);  // count back to 0, generation + 1
         } else {
             unsigned long long spins = 0;
-            while (ld_volatile(&bar->gen) == gen) {
-                if (ld_volatile(err) != 0) break;
+            while (static_cast<unsigned>(*reinterpret_cast<volatile unsigned long long*>(word) >> 32) == gen) {
+                if ((spins & 63) == 63 && ld_volatile(err) != 0) break;
                 if (++spins > max_spins) {
                     atomicCAS(err, 0, WR_ETIMEOUT);
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();

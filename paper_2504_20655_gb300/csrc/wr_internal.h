@@ -100,7 +100,7 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
 // device-side structures
 // --------------------------------------------------------------------------
 
-struct GridBar {
+struct alignas(8) GridBar {  // one 64-bit word: count (low), generation (high)
     unsigned int count;
     unsigned int gen;
 };

@@ -748,3 +748,34 @@ def test_route_held_karp_full_batch_and_small_budget(wr, orc):
         finally:
             r.close()
         assert (status == s).all() and (cost == c).all() and (perm[:len(p)] == p).all(), budget
+
+
+def test_route_nodes_device_buffers_one_call(wr):
+    """wr_route_nodes with device buffers and a node buffer sized from a count-only call:
+    one call writes the same nodes as the host path; a buffer one node short is ENOMEM."""
+    import torch
+    g, o = synth.medium_workload(n_orders=64)
+    r = wr.Router(device=0)
+    try:
+        r.load_graph(g)
+        _, perm, _ = r.route_orders(o.offs, o.picks)
+        perm = np.ascontiguousarray(perm[:o.offs[-1]])
+        h_offs, h_nodes = r.route_nodes(o.offs, o.picks, perm)
+        dev = torch.device("cuda", 0)
+        offs = torch.from_numpy(o.offs).to(dev)
+        picks = torch.from_numpy(o.picks).to(dev)
+        dperm = torch.from_numpy(perm).to(dev)
+        node_offs = torch.zeros(o.n + 1, dtype=torch.int64, device=dev)
+        wr.wr_route_nodes(r.ctx, offs, picks, dperm, node_offs, None, 0)
+        torch.cuda.synchronize()
+        total = int(node_offs[-1].item())
+        assert total == len(h_nodes)
+        nodes = torch.empty(total, dtype=torch.int32, device=dev)
+        wr.wr_route_nodes(r.ctx, offs, picks, dperm, node_offs, nodes, total)
+        torch.cuda.synchronize()
+        assert (node_offs.cpu().numpy() == h_offs).all() and (nodes.cpu().numpy() == h_nodes).all()
+        with pytest.raises(wr.WrError) as e:
+            wr.wr_route_nodes(r.ctx, offs, picks, dperm, node_offs, nodes, total - 1)
+        assert e.value.code == wr.WR_ENOMEM
+    finally:
+        r.close()
