@@ -255,8 +255,11 @@ __device__ __noinline__ uint32_t warp_passes_generic(const BfParams& p, WarpTile
 // own lines.  Returns true (warp-uniform) if a row dropped.  A group slot
 // past G (ng < GPW) is neither staged nor written back; its columns hold
 // stale values that only feed its own discarded chains.
+__device__ __forceinline__ void prefetch_l2(const void* a) { asm volatile("prefetch.global.L2 [%0];" ::"l"(a)); }
+
 template <int TILE, int GPW>
-__device__ __forceinline__ bool warp_tile(const BfParams& p, const TileMeta& m, WarpTile<TILE, GPW>& t, int lane) {
+__device__ __forceinline__ bool warp_tile(const BfParams& p, const TileMeta& m, WarpTile<TILE, GPW>& t, int lane,
+                                          const TileMeta* next = nullptr) {
     const int64_t ld = p.seg.ld;
     uint32_t* rows = p.seg.rows;
     const bool compact = (m.flags & RUN_COMPACT) != 0;
@@ -289,6 +292,17 @@ __device__ __forceinline__ bool warp_tile(const BfParams& p, const TileMeta& m, 
         for (int i = sub; i < m.rs.w; i += SPI, gp += SPI * ld) cp_async16(&t.rows[m.rs.y + i][cpart], gp);
     }
     cp_async_commit();
+    // the next tile's own lines and descriptors towards L2 while this one is relaxed
+    if (next != nullptr && next->len > 0) {
+        for (int g = 0; g < next->ng; ++g) {
+            const int64_t c1 = seg_col0(p.seg, next->g + g);
+            for (int i = lane; i < next->len; i += 32)
+                prefetch_l2(rows + static_cast<int64_t>(run_node(next->rs, i)) * ld + c1);
+        }
+        if (next->flags & RUN_COMPACT)
+            for (int i = 4 * lane; i < next->len; i += 128)
+                prefetch_l2(p.g.cdesc + 2 * static_cast<int64_t>(run_node(next->rs, i)));
+    }
 
     uint32_t chg = 0;
     if (compact) {
@@ -432,7 +446,7 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
             if (lane == 0) it2 = atomicAdd(claim, 1);
             TileMeta m1{};
             if (it1 < cnt) m1 = load_meta<GPW>(p, list, it1, G);
-            const bool ch = warp_tile<TILE, GPW>(p, m, t, lane);
+            const bool ch = warp_tile<TILE, GPW>(p, m, t, lane, it1 < cnt ? &m1 : nullptr);
             if (ch) {
                 // the tile itself and the runs it feeds, for the next sweep
                 const int q0 = __ldg(p.g.rout_ptr + m.r), nq = __ldg(p.g.rout_ptr + m.r + 1) - q0;
