@@ -155,8 +155,8 @@ def dist_setup(args):
 # it was taken on (hash below) and the tuning is the default one; otherwise null.
 TRAFFIC_SOURCES = ["paper_2504_20655_gb300/csrc/wr_bf_warp.cu", "paper_2504_20655_gb300/csrc/wr_bf_common.cuh",
                    "paper_2504_20655_gb300/csrc/wr_graph.cpp"]
-TRAFFIC_HASH = "f3d9cbd5395e5ff1"
-TRAFFIC = {"medium": 734220032 + 468953088, "scale": 18333193000 + 9752776000}
+TRAFFIC_HASH = "913f9ee08ed22689"
+TRAFFIC = {"medium": 760238080 + 478046976, "scale": 18147120000 + 8859688000}
 
 
 def traffic_for(workload, tuned):
