@@ -197,7 +197,7 @@ int run_bf_segment(wr_ctx* c, const wr::BfSegment& seg, cudaStream_t s) {
     {
         PhaseTimer t(c, s, 1);
         CK(wr::bf_launch_init(c->dg, seg, w, s));
-        c->launches++;
+        c->launches += 2;
     }
     {
         PhaseTimer t(c, s, 2);
@@ -526,8 +526,8 @@ void wr_destroy(wr_ctx* c) {
                     &c->n_src, &c->block_sums, &c->offs, &c->picks, &c->order_status, &c->order_flags, &c->D,
                     &c->unit_off, &c->best, &c->unit_ctr, &c->out_cost, &c->out_perm, &c->out_status, &c->kbuf,
                     &c->dgiven, &c->src_in, &c->sub, &c->check, &c->trace,
-                    &c->hk_list, &c->hk_count, &c->hk_D, &c->hk_h, &c->g_in_ptr, &c->g_in_src, &c->g_in_w,
-                    &c->leg_len, &c->perm_in, &c->node_offs_d, &c->nodes_d, &c->g_coords,
+                    &c->hk_list, &c->hk_count, &c->hk_D, &c->hk_h, &c->g_in_ptr, &c->g_in_src, &c->g_in_w, &c->g_in4,
+                    &c->leg_len, &c->leg_cache, &c->seg_long, &c->perm_in, &c->node_offs_d, &c->nodes_d, &c->g_coords,
                     &c->cl_k, &c->cl_status, &c->cl_flags, &c->cl_D, &c->cl_mem, &c->cl_perm, &c->cl_state, &c->cl_nc,
                     &c->cl_unit_off, &c->cl_best, &c->cl_cost, &c->cl_ostatus};
     for (DBuf* b : bufs) b->release();
@@ -933,6 +933,21 @@ int wr_route_nodes(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pic
         RC(upload(c->g_in_ptr, c->hg.in_ptr.data(), c->hg.in_ptr.size() * 8));
         RC(upload(c->g_in_src, c->hg.in_src.data(), c->hg.in_src.size() * 4));
         RC(upload(c->g_in_w, c->hg.in_w.data(), c->hg.in_w.size() * 4));
+        // fixed records of up to 4 in-arcs per node (u = -1 pads; u0 = -2: more arcs, in the CSR)
+        std::vector<int32_t> in4(static_cast<size_t>(V) * 8, -1);
+        for (int32_t v = 0; v < V; ++v) {
+            const int64_t e0 = c->hg.in_ptr[static_cast<size_t>(v)], e1 = c->hg.in_ptr[static_cast<size_t>(v) + 1];
+            int32_t* r = in4.data() + static_cast<size_t>(v) * 8;
+            if (e1 - e0 > 4) {
+                r[0] = -2;
+                continue;
+            }
+            for (int64_t e = e0; e < e1; ++e) {
+                r[2 * (e - e0)] = c->hg.in_src[static_cast<size_t>(e)];
+                r[2 * (e - e0) + 1] = c->hg.in_w[static_cast<size_t>(e)];
+            }
+        }
+        RC(upload(c->g_in4, in4.data(), in4.size() * 4));
         c->in_csr_uploaded = true;
     }
     RC(begin_call(c, s));
@@ -954,8 +969,13 @@ int wr_route_nodes(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pic
     }
     wr::TourBufs tb{};
     RC(ensure_tour_bufs(c, n, tb));
-    RC(ensure(c->leg_len, (static_cast<size_t>(np) + n) * 4 + 4));
+    const size_t n_legs = static_cast<size_t>(np) + static_cast<size_t>(n);
+    RC(ensure(c->leg_len, n_legs * 4 + 4));
     RC(ensure(c->node_offs_d, (static_cast<size_t>(n) + 1) * 8));
+    // leg cache: up to LEG_CACHE_NODES nodes per leg, at most LEG_CACHE_WORDS words in all
+    const size_t per_leg = LEG_CACHE_WORDS / n_legs;
+    const int32_t cache_cap = static_cast<int32_t>(per_leg < LEG_CACHE_NODES ? per_leg : LEG_CACHE_NODES);
+    if (cache_cap > 0) RC(ensure(c->leg_cache, n_legs * static_cast<size_t>(cache_cap) * 4));
     CK(cudaMemsetAsync(c->node_flag.p, 0, static_cast<size_t>(V), s));
     CK(wr::tour_launch_select(n, d_offs, d_picks, V, c->dg.depot, c->cfg.max_k, c->node_flag.as<uint8_t>(),
                               tb.order_status, s));
@@ -971,7 +991,10 @@ int wr_route_nodes(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pic
     RC(ensure_bf(c, seg_lanes));
     wr::PathsLaunch pl{n, d_offs, d_picks, d_perm, tb.order_status, c->route_mode == WR_ROUTE_OPEN, c->dg.depot,
                        c->src_index.as<int32_t>(), c->g_in_ptr.as<int64_t>(), c->g_in_src.as<int32_t>(),
-                       c->g_in_w.as<int32_t>(), V, c->leg_len.as<int32_t>()};
+                       c->g_in_w.as<int32_t>(), c->g_in4.as<int4>(), V, c->leg_len.as<int32_t>(),
+                       cache_cap > 0 ? c->leg_cache.as<int32_t>() : nullptr, cache_cap};
+    RC(ensure(c->seg_long, static_cast<size_t>(n_seg) * 4));
+    CK(cudaMemsetAsync(c->seg_long.p, 0, static_cast<size_t>(n_seg) * 4, s));
     auto segment = [&](int32_t sg) {
         wr::BfSegment seg;
         seg.rows = c->rows.as<uint32_t>();
@@ -983,12 +1006,12 @@ int wr_route_nodes(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pic
         seg.lanes = seg_lanes;
         return seg;
     };
-    // count pass: every leg's length, in the segment holding its source
+    // count walk: every leg's length, in the segment holding its source; short legs cached
     for (int32_t sg = 0; sg < n_seg; ++sg) {
         const wr::BfSegment seg = segment(sg);
         RC(run_bf_segment(c, seg, s));
         PhaseTimer t(c, s, 5);  // the walks are the decode of routes into nodes
-        CK(wr::paths_launch(pl, seg, nullptr, nullptr, s));
+        CK(wr::paths_launch(pl, &seg, 0, c->seg_long.as<int32_t>() + sg, nullptr, nullptr, s));
         c->launches++;
     }
     {
@@ -997,7 +1020,9 @@ int wr_route_nodes(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pic
         c->launches++;
     }
     int64_t total = 0;
+    std::vector<int32_t> seg_long(static_cast<size_t>(n_seg));
     CK(cudaMemcpyAsync(&total, c->node_offs_d.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(seg_long.data(), c->seg_long.p, static_cast<size_t>(n_seg) * 4, cudaMemcpyDeviceToHost, s));
     if (ptr_kind == WR_HOST)
         CK(cudaMemcpyAsync(node_offs, c->node_offs_d.p, (static_cast<size_t>(n) + 1) * 8, cudaMemcpyDeviceToHost, s));
     else
@@ -1011,12 +1036,20 @@ int wr_route_nodes(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pic
         RC(ensure(c->nodes_d, static_cast<size_t>(total) * 4 + 4));
         d_nodes = c->nodes_d.as<int32_t>();
     }
-    // write pass: the last segment's rows are still in place; earlier ones are computed again
+    // cached legs (and each route's first node) straight into the output
+    {
+        PhaseTimer t(c, s, 5);
+        CK(wr::paths_launch(pl, nullptr, 2, nullptr, d_nodes, c->node_offs_d.as<int64_t>(), s));
+        c->launches++;
+    }
+    // legs longer than the cache are walked again in their segment: the last segment's rows are
+    // still in place, earlier ones are computed again
     for (int32_t sg = n_seg - 1; sg >= 0; --sg) {
+        if (!seg_long[static_cast<size_t>(sg)]) continue;
         const wr::BfSegment seg = segment(sg);
         if (sg != n_seg - 1) RC(run_bf_segment(c, seg, s));
         PhaseTimer t(c, s, 5);
-        CK(wr::paths_launch(pl, seg, d_nodes, c->node_offs_d.as<int64_t>(), s));
+        CK(wr::paths_launch(pl, &seg, 1, nullptr, d_nodes, c->node_offs_d.as<int64_t>(), s));
         c->launches++;
     }
     RC(end_call(c, s));

@@ -22,26 +22,23 @@
 
 namespace wr {
 
-// rows := INF except dist(src_b, src_b) = 0; stamps := 0; counters := 0.
+// rows := INF; stamps := 0; counters := 0.  A warp fills whole rows with
+// 16-byte stores (32 lanes x 4 sources per instruction); the sources' zeros
+// follow in bf_seed_kernel.
 __global__ void bf_init_kernel(BfParams p) {
     const int n_lanes = segment_lanes(p.seg);
     const int G = (n_lanes + 31) >> 5;
-    const int64_t width = static_cast<int64_t>(G) * 32;
-    const int64_t n = static_cast<int64_t>(p.g.V) * width;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    const int64_t w0 = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint4 inf = make_uint4(INF_U, INF_U, INF_U, INF_U);
+    for (int64_t v = w0; v < p.g.V; v += warps) {
+        uint32_t* row = p.seg.rows + v * p.seg.ld;
+        for (int q = lane; q < 8 * G; q += 32)  // uint4 q: group q / 8, lanes 4 (q % 8) ..
+            __stcg(reinterpret_cast<uint4*>(row + seg_col0(p.seg, q >> 3) + 4 * (q & 7)), inf);
+    }
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    // 4 lanes per thread (16-byte stores); width is a multiple of 32
-    for (int64_t e = t0 * 4; e < n; e += stride * 4) {
-        const int64_t v = e / width;
-        const int b = static_cast<int>(e - v * width);
-        uint4 val = make_uint4(INF_U, INF_U, INF_U, INF_U);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int lane = b + q;
-            if (lane < n_lanes && p.seg.src[p.seg.first + lane] == v) (&val.x)[q] = 0u;
-        }
-        __stcg(reinterpret_cast<uint4*>(p.seg.rows + v * p.seg.ld + seg_col0(p.seg, b >> 5) + (b & 31)), val);
-    }
     const int64_t n_items = static_cast<int64_t>(p.g.n_runs) * G;
     for (int64_t i = t0; i < n_items; i += stride) p.w.stamp[i] = 0;
     if (t0 < 8) p.w.counts[t0] = 0;
@@ -53,6 +50,14 @@ __global__ void bf_init_kernel(BfParams p) {
         p.w.bar->count = 0;
         p.w.bar->gen = 0;
     }
+}
+
+// dist(src_b, src_b) = 0, after the fill.
+__global__ void bf_seed_kernel(BfParams p) {
+    const int n_lanes = segment_lanes(p.seg);
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n_lanes)
+        p.seg.rows[static_cast<int64_t>(p.seg.src[p.seg.first + b]) * p.seg.ld + seg_col0(p.seg, b >> 5) + (b & 31)] = 0u;
 }
 
 // Shared memory of one warp: the tile's rows (own nodes then halo), the
@@ -483,7 +488,10 @@ int bf_prepare(int tile_cap, int warps, int device, BfLaunchInfo* info) {
 
 cudaError_t bf_launch_init(const DevGraph& g, const BfSegment& seg, const BfWork& w, cudaStream_t s) {
     BfParams p{g, seg, w};
-    bf_init_kernel<<<1024, 256, 0, s>>>(p);
+    bf_init_kernel<<<1216, 256, 0, s>>>(p);  // 8 blocks per SM
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bf_seed_kernel<<<(seg.lanes + 255) / 256 + (seg.lanes == 0), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,10 @@ struct DBuf {
 };
 
 constexpr unsigned long long DEFAULT_SPINS = 1ull << 24;  // x 64 ns sleeps: about a second
+// node-level routes: legs of at most LEG_CACHE_NODES nodes keep their walk for the output, in
+// a cache of at most LEG_CACHE_WORDS node ids (256 MiB)
+constexpr size_t LEG_CACHE_NODES = 256;
+constexpr size_t LEG_CACHE_WORDS = size_t(1) << 26;
 constexpr uint64_t DEFAULT_BUDGET = 2ull << 30;
 
 }  // namespace wrc
@@ -62,7 +66,7 @@ struct wr_ctx {
     wrc::DBuf hk_list, hk_count, hk_D, hk_h;  // Held-Karp orders (k > WR_MAX_K)
     int hk_blocks = 0;
     int route_mode = WR_ROUTE_TOUR;
-    wrc::DBuf g_in_ptr, g_in_src, g_in_w, leg_len, perm_in, node_offs_d, nodes_d;  // node-level routes
+    wrc::DBuf g_in_ptr, g_in_src, g_in_w, g_in4, leg_len, leg_cache, seg_long, perm_in, node_offs_d, nodes_d;  // node-level routes
     bool in_csr_uploaded = false;
     bool positive_weights = false;  // every arc weight > 0: node-level routes are defined
     int32_t cluster_m = 0;          // > 0: cluster-patched approximate routing with at most this many clusters

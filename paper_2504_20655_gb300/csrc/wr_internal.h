@@ -231,12 +231,17 @@ struct PathsLaunch {
     const int64_t* in_ptr;  // in-arc CSR with node ids
     const int32_t* in_src;
     const int32_t* in_w;
+    const int4* in4;        // per node 2 x int4: up to 4 in-arcs (u, w); u0 = -2: more, in the CSR
     int32_t V;
     int32_t* leg_len;       // offs[n] + n entries
+    int32_t* leg_cache;     // (offs[n] + n) x cache_cap node ids: the legs of at most cache_cap nodes
+    int32_t cache_cap;      // 0: no cache
 };
-// count pass (nodes == nullptr) or write pass over the legs whose source lies in seg
-cudaError_t paths_launch(const PathsLaunch& l, const BfSegment& seg, int32_t* nodes, const int64_t* node_offs,
-                         cudaStream_t s);
+// mode 0 (count walk over the legs whose source lies in *seg; a leg longer than the cache sets
+// *seg_long), 1 (write walk of those legs that are longer than the cache) or 2 (copy of every
+// cached leg; seg unused)
+cudaError_t paths_launch(const PathsLaunch& l, const BfSegment* seg, int mode, int32_t* seg_long, int32_t* nodes,
+                         const int64_t* node_offs, cudaStream_t s);
 cudaError_t paths_launch_offsets(const PathsLaunch& l, int64_t* node_offs, cudaStream_t s);
 
 // Cluster-patched approximate routing (wr_cluster.cu); xy: 2 int32 plan coordinates per node.

@@ -656,6 +656,40 @@ def test_route_nodes_against_oracle(wr, orc):
         r.close()
 
 
+def test_route_nodes_long_legs_several_segments(wr, orc):
+    """Node-level routes whose legs outgrow the 256-node leg cache (aisle faces of 300 slots:
+    a leg along a face and back along another passes 300 to 600 nodes) mixed with short
+    legs, in one segment and in several small ones, closed and open: the cached legs are
+    copied and the long ones walked again, element by element against the oracle."""
+    lay = synth.Layout(A=3, S=300, F=2, C=2, step_lo=80, step_hi=120, seed=synth.SEED_BASE + 41)
+    g = lay.build()
+    o = synth.uniform_slot_orders(40, 5, lay.n_slots, synth.SEED_BASE + 42)
+    for open_path, budget in ((False, 2 << 30), (False, 32 * g.V * 4), (True, 32 * g.V * 4)):
+        r = wr.Router(device=0, mem_budget_bytes=budget)
+        try:
+            r.load_graph(g)
+            r.set_route_mode(open_path)
+            cost, perm, status = r.route_orders(o.offs, o.picks)
+            perm = np.ascontiguousarray(perm[:o.offs[-1]])
+            node_offs, nodes = r.route_nodes(o.offs, o.picks, perm)
+        finally:
+            r.close()
+        want_offs, want_nodes = orc.route_nodes(g, o, perm, open_path=open_path, n_threads=NT)
+        assert (node_offs == want_offs).all() and (nodes == want_nodes).all(), (open_path, budget)
+        # the batch really holds legs past the cache and legs within it
+        leg_lens = []
+        for i in range(o.n):
+            route = want_nodes[want_offs[i]:want_offs[i + 1]]
+            seq = o.picks[o.offs[i] + perm[o.offs[i]:o.offs[i + 1]]]
+            stops = list(seq[1:]) if open_path else list(seq) + [g.depot]
+            pos = 0
+            for t in stops:
+                nxt = pos + 1 + int(np.flatnonzero(route[pos + 1:] == t)[0])
+                leg_lens.append(nxt - pos)
+                pos = nxt
+        assert max(leg_lens) > 256 and min(leg_lens) <= 256, (max(leg_lens), min(leg_lens))
+
+
 def test_route_clustered_against_oracle(wr, orc):
     """Cluster-patched approximate routing (Sec. 3) against the oracle's restatement of
     the same steps, element by element, for closed tours and open paths and several m;
