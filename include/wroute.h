@@ -51,7 +51,7 @@ extern "C" {
 #define WR_ECUDA     3  /* a CUDA runtime call failed */
 #define WR_ETIMEOUT  4  /* a bounded device-side wait (grid barrier) ran out */
 #define WR_ENOGRAPH  5  /* no graph loaded */
-#define WR_EINTERNAL 6  /* Bellman-Ford exceeded its sweep cap (cannot happen with w >= 0) */
+#define WR_EINTERNAL 6  /* an internal bound or check failed (Bellman-Ford past its sweep cap, a Held-Karp table without an optimal next pick): cannot happen with w >= 0 */
 
 /* per-order status */
 #define WR_ORDER_OK          0

@@ -359,7 +359,7 @@ int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_
         RC(ensure(c->hk_count, 16));
         RC(ensure(c->hk_D, static_cast<size_t>(n) * wr::HK_DBLOCK * 4 + 4));
         // tables of a batch of orders solved together: at least one of max_k picks, up to the budget
-        const size_t one = (static_cast<size_t>(1) << c->cfg.max_k) * static_cast<size_t>(c->cfg.max_k) * 4;
+        const size_t one = (static_cast<size_t>(1) << (c->cfg.max_k - 1)) * static_cast<size_t>(c->cfg.max_k) * 4;
         RC(ensure(c->hk_h, one > c->cfg.mem_budget_bytes ? one : static_cast<size_t>(c->cfg.mem_budget_bytes)));
         CK(cudaMemsetAsync(c->hk_count.p, 0, 4, s));
         CK(wr::hk_launch_select(n, tb, c->cfg.max_k, c->hk_list.as<int32_t>(), c->hk_count.as<int32_t>(), s));

@@ -13,11 +13,23 @@
 // and the sequence is rebuilt from the depot by taking, at every step, the
 // smallest pick index j whose D[cur][j] + h(S + j, j) equals what remains.
 //
-// One cooperative persistent kernel fills the tables (2^k x k words per order)
-// level by level (subsets of k picks, then k-1, ... 1) for a whole batch of
-// orders at once, all blocks sharing each level, with one bounded grid
+// One cooperative persistent kernel fills the tables (k x 2^(k-1) words per
+// order) level by level (subsets of k picks, then k-1, ... 1) for a whole batch
+// of orders at once, all blocks sharing each level, with one bounded grid
 // barrier per level; then every order's sequence is rebuilt by one thread.
-// Arithmetic is uint32 with WR_INF saturation; finite sums stay below
+//
+// Table layout: plane c (one per pick, 2^(k-1) words) holds h(S, c) for the
+// subsets S that contain c, indexed by T = S - c with c's bit squeezed out (a
+// subset of the other k-1 picks): first by |T| (blocks of C(k-1, l) words),
+// then by the colex rank of T.  Colex order of equal-size subsets is their
+// numeric order, and squeezing out a bit every subset lacks keeps that order,
+// so the threads that take consecutive subsets S of a level read consecutive
+// words of each plane j (h(S + j, j)) and write consecutive words of each
+// plane c (h(S, c)).  A thread gets both ranks from running prefix sums of
+// binomial terms over the bits of S.
+// Arithmetic is uint32 on values of at most WR_INF = 2^31 - 1 (unreachable):
+// a sum of two does not wrap, and a minimum started at WR_INF stays at most
+// WR_INF, so a transition is one fused add-min; finite sums stay below
 // 21 x WR_LEG_MAX < 2^31.
 #include "wr_bf_common.cuh"
 
@@ -78,6 +90,19 @@ struct HkParams {
 };
 
 constexpr int HK_BATCH = 512;  // orders solved together, at most
+constexpr int HK_ITEMS = 1;    // subsets per thread whose loads are in flight together (2 and 3: fewer warps, slower)
+
+// One subset S of a level: its order (index in the batch), S, and h(S + j, j) for the picks j outside S.
+struct HkItem {
+    int qi;
+    unsigned s;
+    uint32_t pc_tot;
+    uint32_t hv[HK_MAX_K];
+};
+
+__device__ __forceinline__ uint32_t bn(const uint32_t (&binom)[HK_MAX_K + 1][HK_MAX_K + 1], int n, int r) {
+    return n < 0 ? 0u : binom[n][r];
+}
 
 // Picks of listed order q (0 for an order whose D holds an out-of-range leg:
 // its status comes from the decode of the other orders).
@@ -87,16 +112,16 @@ __device__ __forceinline__ int hk_k(const HkParams& p, int q) {
     return static_cast<int>(p.t.offs[o + 1] - p.t.offs[o]);
 }
 
-// Orders are solved in batches whose tables (2^k x k words each) fit the buffer;
-// within a batch all orders share every level: level L holds, for every order of
-// k >= L picks, its C(k, L) subsets S of size L, in increasing bitmask order per
-// order, orders one after another.  Consecutive threads take consecutive items
-// (grid-stride), each unranking its subset (combinatorial number system), and a
-// table is pick-major, h[c][S], so the lanes of a warp read and write
-// neighbouring words.  One grid barrier per level; then one thread per order
+// Orders are solved in batches whose tables (k x 2^(k-1) words each) fit the
+// buffer; within a batch all orders share every level: level L holds, for every
+// order of k >= L picks, its C(k, L) subsets S of size L, in increasing bitmask
+// order per order, orders one after another.  Consecutive threads take
+// consecutive items (grid-stride), each unranking its subset (combinatorial
+// number system).  One grid barrier per level; then one thread per order
 // rebuilds its first optimal sequence.
 __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
     __shared__ uint32_t binom[HK_MAX_K + 1][HK_MAX_K + 1];
+    __shared__ uint32_t loff[HK_MAX_K + 1][HK_MAX_K + 2];  // loff[k][l]: sum of C(k-1, l') over l' < l
     __shared__ unsigned long long pre[HK_BATCH + 1];  // level prefix of C(k_q, L)
     __shared__ unsigned long long base[HK_BATCH + 1];  // table offsets (words)
     __shared__ int kq[HK_BATCH];
@@ -107,6 +132,11 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
         if (r > n) c = 0;
         for (int j = 1; j <= r && j <= n; ++j) c = c * static_cast<unsigned long long>(n - r + j) / j;
         binom[n][r] = static_cast<uint32_t>(c);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k <= HK_MAX_K; k += blockDim.x) {
+        loff[k][0] = 0;
+        for (int l = 0; l <= HK_MAX_K; ++l) loff[k][l + 1] = loff[k][l] + (k >= 1 ? binom[k - 1][l] : 0u);
     }
     const int n_big = ld_volatile(p.count);
     const long long gtid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -121,7 +151,7 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
             base[0] = 0;
             while (q < n_big && q - q0 < HK_BATCH) {
                 const int k = hk_k(p, q);
-                const unsigned long long sz = k > 0 ? (1ull << k) * static_cast<unsigned long long>(k) : 0ull;
+                const unsigned long long sz = k > 0 ? (1ull << (k - 1)) * static_cast<unsigned long long>(k) : 0ull;
                 if (q > q0 && acc + sz > p.h_words) break;
                 kq[q - q0] = k;
                 acc += sz;
@@ -143,80 +173,162 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
             __syncthreads();
             const unsigned long long total = pre[nb];
             int qi = 0;
-            for (unsigned long long w = static_cast<unsigned long long>(gtid); w < total;
-                 w += static_cast<unsigned long long>(nthreads)) {
+            // unrank item w, then issue the loads h(S + j, j) for every pick j outside S (plane j,
+            // block |S|, rank of S with bit j squeezed out = its bits below j as they are plus
+            // its bits above j one lower)
+            auto load_item = [&](unsigned long long w, HkItem& it) {
                 while (pre[qi + 1] <= w) ++qi;  // the order holding item w
                 const int k = kq[qi];
-                // unrank: the subset of rank w - pre[qi] among the L-subsets of k picks
+                it.qi = qi;
+                // the subset of rank w - pre[qi] among the L-subsets of k picks, bits from the
+                // top: each the largest c below the previous one with C(c, i) <= rr
                 unsigned s = 0;
                 unsigned long long rr = w - pre[qi];
+                int c_hi = k;
                 for (int i = L; i >= 1; --i) {
-                    int c = i - 1;
-                    while (c + 1 < k && binom[c + 1][i] <= rr) ++c;
+                    int c = c_hi - 1;
+                    while (binom[c][i] > rr) --c;  // ends by c = i - 1: C(i - 1, i) = 0
                     s |= 1u << c;
                     rr -= binom[c][i];
+                    c_hi = c;
                 }
-                const unsigned full = (1u << k) - 1u;
-                const int64_t side = static_cast<int64_t>(1) << k;  // words per pick in the table
-                const uint32_t* D = p.D21 + static_cast<int64_t>(q0 + qi) * HK_DBLOCK;
-                uint32_t* hq = p.h + base[qi];
-                // h(S + j, j) for every pick j outside S, all loads in flight together
-                uint32_t hv[HK_MAX_K];
+                it.s = s;
+                // over the bits b_0 < b_1 < ... of S: pb = sum C(b_t - 1, t + 1), pc = sum C(b_t - 1, t)
+                uint32_t pb_tot = 0, pc_tot = 0;
+                {
+                    int t = 0;
+                    for (unsigned m = s; m; m &= m - 1, ++t) {
+                        const int b = __ffs(m) - 1;
+                        pb_tot += bn(binom, b - 1, t + 1);
+                        pc_tot += bn(binom, b - 1, t);
+                    }
+                }
+                it.pc_tot = pc_tot;
+                const int64_t half = static_cast<int64_t>(1) << (k - 1);  // words per plane
+                const uint32_t* hq = p.h + base[qi];
+                const uint32_t lo = loff[k][L];
+                uint32_t pa = 0, pb = 0;
+                int m = 0;
 #pragma unroll
-                for (int j = 0; j < HK_MAX_K; ++j)
-                    hv[j] = (j < k && !((s >> j) & 1u)) ? __ldcg(hq + j * side + (s | (1u << j))) : INF_U;
-                for (unsigned cm = s; cm; cm &= cm - 1) {
+                for (int j = 0; j < HK_MAX_K; ++j) {
+                    it.hv[j] = INF_U;
+                    if (j < k) {
+                        if ((s >> j) & 1u) {
+                            pa += binom[j][m + 1];
+                            pb += bn(binom, j - 1, m + 1);
+                            ++m;
+                        } else {
+                            it.hv[j] = __ldcg(hq + j * half + lo + (pa + pb_tot - pb));
+                        }
+                    }
+                }
+            };
+            // h(S, c) for every c in S: plane c, block |S| - 1, rank of S - c with c's bit squeezed out
+            auto store_item = [&](const HkItem& it) {
+                const int k = kq[it.qi];
+                const unsigned s = it.s, full = (1u << k) - 1u;
+                const int64_t half = static_cast<int64_t>(1) << (k - 1);
+                const uint32_t* D = p.D21 + static_cast<int64_t>(q0 + it.qi) * HK_DBLOCK;
+                uint32_t* hq = p.h + base[it.qi];
+                const uint32_t lo = loff[k][L - 1];
+                uint32_t pa = 0, pc = 0;
+                int t = 0;
+                for (unsigned cm = s; cm; cm &= cm - 1, ++t) {
                     const int c = __ffs(cm) - 1;
                     const uint32_t* Dr = D + (c + 1) * HK_DSTRIDE;
                     uint32_t best;
                     if (s == full) {
                         best = __ldg(Dr);
                     } else {
+                        // D and h are at most INF_U = 2^31 - 1, so D + h does not wrap, and a minimum
+                        // started at INF_U stays at most INF_U: one fused add-min per transition
                         best = INF_U;
 #pragma unroll
                         for (int j = 0; j < HK_MAX_K; ++j)
-                            if (j < k && !((s >> j) & 1u)) best = min(best, sat_add(__ldg(Dr + j + 1), hv[j]));
+                            if (j < k && !((s >> j) & 1u)) best = __viaddmin_u32(__ldg(Dr + j + 1), it.hv[j], best);
                     }
-                    __stcg(hq + c * side + s, best);
+                    const uint32_t cc = bn(binom, c - 1, t);
+                    __stcg(hq + c * half + lo + (pa + it.pc_tot - pc - cc), best);
+                    pa += binom[c][t + 1];
+                    pc += cc;
                 }
+            };
+            // HK_ITEMS items per thread and round, all their loads issued before the first is used
+            const unsigned long long step = static_cast<unsigned long long>(nthreads);
+            for (unsigned long long w = static_cast<unsigned long long>(gtid); w < total; w += HK_ITEMS * step) {
+                HkItem it[HK_ITEMS];
+#pragma unroll
+                for (int u = 0; u < HK_ITEMS; ++u)
+                    if (w + u * step < total) load_item(w + u * step, it[u]);
+#pragma unroll
+                for (int u = 0; u < HK_ITEMS; ++u)
+                    if (w + u * step < total) store_item(it[u]);
             }
             if (!grid_sync(p.bar, p.err, p.max_spins)) return;
         }
-        // rebuild: one thread per order, lexicographically first optimal sequence
-        for (long long qi = gtid; qi < nb; qi += nthreads) {
-            const int q = q0 + static_cast<int>(qi);
-            const int k = kq[qi];
-            if (k == 0) continue;
-            const int o = p.list[q];
-            const int64_t b = p.t.offs[o];
-            const uint32_t* D = p.D21 + static_cast<int64_t>(q) * HK_DBLOCK;
-            const uint32_t* hq = p.h + base[qi];
-            const int64_t side = static_cast<int64_t>(1) << k;
-            uint32_t best = INF_U;
-            for (int j = 0; j < k; ++j) best = min(best, sat_add(__ldg(D + j + 1), __ldcg(hq + j * side + (1u << j))));
-            int32_t* pp = p.perm + b;
-            if (best >= INF_U) {
-                p.cost[o] = WR_INF;
-                p.status[o] = WR_ORDER_UNREACHABLE;
-                for (int i = 0; i < k; ++i) pp[i] = i;
-            } else {
-                p.cost[o] = static_cast<int32_t>(best);
-                p.status[o] = WR_ORDER_OK;
+        // rebuild: one warp per order, lanes over the candidate next picks; the
+        // lexicographically first optimal sequence takes at every step the smallest j
+        // whose leg plus what remains after it equals what remains now
+        {
+            const int lane = threadIdx.x & 31;
+            const long long nw = nthreads >> 5;
+            for (long long qi = gtid >> 5; qi < nb; qi += nw) {
+                const int q = q0 + static_cast<int>(qi);
+                const int k = kq[qi];
+                if (k == 0) continue;
+                const int o = p.list[q];
+                const int64_t b = p.t.offs[o];
+                const uint32_t* D = p.D21 + static_cast<int64_t>(q) * HK_DBLOCK;
+                const uint32_t* hq = p.h + base[qi];
+                const int64_t half = static_cast<int64_t>(1) << (k - 1);
+                // h(set + j, j) for j outside set: plane j, block |set|, rank of set with bit j squeezed out
+                auto h_at = [&](unsigned set, int j) {
+                    uint32_t r = 0;
+                    int i = 0;
+                    for (unsigned m = set; m; m &= m - 1, ++i) {
+                        const int bb = __ffs(m) - 1;
+                        r += binom[bb > j ? bb - 1 : bb][i + 1];
+                    }
+                    return __ldcg(hq + j * half + loff[k][__popc(set)] + r);
+                };
+                uint32_t best = lane < k ? sat_add(__ldg(D + lane + 1), h_at(0u, lane)) : INF_U;
+#pragma unroll
+                for (int d = 16; d >= 1; d >>= 1) best = min(best, __shfl_xor_sync(FULL_MASK, best, d));
+                int32_t* pp = p.perm + b;
+                if (best >= INF_U) {
+                    if (lane == 0) {
+                        p.cost[o] = WR_INF;
+                        p.status[o] = WR_ORDER_UNREACHABLE;
+                    }
+                    if (lane < k) pp[lane] = lane;
+                    continue;
+                }
                 unsigned s = 0;
                 int cur = 0;  // matrix index of the current stop (0 = depot)
                 uint32_t rem = best;
+                bool ok = true;
                 for (int pos = 0; pos < k; ++pos) {
-                    for (int j = 0; j < k; ++j) {
-                        if (s & (1u << j)) continue;
-                        const uint32_t r = __ldcg(hq + j * side + (s | (1u << j)));
-                        if (sat_add(__ldg(D + cur * HK_DSTRIDE + j + 1), r) == rem) {
-                            pp[pos] = j;
-                            s |= 1u << j;
-                            rem = r;
-                            cur = j + 1;
-                            break;
-                        }
+                    uint32_t r = INF_U;
+                    bool hit = false;
+                    if (lane < k && !((s >> lane) & 1u)) {
+                        r = h_at(s, lane);
+                        hit = sat_add(__ldg(D + cur * HK_DSTRIDE + lane + 1), r) == rem;
                     }
+                    const unsigned m = __ballot_sync(FULL_MASK, hit);
+                    if (m == 0u) {  // cannot happen on a consistent table
+                        ok = false;
+                        break;
+                    }
+                    const int j = __ffs(m) - 1;
+                    rem = __shfl_sync(FULL_MASK, r, j);
+                    if (lane == 0) pp[pos] = j;
+                    s |= 1u << j;
+                    cur = j + 1;
+                }
+                if (lane == 0) {
+                    p.cost[o] = ok ? static_cast<int32_t>(best) : WR_INF;
+                    p.status[o] = ok ? WR_ORDER_OK : WR_ORDER_UNREACHABLE;
+                    if (!ok) atomicCAS(p.err, 0, WR_EINTERNAL);
                 }
             }
         }
