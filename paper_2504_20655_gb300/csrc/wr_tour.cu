@@ -691,20 +691,32 @@ __device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, unsigne
 }
 
 constexpr int ENUM_THREADS = 128;
+constexpr bool ENUM_GUIDED = true;  // chunk sizes shrink as the unit counter nears the end
 
 __global__ void __launch_bounds__(ENUM_THREADS) enum_kernel(int32_t n, const int32_t* __restrict__ k_given, TourBufs t,
                                                             long long u_begin, long long u_end, int upt) {
     const int lane = threadIdx.x & 31;
     const long long total = min(u_end, static_cast<long long>(__ldcg(t.unit_off + n)));
-    const long long chunk = 32ll * upt;
+    const long long warps = static_cast<long long>(gridDim.x) * (blockDim.x >> 5);
     long long seqs = 0;
     for (;;) {
+        // guided claims: upt units per lane while at least 4 such chunks per warp remain, then
+        // fewer, down to one, so that the last chunks end close together
         long long c0 = 0;
-        if (lane == 0) c0 = static_cast<long long>(atomicAdd(t.unit_ctr, static_cast<unsigned long long>(chunk)));
+        int per = upt;
+        if (lane == 0) {
+            if (ENUM_GUIDED) {
+                const long long left = total - u_begin - static_cast<long long>(__ldcg(t.unit_ctr));
+                const long long fair = left / (32ll * 4ll * warps);
+                per = fair >= upt ? upt : (fair < 1 ? 1 : static_cast<int>(fair));
+            }
+            c0 = static_cast<long long>(atomicAdd(t.unit_ctr, 32ull * static_cast<unsigned long long>(per)));
+        }
         c0 = __shfl_sync(FULL_MASK, c0, 0) + u_begin;
+        per = __shfl_sync(FULL_MASK, per, 0);
         if (c0 >= total) break;
-        long long u = c0 + static_cast<long long>(lane) * upt;
-        const long long ue = min(u + upt, total);
+        long long u = c0 + static_cast<long long>(lane) * per;
+        const long long ue = min(u + per, total);
         while (u < ue) {
             // order holding unit u: last o with unit_off[o] <= u
             int lo = 0, hi = n - 1;
