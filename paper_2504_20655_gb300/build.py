@@ -15,7 +15,7 @@ LIB = os.path.join(HERE, "libwroute.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["wr_api.cu", "wr_bf.cu", "wr_bf_warp.cu", "wr_tour.cu", "wr_static.cu", "wr_serve.cu", "wr_hk.cu", "wr_paths.cu", "wr_cluster.cu", "wr_graph.cpp"]
-HEADERS = ["wr_internal.h", "wr_device.cuh"]
+HEADERS = sorted(f for f in os.listdir(CSRC) if f.endswith((".h", ".cuh")))  # every source depends on all of them
 
 
 def nvcc() -> str:

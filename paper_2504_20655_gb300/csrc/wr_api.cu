@@ -330,25 +330,32 @@ int finish_graph(wr_ctx* c) {
 // a1-a7 for n orders whose offs/picks are on the device, np_bound >= offs[n]:
 // enqueues everything on s with no host synchronisation (the segments are
 // planned for the worst case of np_bound + 1 distinct sources).
-int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_picks, int64_t np_bound,
-                  int32_t* o_cost, int32_t* o_perm, int32_t* o_status, cudaStream_t s) {
+// a2: sources = depot + distinct pick nodes of valid orders (needs no host-side pick count)
+int enqueue_select(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_picks, cudaStream_t s) {
     const int32_t V = c->dg.V;
     wr::TourBufs tb{};
     tb.offs = d_offs;
     tb.picks = d_picks;
     RC(ensure_tour_bufs(c, n, tb));
-    // a2: sources = depot + distinct pick nodes of valid orders
-    {
-        PhaseTimer t(c, s, 0);
-        CK(cudaMemsetAsync(c->node_flag.p, 0, static_cast<size_t>(V), s));
-        CK(cudaMemsetAsync(c->order_flags.p, 0, static_cast<size_t>(n) * 4, s));
-        CK(wr::tour_launch_select(n, d_offs, d_picks, V, c->dg.depot, c->cfg.max_k, c->node_flag.as<uint8_t>(),
-                                  tb.order_status, s));
-        c->launches++;
-        CK(wr::tour_launch_compact(V, c->node_flag.as<uint8_t>(), c->src_index.as<int32_t>(),
-                                   c->src_list.as<int32_t>(), c->n_src.as<int32_t>(), c->block_sums.as<int32_t>(), s,
-                                   &c->launches));
-    }
+    PhaseTimer t(c, s, 0);
+    CK(cudaMemsetAsync(c->node_flag.p, 0, static_cast<size_t>(V), s));
+    CK(cudaMemsetAsync(c->order_flags.p, 0, static_cast<size_t>(n) * 4, s));
+    CK(wr::tour_launch_select(n, d_offs, d_picks, V, c->dg.depot, c->cfg.max_k, c->node_flag.as<uint8_t>(),
+                              tb.order_status, s));
+    c->launches++;
+    CK(wr::tour_launch_compact(V, c->node_flag.as<uint8_t>(), c->src_index.as<int32_t>(), c->src_list.as<int32_t>(),
+                               c->n_src.as<int32_t>(), c->block_sums.as<int32_t>(), s, &c->launches));
+    return WR_OK;
+}
+
+int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_picks, int64_t np_bound,
+                  int32_t* o_cost, int32_t* o_perm, int32_t* o_status, cudaStream_t s, bool selected) {
+    const int32_t V = c->dg.V;
+    wr::TourBufs tb{};
+    tb.offs = d_offs;
+    tb.picks = d_picks;
+    RC(ensure_tour_bufs(c, n, tb));
+    if (!selected) RC(enqueue_select(c, n, d_offs, d_picks, s));
     // orders above WR_MAX_K picks (when the context admits them): Held-Karp; the clustered
     // approximation takes at most WR_MAX_K picks
     const bool clustered = c->cluster_m > 0;
@@ -520,6 +527,8 @@ void wr_destroy(wr_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    if (c->h_offs) cudaFreeHost(c->h_offs);
+    if (c->ev_offs) cudaEventDestroy(c->ev_offs);
     DBuf* bufs[] = {&c->g_desc, &c->g_ref, &c->g_w, &c->g_arc2, &c->g_run_ptr, &c->g_run_x, &c->g_halo_ptr, &c->g_halo_nodes, &c->g_rin_ptr,
                     &c->g_rin_list, &c->g_rout_ptr, &c->g_rout_list, &c->g_wx, &c->g_run_wx, &c->g_run_of, &c->g_meta, &c->g_flags, &c->g_ix, &c->g_xarc, &c->g_cdesc, &c->rows, &c->stamp, &c->list0, &c->list1, &c->list2,
                     &c->counts, &c->bar, &c->ring, &c->ring_seq, &c->qctl, &c->err, &c->stats, &c->node_flag, &c->src_index, &c->src_list,
@@ -590,13 +599,31 @@ int wr_route_orders(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pi
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // total picks
     int64_t np = 0, first = 0;
+    bool selected = false;
     if (ptr_kind == WR_HOST) {
         first = offs[0];
         np = offs[n];
         for (int32_t i = 0; i < n; ++i)
             if (offs[i + 1] < offs[i]) return WR_EINVAL;
+    } else if (n > 0 && picks) {
+        // offs[0] and offs[n] come back through pinned memory, ordered after the caller's work on
+        // its stream; the source selection, which needs neither, is queued before the host waits
+        if (!c->h_offs) {
+            void* h = nullptr;
+            CK(cudaMallocHost(&h, 16));
+            c->h_offs = static_cast<int64_t*>(h);
+        }
+        if (!c->ev_offs) CK(cudaEventCreateWithFlags(&c->ev_offs, cudaEventDisableTiming));
+        CK(cudaMemcpyAsync(c->h_offs, offs, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(c->h_offs + 1, offs + n, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(c->ev_offs, s));
+        RC(begin_call(c, s));
+        RC(enqueue_select(c, n, offs, picks, s));
+        selected = true;
+        CK(cudaEventSynchronize(c->ev_offs));
+        first = c->h_offs[0];
+        np = c->h_offs[1];
     } else {
-        // ordered after the caller's work on its stream (which may not sync with the legacy stream)
         CK(cudaMemcpyAsync(&first, offs, 8, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(&np, offs + n, 8, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -604,7 +631,7 @@ int wr_route_orders(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pi
     if (first != 0 || np < 0) return WR_EINVAL;
     if (np > 0 && (!picks || !perm)) return WR_EINVAL;
     if (n == 0) return WR_OK;
-    RC(begin_call(c, s));
+    if (!selected) RC(begin_call(c, s));
     // inputs on the device
     const int64_t* d_offs = offs;
     const int32_t* d_picks = picks;
@@ -627,7 +654,7 @@ int wr_route_orders(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pi
         o_status = c->out_status.as<int32_t>();
         o_perm = c->out_perm.as<int32_t>();
     }
-    RC(enqueue_route(c, n, d_offs, d_picks, np, o_cost, o_perm, o_status, s));
+    RC(enqueue_route(c, n, d_offs, d_picks, np, o_cost, o_perm, o_status, s, selected));
     RC(end_call(c, s));
     c->last.n_orders = n;
     if (ptr_kind == WR_HOST) {

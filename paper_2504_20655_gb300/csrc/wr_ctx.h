@@ -85,6 +85,8 @@ struct wr_ctx {
     std::vector<cudaEvent_t> events;
     int n_events_used = 0;
     int ev_call_begin = -1, ev_call_end = -1;
+    int64_t* h_offs = nullptr;   // pinned: offs[0], offs[n] of a call with device buffers
+    cudaEvent_t ev_offs = nullptr;
     std::vector<std::pair<int, int>> ev_phase[6];  // select, init, bf, gather, enum, finish
     int launches = 0;
     cudaStream_t last_stream = nullptr;
@@ -137,7 +139,9 @@ int run_tours(wr_ctx* c, int32_t n, const int32_t* k_dev, const wr::TourBufs& tb
               int perm_stride, int32_t* status, cudaStream_t s);
 int ensure_tour_bufs(wr_ctx* c, int32_t n, wr::TourBufs& tb);
 int finish_graph(wr_ctx* c);
+int enqueue_select(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_picks, cudaStream_t s);
+// selected: enqueue_select already queued for this call
 int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_picks, int64_t np_bound,
-                  int32_t* o_cost, int32_t* o_perm, int32_t* o_status, cudaStream_t s);
+                  int32_t* o_cost, int32_t* o_perm, int32_t* o_status, cudaStream_t s, bool selected = false);
 
 }  // namespace wrc
