@@ -136,8 +136,9 @@ int wr_load_graph(wr_ctx* ctx, int32_t V, int64_t E, const int64_t* row_ptr, con
 
 /* a1-a7 -- Route a batch of orders.  Order i has picks picks[offs[i] .. offs[i+1]),
  * offs has n_orders+1 non-decreasing entries with offs[0] = 0 (checked for host
- * input, WR_EINVAL; with device input an order whose range leaves [0, offs[n]]
- * is reported WR_ORDER_BAD and gets no perm writes).
+ * input, WR_EINVAL; with device input offs[0] != 0 or offs[n] < 0 is WR_EINVAL
+ * and no pick is read, and an order whose range leaves [0, offs[n]] is
+ * reported WR_ORDER_BAD and gets no perm writes).
  * Writes cost[i], status[i] and perm[offs[i] + j].
  * Sources (depot + distinct pick nodes) are deduplicated on the device and
  * processed in segments of at most mem_budget_bytes of rows. */

@@ -31,7 +31,9 @@ __global__ void select_kernel(int32_t n, const int64_t* __restrict__ offs, const
     const int64_t b = offs[o], e = offs[o + 1];
     const int64_t k = e - b;
     int st = WR_ORDER_OK;
-    if (k < 1 || k > max_k || b < 0 || e > offs[n]) {
+    // offsets that do not start at 0 make the whole call invalid: no pick is read (the host
+    // returns WR_EINVAL once it has read them back)
+    if (k < 1 || k > max_k || b < 0 || e > offs[n] || offs[0] != 0) {
         st = WR_ORDER_BAD;
     } else {
         for (int64_t i = b; i < e; ++i)

@@ -784,6 +784,41 @@ def test_route_held_karp_full_batch_and_small_budget(wr, orc):
         assert (status == s).all() and (cost == c).all() and (perm[:len(p)] == p).all(), budget
 
 
+def test_route_orders_device_buffers_bad_offsets(wr):
+    """wr_route_orders with device buffers whose offsets do not start at 0, or decrease, or
+    end below 0: WR_EINVAL, no pick read past the buffer, and the context still routes a
+    valid batch afterwards with the same bits as before."""
+    import torch
+    g, o = synth.medium_workload(n_orders=16)
+    dev = torch.device("cuda", 0)
+    r = wr.Router(device=0)
+    try:
+        r.load_graph(g)
+        want = r.route_orders(o.offs, o.picks)
+        n = 3
+        picks = torch.from_numpy(o.picks[:6].copy()).to(dev)  # 6 picks only
+        cost = torch.empty(n, dtype=torch.int32, device=dev)
+        perm = torch.empty(6, dtype=torch.int32, device=dev)
+        status = torch.empty(n, dtype=torch.int32, device=dev)
+        stream = torch.cuda.current_stream(dev).cuda_stream
+        for bad in ([4, 6, 8, 10], [0, 2, 4, -1]):
+            offs = torch.tensor(bad, dtype=torch.int64, device=dev)
+            with pytest.raises(wr.WrError) as e:
+                wr.wr_route_orders(r.ctx, offs, picks, cost, perm, status, stream)
+            assert e.value.code == wr.WR_EINVAL, bad
+        # a decreasing offset is a bad order, not a bad call: the other orders are routed
+        offs = torch.tensor([0, 4, 2, 6], dtype=torch.int64, device=dev)
+        wr.wr_route_orders(r.ctx, offs, picks, cost, perm, status, stream)
+        torch.cuda.synchronize()
+        st = status.cpu().numpy()
+        assert st[1] == wr.WR_ORDER_BAD and st[0] == wr.WR_ORDER_OK and st[2] == wr.WR_ORDER_OK, st
+        again = r.route_orders(o.offs, o.picks)
+        for a, b in zip(want, again):
+            assert (np.asarray(a) == np.asarray(b)).all()
+    finally:
+        r.close()
+
+
 def test_route_nodes_device_buffers_one_call(wr):
     """wr_route_nodes with device buffers and a node buffer sized from a count-only call:
     one call writes the same nodes as the host path; a buffer one node short is ENOMEM."""
