@@ -43,6 +43,7 @@ int record(wr_ctx* c, cudaStream_t s, int* idx) {
 
 int begin_call(wr_ctx* c, cudaStream_t s) {
     c->n_events_used = 0;
+    c->ev_call_end = -1;  // a call that fails after this point reports no total
     for (auto& v : c->ev_phase) v.clear();
     c->launches = 0;
     c->last_stream = s;
