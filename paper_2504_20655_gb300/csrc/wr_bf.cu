@@ -543,8 +543,9 @@ __global__ void bf_submatrix_kernel(BfSegment seg, int32_t V, int32_t n_dst, con
                    static_cast<unsigned long long>(2 * v + 1);
         atomicAdd(check + seg.first + b, acc);
     }
-    if (blockIdx.x == 0 && b < n_lanes) {
-        for (int j = sub_row; j < n_dst; j += 8)
+    // the submatrix entries, spread over every block of this lane group (a few loads per thread)
+    if (b < n_lanes) {
+        for (int j = blockIdx.x * 8 + sub_row; j < n_dst; j += gridDim.x * 8)
             sub[static_cast<int64_t>(seg.first + b) * n_dst + j] =
                 static_cast<int32_t>(__ldcg(seg.rows + static_cast<int64_t>(dst[j]) * seg.ld + b));
     }
