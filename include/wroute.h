@@ -46,7 +46,8 @@ extern "C" {
 
 /* return codes */
 #define WR_OK        0
-#define WR_EINVAL    1  /* bad argument, malformed CSR, negative weight, size out of range */
+#define WR_EINVAL    1  /* bad argument, malformed CSR, negative weight, distances that could reach
+                           WR_INF (see wr_load_graph), size out of range */
 #define WR_ENOMEM    2  /* allocation failed, or the memory budget holds fewer than 32 rows */
 #define WR_ECUDA     3  /* a CUDA runtime call failed */
 #define WR_ETIMEOUT  4  /* a bounded device-side wait (grid barrier) ran out */
@@ -130,7 +131,12 @@ int wr_sync(wr_ctx* ctx);
  * arcs of node u are [row_ptr[u], row_ptr[u+1]) with heads col[] and int32
  * weights w[] >= 0.  row_ptr has V+1 entries, row_ptr[0] = 0, row_ptr[V] = E.
  * depot in [0, V) is P_0 of every order.  Copies everything; replaces any
- * previous graph.  WR_EINVAL on malformed input or a negative weight. */
+ * previous graph.  WR_EINVAL on malformed input or a negative weight.
+ * Distances are int32 and WR_INF marks an unreachable node, so a finite distance
+ * must stay below WR_INF.  Every shortest path is simple (w >= 0): it has at most
+ * V - 1 arcs and uses no arc twice.  The graph is therefore accepted only when
+ *   min((V - 1) * max w, sum of all w) < WR_INF     (over the arcs as given),
+ * and WR_EINVAL otherwise; every finite distance is then exact. */
 int wr_load_graph(wr_ctx* ctx, int32_t V, int64_t E, const int64_t* row_ptr, const int32_t* col,
                   const int32_t* w, int32_t depot, int ptr_kind);
 

@@ -21,6 +21,7 @@ MAX_K = 12
 MAX_K_HK = 20
 LEG_MAX = 10324440
 OK, UNREACHABLE, BADORDER, RANGE = 0, 1, 2, 3
+EDIST = -4  # a finite distance would reach INF
 SSSP = {"rounds": 0, "fifo": 1, "dijkstra": 2}
 TOUR = {"brute": 0, "heldkarp": 1}
 OPEN_PATH = 16
@@ -55,6 +56,8 @@ def _configure(L):
     L.or_factorial.restype = i64
     L.or_tour_clustered.argtypes = [i32, P, P, i32, I, P, P]
     L.or_patched_route_count.argtypes = [i32, P]
+    L.or_graph_check.argtypes = [i32, P, P, P]
+    L.or_kmeans.argtypes = [i32, P, i32, P, P, P, P, P]
     L.or_patched_route_count.restype = i64
     return L
 
@@ -95,9 +98,25 @@ def _csr(g):
             np.ascontiguousarray(g.w, dtype=np.int32))
 
 
+class DistanceRangeError(RuntimeError):
+    """A finite distance would reach INF (2^31 - 1): the graph breaks the int32 rule."""
+
+
 def _check(rc, what):
+    if rc == EDIST:
+        raise DistanceRangeError(f"oracle {what}: a finite distance would reach INF")
     if rc != 0:
         raise RuntimeError(f"oracle {what} failed with {rc}")
+
+
+def graph_check(g) -> bool:
+    """True when every finite distance of g must stay below INF, by the bound
+    min((V-1) * max w, sum of w) over the arcs as given."""
+    rp, c, w = _csr(g)
+    rc = lib().or_graph_check(g.V, _p(rp), _p(c), _p(w))
+    if rc not in (0, EDIST):
+        raise RuntimeError(f"oracle graph_check failed with {rc}")
+    return rc == 0
 
 
 def bf_rounds(g, src: int):
@@ -264,6 +283,22 @@ def tour_clustered(D, xy, m: int, open_path: bool = False):
     if st < 0:
         raise RuntimeError(f"oracle clustered tour failed with {st}")
     return int(st), int(cost[0]), perm[:k].copy()
+
+
+def kmeans(xy, m: int):
+    """The k-means step of the cluster-patched route (Sec. 3) on the k stops' plan
+    coordinates xy (k x 2), at most m clusters.  Returns (assign, Sx, Sy, cnt, steps):
+    stop i's cluster assign[i], centre c's coordinate sums Sx[c], Sy[c] over its cnt[c]
+    stops (the mean is Sx/cnt, Sy/cnt), and the number of assignment passes run."""
+    xy = np.ascontiguousarray(xy, dtype=np.int32)
+    k = xy.shape[0]
+    assign = np.zeros(max(k, 1), np.int32)
+    sx, sy, cnt = (np.zeros(max(k, 1), np.int64) for _ in range(3))
+    steps = np.zeros(1, np.int32)
+    nc = lib().or_kmeans(k, _p(xy), int(m), _p(assign), _p(sx), _p(sy), _p(cnt), _p(steps))
+    if nc < 0:
+        raise RuntimeError(f"oracle kmeans failed with {nc}")
+    return assign[:k].copy(), sx[:nc].copy(), sy[:nc].copy(), cnt[:nc].copy(), int(steps[0])
 
 
 def route_orders_clustered(g, orders, xy, m: int, open_path: bool = False, n_threads: int = 1):

@@ -16,6 +16,35 @@ typedef int64_t i64;
 /* Single-source shortest paths                                        */
 /* ------------------------------------------------------------------ */
 
+/* Distances are int32 with OR_INF (2^31 - 1) meaning unreachable: a finite
+ * distance (below BIG) at or above OR_INF has no int32 value and is an
+ * error, never a cast. */
+static int fits_int32(const i64* d, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (d[i] < BIG && d[i] >= (i64)OR_INF) return 0;
+    return 1;
+}
+
+/* The graph rule: a shortest path is simple (w >= 0), so it has at most V-1
+ * arcs and uses no arc twice; its length is at most min((V-1) max w, sum w),
+ * taken over the arcs as given.  The graph is accepted when that bound is below
+ * OR_INF, so every finite distance fits int32. */
+int or_graph_check(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w) {
+    if (V <= 0 || row_ptr[0] != 0) return -1;
+    i64 max_w = 0, sum_w = 0;
+    for (int32_t u = 0; u < V; ++u) {
+        if (row_ptr[u + 1] < row_ptr[u]) return -1;
+        for (int64_t a = row_ptr[u]; a < row_ptr[u + 1]; ++a) {
+            if (col[a] < 0 || col[a] >= V || w[a] < 0) return -1;
+            if (w[a] > max_w) max_w = w[a];
+            if (sum_w < BIG) sum_w += w[a];
+        }
+    }
+    i64 bound = (i64)(V - 1) * max_w;
+    if (sum_w < bound) bound = sum_w;
+    return bound < (i64)OR_INF ? 0 : OR_EDIST;
+}
+
 /* Sec. 4.7: Bellman-Ford relaxes every arc of the arc list per round and
  * needs at most V-1 rounds.  Each round here reads the previous round's
  * distances (a Jacobi round); the loop stops at the first round that
@@ -43,6 +72,7 @@ int or_bf_rounds(int32_t V, const int64_t* row_ptr, const int32_t* col, const in
         if (!changed) break;
         ++rounds;
     }
+    if (!fits_int32(cur, (size_t)V)) { free(cur); free(nxt); return OR_EDIST; }
     for (int32_t v = 0; v < V; ++v) dist[v] = cur[v] >= BIG ? OR_INF : (int32_t)cur[v];
     if (rounds_out) *rounds_out = rounds;
     free(cur); free(nxt);
@@ -72,6 +102,7 @@ int or_bf_fifo(int32_t V, const int64_t* row_ptr, const int32_t* col, const int3
             }
         }
     }
+    if (!fits_int32(d, (size_t)V)) { free(d); free(q); free(inq); return OR_EDIST; }
     for (int32_t v = 0; v < V; ++v) dist[v] = d[v] >= BIG ? OR_INF : (int32_t)d[v];
     free(d); free(q); free(inq);
     return 0;
@@ -129,6 +160,7 @@ int or_dijkstra(int32_t V, const int64_t* row_ptr, const int32_t* col, const int
             if (cand < d[v]) { d[v] = cand; hitem x = {cand, v}; heap_push(h, &n, x); }
         }
     }
+    if (!fits_int32(d, (size_t)V)) { free(d); free(done); free(h); return OR_EDIST; }
     for (int32_t v = 0; v < V; ++v) dist[v] = d[v] >= BIG ? OR_INF : (int32_t)d[v];
     free(d); free(done); free(h);
     return 0;
@@ -154,6 +186,7 @@ int or_floyd_warshall(int32_t V, const int64_t* row_ptr, const int32_t* col, con
                 if (c < d[i * n + j]) d[i * n + j] = c;
             }
         }
+    if (!fits_int32(d, n * n)) { free(d); return OR_EDIST; }
     for (size_t i = 0; i < n * n; ++i) dist[i] = d[i] >= BIG ? OR_INF : (int32_t)d[i];
     free(d);
     return 0;
@@ -348,16 +381,19 @@ static i64 leg64(const int32_t* D, int32_t n, int32_t a, int32_t b) {
 }
 static int frac_less(i64 num1, i64 den1, i64 num2, i64 den2) { return num1 * den2 < num2 * den1; }
 
-int or_tour_clustered(int32_t k, const int32_t* D, const int32_t* xy, int32_t m, int open_path,
-                      int32_t* cost, int32_t* perm) {
-    if (k < 1 || k > OR_MAX_K || m < 1) return OR_BADORDER;
-    if (!range_check(k, D)) { *cost = OR_INF; identity(k, perm); return OR_RANGE; }
-    const int32_t n = k + 1;
-    /* k-means on the stops' coordinates */
-    int32_t centre_of_init[OR_MAX_K];
-    i64 Sx[OR_MAX_K], Sy[OR_MAX_K], cnt[OR_MAX_K];
+/* k-means on the stops' plan coordinates (Sec. 3 clusters the stops with
+ * K-means): farthest-first initial centres, then Lloyd steps (assign every stop
+ * to its nearest centre, move every non-empty centre to the mean of its stops)
+ * until no assignment changes, at most 64 steps.  A centre is kept as the sums
+ * (Sx, Sy) of its stops' coordinates and their count cnt, so the mean is
+ * (Sx/cnt, Sy/cnt) without rounding; an initial centre is one stop (cnt = 1).
+ * Returns the number of centres nc (assign[i] in [0, nc)); *steps = the number
+ * of assignment passes run, the last one changing nothing unless the 64-step cap
+ * was reached. */
+int or_kmeans(int32_t k, const int32_t* xy, int32_t m, int32_t* assign, int64_t* Sx, int64_t* Sy,
+              int64_t* cnt, int32_t* steps) {
+    if (k < 1 || k > OR_MAX_K || m < 1) return -1;
     int32_t nc = 0;
-    centre_of_init[nc] = 0;
     Sx[nc] = xy[0]; Sy[nc] = xy[1]; cnt[nc] = 1; ++nc;
     while (nc < m && nc < k) {
         int32_t best_i = -1;
@@ -372,12 +408,12 @@ int or_tour_clustered(int32_t k, const int32_t* D, const int32_t* xy, int32_t m,
             if (dmin > best_d) { best_d = dmin; best_i = i; }
         }
         if (best_d <= 0) break;
-        centre_of_init[nc] = best_i;
         Sx[nc] = xy[2 * best_i]; Sy[nc] = xy[2 * best_i + 1]; cnt[nc] = 1; ++nc;
     }
-    int32_t assign[OR_MAX_K];
     for (int32_t i = 0; i < k; ++i) assign[i] = -1;
-    for (int it = 0; it < 64; ++it) {
+    int32_t it = 0;
+    while (it < 64) {
+        ++it;
         int changed = 0;
         for (int32_t i = 0; i < k; ++i) {
             int32_t bc = 0;
@@ -397,7 +433,18 @@ int or_tour_clustered(int32_t k, const int32_t* D, const int32_t* xy, int32_t m,
             if (ct > 0) { Sx[c] = sx; Sy[c] = sy; cnt[c] = ct; }
         }
     }
-    (void)centre_of_init;
+    if (steps) *steps = it;
+    return nc;
+}
+
+int or_tour_clustered(int32_t k, const int32_t* D, const int32_t* xy, int32_t m, int open_path,
+                      int32_t* cost, int32_t* perm) {
+    if (k < 1 || k > OR_MAX_K || m < 1) return OR_BADORDER;
+    if (!range_check(k, D)) { *cost = OR_INF; identity(k, perm); return OR_RANGE; }
+    const int32_t n = k + 1;
+    int32_t assign[OR_MAX_K];
+    i64 Sx[OR_MAX_K], Sy[OR_MAX_K], cnt[OR_MAX_K];
+    const int32_t nc = or_kmeans(k, xy, m, assign, Sx, Sy, cnt, 0);
     /* clusters in centre order, stops in increasing index */
     int32_t members[OR_MAX_K][OR_MAX_K], size[OR_MAX_K], M = 0;
     for (int32_t c = 0; c < nc; ++c) {
@@ -560,6 +607,8 @@ int or_route_orders(int32_t V, const int64_t* row_ptr, const int32_t* col, const
                     int sssp_kind, int tour_kind, int n_threads,
                     int32_t* cost, int32_t* perm, int32_t* status) {
     if (V <= 0 || depot < 0 || depot >= V || n_orders < 0) return -1;
+    int grc = or_graph_check(V, row_ptr, col, w);
+    if (grc) return grc;
     int64_t np = offs[n_orders];
     int32_t* nodes = (int32_t*)malloc(sizeof(int32_t) * (size_t)(np + 1));
     if (!nodes) return -2;

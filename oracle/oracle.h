@@ -21,6 +21,8 @@
  *
  * Conventions (readings of points the paper leaves open):
  *   - distances are int32, unreachable = OR_INF (INT32_MAX); weights >= 0;
+ *     a graph whose distances could reach OR_INF is refused (or_graph_check),
+ *     and no distance at or above OR_INF is ever cast to int32 (OR_EDIST);
  *   - a tour with an unreachable leg is not a candidate; if every tour has
  *     one the order is OR_UNREACHABLE (cost OR_INF, perm = identity);
  *   - any finite off-diagonal D entry above OR_LEG_MAX makes the order
@@ -44,6 +46,8 @@
 #define OR_UNREACHABLE 1
 #define OR_BADORDER 2
 #define OR_RANGE 3
+/* error return: a finite distance would reach OR_INF (see or_graph_check) */
+#define OR_EDIST (-4)
 
 #define OR_SSSP_ROUNDS 0
 #define OR_SSSP_FIFO 1
@@ -58,7 +62,8 @@
 extern "C" {
 #endif
 
-/* Out-arc CSR: arcs of u are [row_ptr[u], row_ptr[u+1]) with head col[] and weight w[]. */
+/* Out-arc CSR: arcs of u are [row_ptr[u], row_ptr[u+1]) with head col[] and weight w[].
+ * The shortest-path functions return OR_EDIST instead of a distance at or above OR_INF. */
 int or_bf_rounds(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
                  int32_t src, int32_t* dist, int32_t* rounds_out);
 int or_bf_fifo(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
@@ -68,6 +73,11 @@ int or_dijkstra(int32_t V, const int64_t* row_ptr, const int32_t* col, const int
 /* dist is V*V, row-major dist[s*V + t]. */
 int or_floyd_warshall(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
                       int32_t* dist);
+
+/* 0 when every finite distance of the graph must stay below OR_INF, by the bound
+ * min((V-1) * max w, sum of w) over the arcs as given; OR_EDIST when the bound
+ * reaches OR_INF; -1 on a malformed CSR.  or_route_orders refuses such graphs. */
+int or_graph_check(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w);
 
 /* Rows for n_src sources: rows[i*V + v] = dist(src[i], v).  kind = OR_SSSP_*. */
 int or_sssp_rows(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
@@ -82,6 +92,14 @@ int or_tour_held_karp(int32_t k, const int32_t* D, int32_t* cost, int32_t* perm)
  * 10 stops (more: OR_BADORDER); open_path != 0 leaves the depot legs out. */
 int or_tour_clustered(int32_t k, const int32_t* D, const int32_t* xy, int32_t m, int open_path,
                       int32_t* cost, int32_t* perm);
+
+/* The k-means step of the cluster-patched route (Sec. 3): farthest-first initial
+ * centres, Lloyd steps until no assignment changes (at most 64).  Returns the number
+ * of centres nc; assign[i] in [0, nc) is stop i's cluster; centre c's mean is
+ * (Sx[c]/cnt[c], Sy[c]/cnt[c]) (arrays of at least min(m, k) entries); *steps (may be
+ * NULL) = assignment passes run.  -1 on bad arguments (k outside 1..OR_MAX_K, m < 1). */
+int or_kmeans(int32_t k, const int32_t* xy, int32_t m, int32_t* assign, int64_t* Sx, int64_t* Sy,
+              int64_t* cnt, int32_t* steps);
 
 /* Whole path for a batch of orders; picks of order i are picks[offs[i]..offs[i+1]). */
 int or_route_orders(int32_t V, const int64_t* row_ptr, const int32_t* col, const int32_t* w,

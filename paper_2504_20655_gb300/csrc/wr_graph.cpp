@@ -25,8 +25,19 @@ int build_host_graph(int32_t V, int64_t E, const int64_t* row_ptr, const int32_t
     if (row_ptr[0] != 0 || row_ptr[V] != E) return WR_EINVAL;
     for (int32_t u = 0; u < V; ++u)
         if (row_ptr[u + 1] < row_ptr[u]) return WR_EINVAL;
-    for (int64_t a = 0; a < E; ++a)
+    // Distances are int32 with WR_INF = 2^31 - 1 meaning unreachable.  A shortest
+    // path is simple (w >= 0), so it has at most V - 1 arcs and uses each arc at most
+    // once: its length is at most min((V - 1) * max w, sum of all w).  The graph is
+    // accepted only when that bound stays below WR_INF, so every finite distance is
+    // exact and none can be mistaken for unreachable.  The bound is taken over the arcs
+    // as given (self loops and parallel arcs included).
+    int64_t max_w = 0, sum_w = 0;
+    for (int64_t a = 0; a < E; ++a) {
         if (col[a] < 0 || col[a] >= V || w[a] < 0) return WR_EINVAL;
+        max_w = std::max<int64_t>(max_w, w[a]);
+        sum_w = std::min<int64_t>(sum_w + w[a], int64_t(1) << 40);  // saturate: only "< WR_INF" matters
+    }
+    if (std::min<int64_t>(static_cast<int64_t>(V - 1) * max_w, sum_w) >= WR_INF) return WR_EINVAL;
 
     std::vector<int64_t> cnt(static_cast<size_t>(V) + 1, 0);
     for (int32_t u = 0; u < V; ++u)

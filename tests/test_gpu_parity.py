@@ -745,6 +745,79 @@ def test_wait_limit_reports_timeout_and_device_stays_usable(wr, orc, tiling):
         r2.close()
 
 
+def test_route_clustered_kmeans_by_hand(wr, orc):
+    """The hand-worked k-means cases (tests/golden/kmeans_by_hand.json: Lloyd steps that
+    move centres and change assignments, ties, fewer spots than clusters) through the
+    GPU's clustered routing: stops at the cases' coordinates on a complete graph of
+    seeded asymmetric weights, the picks given in several orders, tours and open paths;
+    equal to the oracle element by element."""
+    import itertools
+    import json
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "kmeans_by_hand.json")))
+    for ci, case in enumerate(gold["cases"]):
+        xy_stops = np.array(case["xy"], np.int32)
+        k = len(xy_stops)
+        V = k + 1  # node k is the depot
+        u, v = np.nonzero(~np.eye(V, dtype=bool))
+        w = synth.uniform_int(7100 + ci, u.shape[0], 1, 60)
+        rp, col, wt = synth.csr_from_arcs(V, u, v, w)
+        g = synth.Graph(V=V, row_ptr=rp, col=col, w=wt, depot=k, n_slots=k)
+        xy = np.vstack([xy_stops, [[0, 0]]]).astype(np.int32)
+        orders = [list(range(k)), list(range(k))[::-1]] + \
+            [list(p) for p in itertools.islice(itertools.permutations(range(k)), 3, 40, 7)]
+        offs = np.arange(len(orders) + 1, dtype=np.int64) * k
+        o = synth.Orders(offs, np.array(sum(orders, []), np.int32))
+        for open_path in (False, True):
+            r = wr.Router(device=0)
+            try:
+                r.load_graph(g)
+                r.set_route_mode(open_path)
+                r.set_clusters(case["m"], xy)
+                cost, perm, status = r.route_orders(o.offs, o.picks)
+            finally:
+                r.close()
+            c, p, s_ = orc.route_orders_clustered(g, o, xy, case["m"], open_path, 1)
+            assert (status == s_).all() and (cost == c).all() and (perm[:len(p)] == p).all(), \
+                (case["name"], open_path)
+
+
+def test_load_graph_int32_rule(wr, orc):
+    """The int32 distance rule on both sides: graphs whose bound min((V-1) max w, sum w)
+    reaches INF are refused by wr_load_graph (WR_EINVAL, context still usable) and by the
+    oracle; accepted graphs with distances near 2^31 give the oracle's rows exactly, and
+    orders over them the oracle's statuses (legs above WR_LEG_MAX are WR_ORDER_RANGE)."""
+    def graph(V, arcs):
+        u, v, w = (np.array(x, np.int64) for x in zip(*arcs))
+        rp, col, wt = synth.csr_from_arcs(V, u, v, w)
+        return synth.Graph(V=V, row_ptr=rp, col=col, w=wt, depot=0, n_slots=V)
+
+    refused = [graph(3, [(0, 1, 1_500_000_000), (1, 2, 1_500_000_000)]), graph(2, [(0, 1, INF)]),
+               graph(40, [(i, i + 1, 60_000_000) for i in range(39)])]
+    accepted = [graph(3, [(0, 1, 2_000_000_000), (1, 2, 5), (2, 0, 7)]), graph(2, [(0, 1, INF - 1), (1, 0, 3)]),
+                graph(4, [(a, b, 500_000_000 + 11 * a + b) for a in range(4) for b in range(4) if a != b]),
+                graph(40, [(i, i + 1, 55_000_000) for i in range(39)] + [(39, 0, 1)])]
+    r = wr.Router(device=0)
+    try:
+        for g in refused:
+            assert not orc.graph_check(g)
+            with pytest.raises(wr.WrError) as e:
+                r.load_graph(g)
+            assert e.value.code == wr.WR_EINVAL
+        for g in accepted:
+            assert orc.graph_check(g)
+            r.load_graph(g)
+            src = np.arange(g.V, dtype=np.int32)
+            assert (r.bf_rows(src) == orc.sssp_rows(g, src, "dijkstra")).all()
+            ks = [1, 2, min(3, g.V - 1)]
+            picks = np.concatenate([np.arange(1, 1 + k) % g.V for k in ks]).astype(np.int32)
+            o = synth.Orders(np.concatenate([[0], np.cumsum(ks)]).astype(np.int64), picks)
+            cost, perm, status = r.route_orders(o.offs, o.picks)
+            c, p, s_ = orc.route_orders(g, o, "dijkstra", "brute")
+            assert (status == s_).all() and (cost == c).all() and (perm[:len(p)] == p).all()
+    finally:
+        r.close()
+
+
 def test_route_clustered_uneven_orders(wr, orc):
     """Clustered routing of orders of 2..12 picks: with one cluster the orders above ten
     stops are WR_ORDER_BAD on both sides, with four clusters every order is routed; the

@@ -17,6 +17,7 @@ from tests.graphs import path_graph, random_graph
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "tours_by_hand.json")))
+KMEANS = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "kmeans_by_hand.json")))
 
 MUTANTS = [
     ("bf dropped weight", "i64 cand = cur[u] + (i64)w[a];", "i64 cand = cur[u];"),
@@ -41,6 +42,23 @@ MUTANTS = [
      "for (uint32_t dir = 0; dir < 1u; ++dir) {"),
     ("patching last minimiser", "int better = !have || t < best;", "int better = !have || t <= best;"),
     ("patching no return leg", "t = back >= BIG ? BIG : t + back;", "t = back >= BIG ? BIG : t;"),
+    ("kmeans single pass", "while (it < 64) {", "while (it < 1) {"),
+    ("kmeans centres never moved", "if (ct > 0) { Sx[c] = sx; Sy[c] = sy; cnt[c] = ct; }",
+     "if (ct < 0) { Sx[c] = sx; Sy[c] = sy; cnt[c] = ct; }"),
+    ("kmeans mean off by one", "if (ct > 0) { Sx[c] = sx; Sy[c] = sy; cnt[c] = ct; }",
+     "if (ct > 0) { Sx[c] = sx; Sy[c] = sy; cnt[c] = ct + 1; }"),
+    ("kmeans ties to highest centre", "if (c == 0 || frac_less(num, den, bnum, bden)) {",
+     "if (c == 0 || !frac_less(bnum, bden, num, den)) {"),
+    ("kmeans farthest tie to highest stop", "if (dmin > best_d) { best_d = dmin; best_i = i; }",
+     "if (dmin >= best_d) { best_d = dmin; best_i = i; }"),
+    ("int32 rule inclusive bound", "return bound < (i64)OR_INF ? 0 : OR_EDIST;",
+     "return bound <= (i64)OR_INF ? 0 : OR_EDIST;"),
+    ("int32 rule max term only", "if (sum_w < bound) bound = sum_w;", "(void)sum_w;"),
+    ("int32 rule sum term only", "if (sum_w < bound) bound = sum_w;", "bound = sum_w;"),
+    ("distance cast at INF", "if (d[i] < BIG && d[i] >= (i64)OR_INF) return 0;",
+     "if (d[i] < BIG && d[i] > (i64)OR_INF) return 0;"),
+    ("kmeans x only", "i64 num = dx * dx + dy * dy, den = cnt[c] * cnt[c];",
+     "i64 num = dx * dx, den = cnt[c] * cnt[c];"),
 ]
 
 
@@ -109,13 +127,28 @@ def pins_pass() -> bool:
             st, c, pm = oracle.tour_clustered(D, xy, 2, False)
             if (c, pm.tolist()) != best:
                 return False
+        # k-means step: the hand-worked cases and the fixed point of the Lloyd map
+        from tests.test_oracle_kmeans import _fixed_point
+        for case in KMEANS["cases"]:
+            a, sx, sy, cnt, steps = oracle.kmeans(np.array(case["xy"]), case["m"])
+            if a.tolist() != case["assign"] or cnt.tolist() != case["cnt"] or sx.tolist() != case["Sx"] \
+                    or sy.tolist() != case["Sy"]:
+                return False
+        for seed in range(20):
+            k = 3 + seed % 10
+            xy = synth.uniform_int(500 + seed, 2 * k, 0, 12).reshape(k, 2).astype(np.int64)
+            if not _fixed_point(xy, 3, *oracle.kmeans(xy, 3)[:4]):
+                return False
+        # the int32 distance rule and the refusal to cast a distance at or above INF
+        from tests.test_oracle_sssp import test_int32_rule_refuses_and_accepts
+        test_int32_rule_refuses_and_accepts(oracle)
         D = np.full((5, 5), 7, dtype=np.int32)
         np.fill_diagonal(D, 0)
         D[1, 2] = oracle.LEG_MAX + 1
         if oracle.tour(D, "brute")[0] != oracle.RANGE:
             return False
         return True
-    except Exception:
+    except (Exception, pytest.fail.Exception):  # pytest.raises reports a miss with pytest.fail
         return False
 
 

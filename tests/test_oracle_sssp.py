@@ -137,3 +137,66 @@ def test_one_way_aisles_are_asymmetric(orc):
     rows = orc.sssp_rows(g, src, "dijkstra", n_threads=4)
     sub = rows[:, src]
     assert (sub != sub.T).any()
+
+
+def _graph(V, arcs):
+    u, v, w = (np.array(x, np.int64) for x in zip(*arcs))
+    rp, col, wt = synth.csr_from_arcs(V, u, v, w)
+    return synth.Graph(V=V, row_ptr=rp, col=col, w=wt, depot=0, n_slots=V)
+
+
+def _all_sssp(orc, g, s):
+    return [orc.bf_rounds(g, s)[0], orc.bf_fifo(g, s), orc.dijkstra(g, s), orc.floyd_warshall(g)[s]]
+
+
+def test_int32_rule_refuses_and_accepts(orc):
+    """Distances are int32 with INF = 2^31 - 1 for unreachable.  A graph is accepted when
+    min((V-1) max w, sum w) < INF; every shortest path is simple, so that bounds every
+    finite distance.  Hand-worked cases for both sides of each term of the bound, and no
+    shortest-path routine ever returns a distance at or above INF."""
+    # two arcs of 1.5e9 in a row: the bound (3e9) and the true distance reach INF
+    g = _graph(3, [(0, 1, 1_500_000_000), (1, 2, 1_500_000_000)])
+    assert not orc.graph_check(g)
+    for f in (lambda: orc.bf_rounds(g, 0), lambda: orc.bf_fifo(g, 0), lambda: orc.dijkstra(g, 0),
+              lambda: orc.floyd_warshall(g)):
+        with pytest.raises(orc.DistanceRangeError):
+            f()
+    with pytest.raises(orc.DistanceRangeError):
+        orc.route_orders(g, synth.Orders(np.array([0, 1], np.int64), np.array([2], np.int32)))
+    # one heavy arc: (V-1) max w = 4e9 but sum w = 2e9 + 5 < INF, so accepted; exact values
+    g = _graph(3, [(0, 1, 2_000_000_000), (1, 2, 5)])
+    assert orc.graph_check(g)
+    for d in _all_sssp(orc, g, 0):
+        assert d.tolist() == [0, 2_000_000_000, 2_000_000_005]
+    # a complete graph of 4 nodes, every arc 5e8: sum w = 6e9 but (V-1) max w = 1.5e9 < INF
+    g = _graph(4, [(a, b, 500_000_000) for a in range(4) for b in range(4) if a != b])
+    assert orc.graph_check(g)
+    for d in _all_sssp(orc, g, 2):
+        assert d.tolist() == [500_000_000, 500_000_000, 0, 500_000_000]
+    # the edge of the rule: one arc of INF - 1 is a finite distance; one arc of INF is not
+    g = _graph(2, [(0, 1, INF - 1)])
+    assert orc.graph_check(g)
+    for d in _all_sssp(orc, g, 0):
+        assert d.tolist() == [0, INF - 1]
+    g = _graph(2, [(0, 1, INF)])
+    assert not orc.graph_check(g)
+    with pytest.raises(orc.DistanceRangeError):
+        orc.dijkstra(g, 0)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_int32_rule_is_sound(orc, seed):
+    """On random small graphs with weights up to 2^31 - 1: whenever the rule accepts a
+    graph, every source's distances come back (none reaches INF); whenever a distance
+    reaches INF, the rule has refused the graph."""
+    for t in range(40):
+        V = 2 + (t % 6)
+        n = 1 + (7 * t + seed) % (2 * V)
+        hi = [INF, 1 << 30, 700_000_000, 300_000_000][(t + seed) % 4]
+        g = random_graph(V, n, 4000 + 97 * seed + t, w_lo=0, w_hi=hi)
+        ok = orc.graph_check(g)
+        for s in range(V):
+            try:
+                orc.dijkstra(g, s)
+            except orc.DistanceRangeError:
+                assert not ok
