@@ -111,10 +111,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload(name):
+def workload(name, n_orders=1024):
     from paper_2504_20655_gb300 import synth
     if name == "medium":
-        g, o = synth.medium_workload()
+        g, o = synth.medium_workload(n_orders=n_orders)
         desc = "medium: 100 aisles x 100 slots x 2 sides, 4 cross-aisles, 10% one-way (V=20401); " \
                "1024 orders, k~U{4..10}, Zipf(1.1) over 50k SKUs"
     elif name == "batching":
@@ -313,30 +313,38 @@ def run_reference(args):
     return 0
 
 
-def run_scale(args):
+def measure_scale(args):
     """Scale workload: rows of 4096 sources over the 1000 x 500 x 2-level layout
     (V = 1,002,001), produced segment by segment under the memory budget and
-    consumed on the device (4096 x 4096 submatrix + per-row checksum)."""
+    consumed on the device (4096 x 4096 submatrix + per-row checksum).  Returns the
+    line (rank 0) or None."""
     import torch
 
-    from paper_2504_20655_gb300 import synth, wroute
+    from paper_2504_20655_gb300 import shard, synth, wroute
     world, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    g, src = synth.scale_workload(n_src=args.scale_sources)
-    n = len(src)
+    # weak scaling: world x 4096 sources, every rank the rows of its contiguous slice of
+    # them (as many as one GPU alone); one all-gather of the submatrix rows per step
+    g, src_all = synth.scale_workload(n_src=args.scale_sources * world)
+    s_lo, s_hi = shard.even_slice(len(src_all), world, rank)
+    src = np.ascontiguousarray(src_all[s_lo:s_hi])
+    n, n_all = len(src), len(src_all)
     r = wroute.Router(device=local, mem_budget_bytes=args.budget_gib << 30)
     if args.tune:
         r.set_tuning(**json.loads(args.tune))
     r.load_graph(g)
     stream = torch.cuda.current_stream(dev)
     d_src = torch.from_numpy(src).to(dev)
-    sub = torch.empty((n, n), dtype=torch.int32, device=dev)
+    d_dst = torch.from_numpy(np.ascontiguousarray(src_all)).to(dev)
+    sub = torch.empty((n, n_all), dtype=torch.int32, device=dev)
     check = torch.empty(n, dtype=torch.int64, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def step():
-        wroute.wr_submatrix(r.ctx, d_src, d_src, sub, check, stream.cuda_stream)
+        wroute.wr_submatrix(r.ctx, d_src, d_dst, sub, check, stream.cuda_stream)
+        if world > 1:
+            shard.all_gather_rows(sub, world)
 
     for _ in range(args.warmup):
         step()
@@ -368,7 +376,9 @@ def run_scale(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": "scale: 1000 aisles x 500 slots x 2 levels, 2 cross-aisles (V=1002001, 3007998 arcs); "
-                               f"rows of {n} distinct slot sources consumed as a {n}x{n} submatrix + checksums",
+                               f"rows of {n} distinct slot sources consumed as a {n}x{n_all} submatrix + checksums"
+                               + (f"; sources split x{world}, one all-gather of the submatrix rows per step"
+                                  if world > 1 else ""),
                    "budget_gib": args.budget_gib, "segments": st["n_segments"], "tuning": r.tuning(),
                    "l2": "rows (2 GiB per segment) exceed L2; 512 MiB flush between steps"},
         "roofline": {"kernel": sweep_kernel_name(r.tuning()), "bound": "hbm", "achieved": achieved,
@@ -384,27 +394,25 @@ def run_scale(args):
         "paper_convention_mteps": paper_mteps(g.V, g.E, n, ms / 1e3),
     }
     # end to end through the C ABI with host buffers: sources in, submatrix and checksums out
-    h_sub = np.empty((n, n), np.int32)
+    h_sub = np.empty((n, n_all), np.int32)
     h_check = np.empty(n, np.uint64)
     e2e = []
     for i in range(args.warmup + args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        wroute.wr_submatrix(r.ctx, src, src, h_sub, h_check)
+        wroute.wr_submatrix(r.ctx, src, src_all, h_sub, h_check)
         if i >= args.warmup:
             e2e.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(sum(e2e) / len(e2e), world, dev)
-    line["e2e"] = {"value": g.E * n * world / e2e_s / 1e9, "unit": "Gedges/s", "h2d_bytes_per_step": 8 * n,
-                   "d2h_bytes_per_step": 4 * n * n + 8 * n,
+    line["e2e"] = {"value": g.E * n * world / e2e_s / 1e9, "unit": "Gedges/s", "h2d_bytes_per_step": 4 * (n + n_all),
+                   "d2h_bytes_per_step": 4 * n * n_all + 8 * n,
                    "matches_device_run": bool((h_sub == sub.cpu().numpy()).all())}
     if rank == 0 and not args.no_cpu:
         v, cores, sample = cpu_oracle_rows_rate(g, src, budget_s=args.ref_budget)
         line["cpu_baseline"] = {"value": v, "unit": "Gedges/s", "cores": cores, "kind": "oracle", "sample": sample}
-    if rank == 0:
-        print(json.dumps(line))
     r.close()
-    return 0
+    return line if rank == 0 else None
 
 
 def enum_ops(k):
@@ -416,10 +424,12 @@ def enum_ops(k):
     return sum(f // math.factorial(k - l) for l in range(1, k + 1)) + 2 * f
 
 
-def run_batching(args):
+def measure_batching(args):
     """Batching workload: 20,000 orders of k = 2..12 in one CUDA-graph launch per step
-    (the whole path captured once by wr_plan_create), tuned by the library's autotuner;
-    compared, bit for bit and in orders/s, with one plain wr_route_orders call per order."""
+    (the whole path captured once by wr_plan_create), tuned by the library's autotuner on
+    another batch of the same distribution (another seed); compared, bit for bit and in
+    orders/s, with one plain wr_route_orders call per order.  Returns the line (rank 0)
+    or None."""
     import torch
 
     from paper_2504_20655_gb300 import wroute
@@ -435,10 +445,19 @@ def run_batching(args):
     if args.tune:
         r.set_tuning(**json.loads(args.tune))
         tuned_by = "fixed (--tune)"
+        tuning_same_batch = None
     else:
+        # tuned on a batch drawn with another seed, then timed on this one; the tuning the
+        # timed batch itself would pick is reported beside it
+        from paper_2504_20655_gb300 import synth
+        _, o_t = synth.batching_workload(seed=synth.SEED_BASE + 1)
         t0 = time.perf_counter()
-        r.autotune(offs_d, picks_d, reps=1)
-        tuned_by = f"wr_autotune on this batch ({time.perf_counter() - t0:.1f} s, untimed)"
+        r.autotune(torch.from_numpy(o_t.offs).to(dev), torch.from_numpy(o_t.picks).to(dev), reps=1)
+        tuned_by = f"wr_autotune on another batch of the workload (seed {synth.SEED_BASE + 1}; " \
+                   f"{time.perf_counter() - t0:.1f} s, untimed)"
+        chosen = r.tuning()
+        tuning_same_batch = r.autotune(offs_d, picks_d, reps=1)
+        r.set_tuning(**chosen)
     plan = r.plan(n, np_)
     plan.set_batch(offs_d, picks_d)
     stream = torch.cuda.current_stream(dev)
@@ -529,7 +548,7 @@ def run_batching(args):
         "config": {"workload": desc, "orders_per_step": n, "sources": st["n_sources"],
                    "l2": "flushed (512 MiB write) between steps", "launch": "one CUDA graph per step (wr_plan_launch)",
                    "parallelism": f"replicas x{world} (orders are independent)", "tuning": r.tuning(),
-                   "tuned_by": tuned_by},
+                   "tuned_by": tuned_by, "tuning_if_tuned_on_this_batch": tuning_same_batch},
         "roofline": {"kernel": "enum_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak,
                      "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None,
                      "peak_source": "derived: 152 SMs x 64 ALU-pipe lanes (min / add-min) x max SM clock",
@@ -551,11 +570,9 @@ def run_batching(args):
     if rank == 0 and not args.no_cpu:
         v, cores, sample = cpu_oracle_rate(g, o, budget_s=args.ref_budget)
         line["cpu_baseline"] = {"value": v, "unit": "orders/s", "cores": cores, "kind": "oracle", "sample": sample}
-    if rank == 0:
-        print(json.dumps(line))
     plan.close()
     r.close()
-    return 0
+    return line if rank == 0 else None
 
 
 def serving_stream(n, rate, seed=None):
@@ -580,50 +597,89 @@ def serving_stream(n, rate, seed=None):
     return lay, synth.Orders(offs, picks), synth.poisson_arrivals(n, rate, seed)
 
 
-def run_serving(args):
+EPOCH = 100_000  # orders between two relocations of the top 5% SKUs
+
+
+def measure_serving(args, rates=None, seconds=None, max_orders=None, plain_max=None, plain_seconds=None):
     """Serving workload: real-time arrivals, continuous batching with a resident row
     cache (wr_serve_*), p50/p99 arrival-to-result latency and orders/s per arrival rate,
-    next to the plain mode (one order at a time, rows from scratch)."""
+    next to the plain mode (one order at a time, rows from scratch).  Each rate's stream
+    runs as one server call per relocation epoch (EPOCH orders; the server and its row
+    cache persist across calls), so the cache hit rate is reported per epoch; the first
+    arrival of an epoch follows the last result of the one before.  Returns the line
+    (rank 0) or None."""
     import torch
 
-    from paper_2504_20655_gb300 import wroute
+    from paper_2504_20655_gb300 import synth, wroute
     world, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
-    rates = [float(x) for x in args.rates.split(",")]
+    rates = rates or [float(x) for x in args.rates.split(",")]
+    seconds = args.serve_seconds if seconds is None else seconds
+    max_orders = args.serve_max_orders if max_orders is None else max_orders
+    plain_max = args.plain_max_orders if plain_max is None else plain_max
+    plain_seconds = args.plain_seconds if plain_seconds is None else plain_seconds
     lay = None
     r = wroute.Router(device=local, mem_budget_bytes=args.budget_gib << 30)
     results = []
     with ClockSampler(local) as clk:
         for rate in rates:
-            n = int(min(args.serve_max_orders, max(1000, rate * args.serve_seconds)))
+            n = int(min(max_orders, max(2000, rate * seconds)))
             lay_r, o, arr = serving_stream(n, rate)
             if lay is None:
                 lay = lay_r
                 r.load_graph(lay.build())
             row = {"rate": rate, "orders": n}
             for mode in ("batched", "plain"):
-                m = n if mode == "batched" else min(n, args.plain_max_orders)
-                sub = o.subset(np.arange(m))
+                m = n if mode == "batched" else int(min(n, plain_max, max(500, rate * plain_seconds)))
                 sv = r.server(plain=(mode == "plain"), max_batch=args.serve_batch, max_batch_picks=12 * args.serve_batch,
                               n_slots=args.serve_slots, cache_bytes=args.serve_cache_gib << 30)
+                lat, epochs, t_end = [], [], 0.0
+                cost = np.empty(m, np.int32)
+                status = np.empty(m, np.int32)
                 try:
-                    # warm-up on a short prefix (kernels, cache), then the measured run on a fresh server state
-                    sv.run(arr[:200] - arr[0], sub.offs[:201], sub.picks[:sub.offs[200]])
-                    cost, perm, status, done = sv.run(arr[:m], sub.offs, sub.picks)
-                    st = sv.stats()
+                    # warm-up on a short prefix (kernels, cache)
+                    w = min(200, m)
+                    sv.run(arr[:w] - arr[0], o.offs[:w + 1], o.picks[:o.offs[w]])
+                    for lo in range(0, m, EPOCH):
+                        hi = min(m, lo + EPOCH)
+                        sub = o.subset(np.arange(lo, hi))
+                        a = arr[lo:hi] - arr[lo]
+                        c, _, s_, done = sv.run(a, sub.offs, sub.picks)
+                        st = sv.stats()
+                        cost[lo:hi], status[lo:hi] = c, s_
+                        lat.append((done - a) * 1e3)
+                        t_end += max(float(done.max()), float(a[-1]))
+                        looked_up = st["cache_hits"] + st["rows_computed"]
+                        epochs.append({"epoch": lo // EPOCH, "orders": hi - lo, "batches": st["batches"],
+                                       "cache_hit_rate": st["cache_hits"] / looked_up if looked_up else None,
+                                       "rows_computed": st["rows_computed"], "evicted_groups": st["evicted_groups"]})
                 finally:
                     sv.close()
-                lat = (done - arr[:m]) * 1e3
+                lat = np.concatenate(lat)
                 row[mode] = {"orders": m, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                             "orders_per_s": m / max(done.max(), arr[m - 1]), "batches": st["batches"],
-                             "rows_computed": st["rows_computed"], "cache_hits": st["cache_hits"],
-                             "evicted_groups": st["evicted_groups"]}
+                             "orders_per_s": m / t_end, "epochs": len(epochs), "relocations": (m - 1) // EPOCH,
+                             "batches": sum(e["batches"] for e in epochs)}
                 if mode == "batched":
-                    ok_ref = r.route_orders(sub.offs[:2001], sub.picks[:sub.offs[2000]]) if m >= 2000 else None
-                    if ok_ref is not None:
-                        row["batched"]["bit_exact_vs_direct_first_2000"] = bool(
-                            (ok_ref[0] == cost[:2000]).all() and (ok_ref[2] == status[:2000]).all())
+                    row[mode]["per_epoch"] = epochs
+                    chk = min(m, 2000)
+                    ref = r.route_orders(o.offs[:chk + 1], o.picks[:o.offs[chk]])
+                    row[mode]["bit_exact_vs_direct_first_%d" % chk] = bool(
+                        (ref[0] == cost[:chk]).all() and (ref[2] == status[:chk]).all())
+                    batched_cost = cost.copy()
+                else:
+                    row[mode]["bit_exact_vs_batched"] = bool((cost[:m] == batched_cost[:m]).all())
+            row["plain"]["keeps_up"] = row["plain"]["orders_per_s"] >= 0.95 * rate
             results.append(row)
+    # batched against plain at equal p99: for each rate plain keeps up with, the highest
+    # arrival rate the batched server kept up with at a p99 no higher than plain's there
+    matched = []
+    for row in results:
+        if not row["plain"]["keeps_up"]:
+            continue
+        p99 = row["plain"]["p99_ms"]
+        ok = [x["rate"] for x in results if x["batched"]["p99_ms"] <= p99 and x["batched"]["orders_per_s"] >= 0.95 * x["rate"]]
+        matched.append({"plain_rate": row["rate"], "plain_p99_ms": p99, "plain_orders_per_s": row["plain"]["orders_per_s"],
+                        "batched_max_rate_at_that_p99": max(ok) if ok else None})
     top = results[-1]["batched"]
     line = {
         "metric": "served orders/s (p50/p99 latency)", "value": top["orders_per_s"], "unit": "orders/s",
@@ -631,27 +687,36 @@ def run_serving(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": "serving: 200 aisles x 200 slots x 2 sides, 4 cross-aisles (V=80801); Poisson arrivals; "
                                "k=2+Geom(0.3)<=12; Zipf(1.1) over 50k SKUs, top 5% relocated every 1e5 orders",
-                   "rates": rates, "max_batch": args.serve_batch, "slots": args.serve_slots,
-                   "row_cache_gib": args.serve_cache_gib, "tuning": r.tuning()},
+                   "rates": rates, "orders_per_rate": [x["orders"] for x in results], "max_batch": args.serve_batch,
+                   "slots": args.serve_slots, "row_cache_gib": args.serve_cache_gib, "tuning": r.tuning()},
         "serving": results,
+        "batched_vs_plain_at_equal_p99": matched,
         "e2e": {"value": top["orders_per_s"], "unit": "orders/s", "h2d_bytes_per_step": None,
                 "d2h_bytes_per_step": None, "note": "host arrays in and out of every batch: the serving loop is end to end"},
         "clocks": clk.summary(),
     }
-    if rank == 0:
-        print(json.dumps(line))
+    if rank == 0 and not args.no_cpu:
+        _, o, _ = serving_stream(2000, rates[0])
+        v, cores, sample = cpu_oracle_rate(lay.build(), o, budget_s=args.ref_budget)
+        line["cpu_baseline"] = {"value": v, "unit": "orders/s", "cores": cores, "kind": "oracle", "sample": sample}
     r.close()
-    return 0
+    return line if rank == 0 else None
 
 
-def run_ours(args):
+def measure_medium(args):
+    """The default workload: one wr_route_orders call over the medium batch per step.
+    Returns the line (rank 0) or None."""
     import torch
 
     from paper_2504_20655_gb300 import wroute
+    from paper_2504_20655_gb300 import shard
     world, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    g, o, desc = workload(args.workload)
+    # weak scaling: every rank routes its own contiguous slice of 1024 orders of one
+    # stream of world x 1024 orders, with no exchange on the data path
+    g, o_all, desc = workload(args.workload, n_orders=1024 * world)
+    o, o_lo, o_hi = shard.shard_orders(o_all, world, rank)
     r = wroute.Router(device=local, mem_budget_bytes=args.budget_gib << 30)
     if args.tune:
         r.set_tuning(**json.loads(args.tune))
@@ -692,6 +757,9 @@ def run_ours(args):
     ms = sum(times) / len(times)
     ms = max_over_ranks(ms, world, dev)
     value = replica_value(n, ms, world)
+    if world > 1:  # the slices' results in batch order (after the timed region)
+        g_cost, _, _ = shard.gather_order_results(cost, perm[:np_], status, world, rank)
+        gathered = int(g_cost.shape[0])
 
     # end to end through the C ABI with pinned host buffers
     h_offs = torch.from_numpy(o.offs).pin_memory()
@@ -726,7 +794,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
         "config": {"workload": desc, "orders_per_step": n, "sources": st["n_sources"], "l2": "flushed (512 MiB write) between steps",
-                   "parallelism": f"replicas x{world} (orders are independent)", "tuning": r.tuning()},
+                   "parallelism": (f"orders split x{world} (contiguous slices of {1024 * world} orders, gathered after "
+                                   f"timing: {gathered})" if world > 1 else "one GPU (orders are independent)"),
+                   "tuning": r.tuning()},
         "roofline": {"kernel": sweep_kernel_name(r.tuning()), "bound": "hbm", "achieved": achieved,
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
                      "peak_source": pk["source"], "bytes_alg_per_launch": bytes_alg, "ms_per_launch": bf_ms,
@@ -746,10 +816,8 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu:
         v, cores, sample = cpu_oracle_rate(g, o, budget_s=args.ref_budget)
         line["cpu_baseline"] = {"value": v, "unit": "orders/s", "cores": cores, "kind": "oracle", "sample": sample}
-    if rank == 0:
-        print(json.dumps(line))
     r.close()
-    return 0
+    return line if rank == 0 else None
 
 
 def hk_transitions(k):
@@ -956,6 +1024,9 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving: seconds of arrivals per rate")
     ap.add_argument("--serve-max-orders", type=int, default=100_000)
     ap.add_argument("--plain-max-orders", type=int, default=3000)
+    ap.add_argument("--plain-seconds", type=float, default=1.5, help="serving: seconds of arrivals for the plain mode")
+    ap.add_argument("--only", action="store_true",
+                    help="default workload: the medium line alone, without the scale, batching and serving parts")
     ap.add_argument("--serve-batch", type=int, default=256)
     ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--serve-cache-gib", type=int, default=8)
@@ -964,15 +1035,26 @@ def main():
         return run_reference(args)
     from paper_2504_20655_gb300 import build
     build.build()
-    if args.workload == "scale":
-        return run_scale(args)
-    if args.workload == "batching":
-        return run_batching(args)
-    if args.workload == "serving":
-        return run_serving(args)
+    measure = {"scale": measure_scale, "batching": measure_batching, "serving": measure_serving}.get(args.workload)
     if args.workload in ("heldkarp", "open", "clustered", "nodes"):
         return run_next(args)
-    return run_ours(args)
+    if measure is not None:
+        line = measure(args)
+    else:
+        line = measure_medium(args)
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        if line is not None and world == 1 and not args.only and args.workload == "medium":
+            # the rest of the headline metric from the same run: BF Gedges/s at scale against
+            # HBM, the batching plan against plain per-order calls, served p50/p99 against plain
+            line["workloads"] = {
+                "scale": measure_scale(args),
+                "batching": measure_batching(args),
+                "serving": measure_serving(args, rates=[1000, 2000, 5000, 10000, 20000, 50000], seconds=1.0,
+                                           max_orders=50_000, plain_max=1500, plain_seconds=0.75),
+            }
+    if line is not None:
+        print(json.dumps(line))
+    return 0
 
 
 if __name__ == "__main__":

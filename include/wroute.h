@@ -112,11 +112,15 @@ typedef struct {
     int64_t sweeps;           /* Bellman-Ford sweeps, summed over segments */
     int64_t tile_visits;      /* (run, 32-source group) tiles processed, summed over sweeps */
     int64_t node_visits;      /* node x 32-lane group visits */
-    int64_t bytes_alg;        /* algorithmic bytes of the sweeps: per visited node 8*32 (own
-                                 lanes read + written) + 8*indeg + 8 */
+    int64_t bytes_alg;        /* algorithmic bytes of the sweeps: per sweep, 8*32 per visited
+                                 (node, 32-source group) (own lanes read + written), plus
+                                 8*indeg + 8 (arcs, row pointer) once per node visited in any group */
     int64_t sequences;        /* pick sequences evaluated */
     int64_t kernel_launches;  /* kernels launched by the call */
     float ms_select, ms_init, ms_bf, ms_gather, ms_enum, ms_finish, ms_total;
+    int64_t bytes_reread;     /* descriptor bytes read again for a node's further groups within a
+                                 sweep (overhead, not in bytes_alg; the worklist tiling counts
+                                 every visit's descriptors in bytes_alg and leaves this 0) */
 } wr_stats;
 
 /* Create a context on cfg->device (NULL cfg = defaults: device 0, 2 GiB budget, max_k 12). */
@@ -186,14 +190,17 @@ int wr_tour_eval(wr_ctx* ctx, int32_t n_orders, const int32_t* k, const int32_t*
  * by another allocator (a framework's caching allocator, a fixed arena) that must
  * not be grown or fragmented behind its back, or a latency-critical loop that
  * cannot take the device-wide synchronisation cudaMalloc/cudaFree may imply.
- * Same results as wr_tour_eval (same arguments, no context), computed on the
- * current device.  All pointers must be device-accessible (device memory, or
+ * Same results as wr_tour_eval on a context with the default max_k (orders of
+ * 1..WR_MAX_K picks are evaluated, others are WR_ORDER_BAD), with the same
+ * arguments and no context, computed on the current device.  All pointers must be device-accessible (device memory, or
  * managed/mapped memory); the work is enqueued on cuda_stream.
  * Scratch: a file-scope device array sized for WR_STATIC_MAX_ORDERS orders
  * (about 2.9 MB), held by every device that loads the library until the
  * process exits.  n_orders > WR_STATIC_MAX_ORDERS returns WR_EINVAL.
- * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  Every call shares
+ * Set-up: a call outside any stream capture looks up the array's device address
+ * on the current device, every time, so the address stays right after a
+ * cudaDeviceReset; make the first call on a device, and the first call after a
+ * cudaDeviceReset, before any stream capture.  Every call shares
  * the one array, so calls that overlap on the GPU (other streams, other host
  * threads) race: order them on one stream or synchronise between them. */
 #define WR_STATIC_MAX_ORDERS 4096
@@ -284,6 +291,9 @@ int wr_serve_create(wr_ctx* ctx, const wr_serve_config* cfg, wr_server** out);
 int wr_serve_run(wr_server* sv, int32_t n_orders, const double* arrival_s, const int64_t* offs, const int32_t* picks,
                  int32_t* cost, int32_t* perm, int32_t* status, double* done_s);
 int wr_serve_get_stats(wr_server* sv, wr_serve_stats* out);
+/* While a server runs, its batches overlap on the GPU and share the context's device
+ * counters, so wr_get_stats on that context reports mixed figures then; wr_serve_stats
+ * (host-side counts of the last wr_serve_run) is the server's own record. */
 void wr_serve_destroy(wr_server* sv);
 
 /* Node-level routes (the nodes a route passes; the paper has no API for them).  For each

@@ -159,6 +159,7 @@ int ensure_bf(wr_ctx* c, int32_t seg_lanes, bool with_rows) {
     if (with_rows) RC(ensure(c->rows, rows_bytes));
     const size_t items = static_cast<size_t>(c->dg.n_runs) * static_cast<size_t>(seg_lanes / 32);
     RC(ensure(c->stamp, items * 4));
+    RC(ensure(c->run_stamp, static_cast<size_t>(c->dg.n_runs) * 4));
     RC(ensure(c->list0, items * 4));
     RC(ensure(c->list1, items * 4));
     RC(ensure(c->list2, items * 4));
@@ -173,6 +174,7 @@ int ensure_bf(wr_ctx* c, int32_t seg_lanes, bool with_rows) {
 wr::BfWork bf_work(wr_ctx* c, int32_t seg_lanes) {
     wr::BfWork w;
     w.stamp = c->stamp.as<int32_t>();
+    w.run_stamp = c->run_stamp.as<int32_t>();
     w.list0 = c->list0.as<int32_t>();
     w.list1 = c->list1.as<int32_t>();
     w.list2 = c->list2.as<int32_t>();
@@ -531,7 +533,7 @@ void wr_destroy(wr_ctx* c) {
     if (c->h_offs) cudaFreeHost(c->h_offs);
     if (c->ev_offs) cudaEventDestroy(c->ev_offs);
     DBuf* bufs[] = {&c->g_desc, &c->g_ref, &c->g_w, &c->g_arc2, &c->g_run_ptr, &c->g_run_x, &c->g_halo_ptr, &c->g_halo_nodes, &c->g_rin_ptr,
-                    &c->g_rin_list, &c->g_rout_ptr, &c->g_rout_list, &c->g_wx, &c->g_run_wx, &c->g_run_of, &c->g_meta, &c->g_flags, &c->g_ix, &c->g_xarc, &c->g_cdesc, &c->rows, &c->stamp, &c->list0, &c->list1, &c->list2,
+                    &c->g_rin_list, &c->g_rout_ptr, &c->g_rout_list, &c->g_wx, &c->g_run_wx, &c->g_run_of, &c->g_meta, &c->g_flags, &c->g_ix, &c->g_xarc, &c->g_cdesc, &c->rows, &c->stamp, &c->run_stamp, &c->list0, &c->list1, &c->list2,
                     &c->counts, &c->bar, &c->ring, &c->ring_seq, &c->qctl, &c->err, &c->stats, &c->node_flag, &c->src_index, &c->src_list,
                     &c->n_src, &c->block_sums, &c->offs, &c->picks, &c->order_status, &c->order_flags, &c->D,
                     &c->unit_off, &c->best, &c->unit_ctr, &c->out_cost, &c->out_perm, &c->out_status, &c->kbuf,
@@ -887,6 +889,7 @@ int wr_get_stats(wr_ctx* c, wr_stats* out) {
     st.tile_visits = static_cast<int64_t>(h[1]);
     st.node_visits = static_cast<int64_t>(h[2]);
     st.bytes_alg = static_cast<int64_t>(h[3]);
+    st.bytes_reread = static_cast<int64_t>(h[5]);
     st.sequences = static_cast<int64_t>(h[4]);
     st.kernel_launches = c->launches;
     if (c->n_src.p && st.n_sources == 0 && st.n_orders > 0) {

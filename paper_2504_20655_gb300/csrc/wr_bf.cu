@@ -41,6 +41,7 @@ __global__ void bf_init_kernel(BfParams p) {
     const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t n_items = static_cast<int64_t>(p.g.n_runs) * G;
     for (int64_t i = t0; i < n_items; i += stride) p.w.stamp[i] = 0;
+    for (int64_t i = t0; i < p.g.n_runs; i += stride) p.w.run_stamp[i] = 0;
     if (t0 < 8) p.w.counts[t0] = 0;
     if (p.w.async) {
         for (int64_t i = t0; i < 2 * n_items; i += stride) p.w.ring_seq[i] = static_cast<unsigned long long>(i);
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(32 * NQW, NQW == 8 ? 2 : 5) bf_sweeps_kernel(B
     build_list(p, G, 1, true, p.w.list0, p.w.counts + 0);
     if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) return;
 
-    unsigned long long tiles = 0, nodes = 0, bytes = 0;
+    unsigned long long tiles = 0, nodes = 0, bytes = 0, reread = 0;
     int cur = 0;
     int sweep = 1;
     for (;; ++sweep) {
@@ -432,12 +433,17 @@ __global__ void __launch_bounds__(32 * NQW, NQW == 8 ? 2 : 5) bf_sweeps_kernel(B
             const int item = __ldcg(list + it);
             const int r = item / G;
             const int g = item - r * G;
+            // the run's descriptors count once per sweep, whichever of its groups comes first
+            int first_visit = 0;
+            if (threadIdx.x == 0) first_visit = atomicMax(p.w.run_stamp + r, sweep) < sweep;
             const bool ch = sweep_tile<TILE, NQW>(p, r, g, sm, nodes);
             if (threadIdx.x == 0) {
                 if (ch) p.w.stamp[item] = sweep + 1;
                 ++tiles;
-                bytes += static_cast<unsigned long long>(__ldg(p.g.run_meta_bytes + r)) +
+                const unsigned long long meta = static_cast<unsigned long long>(__ldg(p.g.run_meta_bytes + r));
+                bytes += (first_visit ? meta : 0ull) +
                          256ull * static_cast<unsigned long long>(__ldg(&p.g.run_seg[r].y) + __ldg(&p.g.run_seg[r].w));
+                reread += first_visit ? 0ull : meta;
             }
         }
         if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) break;
@@ -449,6 +455,7 @@ __global__ void __launch_bounds__(32 * NQW, NQW == 8 ? 2 : 5) bf_sweeps_kernel(B
         atomicAdd(p.w.stats + 1, tiles);
         atomicAdd(p.w.stats + 2, nodes);
         atomicAdd(p.w.stats + 3, bytes);
+        atomicAdd(p.w.stats + 5, reread);
     }
     if (gtid == 0) atomicAdd(p.w.stats + 0, static_cast<unsigned long long>(sweep - 1));
 }

@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
     }
     if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) return;
 
-    unsigned long long tiles = 0, nodes = 0, bytes = 0;
+    unsigned long long tiles = 0, nodes = 0, bytes = 0, reread = 0;
     int sweep = 1;
     for (;; ++sweep) {
         const int cur = sweep % 3;
@@ -446,6 +446,11 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
             if (lane == 0) it2 = atomicAdd(claim, 1);
             TileMeta m1{};
             if (it1 < cnt) m1 = load_meta<GPW>(p, list, it1, G);
+            // algorithmic bytes take a run's descriptors once per sweep, whichever of its
+            // groups comes first; the answer is used after the tile, so the atomic's latency
+            // hides behind it
+            int first_visit = 0;
+            if (lane == 0) first_visit = atomicMax(p.w.run_stamp + m.r, sweep) < sweep;
             const bool ch = warp_tile<TILE, GPW>(p, m, t, lane, it1 < cnt ? &m1 : nullptr);
             if (ch) {
                 // the tile itself and the runs it feeds, for the next sweep
@@ -457,8 +462,9 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
             if (lane == 0) {
                 ++tiles;
                 nodes += static_cast<unsigned long long>(m.len) * m.ng;
-                bytes += static_cast<unsigned long long>(__ldg(p.g.run_meta_bytes + m.r)) +
-                         256ull * static_cast<unsigned long long>(m.len) * m.ng;
+                const unsigned long long meta = static_cast<unsigned long long>(__ldg(p.g.run_meta_bytes + m.r));
+                bytes += 256ull * static_cast<unsigned long long>(m.len) * m.ng + (first_visit ? meta : 0ull);
+                reread += first_visit ? 0ull : meta;
             }
             it = it1;
             m = m1;
@@ -470,6 +476,7 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
         atomicAdd(p.w.stats + 1, tiles);
         atomicAdd(p.w.stats + 2, nodes);
         atomicAdd(p.w.stats + 3, bytes);
+        atomicAdd(p.w.stats + 5, reread);
     }
     if (gtid == 0) atomicAdd(p.w.stats + 0, static_cast<unsigned long long>(sweep - 1));
 }

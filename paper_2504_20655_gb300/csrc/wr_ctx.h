@@ -59,7 +59,7 @@ struct wr_ctx {
     wr::BfLaunchInfo bf_info{};
     int enum_blocks = 0;
     // working buffers
-    wrc::DBuf rows, stamp, list0, list1, list2, counts, bar, err, stats, ring, ring_seq, qctl;
+    wrc::DBuf rows, stamp, run_stamp, list0, list1, list2, counts, bar, err, stats, ring, ring_seq, qctl;
     wrc::DBuf node_flag, src_index, src_list, n_src, block_sums;
     wrc::DBuf offs, picks, order_status, order_flags, D, unit_off, best, unit_ctr;
     wrc::DBuf out_cost, out_perm, out_status, kbuf, dgiven, src_in, sub, check;

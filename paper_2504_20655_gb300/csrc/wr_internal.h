@@ -147,6 +147,7 @@ struct BfSegment {
 
 struct BfWork {
     int32_t* stamp;   // n_runs * Gcap
+    int32_t* run_stamp;  // n_runs: the last sweep whose byte count took the run's descriptors
     int32_t* list0;   // n_runs * Gcap
     int32_t* list1;
     int32_t* list2;   // third frontier list (warp sweeps: sweep s reads list s mod 3)
@@ -155,7 +156,7 @@ struct BfWork {
     GridBar* bar;
     int* err;
     unsigned long long max_spins;
-    unsigned long long* stats;  // [0] sweeps [1] tiles [2] node visits [3] bytes
+    unsigned long long* stats;  // [0] sweeps [1] tiles [2] node visits [3] bytes [5] descriptor re-read bytes
     long long* trace;           // optional: per sweep t < trace_cap, [2t] = frontier tiles, [2t+1] = ns
     int trace_cap;
     // asynchronous worklist (bf_tiling 3): stamp holds each item's state

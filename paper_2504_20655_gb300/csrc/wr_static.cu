@@ -38,19 +38,23 @@ std::mutex g_setup_mutex;
 StaticScratch* g_scratch_addr[MAX_DEVICES] = {nullptr};
 int g_enum_blocks[MAX_DEVICES] = {0};
 
-// Once per device, with that device current: the device address of the
-// scratch array (in host code its name is only a host-side stand-in).
-int setup_device(int dev, StaticScratch** out, int* blocks) {
+// With the device current: the device address of the scratch array (in host
+// code its name is only a host-side stand-in).  A call outside stream capture
+// looks the address up again every time, so a context that was torn down and
+// created anew (cudaDeviceReset) never leaves a stale address behind; otherwise
+// the address an earlier call found is used.
+int setup_device(int dev, bool capturing, StaticScratch** out, int* blocks) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    if (!capturing) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr) {
             cudaGetLastError();
             return WR_ECUDA;
         }
-        g_enum_blocks[dev] = wr::tour_enum_blocks(dev);
+        if (!g_enum_blocks[dev]) g_enum_blocks[dev] = wr::tour_enum_blocks(dev);
         g_scratch_addr[dev] = static_cast<StaticScratch*>(p);
     }
+    if (!g_scratch_addr[dev]) return WR_ECUDA;  // first call inside a capture: no address yet
     *out = g_scratch_addr[dev];
     *blocks = g_enum_blocks[dev];
     return WR_OK;
@@ -65,11 +69,13 @@ extern "C" int wr_tour_eval_static(int32_t n_orders, const int32_t* k, const int
     if (!k || !D || !cost || !perm || !status) return WR_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return WR_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return WR_ECUDA;
     StaticScratch* s = nullptr;
     int blocks = 0;
-    const int rc = setup_device(dev, &s, &blocks);
+    const int rc = setup_device(dev, cap != cudaStreamCaptureStatusNone, &s, &blocks);
     if (rc != WR_OK) return rc;
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     wr::TourBufs tb{};
     tb.order_status = s->order_status;
     tb.order_flags = s->order_flags;

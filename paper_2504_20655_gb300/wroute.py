@@ -66,7 +66,7 @@ class wr_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("n_orders", "n_sources", "n_segments", "sweeps", "tile_visits",
                                               "node_visits", "bytes_alg", "sequences", "kernel_launches")] + \
                [(n, ctypes.c_float) for n in ("ms_select", "ms_init", "ms_bf", "ms_gather", "ms_enum", "ms_finish",
-                                              "ms_total")]
+                                              "ms_total")] + [("bytes_reread", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -59,6 +59,33 @@ def test_static_entry_point_matches_context_entry_point():
         r.close()
 
 
+def test_static_entry_point_matches_oracle(orc):
+    """The same entry point against the oracle directly: every order's cost, sequence and
+    status equal the oracle's Held-Karp (lexicographically first optimum, pinned against
+    brute force) over its own matrix, on two calls in a row."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2504_20655_gb300 import build, wroute
+    build.build()
+    for n, kmax, hi, seed in ((300, 10, 60, 21), (120, 12, 5, 22)):
+        k, D = _case(n, kmax, hi, seed)
+        cost = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        perm = torch.full((n * 12,), -7, dtype=torch.int32, device="cuda")
+        status = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        wroute.wr_tour_eval_static(torch.from_numpy(k).cuda(), torch.from_numpy(D).cuda(), cost, perm, status)
+        torch.cuda.synchronize()
+        c, p, s = cost.cpu().numpy(), perm.cpu().numpy().reshape(n, 12), status.cpu().numpy()
+        for i in range(n):
+            kk = int(k[i])
+            if kk < 1 or kk > 12:
+                assert s[i] == 2, i
+                continue
+            st, oc, op = orc.tour(D[i, :kk + 1, :kk + 1], "heldkarp")
+            assert (s[i], c[i]) == (st, oc), i
+            assert p[i, :kk].tolist() == op.tolist(), i
+
+
 def test_static_entry_point_rejects_oversize():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
