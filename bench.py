@@ -575,29 +575,15 @@ def measure_batching(args):
     return line if rank == 0 else None
 
 
-def serving_stream(n, rate, seed=None):
-    """Orders of the serving workload: 200 x 200 x 2-side layout, k = 2 + Geometric(0.3)
-    failures (<= 12), Zipf(1.1) picks over 50,000 SKUs whose top 5% move to new slots every
-    100,000 orders; Poisson arrivals at `rate` orders/s."""
-    from paper_2504_20655_gb300 import synth
-    seed = synth.SEED_BASE if seed is None else seed
-    lay = synth.serve_layout(seed)
-    smap = synth.sku_slot_map(50_000, lay.n_slots, seed)
-    k = synth.geometric_k(n, 0.3, 2, 12, seed)
-    parts, epoch = [], 0
-    for lo in range(0, n, 100_000):
-        hi = min(n, lo + 100_000)
-        if lo > 0:
-            epoch += 1
-            smap = synth.relocate_top(smap, 0.05, lay.n_slots, seed, epoch)
-        parts.append(synth.zipf_orders(hi - lo, k[lo:hi], smap, 1.1, seed + epoch))
-    offs = np.zeros(n + 1, np.int64)
-    offs[1:] = np.cumsum(k)
-    picks = np.concatenate([p.picks for p in parts]).astype(np.int32)
-    return lay, synth.Orders(offs, picks), synth.poisson_arrivals(n, rate, seed)
-
-
 EPOCH = 100_000  # orders between two relocations of the top 5% SKUs
+
+
+def serving_stream(n, rate, seed=None):
+    """Orders of the serving workload (synth.serving_workload): relocation of the top 5%
+    SKUs every EPOCH orders, Poisson arrivals at `rate` orders/s."""
+    from paper_2504_20655_gb300 import synth
+    lay, o, arr, _ = synth.serving_workload(n, rate, synth.SEED_BASE if seed is None else seed, EPOCH)
+    return lay, o, arr
 
 
 def measure_serving(args, rates=None, seconds=None, max_orders=None, plain_max=None, plain_seconds=None):

@@ -428,6 +428,27 @@ def large_order_workload(seed: int = SEED_BASE, n_orders: int = 128, k_lo: int =
     return g, zipf_orders(n_orders, k, smap, 1.1, seed, width=160)
 
 
+def serving_workload(n: int, rate: float, seed: int = SEED_BASE, epoch: int = 100_000):
+    """Orders of the serving workload: 200 x 200 x 2-side layout, k = 2 + Geometric(0.3)
+    failures (<= 12), Zipf(1.1) picks over 50,000 SKUs whose top 5% move to new slots
+    every `epoch` orders (a seeded relocation); Poisson arrivals at `rate` orders/s.
+    Returns (layout, orders, arrival times, relocations in the stream)."""
+    lay = serve_layout(seed)
+    smap = sku_slot_map(50_000, lay.n_slots, seed)
+    k = geometric_k(n, 0.3, 2, 12, seed)
+    parts, e = [], 0
+    for lo in range(0, n, epoch):
+        hi = min(n, lo + epoch)
+        if lo > 0:
+            e += 1
+            smap = relocate_top(smap, 0.05, lay.n_slots, seed, e)
+        parts.append(zipf_orders(hi - lo, k[lo:hi], smap, 1.1, seed + e))
+    offs = np.zeros(n + 1, np.int64)
+    offs[1:] = np.cumsum(k)
+    picks = np.concatenate([p.picks for p in parts]).astype(np.int32) if parts else np.zeros(0, np.int32)
+    return lay, Orders(offs, picks), poisson_arrivals(n, rate, seed), e
+
+
 def scale_workload(seed: int = SEED_BASE, n_src: int = 4096):
     lay = scale_layout(seed)
     g = lay.build()

@@ -474,9 +474,12 @@ def _serve_orders(n, seed=2504, rate=20000.0):
 
 
 def test_serve_mix_equals_alone(router, orc):
-    """Serving loop with a small row cache (evictions happen): every order's result is
-    the same in the mix as alone, bad orders are reported, completion follows arrival."""
-    g, o, arr = _serve_orders(3000)
+    """Serving loop with a small row cache (evictions happen) over a stream whose top 5%
+    SKUs move to new slots twice inside the run (every 1000 orders): every order's result
+    is the same in the mix as alone, bad orders are reported, completion follows arrival."""
+    lay, o, arr, relocations = synth.serving_workload(3000, 20000.0, 2504, epoch=1000)
+    assert relocations == 2
+    g = lay.build()
     # two bad orders: a node out of range, an empty order
     picks = o.picks.copy()
     picks[o.offs[7]] = g.V + 5

@@ -75,3 +75,16 @@ def test_zipf_head():
 def test_distinct_sources():
     s = synth.distinct_sources(4096, 1_000_000, 1)
     assert len(np.unique(s)) == 4096 and s.max() < 1_000_000
+
+
+def test_serving_stream_relocates_every_epoch():
+    """The serving stream moves the top 5% SKUs every `epoch` orders: the number of
+    relocations, and the popular picks land on other slots after a relocation."""
+    lay, o, arr, rel = synth.serving_workload(2500, 5000.0, 2504, epoch=1000)
+    assert rel == 2 and o.n == 2500 and (np.diff(arr) > 0).all()
+    smap0 = synth.sku_slot_map(50_000, lay.n_slots, 2504)
+    smap1 = synth.relocate_top(smap0, 0.05, lay.n_slots, 2504, 1)
+    assert (smap1[:2500] != smap0[:2500]).mean() > 0.99 and (smap1[2500:] == smap0[2500:]).all()
+    first = o.picks[:o.offs[1000]]
+    later = o.picks[o.offs[1000]:o.offs[2000]]
+    assert np.isin(smap0[0], first) and np.isin(smap1[0], later)
