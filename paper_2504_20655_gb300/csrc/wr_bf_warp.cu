@@ -431,11 +431,14 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
         const int32_t* list = frontier_list(p, sweep);
         int* claim = p.w.counts + 3 + cur;
         // dynamic tile scheduling, per warp: the item two ahead is claimed and
-        // the next item's run metadata loaded while the current tile is relaxed
+        // the next item's run metadata loaded while the current tile is relaxed.
+        // A sweep with no more items than warps claims one item per warp instead,
+        // so that no warp relaxes two tiles one after the other while others idle
+        const bool ahead = cnt > static_cast<int>(gridDim.x) * NW;
         int it = 0, it1 = 0;
         if (lane == 0) {
             it = atomicAdd(claim, 1);
-            it1 = atomicAdd(claim, 1);
+            it1 = ahead ? atomicAdd(claim, 1) : cnt;
         }
         it = __shfl_sync(FULL_MASK, it, 0);
         it1 = __shfl_sync(FULL_MASK, it1, 0);
@@ -443,7 +446,7 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
         if (it < cnt) m = load_meta<GPW>(p, list, it, G);
         while (it < cnt) {
             int it2 = 0;
-            if (lane == 0) it2 = atomicAdd(claim, 1);
+            if (lane == 0) it2 = ahead ? atomicAdd(claim, 1) : cnt;
             TileMeta m1{};
             if (it1 < cnt) m1 = load_meta<GPW>(p, list, it1, G);
             // algorithmic bytes take a run's descriptors once per sweep, whichever of its

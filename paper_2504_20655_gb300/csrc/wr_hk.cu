@@ -43,7 +43,8 @@ __global__ void hk_select_kernel(int32_t n, TourBufs t, int32_t max_k, int32_t* 
     if (t.order_status[o] == WR_ORDER_OK && k > WR_MAX_K && k <= max_k) list[atomicAdd(count, 1)] = o;
 }
 
-// D of the listed orders, (k+1) x (k+1) at stride HK_DSTRIDE, from one source segment's rows.
+// D of the listed orders, (k+1) x (k+1) at stride HK_DSTRIDE (column j at HK_DOFF + j), from one
+// source segment's rows.
 __global__ void hk_gather_kernel(const int32_t* __restrict__ list, const int32_t* __restrict__ count, TourBufs t,
                                  int32_t depot, const int32_t* __restrict__ src_index, BfSegment seg, uint32_t* D21,
                                  int open_path) {
@@ -58,7 +59,7 @@ __global__ void hk_gather_kernel(const int32_t* __restrict__ list, const int32_t
     for (int e = lane; e < m * m; e += 32) {
         const int i = e / m, j = e - i * m;
         if (open_path && (i == 0 || j == 0)) {  // open path: free entrance/exit legs
-            D21[static_cast<int64_t>(q) * HK_DBLOCK + i * HK_DSTRIDE + j] = 0u;
+            D21[static_cast<int64_t>(q) * HK_DBLOCK + i * HK_DSTRIDE + HK_DOFF + j] = 0u;
             continue;
         }
         const int32_t pi = i == 0 ? depot : t.picks[b + i - 1];
@@ -67,9 +68,15 @@ __global__ void hk_gather_kernel(const int32_t* __restrict__ list, const int32_t
         const int32_t pj = j == 0 ? depot : t.picks[b + j - 1];
         const uint32_t val = __ldcg(seg.rows + static_cast<int64_t>(pj) * seg.ld + si);
         if (val != INF_U && val > static_cast<uint32_t>(WR_LEG_MAX) && i != j) range = true;
-        D21[static_cast<int64_t>(q) * HK_DBLOCK + i * HK_DSTRIDE + j] = val;
+        D21[static_cast<int64_t>(q) * HK_DBLOCK + i * HK_DSTRIDE + HK_DOFF + j] = val;
     }
     if (__any_sync(FULL_MASK, range) && lane == 0) atomicOr(t.order_flags + o, ORDER_FLAG_RANGE);
+    // the rest of the block is unreachable: the solve's transitions then run over every
+    // pick slot with no test (a leg of WR_INF plus any table value never wins a minimum)
+    for (int e = lane; e < HK_DBLOCK; e += 32) {
+        const int i = e / HK_DSTRIDE, j = e - i * HK_DSTRIDE - HK_DOFF;
+        if (i >= m || j < 0 || j >= m) D21[static_cast<int64_t>(q) * HK_DBLOCK + e] = INF_U;
+    }
 }
 
 __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) { return min(a + b, INF_U); }
@@ -235,17 +242,26 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
                 int t = 0;
                 for (unsigned cm = s; cm; cm &= cm - 1, ++t) {
                     const int c = __ffs(cm) - 1;
-                    const uint32_t* Dr = D + (c + 1) * HK_DSTRIDE;
+                    const uint32_t* Dr = D + (c + 1) * HK_DSTRIDE + HK_DOFF;
                     uint32_t best;
                     if (s == full) {
                         best = __ldg(Dr);
                     } else {
                         // D and h are at most INF_U = 2^31 - 1, so D + h does not wrap, and a minimum
-                        // started at INF_U stays at most INF_U: one fused add-min per transition
+                        // started at INF_U stays at most INF_U: one fused add-min per transition.
+                        // hv[j] is INF_U for the picks j in S and past k, and the legs past k are
+                        // INF_U, so their terms never win and need no test
+                        // the row's pick legs D[c][1..HK_MAX_K] as 16-byte loads
+                        const uint4* D4 = reinterpret_cast<const uint4*>(Dr + 1);
                         best = INF_U;
 #pragma unroll
-                        for (int j = 0; j < HK_MAX_K; ++j)
-                            if (j < k && !((s >> j) & 1u)) best = __viaddmin_u32(__ldg(Dr + j + 1), it.hv[j], best);
+                        for (int j4 = 0; j4 < HK_MAX_K / 4; ++j4) {
+                            const uint4 d = __ldg(D4 + j4);
+                            best = __viaddmin_u32(d.x, it.hv[4 * j4], best);
+                            best = __viaddmin_u32(d.y, it.hv[4 * j4 + 1], best);
+                            best = __viaddmin_u32(d.z, it.hv[4 * j4 + 2], best);
+                            best = __viaddmin_u32(d.w, it.hv[4 * j4 + 3], best);
+                        }
                     }
                     const uint32_t cc = bn(binom, c - 1, t);
                     __stcg(hq + c * half + lo + (pa + it.pc_tot - pc - cc), best);
@@ -291,7 +307,7 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
                     }
                     return __ldcg(hq + j * half + loff[k][__popc(set)] + r);
                 };
-                uint32_t best = lane < k ? sat_add(__ldg(D + lane + 1), h_at(0u, lane)) : INF_U;
+                uint32_t best = lane < k ? sat_add(__ldg(D + HK_DOFF + lane + 1), h_at(0u, lane)) : INF_U;
 #pragma unroll
                 for (int d = 16; d >= 1; d >>= 1) best = min(best, __shfl_xor_sync(FULL_MASK, best, d));
                 int32_t* pp = p.perm + b;
@@ -312,7 +328,7 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
                     bool hit = false;
                     if (lane < k && !((s >> lane) & 1u)) {
                         r = h_at(s, lane);
-                        hit = sat_add(__ldg(D + cur * HK_DSTRIDE + lane + 1), r) == rem;
+                        hit = sat_add(__ldg(D + cur * HK_DSTRIDE + HK_DOFF + lane + 1), r) == rem;
                     }
                     const unsigned m = __ballot_sync(FULL_MASK, hit);
                     if (m == 0u) {  // cannot happen on a consistent table
@@ -351,11 +367,13 @@ cudaError_t hk_launch_gather(int32_t n, const int32_t* list, const int32_t* coun
     return cudaGetLastError();
 }
 
+constexpr int HK_BLOCKS_PER_SM = 3;  // measured best: more blocks per SM share L1 among more orders' D rows
+
 int hk_blocks(int device) {
     int occ = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hk_solve_kernel, 256, 0) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    return occ * sms;
+    return (occ < HK_BLOCKS_PER_SM ? occ : HK_BLOCKS_PER_SM) * sms;
 }
 
 cudaError_t hk_launch_solve(const int32_t* list, const int32_t* count, const uint32_t* D21, uint32_t* h,

@@ -19,8 +19,13 @@ constexpr int DBLOCK = DSTRIDE * DSTRIDE;
 constexpr int TAIL = 5;                       // tail walked by one compile-time unrolled walk
 constexpr int UNIT_TAIL = 6;                  // the 720 orderings of six picks are walked from register tables
 constexpr int HK_MAX_K = 20;                  // orders of WR_MAX_K+1 .. 20 picks: Held-Karp
-constexpr int HK_DSTRIDE = HK_MAX_K + 1;
-constexpr int HK_DBLOCK = HK_DSTRIDE * HK_DSTRIDE;
+// Held-Karp D blocks: entry (i, j), i, j in 0..HK_MAX_K, at i * HK_DSTRIDE + HK_DOFF + j, so
+// that the pick legs of a row (j = 1..HK_MAX_K) start on a 16-byte boundary
+constexpr int HK_DSTRIDE = 24;
+constexpr int HK_DOFF = 3;
+constexpr int HK_DBLOCK = (HK_MAX_K + 1) * HK_DSTRIDE;
+static_assert(HK_MAX_K % 4 == 0 && (HK_DOFF + 1) % 4 == 0 && HK_DSTRIDE % 4 == 0 && HK_DOFF + HK_MAX_K < HK_DSTRIDE,
+              "Held-Karp D rows: pick legs on 16-byte boundaries, inside the row");
 constexpr int ORDER_FLAG_RANGE = 1;
 constexpr int32_t RUN_SIMPLE = 1;             // run's extra arcs fit the tile buffer, halo fully staged
 constexpr uint32_t IX_EXTRA = 1u << 24;       // node has arcs beyond the inline ones
