@@ -34,7 +34,7 @@ template <int TILE, int GPW = 1>
 struct __align__(128) WarpTile {
     uint32_t rows[TILE][32 * GPW];  // slot-major: rows[i][32 g + b] = source b of group g at tile slot i
     uint4 desc[2 * TILE];           // compact descriptors of the run's nodes: forward, backward
-    uint2 wx[2 * TILE];             // the run's extra arcs: forward, then backward
+    uint2 wx[wx_cap(TILE)];         // the run's extra arcs: forward, then backward
 };
 
 constexpr int BLK = 4;  // nodes per pipelined block
@@ -758,13 +758,13 @@ static int prepare_warp_one(int device, BfLaunchInfo* info) {
 }
 
 // Warps per CTA: as many warp tiles as fit 227 KB of shared memory: 128-slot
-// tiles of one source group (10 warps) or two (5 warps), 256-slot tiles of one (5).
+// tiles of one source group (11 warps of 20.5 KB) or two (6 warps), 256-slot tiles of one (5).
 int bf_prepare_warp(int tile_cap, int mode, int device, BfLaunchInfo* info) {
     switch (tile_cap) {
         case 128:
-            if (mode == WARP_ASYNC) return prepare_warp_one<128, 10, true>(device, info);
-            if (mode == WARP_PAIRS) return prepare_warp_one<128, 5, false, 2>(device, info);
-            return prepare_warp_one<128, 10, false>(device, info);
+            if (mode == WARP_ASYNC) return prepare_warp_one<128, 11, true>(device, info);
+            if (mode == WARP_PAIRS) return prepare_warp_one<128, 6, false, 2>(device, info);
+            return prepare_warp_one<128, 11, false>(device, info);
         case 256:
             if (mode == WARP_ASYNC) return prepare_warp_one<256, 5, true>(device, info);
             if (mode == WARP_PAIRS) return WR_EINVAL;

@@ -404,8 +404,8 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
                 compact = false;
             }
         }
-        // warp tiling extras: at most 2 x tile_cap entries fit the warp's shared memory
-        if (wxf.size() + wxb.size() > 2 * static_cast<size_t>(tile_cap)) compact = false;
+        // warp tiling extras: at most wx_cap(tile_cap) entries fit the warp's shared memory
+        if (wxf.size() + wxb.size() > static_cast<size_t>(wx_cap(tile_cap))) compact = false;
         p.run_wx.push_back(compact ? make_int4(static_cast<int>(p.wx.size()), static_cast<int>(wxf.size()),
                                                static_cast<int>(wxb.size()), 0)
                                    : make_int4(static_cast<int>(p.wx.size()), 0, 0, 0));

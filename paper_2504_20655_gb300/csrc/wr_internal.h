@@ -30,6 +30,9 @@ constexpr int ORDER_FLAG_RANGE = 1;
 constexpr int32_t RUN_SIMPLE = 1;             // run's extra arcs fit the tile buffer, halo fully staged
 constexpr uint32_t IX_EXTRA = 1u << 24;       // node has arcs beyond the inline ones
 constexpr int32_t RUN_COMPACT = 2;            // every node's arcs are staged: compact descriptors + extras (warp tiling)
+// extra arcs a compact run may have (they are staged with the tile): tile_cap / 2 entries, so
+// that a 128-slot warp tile takes 20.5 KB of shared memory and 11 of them fit one SM
+__host__ __device__ constexpr int wx_cap(int tile_cap) { return tile_cap / 2; }
 
 // --------------------------------------------------------------------------
 // graph preprocessing (host, wr_graph.cpp)

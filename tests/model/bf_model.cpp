@@ -90,7 +90,7 @@ static int relax_item_warp(const HostPartition& p, std::vector<uint32_t>& rows, 
     if (len + hn > tile_cap) return 98;
     const bool compact = (p.run_flags[r] & RUN_COMPACT) != 0;
     const int4 rx = p.run_wx[r];
-    if (compact && rx.y + rx.z > 2 * tile_cap) return 97;
+    if (compact && rx.y + rx.z > wx_cap(tile_cap)) return 97;
     bool changed = false;
     for (int lane = 0; lane < 32; ++lane) {
         const size_t c = static_cast<size_t>(gg) * 32 + lane;
@@ -468,7 +468,7 @@ extern "C" int bfm_check_partition(int V, long long E, const long long* rp, cons
         // hold the same arcs
         if (p.run_flags[r] & RUN_COMPACT) {
             const int4 rx = p.run_wx[r];
-            if (rx.x & 1 || rx.y + rx.z > 2 * tile_cap || rx.x + rx.y + rx.z > static_cast<int>(p.wx.size())) return 20;
+            if (rx.x & 1 || rx.y + rx.z > wx_cap(tile_cap) || rx.x + rx.y + rx.z > static_cast<int>(p.wx.size())) return 20;
             std::vector<std::vector<std::pair<uint32_t, uint32_t>>> xf(static_cast<size_t>(len)), xb(static_cast<size_t>(len));
             for (int e = 0; e < rx.y + rx.z; ++e) {
                 const uint2 x = p.wx[static_cast<size_t>(rx.x + e)];
