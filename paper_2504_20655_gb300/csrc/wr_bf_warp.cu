@@ -42,6 +42,9 @@ constexpr int BLK = 4;  // nodes per pipelined block
 // Run metadata of one work item (the same in every lane).
 struct TileMeta {
     int item, r, g, len, h0, hn, flags;
+    int hid;    // this lane's halo node (lane < hn), loaded with the metadata when hn <= 32
+    bool hids;  // hid holds the halo
+    int q0, nq, rq;  // the runs fed: rout_list[q0 .. q0 + nq); rq = this lane's (lane < nq <= 32)
     int ng;   // source groups of the item (GPW, or fewer for the last item of a run)
     int4 rs;  // {a0, alen, b0, blen}
     int4 rx;  // extras {first entry, forward count, backward count, 0}
@@ -49,7 +52,7 @@ struct TileMeta {
 
 // Item = run x items_per_run + j, its groups GPW j .. GPW j + GPW - 1 (those below G).
 template <int GPW>
-__device__ __forceinline__ TileMeta load_meta(const BfParams& p, const int32_t* list, int it, int G) {
+__device__ __forceinline__ TileMeta load_meta(const BfParams& p, const int32_t* list, int it, int G, int lane) {
     const int ipr = (G + GPW - 1) / GPW;
     TileMeta m;
     m.item = __ldcg(list + it);
@@ -62,6 +65,13 @@ __device__ __forceinline__ TileMeta load_meta(const BfParams& p, const int32_t* 
     m.hn = __ldg(p.g.halo_ptr + m.r + 1) - m.h0;
     m.flags = __ldg(p.g.run_flags + m.r);
     m.rx = __ldg(p.g.run_wx + m.r);
+    // the halo's node ids, one per lane, so that staging needs no dependent load for them
+    m.hids = m.hn <= 32;
+    m.hid = (m.hids && lane < m.hn) ? __ldg(p.g.halo_nodes + m.h0 + lane) : 0;
+    // the runs it feeds, for the frontier pushes after the tile
+    m.q0 = __ldg(p.g.rout_ptr + m.r);
+    m.nq = __ldg(p.g.rout_ptr + m.r + 1) - m.q0;
+    m.rq = lane < m.nq ? __ldg(p.g.rout_list + m.q0 + lane) : 0;
     return m;
 }
 
@@ -277,11 +287,20 @@ __device__ __forceinline__ bool warp_tile(const BfParams& p, const TileMeta& m, 
             cp_async16(&t.desc[e], p.g.cdesc + 2 * static_cast<int64_t>(run_node(m.rs, e >> 1)) + (e & 1));
         for (int e = lane; 2 * e < nx; e += 32) cp_async16(&t.wx[2 * e], p.g.wx + m.rx.x + 2 * e);
     }
-    if (act) {
+    if (m.hids) {
+        for (int hb = 0; hb < m.hn; hb += SPI) {  // the same trip count in every lane
+            const int h = hb + sub;
+            const int node = __shfl_sync(FULL_MASK, m.hid, h & 31);
+            if (act && h < m.hn)
+                cp_async16(&t.rows[m.len + h][cpart], rows + static_cast<int64_t>(node) * ld + col0 + part);
+        }
+    } else if (act) {
         for (int h = sub; h < m.hn; h += SPI) {
             const int node = __ldg(p.g.halo_nodes + m.h0 + h);
             cp_async16(&t.rows[m.len + h][cpart], rows + static_cast<int64_t>(node) * ld + col0 + part);
         }
+    }
+    if (act) {
         const uint32_t* gp = rows + static_cast<int64_t>(m.rs.x + sub) * ld + col0 + part;
         for (int i = sub; i < m.rs.y; i += SPI, gp += SPI * ld) cp_async16(&t.rows[i][cpart], gp);
     }
@@ -443,12 +462,12 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
         it = __shfl_sync(FULL_MASK, it, 0);
         it1 = __shfl_sync(FULL_MASK, it1, 0);
         TileMeta m{};
-        if (it < cnt) m = load_meta<GPW>(p, list, it, G);
+        if (it < cnt) m = load_meta<GPW>(p, list, it, G, lane);
         while (it < cnt) {
             int it2 = 0;
             if (lane == 0) it2 = ahead ? atomicAdd(claim, 1) : cnt;
             TileMeta m1{};
-            if (it1 < cnt) m1 = load_meta<GPW>(p, list, it1, G);
+            if (it1 < cnt) m1 = load_meta<GPW>(p, list, it1, G, lane);
             // algorithmic bytes take a run's descriptors once per sweep, whichever of its
             // groups comes first; the answer is used after the tile, so the atomic's latency
             // hides behind it
@@ -456,11 +475,16 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
             if (lane == 0) first_visit = atomicMax(p.w.run_stamp + m.r, sweep) < sweep;
             const bool ch = warp_tile<TILE, GPW>(p, m, t, lane, it1 < cnt ? &m1 : nullptr);
             if (ch) {
-                // the tile itself and the runs it feeds, for the next sweep
-                const int q0 = __ldg(p.g.rout_ptr + m.r), nq = __ldg(p.g.rout_ptr + m.r + 1) - q0;
+                // the tile itself and the runs it feeds, for the next sweep; up to 31 fed runs
+                // come from the registers loaded with the metadata
+                const int q0 = m.q0, nq = m.nq;
                 const int item = m.item, g = m.g / GPW;
-                frontier_push_warp(p, nq + 1, sweep + 1, lane,
-                                   [&](int j) { return j == 0 ? item : __ldg(p.g.rout_list + q0 + j - 1) * ipr + g; });
+                const int fed = __shfl_sync(FULL_MASK, m.rq, (lane + 31) & 31) * ipr + g;  // lane j: fed run j - 1
+                if (nq < 32)
+                    frontier_push_warp(p, nq + 1, sweep + 1, lane, [&](int j) { return j == 0 ? item : fed; });
+                else
+                    frontier_push_warp(p, nq + 1, sweep + 1, lane,
+                                       [&](int j) { return j == 0 ? item : __ldg(p.g.rout_list + q0 + j - 1) * ipr + g; });
             }
             if (lane == 0) {
                 ++tiles;
@@ -714,6 +738,8 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_async_kernel(BfParams p) {
         m.hn = __ldg(p.g.halo_ptr + m.r + 1) - m.h0;
         m.flags = __ldg(p.g.run_flags + m.r);
         m.rx = __ldg(p.g.run_wx + m.r);
+        m.hids = false;  // the halo's node ids are read while staging
+        m.hid = 0;
         const bool ch = warp_tile<TILE, 1>(p, m, t, lane);
         bool ok = true;
         if (ch) {
