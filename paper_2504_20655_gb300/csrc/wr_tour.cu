@@ -684,9 +684,13 @@ __device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, unsigne
             }
         }
         seqs += static_cast<long long>(uhi - ulo) * 720 * nsub;
-        if (rec.have)
+        if (rec.have) {
+            // when another thread has meanwhile published a cheaper sequence of this order, this
+            // range cannot hold the result: no search, nothing to publish
+            if (static_cast<uint32_t>(__ldcg(out) >> 32) < best_c) return;
             best_r = rec.rank0 + static_cast<unsigned>(first_of_five(Dm, rec.acc, rec.sj, rec.five, best_c, rec.lo,
                                                                      rec.lo + AccSpan<5>::value));
+        }
     }
     const unsigned long long packed = (static_cast<unsigned long long>(best_c) << 32) | best_r;
     if (packed < g0) atomicMin(out, packed);
