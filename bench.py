@@ -155,8 +155,8 @@ def dist_setup(args):
 # it was taken on (hash below) and the tuning is the default one; otherwise null.
 TRAFFIC_SOURCES = ["paper_2504_20655_gb300/csrc/wr_bf_warp.cu", "paper_2504_20655_gb300/csrc/wr_bf_common.cuh",
                    "paper_2504_20655_gb300/csrc/wr_graph.cpp"]
-TRAFFIC_HASH = "5a971170e4d58a29"
-TRAFFIC = {"medium": 746380544 + 454820096, "scale": 18411243000 + 8947309000}
+TRAFFIC_HASH = "166716ae05341449"
+TRAFFIC = {"medium": 738482688 + 452171264, "scale": 18487907000 + 8870082000}
 
 
 def traffic_for(workload, tuned):
