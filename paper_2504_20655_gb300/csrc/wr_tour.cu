@@ -140,9 +140,52 @@ __global__ void __launch_bounds__(SCAN_THREADS) compact_apply_kernel(int32_t V, 
     }
 }
 
+// The same compaction by one block walking the chunks in order with a running
+// carry: one launch instead of three for graphs of up to SINGLE_MAX_CHUNKS chunks.
+constexpr int SINGLE_MAX_CHUNKS = 64;
+
+__global__ void __launch_bounds__(SCAN_THREADS) compact_single_kernel(int32_t V, const uint8_t* __restrict__ flag,
+                                                                        int32_t* src_index, int32_t* src_list,
+                                                                        int32_t* n_src) {
+    __shared__ int ws[32];
+    __shared__ int tot;
+    int carry = 0;
+    for (int64_t chunk = 0; chunk < V; chunk += SCAN_CHUNK) {
+        const int64_t base = chunk + threadIdx.x * SCAN_ITEMS;
+        int f[SCAN_ITEMS];
+        int c = 0;
+#pragma unroll
+        for (int q = 0; q < SCAN_ITEMS; ++q) {
+            f[q] = (base + q < V) ? flag[base + q] : 0;
+            c += f[q];
+        }
+        int pos = carry + block_exclusive_scan(c, ws, &tot);
+#pragma unroll
+        for (int q = 0; q < SCAN_ITEMS; ++q) {
+            if (base + q < V) {
+                const int32_t v = static_cast<int32_t>(base + q);
+                if (f[q]) {
+                    src_index[v] = pos;
+                    src_list[pos] = v;
+                    ++pos;
+                } else {
+                    src_index[v] = -1;
+                }
+            }
+        }
+        carry += tot;  // every thread reads the chunk's total before the next scan overwrites it
+    }
+    if (threadIdx.x == 0) *n_src = carry;
+}
+
 cudaError_t tour_launch_compact(int32_t V, const uint8_t* node_flag, int32_t* src_index, int32_t* src_list,
                                 int32_t* n_src, int32_t* block_sums, cudaStream_t s, int* launches) {
     const int nb = (V + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    if (nb <= SINGLE_MAX_CHUNKS) {
+        compact_single_kernel<<<1, SCAN_THREADS, 0, s>>>(V, node_flag, src_index, src_list, n_src);
+        *launches += 1;
+        return cudaGetLastError();
+    }
     compact_count_kernel<<<nb, SCAN_THREADS, 0, s>>>(V, node_flag, block_sums);
     compact_top_kernel<<<1, SCAN_THREADS, 0, s>>>(nb, block_sums, n_src);
     compact_apply_kernel<<<nb, SCAN_THREADS, 0, s>>>(V, node_flag, block_sums, src_index, src_list);

@@ -821,6 +821,21 @@ def test_load_graph_int32_rule(wr, orc):
         r.close()
 
 
+def test_route_orders_on_scale_layout(wr, orc):
+    """Orders on the scale layout (V = 1,002,001): source selection over a graph larger than one
+    block's compaction (the three-kernel path), against the oracle."""
+    g, _ = synth.scale_workload(n_src=8)
+    o = synth.uniform_slot_orders(6, 4, g.n_slots, 77)
+    r = wr.Router(device=0)
+    try:
+        r.load_graph(g)
+        cost, perm, status = r.route_orders(o.offs, o.picks)
+    finally:
+        r.close()
+    c, p, s = orc.route_orders(g, o, "dijkstra", "brute", NT)
+    assert (status == s).all() and (cost == c).all() and (perm[:len(p)] == p).all()
+
+
 def test_route_clustered_uneven_orders(wr, orc):
     """Clustered routing of orders of 2..12 picks: with one cluster the orders above ten
     stops are WR_ORDER_BAD on both sides, with four clusters every order is routed; the
