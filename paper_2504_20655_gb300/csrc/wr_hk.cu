@@ -367,7 +367,7 @@ cudaError_t hk_launch_gather(int32_t n, const int32_t* list, const int32_t* coun
     return cudaGetLastError();
 }
 
-constexpr int HK_BLOCKS_PER_SM = 3;  // measured best: more blocks per SM share L1 among more orders' D rows
+constexpr int HK_BLOCKS_PER_SM = 4;  // measured: 3.37 ms at 4 blocks per SM (the register limit), 3.53 at 3, 4.44 at 2
 
 int hk_blocks(int device) {
     int occ = 0, sms = 0;
