@@ -163,7 +163,7 @@ int ensure_bf(wr_ctx* c, int32_t seg_lanes, bool with_rows) {
     RC(ensure(c->list0, items * 4));
     RC(ensure(c->list1, items * 4));
     RC(ensure(c->list2, items * 4));
-    RC(ensure(c->counts, 32));
+    RC(ensure(c->counts, 64));
     RC(ensure(c->bar, sizeof(wr::GridBar)));
     RC(ensure(c->ring, 2 * items * 4));
     RC(ensure(c->ring_seq, 2 * items * 8));
@@ -179,6 +179,7 @@ wr::BfWork bf_work(wr_ctx* c, int32_t seg_lanes) {
     w.list1 = c->list1.as<int32_t>();
     w.list2 = c->list2.as<int32_t>();
     w.counts = c->counts.as<int32_t>();
+    w.prio = 0;
     w.gcap = seg_lanes / 32;
     w.bar = c->bar.as<wr::GridBar>();
     w.err = c->err.as<int>();
@@ -196,6 +197,7 @@ wr::BfWork bf_work(wr_ctx* c, int32_t seg_lanes) {
 // One Bellman-Ford segment: init + sweeps.
 int run_bf_segment(wr_ctx* c, const wr::BfSegment& seg, cudaStream_t s) {
     wr::BfWork w = bf_work(c, seg.lanes);
+    w.prio = seg.sorted && static_cast<int64_t>(seg.lanes) * 64 >= static_cast<int64_t>(c->dg.V);
     if (w.trace) CK(cudaMemsetAsync(w.trace, 0xFF, static_cast<size_t>(w.trace_cap) * 16, s));
     {
         PhaseTimer t(c, s, 1);
@@ -388,6 +390,7 @@ int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_
         seg.rows = c->rows.as<uint32_t>();
         seg.ld = seg_lanes;
         seg.src = c->src_list.as<int32_t>();
+        seg.sorted = true;  // the distinct sources of the orders, in node id order
         seg.n_src_dev = c->n_src.as<int32_t>();
         seg.n_src_host = 0;
         seg.first = sg * seg_lanes;
@@ -1031,6 +1034,7 @@ int wr_route_nodes(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pic
         seg.rows = c->rows.as<uint32_t>();
         seg.ld = seg_lanes;
         seg.src = c->src_list.as<int32_t>();
+        seg.sorted = true;  // the distinct sources of the orders, in node id order
         seg.n_src_dev = c->n_src.as<int32_t>();
         seg.n_src_host = 0;
         seg.first = sg * seg_lanes;

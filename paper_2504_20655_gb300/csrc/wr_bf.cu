@@ -42,7 +42,7 @@ __global__ void bf_init_kernel(BfParams p) {
     const int64_t n_items = static_cast<int64_t>(p.g.n_runs) * G;
     for (int64_t i = t0; i < n_items; i += stride) p.w.stamp[i] = 0;
     for (int64_t i = t0; i < p.g.n_runs; i += stride) p.w.run_stamp[i] = 0;
-    if (t0 < 8) p.w.counts[t0] = 0;
+    if (t0 < 16) p.w.counts[t0] = 0;
     if (p.w.async) {
         for (int64_t i = t0; i < 2 * n_items; i += stride) p.w.ring_seq[i] = static_cast<unsigned long long>(i);
         if (t0 < 4) p.w.qctl[t0] = 0ull;

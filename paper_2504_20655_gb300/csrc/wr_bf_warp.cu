@@ -45,6 +45,7 @@ struct TileMeta {
     int hid;    // this lane's halo node (lane < hn), loaded with the metadata when hn <= 32
     bool hids;  // hid holds the halo
     int q0, nq, rq;  // the runs fed: rout_list[q0 .. q0 + nq); rq = this lane's (lane < nq <= 32)
+    bool rqp;        // run rq is a priority run
     int ng;   // source groups of the item (GPW, or fewer for the last item of a run)
     int4 rs;  // {a0, alen, b0, blen}
     int4 rx;  // extras {first entry, forward count, backward count, 0}
@@ -52,10 +53,10 @@ struct TileMeta {
 
 // Item = run x items_per_run + j, its groups GPW j .. GPW j + GPW - 1 (those below G).
 template <int GPW>
-__device__ __forceinline__ TileMeta load_meta(const BfParams& p, const int32_t* list, int it, int G, int lane) {
+__device__ __forceinline__ TileMeta load_meta(const BfParams& p, int32_t item, int G, int lane) {
     const int ipr = (G + GPW - 1) / GPW;
     TileMeta m;
-    m.item = __ldcg(list + it);
+    m.item = item;
     m.r = m.item / ipr;
     m.g = (m.item - m.r * ipr) * GPW;
     m.ng = min(GPW, G - m.g);
@@ -72,6 +73,7 @@ __device__ __forceinline__ TileMeta load_meta(const BfParams& p, const int32_t* 
     m.q0 = __ldg(p.g.rout_ptr + m.r);
     m.nq = __ldg(p.g.rout_ptr + m.r + 1) - m.q0;
     m.rq = lane < m.nq ? __ldg(p.g.rout_list + m.q0 + lane) : 0;
+    m.rqp = p.w.prio && lane < m.nq && (__ldg(p.g.run_flags + m.rq) & RUN_PRIORITY) != 0;
     return m;
 }
 
@@ -375,30 +377,55 @@ __device__ __forceinline__ int32_t* frontier_list(const BfParams& p, int s) {
     return i == 0 ? p.w.list0 : i == 1 ? p.w.list1 : p.w.list2;
 }
 
+// Items of runs that feed many others (RUN_PRIORITY: the cross-aisle pieces) are
+// listed first: they fill each list from its end (count counts[6 + s % 3]), the
+// others from its start (counts[s % 3]), and claim c takes the c-th priority item
+// while there are any.  So a sweep relaxes the cross-aisle tiles in its first
+// wave, and the aisle tiles claimed after them already read their new values.
+// cap = items of the segment (no list holds an item twice, so the two ends never meet).
+__device__ __forceinline__ int32_t list_item(const int32_t* list, int c, int n_prio, int cap) {
+    return __ldcg(list + (c < n_prio ? cap - 1 - c : c - n_prio));
+}
+
+__device__ __forceinline__ bool item_priority(const BfParams& p, int32_t item, int ipr) {
+    return p.w.prio && (__ldg(p.g.run_flags + item / ipr) & RUN_PRIORITY) != 0;
+}
+
 // One thread lists one item for sweep s (seeding).
-__device__ __forceinline__ void frontier_push(const BfParams& p, int32_t item, int s) {
-    if (atomicMax(p.w.stamp + item, s) < s) frontier_list(p, s)[atomicAdd(p.w.counts + s % 3, 1)] = item;
+__device__ __forceinline__ void frontier_push(const BfParams& p, int32_t item, int s, int ipr, int cap) {
+    if (atomicMax(p.w.stamp + item, s) < s) {
+        int32_t* list = frontier_list(p, s);
+        if (item_priority(p, item, ipr)) list[cap - 1 - atomicAdd(p.w.counts + 6 + s % 3, 1)] = item;
+        else list[atomicAdd(p.w.counts + s % 3, 1)] = item;
+    }
 }
 
 // The warp lists up to n items cand(j) for sweep s: one item per lane and
-// round, one list reservation per round.
-template <class Cand>
-__device__ __forceinline__ void frontier_push_warp(const BfParams& p, int n, int s, int lane, Cand cand) {
+// round, one reservation per list end and round.
+template <class Cand, class Prio>
+__device__ __forceinline__ void frontier_push_warp(const BfParams& p, int n, int s, int lane, int ipr, int cap, Cand cand,
+                                                   Prio prio) {
     int32_t* list = frontier_list(p, s);
     for (int base = 0; base < n; base += 32) {
         const int j = base + lane;
         int32_t item = -1;
-        bool add = false;
+        bool add = false, pr = false;
         if (j < n) {
             item = cand(j);
             add = atomicMax(p.w.stamp + item, s) < s;
+            pr = add && prio(j, item);
         }
-        const unsigned m = __ballot_sync(FULL_MASK, add);
-        if (m == 0u) continue;
-        int pos = 0;
-        if (lane == 0) pos = atomicAdd(p.w.counts + s % 3, __popc(m));
-        pos = __shfl_sync(FULL_MASK, pos, 0);
-        if (add) list[pos + __popc(m & lanemask_lt())] = item;
+        const unsigned mn = __ballot_sync(FULL_MASK, add && !pr), mp = __ballot_sync(FULL_MASK, pr);
+        if ((mn | mp) == 0u) continue;
+        int pn = 0, pp = 0;
+        if (lane == 0) {
+            if (mn) pn = atomicAdd(p.w.counts + s % 3, __popc(mn));
+            if (mp) pp = atomicAdd(p.w.counts + 6 + s % 3, __popc(mp));
+        }
+        pn = __shfl_sync(FULL_MASK, pn, 0);
+        pp = __shfl_sync(FULL_MASK, pp, 0);
+        if (pr) list[cap - 1 - (pp + __popc(mp & lanemask_lt()))] = item;
+        else if (add) list[pn + __popc(mn & lanemask_lt())] = item;
     }
 }
 
@@ -412,6 +439,7 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
     const int G = (n_lanes + 31) >> 5;
     if (G == 0) return;  // same decision in every block
     const int ipr = (G + GPW - 1) / GPW;  // items per run: GPW groups each
+    const int cap = p.g.n_runs * ipr;     // items of the segment: the lists' length
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthreads = gridDim.x * blockDim.x;
 
@@ -420,9 +448,9 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
     for (int b = gtid; b < n_lanes; b += nthreads) {
         const int r = __ldg(p.g.run_of_node + p.seg.src[p.seg.first + b]);
         const int g = (b >> 5) / GPW;
-        frontier_push(p, r * ipr + g, 1);
+        frontier_push(p, r * ipr + g, 1, ipr, cap);
         const int q1 = __ldg(p.g.rout_ptr + r + 1);
-        for (int q = __ldg(p.g.rout_ptr + r); q < q1; ++q) frontier_push(p, __ldg(p.g.rout_list + q) * ipr + g, 1);
+        for (int q = __ldg(p.g.rout_ptr + r); q < q1; ++q) frontier_push(p, __ldg(p.g.rout_list + q) * ipr + g, 1, ipr, cap);
     }
     if (!grid_sync(p.w.bar, p.w.err, p.w.max_spins)) return;
 
@@ -430,7 +458,8 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
     int sweep = 1;
     for (;; ++sweep) {
         const int cur = sweep % 3;
-        const int cnt = ld_volatile(p.w.counts + cur);
+        const int n_prio = ld_volatile(p.w.counts + 6 + cur);
+        const int cnt = ld_volatile(p.w.counts + cur) + n_prio;
         if (gtid == 0 && sweep <= p.w.trace_cap) {
             long long tm;
             asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tm));
@@ -446,6 +475,7 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
             const int nx = (sweep + 2) % 3;  // the list sweep s+2 fills; sweep s-1 read it
             p.w.counts[nx] = 0;
             p.w.counts[3 + nx] = 0;
+            p.w.counts[6 + nx] = 0;
         }
         const int32_t* list = frontier_list(p, sweep);
         int* claim = p.w.counts + 3 + cur;
@@ -462,12 +492,12 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
         it = __shfl_sync(FULL_MASK, it, 0);
         it1 = __shfl_sync(FULL_MASK, it1, 0);
         TileMeta m{};
-        if (it < cnt) m = load_meta<GPW>(p, list, it, G, lane);
+        if (it < cnt) m = load_meta<GPW>(p, list_item(list, it, n_prio, cap), G, lane);
         while (it < cnt) {
             int it2 = 0;
             if (lane == 0) it2 = ahead ? atomicAdd(claim, 1) : cnt;
             TileMeta m1{};
-            if (it1 < cnt) m1 = load_meta<GPW>(p, list, it1, G, lane);
+            if (it1 < cnt) m1 = load_meta<GPW>(p, list_item(list, it1, n_prio, cap), G, lane);
             // algorithmic bytes take a run's descriptors once per sweep, whichever of its
             // groups comes first; the answer is used after the tile, so the atomic's latency
             // hides behind it
@@ -480,11 +510,15 @@ __global__ void __launch_bounds__(32 * NW, 1) bf_warp_kernel(BfParams p) {
                 const int q0 = m.q0, nq = m.nq;
                 const int item = m.item, g = m.g / GPW;
                 const int fed = __shfl_sync(FULL_MASK, m.rq, (lane + 31) & 31) * ipr + g;  // lane j: fed run j - 1
+                const bool fedp = __shfl_sync(FULL_MASK, m.rqp, (lane + 31) & 31);
+                const bool selfp = p.w.prio && (m.flags & RUN_PRIORITY) != 0;
                 if (nq < 32)
-                    frontier_push_warp(p, nq + 1, sweep + 1, lane, [&](int j) { return j == 0 ? item : fed; });
+                    frontier_push_warp(p, nq + 1, sweep + 1, lane, ipr, cap, [&](int j) { return j == 0 ? item : fed; },
+                                       [&](int j, int32_t) { return j == 0 ? selfp : fedp; });
                 else
-                    frontier_push_warp(p, nq + 1, sweep + 1, lane,
-                                       [&](int j) { return j == 0 ? item : __ldg(p.g.rout_list + q0 + j - 1) * ipr + g; });
+                    frontier_push_warp(p, nq + 1, sweep + 1, lane, ipr, cap,
+                                       [&](int j) { return j == 0 ? item : __ldg(p.g.rout_list + q0 + j - 1) * ipr + g; },
+                                       [&](int, int32_t it) { return item_priority(p, it, ipr); });
             }
             if (lane == 0) {
                 ++tiles;

@@ -441,6 +441,10 @@ void build_partition(const HostGraph& g, int run_target, int tile_cap, HostParti
         for (int32_t r = 0; r < p.n_runs; ++r)
             for (int32_t q = p.rin_ptr[r]; q < p.rin_ptr[r + 1]; ++q) p.rout_list[fill[p.rin_list[q]]++] = r;
     }
+    // runs that feed many others (the cross-aisle pieces, which feed every aisle they cross)
+    // are listed first in every sweep of the warp tiling
+    for (int32_t r = 0; r < p.n_runs; ++r)
+        if (p.rout_ptr[r + 1] - p.rout_ptr[r] >= PRIORITY_FEEDS) p.run_flags[r] |= RUN_PRIORITY;
     int4 sentinel;
     sentinel.x = static_cast<int>(NO_CARRY);
     sentinel.y = static_cast<int>(NO_CARRY);

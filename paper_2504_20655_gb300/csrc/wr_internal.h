@@ -30,6 +30,8 @@ constexpr int ORDER_FLAG_RANGE = 1;
 constexpr int32_t RUN_SIMPLE = 1;             // run's extra arcs fit the tile buffer, halo fully staged
 constexpr uint32_t IX_EXTRA = 1u << 24;       // node has arcs beyond the inline ones
 constexpr int32_t RUN_COMPACT = 2;            // every node's arcs are staged: compact descriptors + extras (warp tiling)
+constexpr int32_t RUN_PRIORITY = 8;           // feeds at least PRIORITY_FEEDS runs: listed first in every sweep
+constexpr int PRIORITY_FEEDS = 6;
 // extra arcs a compact run may have (they are staged with the tile): tile_cap / 2 entries, so
 // that a 128-slot warp tile takes 20.5 KB of shared memory and 11 of them fit one SM
 __host__ __device__ constexpr int wx_cap(int tile_cap) { return tile_cap / 2; }
@@ -151,6 +153,9 @@ struct BfSegment {
     // [32 gcol[g], 32 gcol[g] + 32) instead of [32g, 32g + 32) (a row cache
     // whose free column groups are scattered); nullptr = contiguous
     const int32_t* gcol = nullptr;
+    // the sources are sorted by node id (the distinct sources of a batch of orders), so the 32
+    // sources of a group are neighbours when they are dense enough; see BfWork::prio
+    bool sorted = false;
 };
 
 struct BfWork {
@@ -159,7 +164,14 @@ struct BfWork {
     int32_t* list0;   // n_runs * Gcap
     int32_t* list1;
     int32_t* list2;   // third frontier list (warp sweeps: sweep s reads list s mod 3)
-    int32_t* counts;  // 8: list sizes, then claim counters
+    int32_t* counts;  // 16: list sizes, claim counters, priority list sizes (warp sweeps)
+    // warp sweeps: list the items of RUN_PRIORITY runs first in every sweep.  Taken for sorted
+    // sources with at least one lane per 64 nodes: a group's 32 sources then lie within a few
+    // aisles, its distances spread out from there through the cross-aisles, and relaxing the
+    // cross-aisle tiles first lets each sweep's aisle tiles read their new values (and keeps those
+    // long tiles from ending the sweep last).  Sparse or scattered sources (the scale rows) reach
+    // the cross-aisles from every aisle at once, and there it cost more tile visits.
+    int prio;
     int32_t gcap;
     GridBar* bar;
     int* err;
