@@ -505,6 +505,9 @@ extern "C" int bfm_check_partition(int V, long long E, const long long* rp, cons
         std::sort(rin.begin(), rin.end());
         if (rin != runs_in) return 11;
     }
+    // the runs listed first in the warp sweeps feed at least PRIORITY_FEEDS runs
+    for (int r = 0; r < p.n_runs; ++r)
+        if (((p.run_flags[r] & RUN_PRIORITY) != 0) != (p.rout_ptr[r + 1] - p.rout_ptr[r] >= PRIORITY_FEEDS)) return 23;
     return 0;
 }
 
