@@ -564,12 +564,27 @@ struct BlockRec {
     bool have;
 };
 
+// k-th smallest of 0..4 outside the bit set used (compile-time relabeling).
+__host__ __device__ constexpr int kth_free5(unsigned used, int k) {
+    for (int i = 0; i < 5; ++i)
+        if (!(used & (1u << i))) {
+            if (k == 0) return i;
+            --k;
+        }
+    return -1;
+}
+
 // One block of 120 sequences of a 720-sequence unit: the six remaining picks
 // s_0 < ... < s_5 (matrix indices packed in sp), s_J next, then the 120
-// orderings of the other five, walked over compile-time views of the six's
+// orderings of the other five, costed from compile-time views of the six's
 // tables: legs between them (d6) and every three-leg suffix ending at the
 // depot (t3f[a][b][c] = D[s_a][s_b] + D[s_b][s_c] + D[s_c][0]).  acc = cost
-// of the sequence through s_J.
+// of the sequence through s_J.  The five subtrees below the first of the five
+// (24 sequences each, SUB24) are walked side by side: each step does the same
+// relative move in all five, so the five running minima (one per subtree)
+// form five independent add-min chains instead of one long one.
+constexpr int SUB24 = 24;
+
 template <int J>
 __device__ __forceinline__ void tail6_block(const uint32_t (&d6)[6][6], const uint32_t (&t3f)[6][6][6], unsigned sp,
                                             uint32_t acc, unsigned rank0, uint32_t& cur_c, unsigned& cur_r,
@@ -595,25 +610,61 @@ __device__ __forceinline__ void tail6_block(const uint32_t (&d6)[6][6], const ui
                 if (a == b || a == c || b == c) continue;
                 T.t3[a][b][c] = t3f[a < J ? a : a + 1][b < J ? b : b + 1][c < J ? c : c + 1];
             }
-    uint32_t mins[NACC];
+    uint32_t mn[5], a0[5];
 #pragma unroll
-    for (int i = 0; i < NACC; ++i) mins[i] = 0xFFFFFFFFu;
-    Scan<5, 31u, -1, 0>::run(acc, T, mins);
-    const uint32_t mn = min_of(mins);
+    for (int s = 0; s < 5; ++s) {
+        mn[s] = 0xFFFFFFFFu;
+        a0[s] = acc + T.x[s];
+    }
+#pragma unroll
+    for (int i1 = 0; i1 < 4; ++i1) {
+        uint32_t a1[5];
+#pragma unroll
+        for (int s = 0; s < 5; ++s) a1[s] = a0[s] + T.d[s][kth_free5(1u << s, i1)];
+#pragma unroll
+        for (int i2 = 0; i2 < 3; ++i2) {
+            uint32_t a2[5];
+#pragma unroll
+            for (int s = 0; s < 5; ++s) {
+                const int p1 = kth_free5(1u << s, i1);
+                a2[s] = a1[s] + T.d[p1][kth_free5((1u << s) | (1u << p1), i2)];
+            }
+            // the two orderings of the last two picks b < c: (b, c) first, then (c, b)
+#pragma unroll
+            for (int s = 0; s < 5; ++s) {
+                const int p1 = kth_free5(1u << s, i1);
+                const unsigned u2 = (1u << s) | (1u << p1);
+                const int p2 = kth_free5(u2, i2);
+                const unsigned u3 = u2 | (1u << p2);
+                mn[s] = __viaddmin_u32(a2[s], T.t3[p2][kth_free5(u3, 0)][kth_free5(u3, 1)], mn[s]);
+            }
+#pragma unroll
+            for (int s = 0; s < 5; ++s) {
+                const int p1 = kth_free5(1u << s, i1);
+                const unsigned u2 = (1u << s) | (1u << p1);
+                const int p2 = kth_free5(u2, i2);
+                const unsigned u3 = u2 | (1u << p2);
+                mn[s] = __viaddmin_u32(a2[s], T.t3[p2][kth_free5(u3, 1)][kth_free5(u3, 0)], mn[s]);
+            }
+        }
+    }
+    uint32_t m = mn[0];
+#pragma unroll
+    for (int s = 1; s < 5; ++s) m = min(m, mn[s]);
     // cur_r: the exact rank of the order's best, or the first rank of the
-    // recorded range; every later block starts above both
-    if (mn < cur_c || (mn == cur_c && rank0 < cur_r)) {
-        int a = NACC - 1;
+    // recorded subtree; every later block starts above both
+    if (m < cur_c || (m == cur_c && rank0 < cur_r)) {
+        int a = 4;
 #pragma unroll
-        for (int i = NACC - 2; i >= 0; --i)
-            if (mins[i] == mn) a = i;
-        cur_c = mn;
-        cur_r = rank0 + static_cast<unsigned>(a * AccSpan<5>::value);
+        for (int s = 3; s >= 0; --s)
+            if (mn[s] == m) a = s;
+        cur_c = m;
+        cur_r = rank0 + static_cast<unsigned>(a * SUB24);
         rec.acc = acc;
         rec.five = (sp & ((1u << (4 * J)) - 1u)) | ((sp >> (4 * J + 4)) << (4 * J));
         rec.sj = static_cast<int>((sp >> (4 * J)) & 15u);
         rec.rank0 = rank0;
-        rec.lo = a * AccSpan<5>::value;
+        rec.lo = a * SUB24;
         rec.have = true;
     }
 }
@@ -732,7 +783,7 @@ __device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, unsigne
             // range cannot hold the result: no search, nothing to publish
             if (static_cast<uint32_t>(__ldcg(out) >> 32) < best_c) return;
             best_r = rec.rank0 + static_cast<unsigned>(first_of_five(Dm, rec.acc, rec.sj, rec.five, best_c, rec.lo,
-                                                                     rec.lo + AccSpan<5>::value));
+                                                                     rec.lo + SUB24));
         }
     }
     const unsigned long long packed = (static_cast<unsigned long long>(best_c) << 32) | best_r;

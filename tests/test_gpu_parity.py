@@ -274,6 +274,30 @@ def test_tour_eval_vs_held_karp(router, orc, k):
             assert status[i] == st and cost[i] == c and perm[i, :k].tolist() == p.tolist()
 
 
+def test_enumeration_batch_and_single_calls(router, orc):
+    """14 orders of 7..12 picks with legs in 0..3 (ties everywhere, so the tie rule decides every
+    result), in one call and one order per call: the same bits, equal to the oracle's Held-Karp
+    with the same tie rule."""
+    kk = np.array([12] * 12 + [7, 11], np.int32)
+    D, _ = _rand_D(len(kk), 12, 5150, 3)
+    cost, perm, status = router.tour_eval(kk, D)
+    for i, k in enumerate(kk):
+        st, c, p = orc.tour(D[i, :k + 1, :k + 1], "heldkarp")
+        assert status[i] == st == 0 and cost[i] == c and perm[i, :k].tolist() == p.tolist(), i
+        c1, p1, s1 = router.tour_eval(kk[i:i + 1], D[i:i + 1])
+        assert c1[0] == cost[i] and s1[0] == status[i] and (p1[0, :k] == perm[i, :k]).all(), i
+
+
+def test_tour_eval_large_legs(router, orc):
+    """Legs up to 10^6 (sequence costs up to 1.3e7): the 32-bit sums stay exact."""
+    for k in (6, 8, 10, 12):
+        D, m = _rand_D(3, k, 991 * k, 10**6)
+        cost, perm, status = router.tour_eval(np.full(3, k, np.int32), D)
+        for i in range(3):
+            st, c, p = orc.tour(D[i, :m, :m], "brute" if k <= 8 else "heldkarp")
+            assert status[i] == st == 0 and cost[i] == c and perm[i, :k].tolist() == p.tolist(), (k, i)
+
+
 def test_tour_eval_statuses(router, orc):
     D, _ = _rand_D(4, 6, 9, 100)
     kk = np.array([0, 13, 6, 6], np.int32)
