@@ -586,6 +586,37 @@ def serving_stream(n, rate, seed=None):
     return lay, o, arr
 
 
+def serving_batch_roofline(r, args, reps=5):
+    """Sweep and enumeration rooflines of one serving batch (max_batch orders of the stream),
+    routed directly with every row computed; medians of reps calls after one warm-up."""
+    import torch
+
+    _, o, _ = serving_stream(args.serve_batch, 1000.0)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stats = []
+    for i in range(reps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        r.route_orders(o.offs, o.picks)
+        if i:
+            stats.append(r.stats())
+    pk = peaks()
+    bf_ms = statistics.median(s["ms_bf"] for s in stats)
+    enum_ms = statistics.median(s["ms_enum"] for s in stats)
+    st = stats[-1]
+    achieved = st["bytes_alg"] / (bf_ms / 1e3) / 1e9 if bf_ms > 0 else 0.0
+    alu_peak = alu_min_peak(pk)
+    tops = st["sequences"] / (enum_ms / 1e3) / 1e12 if enum_ms > 0 else 0.0
+    how = (f"one batch of {args.serve_batch} orders of the stream through wr_route_orders, every row computed "
+           f"(a served batch computes only its cache misses); L2 flushed before each of {reps} calls, medians")
+    return {"bf": {"kernel": sweep_kernel_name(r.tuning()), "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                   "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"],
+                   "bytes_alg_per_launch": st["bytes_alg"], "ms_per_launch": bf_ms, "sources": st["n_sources"],
+                   "measured_on": how},
+            "enum": {"kernel": "enum_kernel", "bound": "alu", "achieved": tops, "peak": alu_peak, "unit": "Tops/s",
+                     "frac": tops / alu_peak, "sequences": st["sequences"], "ms": enum_ms, "measured_on": how}}
+
+
 def measure_serving(args, rates=None, seconds=None, max_orders=None, plain_max=None, plain_seconds=None):
     """Serving workload: real-time arrivals, continuous batching with a resident row
     cache (wr_serve_*), p50/p99 arrival-to-result latency and orders/s per arrival rate,
@@ -666,6 +697,10 @@ def measure_serving(args, rates=None, seconds=None, max_orders=None, plain_max=N
         ok = [x["rate"] for x in results if x["batched"]["p99_ms"] <= p99 and x["batched"]["orders_per_s"] >= 0.95 * x["rate"]]
         matched.append({"plain_rate": row["rate"], "plain_p99_ms": p99, "plain_orders_per_s": row["plain"]["orders_per_s"],
                         "batched_max_rate_at_that_p99": max(ok) if ok else None})
+    # roofline of the serving batches' dominant kernels, on one batch of max_batch orders of the
+    # stream through wr_route_orders with every row computed (a served batch computes only the rows
+    # its row cache lacks): the sweep kernel against HBM, the enumeration against the ALU pipe
+    roof = serving_batch_roofline(r, args)
     top = results[-1]["batched"]
     line = {
         "metric": "served orders/s (p50/p99 latency)", "value": top["orders_per_s"], "unit": "orders/s",
@@ -680,6 +715,8 @@ def measure_serving(args, rates=None, seconds=None, max_orders=None, plain_max=N
         "e2e": {"value": top["orders_per_s"], "unit": "orders/s", "h2d_bytes_per_step": None,
                 "d2h_bytes_per_step": None, "note": "host arrays in and out of every batch: the serving loop is end to end"},
         "clocks": clk.summary(),
+        "roofline": roof["bf"],
+        "roofline_enum": roof["enum"],
     }
     if rank == 0 and not args.no_cpu:
         _, o, _ = serving_stream(2000, rates[0])
