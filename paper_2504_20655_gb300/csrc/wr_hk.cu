@@ -132,13 +132,15 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
     __shared__ unsigned long long pre[HK_BATCH + 1];  // level prefix of C(k_q, L)
     __shared__ unsigned long long base[HK_BATCH + 1];  // table offsets (words)
     __shared__ int kq[HK_BATCH];
-    __shared__ int nb_s;
+    __shared__ int nb_s, kmax_s;
     for (int i = threadIdx.x; i < (HK_MAX_K + 1) * (HK_MAX_K + 1); i += blockDim.x) {
         const int n = i / (HK_MAX_K + 1), r = i % (HK_MAX_K + 1);
-        unsigned long long c = 1;  // C(n, r) by the multiplicative formula (exact at each step)
+        // C(n, r) by the multiplicative formula: exact at each step, C(n - r + j, j) * (n - r + j + 1)
+        // stays below C(20, 10) * 21 < 2^32
+        uint32_t c = 1;
         if (r > n) c = 0;
-        for (int j = 1; j <= r && j <= n; ++j) c = c * static_cast<unsigned long long>(n - r + j) / j;
-        binom[n][r] = static_cast<uint32_t>(c);
+        for (int j = 1; j <= r && j <= n; ++j) c = c * static_cast<uint32_t>(n - r + j) / static_cast<uint32_t>(j);
+        binom[n][r] = c;
     }
     __syncthreads();
     for (int k = threadIdx.x; k <= HK_MAX_K; k += blockDim.x) {
@@ -150,32 +152,52 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
     const long long nthreads = static_cast<long long>(gridDim.x) * blockDim.x;
     int q0 = 0;
     while (q0 < n_big) {
-        // the batch: orders q0 .. q1-1 whose tables fit (the same in every block)
+        // the batch: orders q0 .. q1-1 whose tables fit (the same in every block); every thread
+        // reads the picks of its share of the candidates, then one thread sums the sizes
+        __syncthreads();
+        for (int i = threadIdx.x; i < HK_BATCH && q0 + i < n_big; i += blockDim.x) kq[i] = hk_k(p, q0 + i);
         __syncthreads();
         if (threadIdx.x == 0) {
             unsigned long long acc = 0;
-            int q = q0;
+            int q = q0, km = 0;
             base[0] = 0;
             while (q < n_big && q - q0 < HK_BATCH) {
-                const int k = hk_k(p, q);
+                const int k = kq[q - q0];
                 const unsigned long long sz = k > 0 ? (1ull << (k - 1)) * static_cast<unsigned long long>(k) : 0ull;
                 if (q > q0 && acc + sz > p.h_words) break;
-                kq[q - q0] = k;
                 acc += sz;
                 base[q - q0 + 1] = acc;
+                km = max(km, k);
                 ++q;
             }
             nb_s = q - q0;  // batch size
+            kmax_s = km;
         }
         __syncthreads();
         const int nb = nb_s;
-        int kmax = 0;
-        for (int i = 0; i < nb; ++i) kmax = max(kmax, kq[i]);
+        const int kmax = kmax_s;
         for (int L = kmax; L >= 1; --L) {
             __syncthreads();
-            if (threadIdx.x == 0) {
-                pre[0] = 0;
-                for (int i = 0; i < nb; ++i) pre[i + 1] = pre[i] + (kq[i] >= L ? binom[kq[i]][L] : 0u);
+            if (threadIdx.x < 32) {
+                // pre[i] = items of the batch's orders before i at this level: a warp scan, lane l
+                // over orders [l * per, (l + 1) * per)
+                const int lane = threadIdx.x;
+                const int per = (nb + 31) / 32;
+                const int i0 = min(lane * per, nb), i1 = min(i0 + per, nb);
+                unsigned long long sum = 0;
+                for (int i = i0; i < i1; ++i) sum += kq[i] >= L ? binom[kq[i]][L] : 0u;
+                unsigned long long inc = sum;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const unsigned long long y = __shfl_up_sync(FULL_MASK, inc, d);
+                    if (lane >= d) inc += y;
+                }
+                unsigned long long run = inc - sum;
+                for (int i = i0; i < i1; ++i) {
+                    pre[i] = run;
+                    run += kq[i] >= L ? binom[kq[i]][L] : 0u;
+                }
+                if (lane == 31) pre[nb] = inc;
             }
             __syncthreads();
             const unsigned long long total = pre[nb];
@@ -184,7 +206,16 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
             // block |S|, rank of S with bit j squeezed out = its bits below j as they are plus
             // its bits above j one lower)
             auto load_item = [&](unsigned long long w, HkItem& it) {
-                while (pre[qi + 1] <= w) ++qi;  // the order holding item w
+                // the order holding item w: the last i with pre[i] <= w (an order with no items at
+                // this level shares its pre with the next, so the last one holds w), by bisection
+                // from the order of the thread's previous item
+                {
+                    int hi = nb - 1;
+                    while (qi < hi) {
+                        const int mid = (qi + hi + 1) >> 1;
+                        if (pre[mid] <= w) qi = mid; else hi = mid - 1;
+                    }
+                }
                 const int k = kq[qi];
                 it.qi = qi;
                 // the subset of rank w - pre[qi] among the L-subsets of k picks, bits from the
