@@ -107,10 +107,6 @@ struct HkItem {
     uint32_t hv[HK_MAX_K];
 };
 
-__device__ __forceinline__ uint32_t bn(const uint32_t (&binom)[HK_MAX_K + 1][HK_MAX_K + 1], int n, int r) {
-    return n < 0 ? 0u : binom[n][r];
-}
-
 // Picks of listed order q (0 for an order whose D holds an out-of-range leg:
 // its status comes from the decode of the other orders).
 __device__ __forceinline__ int hk_k(const HkParams& p, int q) {
@@ -128,6 +124,7 @@ __device__ __forceinline__ int hk_k(const HkParams& p, int q) {
 // rebuilds its first optimal sequence.
 __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
     __shared__ uint32_t binom[HK_MAX_K + 1][HK_MAX_K + 1];
+    __shared__ uint32_t binx[HK_MAX_K + 2][HK_MAX_K + 2];  // binx[n + 1][r] = C(n, r); C(-1, r) = 0
     __shared__ uint32_t loff[HK_MAX_K + 1][HK_MAX_K + 2];  // loff[k][l]: sum of C(k-1, l') over l' < l
     __shared__ unsigned long long pre[HK_BATCH + 1];  // level prefix of C(k_q, L)
     __shared__ unsigned long long base[HK_BATCH + 1];  // table offsets (words)
@@ -143,6 +140,10 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
         binom[n][r] = c;
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < (HK_MAX_K + 2) * (HK_MAX_K + 2); i += blockDim.x) {
+        const int n = i / (HK_MAX_K + 2) - 1, r = i % (HK_MAX_K + 2);
+        binx[n + 1][r] = (n < 0 || r > HK_MAX_K) ? 0u : binom[n][r];
+    }
     for (int k = threadIdx.x; k <= HK_MAX_K; k += blockDim.x) {
         loff[k][0] = 0;
         for (int l = 0; l <= HK_MAX_K; ++l) loff[k][l + 1] = loff[k][l] + (k >= 1 ? binom[k - 1][l] : 0u);
@@ -218,45 +219,41 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
                 }
                 const int k = kq[qi];
                 it.qi = qi;
-                // the subset of rank w - pre[qi] among the L-subsets of k picks, bits from the
-                // top: each the largest c below the previous one with C(c, i) <= rr
+                // the subset of rank w - pre[qi] (below C(20, 10): 32-bit) among the L-subsets of k
+                // picks, bits from the top: each the largest c below the previous one with
+                // C(c, i) <= rr.  Bit c is bit t = i - 1 from the bottom, so the same pass sums,
+                // over the bits b_0 < b_1 < ... of S, pb = sum C(b_t - 1, t + 1) and
+                // pc = sum C(b_t - 1, t)
                 unsigned s = 0;
-                unsigned long long rr = w - pre[qi];
-                int c_hi = k;
-                for (int i = L; i >= 1; --i) {
-                    int c = c_hi - 1;
-                    while (binom[c][i] > rr) --c;  // ends by c = i - 1: C(i - 1, i) = 0
+                uint32_t rr = static_cast<uint32_t>(w - pre[qi]);
+                uint32_t pb_tot = 0, pc_tot = 0;
+                int c = k - 1;
+                for (int i = L; i >= 1; --i, --c) {
+                    while (binx[c + 1][i] > rr) --c;  // ends by c = i - 1: C(i - 1, i) = 0
                     s |= 1u << c;
-                    rr -= binom[c][i];
-                    c_hi = c;
+                    rr -= binx[c + 1][i];
+                    pb_tot += binx[c][i];
+                    pc_tot += binx[c][i - 1];
                 }
                 it.s = s;
-                // over the bits b_0 < b_1 < ... of S: pb = sum C(b_t - 1, t + 1), pc = sum C(b_t - 1, t)
-                uint32_t pb_tot = 0, pc_tot = 0;
-                {
-                    int t = 0;
-                    for (unsigned m = s; m; m &= m - 1, ++t) {
-                        const int b = __ffs(m) - 1;
-                        pb_tot += bn(binom, b - 1, t + 1);
-                        pc_tot += bn(binom, b - 1, t);
-                    }
-                }
                 it.pc_tot = pc_tot;
-                const int64_t half = static_cast<int64_t>(1) << (k - 1);  // words per plane
+                // h(S + j, j) sits in plane j (2^(k-1) words), block |S|, at the rank of S with bit
+                // j squeezed out: over the bits b of S, C(b, t + 1) below j and C(b - 1, t + 1)
+                // above, = pb_tot + the sum over the bits below j of C(b - 1, t) (Pascal).
+                // Offsets within the order's table fit 32 bits (20 x 2^19 words at most)
                 const uint32_t* hq = p.h + base[qi];
-                const uint32_t lo = loff[k][L];
-                uint32_t pa = 0, pb = 0;
+                const uint32_t off0 = loff[k][L] + pb_tot;
+                uint32_t pcr = 0;
                 int m = 0;
 #pragma unroll
                 for (int j = 0; j < HK_MAX_K; ++j) {
                     it.hv[j] = INF_U;
                     if (j < k) {
                         if ((s >> j) & 1u) {
-                            pa += binom[j][m + 1];
-                            pb += bn(binom, j - 1, m + 1);
+                            pcr += binx[j][m];
                             ++m;
                         } else {
-                            it.hv[j] = __ldcg(hq + j * half + lo + (pa + pb_tot - pb));
+                            it.hv[j] = __ldcg(hq + ((static_cast<uint32_t>(j) << (k - 1)) + off0 + pcr));
                         }
                     }
                 }
@@ -265,7 +262,6 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
             auto store_item = [&](const HkItem& it) {
                 const int k = kq[it.qi];
                 const unsigned s = it.s, full = (1u << k) - 1u;
-                const int64_t half = static_cast<int64_t>(1) << (k - 1);
                 const uint32_t* D = p.D21 + static_cast<int64_t>(q0 + it.qi) * HK_DBLOCK;
                 uint32_t* hq = p.h + base[it.qi];
                 const uint32_t lo = loff[k][L - 1];
@@ -294,9 +290,9 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
                             best = __viaddmin_u32(d.w, it.hv[4 * j4 + 3], best);
                         }
                     }
-                    const uint32_t cc = bn(binom, c - 1, t);
-                    __stcg(hq + c * half + lo + (pa + it.pc_tot - pc - cc), best);
-                    pa += binom[c][t + 1];
+                    const uint32_t cc = binx[c][t];  // C(c - 1, t)
+                    __stcg(hq + ((static_cast<uint32_t>(c) << (k - 1)) + lo + (pa + it.pc_tot - pc - cc)), best);
+                    pa += binx[c + 1][t + 1];
                     pc += cc;
                 }
             };
