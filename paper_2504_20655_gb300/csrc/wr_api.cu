@@ -202,7 +202,7 @@ int run_bf_segment(wr_ctx* c, const wr::BfSegment& seg, cudaStream_t s) {
     {
         PhaseTimer t(c, s, 1);
         CK(wr::bf_launch_init(c->dg, seg, w, s));
-        c->launches += 2;
+        c->launches += seg.src_index ? 1 : 2;
     }
     {
         PhaseTimer t(c, s, 2);
@@ -343,13 +343,10 @@ int enqueue_select(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d
     tb.picks = d_picks;
     RC(ensure_tour_bufs(c, n, tb));
     PhaseTimer t(c, s, 0);
-    CK(cudaMemsetAsync(c->node_flag.p, 0, static_cast<size_t>(V), s));
-    CK(cudaMemsetAsync(c->order_flags.p, 0, static_cast<size_t>(n) * 4, s));
-    CK(wr::tour_launch_select(n, d_offs, d_picks, V, c->dg.depot, c->cfg.max_k, c->node_flag.as<uint8_t>(),
-                              tb.order_status, s));
-    c->launches++;
-    CK(wr::tour_launch_compact(V, c->node_flag.as<uint8_t>(), c->src_index.as<int32_t>(), c->src_list.as<int32_t>(),
-                               c->n_src.as<int32_t>(), c->block_sums.as<int32_t>(), s, &c->launches));
+    CK(wr::tour_launch_select_compact(n, d_offs, d_picks, V, c->dg.depot, c->cfg.max_k, c->node_flag.as<uint8_t>(),
+                                      tb.order_status, c->order_flags.as<int32_t>(), c->src_index.as<int32_t>(),
+                                      c->src_list.as<int32_t>(), c->n_src.as<int32_t>(), c->block_sums.as<int32_t>(),
+                                      s, &c->launches));
     return WR_OK;
 }
 
@@ -391,6 +388,7 @@ int enqueue_route(wr_ctx* c, int32_t n, const int64_t* d_offs, const int32_t* d_
         seg.ld = seg_lanes;
         seg.src = c->src_list.as<int32_t>();
         seg.sorted = true;  // the distinct sources of the orders, in node id order
+        seg.src_index = c->src_index.as<int32_t>();
         seg.n_src_dev = c->n_src.as<int32_t>();
         seg.n_src_host = 0;
         seg.first = sg * seg_lanes;
@@ -1010,12 +1008,9 @@ int wr_route_nodes(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pic
     const size_t per_leg = LEG_CACHE_WORDS / n_legs;
     const int32_t cache_cap = static_cast<int32_t>(per_leg < LEG_CACHE_NODES ? per_leg : LEG_CACHE_NODES);
     if (cache_cap > 0) RC(ensure(c->leg_cache, n_legs * static_cast<size_t>(cache_cap) * 4));
-    CK(cudaMemsetAsync(c->node_flag.p, 0, static_cast<size_t>(V), s));
-    CK(wr::tour_launch_select(n, d_offs, d_picks, V, c->dg.depot, c->cfg.max_k, c->node_flag.as<uint8_t>(),
-                              tb.order_status, s));
-    c->launches++;
-    CK(wr::tour_launch_compact(V, c->node_flag.as<uint8_t>(), c->src_index.as<int32_t>(), c->src_list.as<int32_t>(),
-                               c->n_src.as<int32_t>(), c->block_sums.as<int32_t>(), s, &c->launches));
+    CK(wr::tour_launch_select_compact(n, d_offs, d_picks, V, c->dg.depot, c->cfg.max_k, c->node_flag.as<uint8_t>(),
+                                      tb.order_status, nullptr, c->src_index.as<int32_t>(), c->src_list.as<int32_t>(),
+                                      c->n_src.as<int32_t>(), c->block_sums.as<int32_t>(), s, &c->launches));
     const int64_t worst = np + 1 < V ? np + 1 : V;
     const int32_t lanes_needed = static_cast<int32_t>((worst + 31) / 32 * 32);
     const int32_t blanes = budget_lanes(c);
@@ -1035,6 +1030,7 @@ int wr_route_nodes(wr_ctx* c, int32_t n, const int64_t* offs, const int32_t* pic
         seg.ld = seg_lanes;
         seg.src = c->src_list.as<int32_t>();
         seg.sorted = true;  // the distinct sources of the orders, in node id order
+        seg.src_index = c->src_index.as<int32_t>();
         seg.n_src_dev = c->n_src.as<int32_t>();
         seg.n_src_host = 0;
         seg.first = sg * seg_lanes;

@@ -23,8 +23,9 @@
 namespace wr {
 
 // rows := INF; stamps := 0; counters := 0.  A warp fills whole rows with
-// 16-byte stores (32 lanes x 4 sources per instruction); the sources' zeros
-// follow in bf_seed_kernel.
+// 16-byte stores (32 lanes x 4 sources per instruction).  The sources' zeros
+// go in with the fill when the segment maps nodes to its sources (src_index),
+// else bf_seed_kernel writes them after it.
 __global__ void bf_init_kernel(BfParams p) {
     const int n_lanes = segment_lanes(p.seg);
     const int G = (n_lanes + 31) >> 5;
@@ -34,8 +35,23 @@ __global__ void bf_init_kernel(BfParams p) {
     const uint4 inf = make_uint4(INF_U, INF_U, INF_U, INF_U);
     for (int64_t v = w0; v < p.g.V; v += warps) {
         uint32_t* row = p.seg.rows + v * p.seg.ld;
-        for (int q = lane; q < 8 * G; q += 32)  // uint4 q: group q / 8, lanes 4 (q % 8) ..
-            __stcg(reinterpret_cast<uint4*>(row + seg_col0(p.seg, q >> 3) + 4 * (q & 7)), inf);
+        // the lane of this segment whose source is v, if any: its entry gets the seed 0
+        int sl = -1;
+        if (p.seg.src_index) {
+            const int b = __ldg(p.seg.src_index + v) - p.seg.first;
+            if (b >= 0 && b < n_lanes) sl = b;
+        }
+        for (int q = lane; q < 8 * G; q += 32) {  // uint4 q: group q / 8, lanes 4 (q % 8) ..
+            uint4 x = inf;
+            if (q == (sl >> 2)) {
+                const int comp = sl & 3;
+                x.x = comp == 0 ? 0u : INF_U;
+                x.y = comp == 1 ? 0u : INF_U;
+                x.z = comp == 2 ? 0u : INF_U;
+                x.w = comp == 3 ? 0u : INF_U;
+            }
+            __stcg(reinterpret_cast<uint4*>(row + seg_col0(p.seg, q >> 3) + 4 * (q & 7)), x);
+        }
     }
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -497,7 +513,7 @@ cudaError_t bf_launch_init(const DevGraph& g, const BfSegment& seg, const BfWork
     BfParams p{g, seg, w};
     bf_init_kernel<<<1216, 256, 0, s>>>(p);  // 8 blocks per SM
     const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || seg.src_index) return e;  // seeds written with the fill
     bf_seed_kernel<<<(seg.lanes + 255) / 256 + (seg.lanes == 0), 256, 0, s>>>(p);
     return cudaGetLastError();
 }

@@ -156,6 +156,9 @@ struct BfSegment {
     // the sources are sorted by node id (the distinct sources of a batch of orders), so the 32
     // sources of a group are neighbours when they are dense enough; see BfWork::prio
     bool sorted = false;
+    // optional: node -> index in src (-1: not a source), so that the init kernel writes the
+    // seeds d(s, s) = 0 with the fill; nullptr = a separate seed kernel
+    const int32_t* src_index = nullptr;
 };
 
 struct BfWork {
@@ -223,6 +226,11 @@ struct TourBufs {
 cudaError_t tour_launch_select(int32_t n, const int64_t* offs, const int32_t* picks, int32_t V,
                                int32_t depot, int32_t max_k, uint8_t* node_flag,
                                int32_t* order_status, cudaStream_t s);
+// Node flags (and order flags, when given) cleared, select, compact: one launch for small calls.
+cudaError_t tour_launch_select_compact(int32_t n, const int64_t* offs, const int32_t* picks, int32_t V, int32_t depot,
+                                       int32_t max_k, uint8_t* node_flag, int32_t* order_status, int32_t* order_flags,
+                                       int32_t* src_index, int32_t* src_list, int32_t* n_src, int32_t* block_sums,
+                                       cudaStream_t s, int* launches);
 cudaError_t tour_launch_compact(int32_t V, const uint8_t* node_flag, int32_t* src_index,
                                 int32_t* src_list, int32_t* n_src, int32_t* block_sums,
                                 cudaStream_t s, int* launches);

@@ -23,11 +23,10 @@ namespace wr {
 // a2: source selection
 // ---------------------------------------------------------------------------
 
-__global__ void select_kernel(int32_t n, const int64_t* __restrict__ offs, const int32_t* __restrict__ picks,
-                              int32_t V, int32_t depot, int32_t max_k, uint8_t* node_flag, int32_t* order_status) {
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o == 0) node_flag[depot] = 1;
-    if (o >= n) return;
+// Order o: its status, and node_flag set at its picks when it is valid.
+__device__ __forceinline__ void select_order(int o, int32_t n, const int64_t* __restrict__ offs,
+                                             const int32_t* __restrict__ picks, int32_t V, int32_t max_k,
+                                             uint8_t* node_flag, int32_t* order_status) {
     const int64_t b = offs[o], e = offs[o + 1];
     const int64_t k = e - b;
     int st = WR_ORDER_OK;
@@ -42,6 +41,13 @@ __global__ void select_kernel(int32_t n, const int64_t* __restrict__ offs, const
             for (int64_t i = b; i < e; ++i) node_flag[picks[i]] = 1;
     }
     order_status[o] = st;
+}
+
+__global__ void select_kernel(int32_t n, const int64_t* __restrict__ offs, const int32_t* __restrict__ picks,
+                              int32_t V, int32_t depot, int32_t max_k, uint8_t* node_flag, int32_t* order_status) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o == 0) node_flag[depot] = 1;
+    if (o < n) select_order(o, n, offs, picks, V, max_k, node_flag, order_status);
 }
 
 cudaError_t tour_launch_select(int32_t n, const int64_t* offs, const int32_t* picks, int32_t V, int32_t depot,
@@ -144,9 +150,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) compact_apply_kernel(int32_t V, 
 // carry: one launch instead of three for graphs of up to SINGLE_MAX_CHUNKS chunks.
 constexpr int SINGLE_MAX_CHUNKS = 64;
 
-__global__ void __launch_bounds__(SCAN_THREADS) compact_single_kernel(int32_t V, const uint8_t* __restrict__ flag,
-                                                                        int32_t* src_index, int32_t* src_list,
-                                                                        int32_t* n_src) {
+__device__ __forceinline__ void compact_block(int32_t V, const uint8_t* __restrict__ flag, int32_t* src_index,
+                                              int32_t* src_list, int32_t* n_src) {
     __shared__ int ws[32];
     __shared__ int tot;
     int carry = 0;
@@ -176,6 +181,53 @@ __global__ void __launch_bounds__(SCAN_THREADS) compact_single_kernel(int32_t V,
         carry += tot;  // every thread reads the chunk's total before the next scan overwrites it
     }
     if (threadIdx.x == 0) *n_src = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) compact_single_kernel(int32_t V, const uint8_t* __restrict__ flag,
+                                                                        int32_t* src_index, int32_t* src_list,
+                                                                        int32_t* n_src) {
+    compact_block(V, flag, src_index, src_list, n_src);
+}
+
+// Selection and compaction of a small call in one block: clear the node flags
+// (and the order flags), select every order, then compact.  Global writes of
+// the block's threads are visible to each other after __syncthreads.
+__global__ void __launch_bounds__(SCAN_THREADS) select_compact_kernel(int32_t n, const int64_t* __restrict__ offs,
+                                                                        const int32_t* __restrict__ picks, int32_t V,
+                                                                        int32_t depot, int32_t max_k, uint8_t* node_flag,
+                                                                        int32_t* order_status, int32_t* order_flags,
+                                                                        int32_t* src_index, int32_t* src_list,
+                                                                        int32_t* n_src) {
+    for (int v = threadIdx.x; v < V; v += SCAN_THREADS) node_flag[v] = 0;
+    if (order_flags)
+        for (int o = threadIdx.x; o < n; o += SCAN_THREADS) order_flags[o] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) node_flag[depot] = 1;
+    for (int o = threadIdx.x; o < n; o += SCAN_THREADS) select_order(o, n, offs, picks, V, max_k, node_flag, order_status);
+    __syncthreads();
+    compact_block(V, node_flag, src_index, src_list, n_src);
+}
+
+// One block: graphs of up to SINGLE_MAX_CHUNKS chunks and calls of up to this many orders.
+constexpr int FUSED_MAX_ORDERS = 4 * SCAN_THREADS;
+
+cudaError_t tour_launch_select_compact(int32_t n, const int64_t* offs, const int32_t* picks, int32_t V, int32_t depot,
+                                       int32_t max_k, uint8_t* node_flag, int32_t* order_status, int32_t* order_flags,
+                                       int32_t* src_index, int32_t* src_list, int32_t* n_src, int32_t* block_sums,
+                                       cudaStream_t s, int* launches) {
+    const int nb = (V + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    if (nb <= SINGLE_MAX_CHUNKS && n <= FUSED_MAX_ORDERS) {
+        select_compact_kernel<<<1, SCAN_THREADS, 0, s>>>(n, offs, picks, V, depot, max_k, node_flag, order_status,
+                                                          order_flags, src_index, src_list, n_src);
+        *launches += 1;
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaMemsetAsync(node_flag, 0, static_cast<size_t>(V), s);
+    if (e == cudaSuccess && order_flags) e = cudaMemsetAsync(order_flags, 0, static_cast<size_t>(n) * 4, s);
+    if (e == cudaSuccess) e = tour_launch_select(n, offs, picks, V, depot, max_k, node_flag, order_status, s);
+    if (e != cudaSuccess) return e;
+    *launches += 1;
+    return tour_launch_compact(V, node_flag, src_index, src_list, n_src, block_sums, s, launches);
 }
 
 cudaError_t tour_launch_compact(int32_t V, const uint8_t* node_flag, int32_t* src_index, int32_t* src_list,
