@@ -97,7 +97,6 @@ struct HkParams {
 };
 
 constexpr int HK_BATCH = 512;  // orders solved together, at most
-constexpr int HK_ITEMS = 1;    // subsets per thread whose loads are in flight together (2 and 3: fewer warps, slower)
 
 // One subset S of a level: its order (index in the batch), S, and h(S + j, j) for the picks j outside S.
 struct HkItem {
@@ -206,6 +205,48 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
             // unrank item w, then issue the loads h(S + j, j) for every pick j outside S (plane j,
             // block |S|, rank of S with bit j squeezed out = its bits below j as they are plus
             // its bits above j one lower)
+            // h(S + j, j) for the picks j outside S: plane j (2^(k-1) words), block |S|, at the
+            // rank of S with bit j squeezed out: over the bits b of S, C(b, t + 1) below j and
+            // C(b - 1, t + 1) above, = pb_tot + the sum over the bits below j of C(b - 1, t)
+            // (Pascal).  Offsets within the order's table fit 32 bits (20 x 2^19 words at most)
+            auto load_succ = [&](HkItem& it, uint32_t pb_tot) {
+                const int k = kq[it.qi];
+                const unsigned s = it.s;
+                const uint32_t* hq = p.h + base[it.qi];
+                const uint32_t off0 = loff[k][L] + pb_tot;
+                uint32_t pcr = 0;
+                int m = 0;
+#pragma unroll
+                for (int j = 0; j < HK_MAX_K; ++j) {
+                    it.hv[j] = INF_U;
+                    if (j < k) {
+                        if ((s >> j) & 1u) {
+                            pcr += binx[j][m];
+                            ++m;
+                        } else {
+                            it.hv[j] = __ldcg(hq + ((static_cast<uint32_t>(j) << (k - 1)) + off0 + pcr));
+                        }
+                    }
+                }
+            };
+            // the subset after it.s in colex order (the next item of the same order): Gosper's
+            // step to the next larger word with as many bits, then its two rank prefixes
+            auto next_item = [&](HkItem& it) {
+                const unsigned s = it.s;
+                const unsigned u = s & (0u - s);
+                const unsigned v = s + u;
+                const unsigned nx = v | (((v ^ s) >> 2) >> (__ffs(u) - 1));
+                uint32_t pb_tot = 0, pc_tot = 0;
+                int t = 0;
+                for (unsigned m = nx; m; m &= m - 1, ++t) {
+                    const int b = __ffs(m) - 1;
+                    pb_tot += binx[b][t + 1];
+                    pc_tot += binx[b][t];
+                }
+                it.s = nx;
+                it.pc_tot = pc_tot;
+                load_succ(it, pb_tot);
+            };
             auto load_item = [&](unsigned long long w, HkItem& it) {
                 // the order holding item w: the last i with pre[i] <= w (an order with no items at
                 // this level shares its pre with the next, so the last one holds w), by bisection
@@ -237,26 +278,7 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
                 }
                 it.s = s;
                 it.pc_tot = pc_tot;
-                // h(S + j, j) sits in plane j (2^(k-1) words), block |S|, at the rank of S with bit
-                // j squeezed out: over the bits b of S, C(b, t + 1) below j and C(b - 1, t + 1)
-                // above, = pb_tot + the sum over the bits below j of C(b - 1, t) (Pascal).
-                // Offsets within the order's table fit 32 bits (20 x 2^19 words at most)
-                const uint32_t* hq = p.h + base[qi];
-                const uint32_t off0 = loff[k][L] + pb_tot;
-                uint32_t pcr = 0;
-                int m = 0;
-#pragma unroll
-                for (int j = 0; j < HK_MAX_K; ++j) {
-                    it.hv[j] = INF_U;
-                    if (j < k) {
-                        if ((s >> j) & 1u) {
-                            pcr += binx[j][m];
-                            ++m;
-                        } else {
-                            it.hv[j] = __ldcg(hq + ((static_cast<uint32_t>(j) << (k - 1)) + off0 + pcr));
-                        }
-                    }
-                }
+                load_succ(it, pb_tot);
             };
             // h(S, c) for every c in S: plane c, block |S| - 1, rank of S - c with c's bit squeezed out
             auto store_item = [&](const HkItem& it) {
@@ -296,16 +318,21 @@ __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
                     pc += cc;
                 }
             };
-            // HK_ITEMS items per thread and round, all their loads issued before the first is used
-            const unsigned long long step = static_cast<unsigned long long>(nthreads);
-            for (unsigned long long w = static_cast<unsigned long long>(gtid); w < total; w += HK_ITEMS * step) {
-                HkItem it[HK_ITEMS];
-#pragma unroll
-                for (int u = 0; u < HK_ITEMS; ++u)
-                    if (w + u * step < total) load_item(w + u * step, it[u]);
-#pragma unroll
-                for (int u = 0; u < HK_ITEMS; ++u)
-                    if (w + u * step < total) store_item(it[u]);
+            // a level with at least four items per thread: two adjacent items per thread and
+            // round, the second, when it lies in the same order, one colex step after the first
+            // instead of an unranking; a smaller level: one item per thread, so that its items
+            // spread over every thread
+            const unsigned long long per = total >= 4ull * static_cast<unsigned long long>(nthreads) ? 2ull : 1ull;
+            const unsigned long long step = per * static_cast<unsigned long long>(nthreads);
+            for (unsigned long long w = per * static_cast<unsigned long long>(gtid); w < total; w += step) {
+                HkItem it;
+                load_item(w, it);
+                store_item(it);
+                if (per == 2 && w + 1 < total) {
+                    if (w + 1 < pre[it.qi + 1]) next_item(it);
+                    else load_item(w + 1, it);
+                    store_item(it);
+                }
             }
             if (!grid_sync(p.bar, p.err, p.max_spins)) return;
         }
