@@ -118,9 +118,10 @@ __device__ __forceinline__ int hk_k(const HkParams& p, int q) {
 // buffer; within a batch all orders share every level: level L holds, for every
 // order of k >= L picks, its C(k, L) subsets S of size L, in increasing bitmask
 // order per order, orders one after another.  Consecutive threads take
-// consecutive items (grid-stride), each unranking its subset (combinatorial
-// number system).  One grid barrier per level; then one thread per order
-// rebuilds its first optimal sequence.
+// consecutive items (grid-stride; in a level with four or more items per thread,
+// consecutive pairs), unranking a subset in the combinatorial number system or
+// stepping to the next one in colex order.  One grid barrier per level; then
+// one warp per order rebuilds its first optimal sequence.
 __global__ void __launch_bounds__(256) hk_solve_kernel(HkParams p) {
     __shared__ uint32_t binom[HK_MAX_K + 1][HK_MAX_K + 1];
     __shared__ uint32_t binx[HK_MAX_K + 2][HK_MAX_K + 2];  // binx[n + 1][r] = C(n, r); C(-1, r) = 0
