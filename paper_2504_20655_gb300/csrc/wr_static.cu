@@ -22,7 +22,7 @@ struct StaticScratch {
     unsigned long long best[WR_STATIC_MAX_ORDERS];
     int32_t order_status[WR_STATIC_MAX_ORDERS];
     int32_t order_flags[WR_STATIC_MAX_ORDERS];
-    unsigned long long unit_ctr;
+    unsigned long long unit_ctr[2];
     long long seq_count;
 };
 
@@ -82,7 +82,7 @@ extern "C" int wr_tour_eval_static(int32_t n_orders, const int32_t* k, const int
     tb.D = s->D;
     tb.unit_off = s->unit_off;
     tb.best = s->best;
-    tb.unit_ctr = &s->unit_ctr;
+    tb.unit_ctr = s->unit_ctr;
     tb.seq_count = &s->seq_count;
     // Every call reuses the same array.  The kernels below rewrite the
     // statuses, flags, clamped matrices, unit offsets, minima and the

@@ -337,13 +337,26 @@ __device__ __forceinline__ int order_k(const TourBufs& t, const int32_t* k_given
     return k_given ? k_given[o] : static_cast<int>(t.offs[o + 1] - t.offs[o]);
 }
 
+// Orders of at least this many picks enumerate in set units, smaller ones in
+// prefix units (see enum_order_range).
+constexpr int SET_UNITS_FROM = 11;
+
 __device__ __forceinline__ long long units_of(int k) {
-    // k! / 7! for k >= 7 (a unit is a prefix and the 5040 orderings of the last seven picks),
-    // else 1; orders above WR_MAX_K are solved by Held-Karp instead
+    // k <= 6: 1.  Prefix units, 7 <= k < SET_UNITS_FROM: k! / 7! (a unit is an ordered prefix of
+    // k - 7 picks and the 5040 orderings of the last seven).  Set units: C(k, q) sets of the
+    // first q = k - 7 picks x 7 picks next x (q = 5) 5 first picks.  Orders above WR_MAX_K are
+    // solved by Held-Karp instead
     if (k > WR_MAX_K) return 0;
-    long long u = 1;
-    for (int i = UNIT_TAIL + 2; i <= k; ++i) u *= i;
-    return u;
+    if (k <= UNIT_TAIL) return 1;
+    const int q = k - UNIT_TAIL - 1;
+    if (k < SET_UNITS_FROM) {
+        long long u = 1;
+        for (int i = UNIT_TAIL + 2; i <= k; ++i) u *= i;
+        return u;
+    }
+    long long c = 1;  // C(k, q)
+    for (int j = 1; j <= q; ++j) c = c * (k - q + j) / j;
+    return c * 7 * (q == 5 ? 5 : 1);
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS) units_kernel(int32_t n, const int32_t* k_given, TourBufs t) {
@@ -351,13 +364,17 @@ __global__ void __launch_bounds__(SCAN_THREADS) units_kernel(int32_t n, const in
     __shared__ long long tot;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long carry = 0;
+    bool sets = false;  // some order enumerates in set units
     for (int base = 0; base < n; base += SCAN_THREADS) {
         const int o = base + threadIdx.x;
         long long x = 0;
         if (o < n) {
             t.best[o] = ~0ull;
-            if (t.order_status[o] == WR_ORDER_OK && !(t.order_flags[o] & ORDER_FLAG_RANGE))
-                x = units_of(order_k(t, k_given, o));
+            if (t.order_status[o] == WR_ORDER_OK && !(t.order_flags[o] & ORDER_FLAG_RANGE)) {
+                const int k = order_k(t, k_given, o);
+                x = units_of(k);
+                sets |= x > 0 && k >= SET_UNITS_FROM;
+            }
         }
         long long inc = x;
 #pragma unroll
@@ -383,9 +400,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) units_kernel(int32_t n, const in
         carry += tot;
         __syncthreads();
     }
+    sets = __syncthreads_or(sets);
     if (threadIdx.x == 0) {
         t.unit_off[n] = carry;
-        *t.unit_ctr = 0ull;
+        t.unit_ctr[0] = 0ull;
+        t.unit_ctr[1] = sets ? 1ull : 0ull;  // which enumeration kernel runs
     }
 }
 
@@ -736,6 +755,45 @@ struct Tail6 {
 // One 720-sequence unit: a prefix of cost P ending at x (0: the depot), then
 // the 720 orderings of the six picks in `six` (a bit set of matrix indices);
 // rank0 = rank of its first sequence.
+// Register tables of a 720-sequence part: the six picks after x (packed in
+// sp), legs from x to them, legs among them, and their three-leg suffixes.
+struct PartTab {
+    uint32_t d6[6][6], t3f[6][6][6], xl[6];
+    unsigned sp;
+};
+
+__device__ __forceinline__ void part_tables(const uint32_t* __restrict__ Dm, int x, unsigned six, PartTab& T) {
+    int sx[UNIT_TAIL];
+    unsigned sp = 0;
+#pragma unroll
+    for (int i = 0; i < UNIT_TAIL; ++i) {
+        sx[i] = __ffs(six) - 1;
+        six &= six - 1;
+        sp |= static_cast<unsigned>(sx[i]) << (4 * i);
+    }
+    T.sp = sp;
+    uint32_t h6[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const uint32_t* row = Dm + sx[i] * DSTRIDE;
+        T.xl[i] = __ldg(Dm + x * DSTRIDE + sx[i]);
+        h6[i] = __ldg(row);
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+            if (q != i) T.d6[i][q] = __ldg(row + sx[q]);
+    }
+#pragma unroll
+    for (int b = 0; b < 6; ++b)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            if (b == c) continue;
+            const uint32_t tail2 = T.d6[b][c] + h6[c];
+#pragma unroll
+            for (int a = 0; a < 6; ++a)
+                if (a != b && a != c) T.t3f[a][b][c] = T.d6[a][b] + tail2;
+        }
+}
+
 __device__ __forceinline__ void unit720(const uint32_t* __restrict__ Dm, uint32_t P, int x, unsigned six,
                                         unsigned rank0, uint32_t& cur_c, unsigned& cur_r, BlockRec& rec) {
     int sx[UNIT_TAIL];
@@ -770,13 +828,31 @@ __device__ __forceinline__ void unit720(const uint32_t* __restrict__ Dm, uint32_
     Tail6<0>::run(d6, t3f, xl, sp, P, rank0, cur_c, cur_r, rec);
 }
 
+// Small tables of the enumeration kernel (shared memory).
+struct EnumTabs {
+    const uint32_t* cb;    // cb[6 n + r] = C(n, r), n <= 12, r <= 5
+    const uint32_t* fact;  // fact[n] = n!, n <= 12
+    // perm[24 (n - 1) + r] = the r-th ordering (lexicographic) of n <= 4 items: nibble i holds
+    // the item at position i (bits 0-1) and how many of the items before it are smaller (bits 2-3)
+    const uint16_t* perm;
+};
+
 // Enumerate the units [ulo, uhi) of one order (k picks, D block Dm); fold
 // the best (cost, rank) into *out.  k <= 5: one unit of k! sequences; k = 6:
-// one unit of 720; k >= 7: unit u fixes the first k-7 picks (the factorial
-// digits of u) and covers the 5040 orderings of the remaining seven, as seven
-// 720-sequence units (each of the seven, in increasing order, next).
+// one unit of 720.  For k >= 7 let q = k - 7, the picks before the last seven.
+// Prefix units (k < SET_UNITS_FROM): unit u fixes the first q picks in the
+// order of its factorial digits and covers the 5040 orderings of the other
+// seven, as seven 720-sequence parts (each of the seven, in increasing order,
+// next).  Set units (k >= SET_UNITS_FROM): a unit is a set Q of q picks, one
+// pick x of the other seven and, for q = 5, the first pick of Q; it covers
+// every ordering of Q (of the rest of Q after that first pick) followed by x
+// and the 720 orderings of the other six.  A part's leg and suffix tables
+// depend only on x and the six, so a set unit builds them once for all its
+// orderings of Q, each of which adds its own prefix cost and rank.  Either way
+// every sequence is costed and compared on its own.
+template <bool SETS>
 __device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, unsigned ulo, unsigned uhi,
-                                 unsigned long long* out, long long& seqs) {
+                                 unsigned long long* out, long long& seqs, const EnumTabs& tb) {
     // start from the order's current best (a stale read is only larger, so safe)
     const unsigned long long g0 = __ldcg(out);
     uint32_t best_c = static_cast<uint32_t>(g0 >> 32);
@@ -788,48 +864,148 @@ __device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, unsigne
         unit_eval_dispatch(k, Dm, t, best_c, best_r);
         seqs += k == 1 ? 1 : k == 2 ? 2 : k == 3 ? 6 : k == 4 ? 24 : 120;
     } else {
-        const int q = k - UNIT_TAIL - 1;  // picks fixed by the unit index; -1 for k = 6
         const unsigned all = ((1u << k) - 1u) << 1;
-        const int nsub = q < 0 ? 1 : UNIT_TAIL + 1;
         BlockRec rec;
         rec.have = false;
+        if (!SETS || k < SET_UNITS_FROM) {
+            // prefix units: the first q picks in the order of the unit index, then seven
+            // 720-sequence parts (each of the seven next)
+            const int q = k - UNIT_TAIL - 1;  // picks fixed by the unit index; -1 for k = 6
+            const int nsub = q < 0 ? 1 : UNIT_TAIL + 1;
 #pragma unroll 1
-        for (unsigned u = ulo; u < uhi; ++u) {
-            unsigned avail = all;
-            uint32_t S = 0;
-            int last = 0;
-            if (q > 0) {
-                // factorial digits of u, position i in radix k - i
-                unsigned digits = 0, v = u;
-                for (int i = q - 1; i >= 0; --i) {
-                    const unsigned r = static_cast<unsigned>(k - i);
-                    digits |= (v % r) << (4 * i);
-                    v /= r;
+            for (unsigned u = ulo; u < uhi; ++u) {
+                unsigned avail = all;
+                uint32_t S = 0;
+                int last = 0;
+                if (q > 0) {
+                    // factorial digits of u, position i in radix k - i
+                    unsigned digits = 0, v = u;
+                    for (int i = q - 1; i >= 0; --i) {
+                        const unsigned r = static_cast<unsigned>(k - i);
+                        digits |= (v % r) << (4 * i);
+                        v /= r;
+                    }
+                    for (int i = 0; i < q; ++i) {
+                        const int e = nth_bit(avail, static_cast<int>((digits >> (4 * i)) & 15u));
+                        S += __ldg(Dm + last * DSTRIDE + e);
+                        avail &= ~(1u << e);
+                        last = e;
+                    }
                 }
-                for (int i = 0; i < q; ++i) {
-                    const int e = nth_bit(avail, static_cast<int>((digits >> (4 * i)) & 15u));
-                    S += __ldg(Dm + last * DSTRIDE + e);
-                    avail &= ~(1u << e);
-                    last = e;
+                unsigned m = avail;
+#pragma unroll 1
+                for (int j = 0; j < nsub; ++j) {
+                    int x = 0;
+                    unsigned six = all;
+                    uint32_t P = 0;
+                    if (q >= 0) {
+                        x = __ffs(m) - 1;
+                        m &= m - 1;
+                        six = avail & ~(1u << x);
+                        P = S + __ldg(Dm + last * DSTRIDE + x);
+                    }
+                    unit720(Dm, P, x, six, (u * static_cast<unsigned>(nsub) + static_cast<unsigned>(j)) * 720u,
+                            best_c, best_r, rec);
                 }
             }
+            seqs += static_cast<long long>(uhi - ulo) * 720 * nsub;
+        } else {
+        const int q = k - UNIT_TAIL - 1;  // picks before the last seven: -1 (k = 6) .. 5
+        // prefix units (k <= SET_UNITS_FROM - 1): the first q picks in the order the unit index
+        // gives, then seven parts (each of the seven next); set units (k >= SET_UNITS_FROM):
+        // one part, walked after every ordering of the set
+        const bool sets = SETS && k >= SET_UNITS_FROM;
+        const int nf = sets && q == 5 ? 5 : 1;  // q = 5: the unit fixes the first pick too
+        const int qr = !sets ? 0 : q == 5 ? 4 : q;  // picks whose orderings a set unit walks
+        const int nperm = qr == 4 ? 24 : qr == 3 ? 6 : qr == 2 ? 2 : 1;
+        const int lvl0 = nf == 5 ? 1 : 0;  // position of the first walked pick
+        const int nsub = sets || q < 0 ? 1 : UNIT_TAIL + 1;
+#pragma unroll 1
+        for (unsigned u = ulo; u < uhi; ++u) {
+            unsigned avail = all;  // picks after the prefix
+            uint32_t S = 0;        // prefix cost (prefix units; set units: the fixed first pick)
+            int last = 0;          // last prefix pick (0: the depot)
+            unsigned base = 0;     // rank of the unit's first sequence, less the walked digits
+            int xi = -1;           // set units: the index of x among the seven
+            unsigned qpack = 0;    // set units: the walked picks in increasing order, 4 bits each
+            if (!sets) {
+                if (q > 0) {
+                    // factorial digits of u, position i in radix k - i
+                    unsigned digits = 0, v = u;
+                    for (int i = q - 1; i >= 0; --i) {
+                        const unsigned r = static_cast<unsigned>(k - i);
+                        digits |= (v % r) << (4 * i);
+                        v /= r;
+                    }
+                    for (int i = 0; i < q; ++i) {
+                        const int e = nth_bit(avail, static_cast<int>((digits >> (4 * i)) & 15u));
+                        S += __ldg(Dm + last * DSTRIDE + e);
+                        avail &= ~(1u << e);
+                        last = e;
+                    }
+                }
+                base = u * static_cast<unsigned>(nsub) * 720u;
+            } else {
+                unsigned tt = u;
+                const int fi = static_cast<int>(tt % static_cast<unsigned>(nf));
+                tt /= static_cast<unsigned>(nf);
+                xi = static_cast<int>(tt % 7u);
+                tt /= 7u;
+                // Q: the q-subset of colex rank tt of the picks (matrix indices 1..k), bits from
+                // the top: each the largest c below the previous one with C(c, i) <= rr
+                unsigned Q = 0, rr = tt;
+                int c = k - 1;
+                for (int i = q; i >= 1; --i, --c) {
+                    while (tb.cb[6 * c + i] > rr) --c;  // ends by c = i - 1: C(i - 1, i) = 0
+                    Q |= 2u << c;
+                    rr -= tb.cb[6 * c + i];
+                }
+                avail = all & ~Q;
+                base = static_cast<unsigned>(xi) * 720u;  // x: digit xi at position q
+                if (nf == 5) {  // the fixed first pick: digit f - 1 at position 0
+                    last = nth_bit(Q, fi);
+                    Q &= ~(1u << last);
+                    S = __ldg(Dm + last);
+                    base += static_cast<unsigned>(last - 1) * tb.fact[k - 1];
+                }
+                int i = 0;
+                for (unsigned m = Q; m; m &= m - 1, ++i) qpack |= static_cast<unsigned>(__ffs(m) - 1) << (4 * i);
+            }
+            const int f = nf == 5 ? last : 0;
             unsigned m = avail;
 #pragma unroll 1
             for (int j = 0; j < nsub; ++j) {
-                int x = 0;
-                unsigned six = all;
-                uint32_t P = 0;
-                if (q >= 0) {
+                // one part: the six picks after x, its tables, then each walked ordering
+                int x;
+                if (sets) x = nth_bit(avail, xi);
+                else if (q >= 0) {
                     x = __ffs(m) - 1;
                     m &= m - 1;
-                    six = avail & ~(1u << x);
-                    P = S + __ldg(Dm + last * DSTRIDE + x);
+                } else x = 0;
+                PartTab T;
+                part_tables(Dm, x, x ? avail & ~(1u << x) : avail, T);
+#pragma unroll 1
+                for (int r = 0; r < nperm; ++r) {
+                    const unsigned pat = qr > 0 ? tb.perm[24 * (qr - 1) + r] : 0u;
+                    uint32_t P = S;
+                    int lp = last;
+                    unsigned rank = base + static_cast<unsigned>(j) * 720u;
+                    for (int i = 0; i < qr; ++i) {
+                        const unsigned nib = (pat >> (4 * i)) & 15u;
+                        const int p = static_cast<int>((qpack >> (4 * (nib & 3u))) & 15u);
+                        P += __ldg(Dm + lp * DSTRIDE + p);
+                        lp = p;
+                        // rank digit: the unused picks below p (picks 1..p-1 less those used)
+                        const unsigned digit = static_cast<unsigned>(p - 1) - (nib >> 2) - (f != 0 && f < p ? 1u : 0u);
+                        rank += digit * tb.fact[k - 1 - lvl0 - i];
+                    }
+                    if (x) P += __ldg(Dm + lp * DSTRIDE + x);
+                    Tail6<0>::run(T.d6, T.t3f, T.xl, T.sp, P, rank, best_c, best_r, rec);
                 }
-                unit720(Dm, P, x, six, (u * static_cast<unsigned>(nsub) + static_cast<unsigned>(j)) * 720u, best_c,
-                        best_r, rec);
             }
         }
-        seqs += static_cast<long long>(uhi - ulo) * 720 * nsub;
+        seqs += static_cast<long long>(uhi - ulo) * 720 * nsub * nperm;
+        }
         if (rec.have) {
             // when another thread has meanwhile published a cheaper sequence of this order, this
             // range cannot hold the result: no search, nothing to publish
@@ -845,8 +1021,47 @@ __device__ void enum_order_range(const uint32_t* __restrict__ Dm, int k, unsigne
 constexpr int ENUM_THREADS = 128;
 constexpr bool ENUM_GUIDED = true;  // chunk sizes shrink as the unit counter nears the end
 
+// Two builds: SETS walks both unit kinds, the other prefix units only (without
+// the set-unit code it keeps fewer registers live); the units kernel's flag in
+// unit_ctr[1] says which one a call needs, and the other returns at once.
+template <bool SETS>
 __global__ void __launch_bounds__(ENUM_THREADS) enum_kernel(int32_t n, const int32_t* __restrict__ k_given, TourBufs t,
                                                             long long u_begin, long long u_end, int upt) {
+    if ((__ldcg(t.unit_ctr + 1) != 0ull) != SETS) return;  // the other build runs this call
+    __shared__ uint32_t s_cb[13 * 6], s_fact[13];
+    __shared__ uint16_t s_perm[4 * 24];
+    for (int i = threadIdx.x; i < 13 * 6; i += blockDim.x) {
+        const int nn = i / 6, r = i % 6;
+        uint32_t c = r > nn ? 0u : 1u;  // C(nn, r), multiplicative: exact at each step
+        for (int j = 1; j <= r && j <= nn; ++j) c = c * static_cast<uint32_t>(nn - r + j) / static_cast<uint32_t>(j);
+        s_cb[i] = c;
+    }
+    for (int i = threadIdx.x; i < 13; i += blockDim.x) {
+        uint32_t f = 1;
+        for (int j = 2; j <= i; ++j) f *= static_cast<uint32_t>(j);
+        s_fact[i] = f;
+    }
+    for (int i = threadIdx.x; i < 4 * 24; i += blockDim.x) {
+        const int nn = i / 24 + 1, r = i % 24;
+        int nf = 1;
+        for (int j = 2; j <= nn; ++j) nf *= j;
+        unsigned pat = 0;
+        if (r < nf) {
+            unsigned used = 0;
+            int rr = r, f = nf;
+            for (int pos = 0; pos < nn; ++pos) {
+                f /= nn - pos;
+                const int d = rr / f;  // the d-th unused item
+                rr -= d * f;
+                const int item = nth_bit(~used & ((1u << nn) - 1u), d);
+                pat |= static_cast<unsigned>(item | (__popc(used & ((1u << item) - 1u)) << 2)) << (4 * pos);
+                used |= 1u << item;
+            }
+        }
+        s_perm[i] = static_cast<uint16_t>(pat);
+    }
+    __syncthreads();
+    const EnumTabs tb{s_cb, s_fact, s_perm};
     const int lane = threadIdx.x & 31;
     const long long total = min(u_end, static_cast<long long>(__ldcg(t.unit_off + n)));
     const long long warps = static_cast<long long>(gridDim.x) * (blockDim.x >> 5);
@@ -880,8 +1095,8 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_kernel(int32_t n, const int
             const long long ob = __ldg(t.unit_off + o), oe = __ldg(t.unit_off + o + 1);
             const long long stop = min(ue, oe);
             const int k = order_k(t, k_given, o);
-            enum_order_range(t.D + static_cast<int64_t>(o) * DBLOCK, k, static_cast<unsigned>(u - ob),
-                             static_cast<unsigned>(stop - ob), t.best + o, seqs);
+            enum_order_range<SETS>(t.D + static_cast<int64_t>(o) * DBLOCK, k, static_cast<unsigned>(u - ob),
+                             static_cast<unsigned>(stop - ob), t.best + o, seqs, tb);
             u = stop;
         }
     }
@@ -890,14 +1105,15 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_kernel(int32_t n, const int
 
 int tour_enum_blocks(int device) {
     int occ = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, enum_kernel, ENUM_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, enum_kernel<true>, ENUM_THREADS, 0);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     return (occ < 1 ? 1 : occ) * (sms < 1 ? 1 : sms);
 }
 
 cudaError_t tour_launch_enum(int32_t n, const int32_t* k_given, const TourBufs& t, long long u_begin, long long u_end,
                              int units_per_thread, int blocks, cudaStream_t s) {
-    enum_kernel<<<blocks, ENUM_THREADS, 0, s>>>(n, k_given, t, u_begin, u_end, units_per_thread);
+    enum_kernel<false><<<blocks, ENUM_THREADS, 0, s>>>(n, k_given, t, u_begin, u_end, units_per_thread);
+    enum_kernel<true><<<blocks, ENUM_THREADS, 0, s>>>(n, k_given, t, u_begin, u_end, units_per_thread);
     return cudaGetLastError();
 }
 
