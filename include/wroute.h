@@ -93,7 +93,10 @@ typedef struct {
     int32_t run_target;     /* Bellman-Ford tile: target nodes per run (consecutive ids) */
     int32_t tile_cap;       /* nodes (run + halo) staged in shared memory per tile: 128, 256 or 512 */
     int32_t enum_units;     /* sequence units per thread per scheduled chunk (a unit: a prefix and the
-                               5040 orderings of the last 7 picks; an order of k <= 6 is one unit) */
+                               5040 orderings of the last 7 picks; for k >= 11, a set of the first
+                               k - 7 picks (k = 12: and its first pick), the next pick, and the
+                               orderings of the set (24) and of the last 6 (720); an order of k <= 6
+                               is one unit) */
     int32_t enum_max_units_per_launch; /* rank-range segment: units per enumeration launch (0 = all) */
     int32_t bf_warps;       /* CTA tiling: warps sharing one sweep tile, 4 or 8 (0 = 8 for 512-node tiles, else 4) */
     int32_t bf_tiling;      /* sweep tiling: 1 = one warp per tile (lane = source; tile_cap 128 or 256),
