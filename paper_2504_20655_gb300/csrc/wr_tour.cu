@@ -338,10 +338,13 @@ __device__ __forceinline__ int order_k(const TourBufs& t, const int32_t* k_given
 }
 
 // Orders of at least this many picks enumerate in set units, smaller ones in
-// prefix units (see enum_order_range).
+// prefix units (see enum_order_range), in a call with at least SET_UNITS_MIN_ORDERS
+// such orders.  A set unit of 11 or 12 picks holds 17,280 sequences (a prefix
+// unit 5,040): fewer large orders leave too few of them to end close together.
 constexpr int SET_UNITS_FROM = 11;
+constexpr int SET_UNITS_MIN_ORDERS = 32;
 
-__device__ __forceinline__ long long units_of(int k) {
+__device__ __forceinline__ long long units_of(int k, bool sets) {
     // k <= 6: 1.  Prefix units, 7 <= k < SET_UNITS_FROM: k! / 7! (a unit is an ordered prefix of
     // k - 7 picks and the 5040 orderings of the last seven).  Set units: C(k, q) sets of the
     // first q = k - 7 picks x 7 picks next x (q = 5) 5 first picks.  Orders above WR_MAX_K are
@@ -349,7 +352,7 @@ __device__ __forceinline__ long long units_of(int k) {
     if (k > WR_MAX_K) return 0;
     if (k <= UNIT_TAIL) return 1;
     const int q = k - UNIT_TAIL - 1;
-    if (k < SET_UNITS_FROM) {
+    if (!sets || k < SET_UNITS_FROM) {
         long long u = 1;
         for (int i = UNIT_TAIL + 2; i <= k; ++i) u *= i;
         return u;
@@ -364,17 +367,27 @@ __global__ void __launch_bounds__(SCAN_THREADS) units_kernel(int32_t n, const in
     __shared__ long long tot;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long carry = 0;
-    bool sets = false;  // some order enumerates in set units
+    // set units when the call holds enough orders of SET_UNITS_FROM .. WR_MAX_K picks
+    int big = 0;
+    for (int o = threadIdx.x; o < n; o += SCAN_THREADS)
+        if (t.order_status[o] == WR_ORDER_OK && !(t.order_flags[o] & ORDER_FLAG_RANGE)) {
+            const int k = order_k(t, k_given, o);
+            big += k >= SET_UNITS_FROM && k <= WR_MAX_K;
+        }
+    __shared__ int n_big;
+    if (threadIdx.x == 0) n_big = 0;
+    __syncthreads();
+    big = __reduce_add_sync(FULL_MASK, big);
+    if (lane == 0 && big) atomicAdd(&n_big, big);
+    __syncthreads();
+    const bool sets = n_big >= SET_UNITS_MIN_ORDERS;
     for (int base = 0; base < n; base += SCAN_THREADS) {
         const int o = base + threadIdx.x;
         long long x = 0;
         if (o < n) {
             t.best[o] = ~0ull;
-            if (t.order_status[o] == WR_ORDER_OK && !(t.order_flags[o] & ORDER_FLAG_RANGE)) {
-                const int k = order_k(t, k_given, o);
-                x = units_of(k);
-                sets |= x > 0 && k >= SET_UNITS_FROM;
-            }
+            if (t.order_status[o] == WR_ORDER_OK && !(t.order_flags[o] & ORDER_FLAG_RANGE))
+                x = units_of(order_k(t, k_given, o), sets);
         }
         long long inc = x;
 #pragma unroll
@@ -400,7 +413,6 @@ __global__ void __launch_bounds__(SCAN_THREADS) units_kernel(int32_t n, const in
         carry += tot;
         __syncthreads();
     }
-    sets = __syncthreads_or(sets);
     if (threadIdx.x == 0) {
         t.unit_off[n] = carry;
         t.unit_ctr[0] = 0ull;

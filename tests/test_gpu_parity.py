@@ -275,10 +275,12 @@ def test_tour_eval_vs_held_karp(router, orc, k):
 
 
 def test_enumeration_batch_and_single_calls(router, orc):
-    """14 orders of 7..12 picks with legs in 0..3 (ties everywhere, so the tie rule decides every
+    """36 orders of 7..12 picks with legs in 0..3 (ties everywhere, so the tie rule decides every
     result), in one call and one order per call: the same bits, equal to the oracle's Held-Karp
-    with the same tie rule."""
-    kk = np.array([12] * 12 + [7, 11], np.int32)
+    with the same tie rule.  The call holds 34 orders of 11 or 12 picks, enough for set units
+    (a set of the first picks walked in every order after one table build); one order alone
+    takes prefix units."""
+    kk = np.array([12] * 32 + [7, 11, 9, 11], np.int32)
     D, _ = _rand_D(len(kk), 12, 5150, 3)
     cost, perm, status = router.tour_eval(kk, D)
     for i, k in enumerate(kk):
