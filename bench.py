@@ -836,6 +836,18 @@ def measure_medium(args):
         "clocks": clocks,
         "paper_convention_mteps": paper_mteps(g.V, g.E, st["n_sources"], bf_ms / 1e3),
     }
+    if args.trace:
+        # one more call, untimed, with the sweep trace on: per sweep its frontier tiles and the
+        # microseconds until the next sweep starts (the last: until the kernel's exit check)
+        r.set_trace(4096)
+        flush.zero_()
+        torch.cuda.synchronize()
+        step()
+        r.sync()
+        tr = r.trace()
+        r.set_trace(0)
+        line["sweep_trace"] = [[int(tr[i][0]), (int(tr[i + 1][1]) - int(tr[i][1])) / 1e3 if i + 1 < len(tr) else None]
+                               for i in range(len(tr))]
     if rank == 0 and not args.no_cpu:
         v, cores, sample = cpu_oracle_rate(g, o, budget_s=args.ref_budget)
         line["cpu_baseline"] = {"value": v, "unit": "orders/s", "cores": cores, "kind": "oracle", "sample": sample}
@@ -1042,6 +1054,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--scale-sources", type=int, default=4096, help="sources of the scale workload")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--trace", action="store_true",
+                    help="medium line: add the sweep trace of one more, untimed call (frontier tiles, us per sweep)")
     ap.add_argument("--plain-budget", type=float, default=3.0, help="seconds of plain per-order calls (batching)")
     ap.add_argument("--rates", default="1000,5000,20000,50000", help="serving: arrival rates, orders/s")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving: seconds of arrivals per rate")
